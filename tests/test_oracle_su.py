@@ -1,0 +1,187 @@
+"""Pins of the simple-update oracle against values that do not come from it.
+
+* Trees, untruncated (D >= 2^n): simple update applies each gate exactly and keeps
+  the Vidal canonical form, so the mean-field <Z_i> equals the state-vector value
+  and lambda_e equals the Schmidt spectrum across e.
+* Full lattices, n <= 5: every light cone is a tree (App. C), so with D >= 2^n
+  the oracle matches the light-cone brute force (the paper's ~1e-15 claim of the
+  "Benchmarking" section).
+* theta_h = 0 (identity), pi (bit flips: product state) and pi/2 (Clifford:
+  <Z> = 0, App. B) invariants.
+* Planted mistakes in the oracle must break at least one pin.
+"""
+import math
+
+import networkx as nx
+import numpy as np
+import pytest
+
+from oracle import statevector as sv
+from oracle import su
+from oracle.lightcone import lightcone_z
+from workloads import EAGLE, OSPREY, heavy_hex, induced_subgraph
+
+M127, E127 = heavy_hex(*EAGLE)
+
+
+def fragment(verts):
+    return induced_subgraph(E127, verts)
+
+
+TREE16 = fragment(range(16))                    # row 0 + two bridges: a tree with degree-3 sites
+TREE20 = fragment(list(range(18)) + [18, 22])   # row 0, four bridges, two qubits of row 1
+
+
+@pytest.mark.parametrize("frag,theta,steps", [(TREE16, 0.6, 5), (TREE20, 1.0, 4), (TREE16, 0.3, 3)])
+def test_tree_matches_statevector(frag, theta, steps):
+    m, e, _ = frag
+    assert len(e) == m - 1
+    D = 2 ** steps
+    means, zs, peps = su.evolve(m, e, D, theta, steps, per_site=True)
+    ref = sv.kicked_ising_z(m, e, theta, steps)
+    assert np.abs(zs - ref).max() < 1e-12
+    assert np.abs(means - ref.mean(axis=1)).max() < 1e-12
+
+
+def test_tree16_printed_means():
+    """Mean <Z> of the 16-qubit tree at theta=0.6 (independent state vector, 8 digits)."""
+    m, e, _ = TREE16
+    means, _, _ = su.evolve(m, e, 32, 0.6, 5)
+    assert np.allclose(means, [0.82533561, 0.84405954, 0.79485539, 0.79597706, 0.76800776], atol=5e-9)
+
+
+def test_tree_lambda_equals_schmidt_values():
+    m, e, _ = TREE20
+    steps, theta = 3, 0.75
+    D = 2 ** steps
+    _, _, peps = su.evolve(m, e, D, theta, steps)
+    psi = None
+    for psi in sv.kicked_ising_states(m, e, theta, steps):
+        pass
+    g = nx.Graph([tuple(map(int, x)) for x in e])
+    for k, (a, b) in enumerate(e):
+        h = g.copy(); h.remove_edge(int(a), int(b))
+        part = nx.node_connected_component(h, int(a))
+        s = sv.schmidt_values(psi, part)[:D]
+        lam = np.zeros(D); lam[:len(s)] = s
+        assert np.abs(peps.lambdas()[k] - lam).max() < 1e-12
+
+
+@pytest.mark.parametrize("theta,expect", [(0.0, lambda n: 1.0), (math.pi, lambda n: (-1.0) ** n)])
+def test_trivial_angles_full_lattice(theta, expect):
+    means, zs, peps = su.evolve(M127, E127, 4, theta, 3, per_site=True)
+    for n in range(3):
+        assert np.abs(zs[n] - expect(n + 1)).max() < 1e-12
+    lam0 = np.zeros(4); lam0[0] = 1
+    assert np.abs(peps.lambdas() - lam0).max() < 1e-12
+
+
+def test_clifford_point_full_lattice():
+    """theta_h = pi/2 is Clifford: U^-n Z_i U^n keeps an X or Y factor, so <Z_i> = 0 (D >= 2^n)."""
+    from oracle.pauli import backward_conjugate
+    for q in range(M127):
+        x, _ = backward_conjugate(M127, E127, q, 4)
+        assert x.any()
+    _, zs, _ = su.evolve(M127, E127, 16, math.pi / 2, 4, per_site=True)
+    assert np.abs(zs).max() < 1e-12
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.6, 1.0])
+def test_full_lattice_matches_lightcone(theta):
+    steps = 4
+    _, zs, _ = su.evolve(M127, E127, 16, theta, steps, per_site=True)
+    for n in range(1, steps + 1):
+        ref = np.array([lightcone_z(M127, E127, theta, q, n) for q in range(M127)])
+        assert np.abs(zs[n - 1] - ref).max() < 1e-12
+
+
+def test_full_lattice_matches_lightcone_step5():
+    """n = 5, D = 32: the setting of the paper's ~1e-15 benchmark (sampled qubits)."""
+    theta = 0.8
+    _, zs, _ = su.evolve(M127, E127, 32, theta, 5, per_site=True)
+    for q in range(0, M127, 9):
+        assert abs(zs[4, q] - lightcone_z(M127, E127, theta, q, 5)) < 1e-12
+
+
+def test_osprey_matches_lightcone():
+    m, e = heavy_hex(*OSPREY)
+    theta = 0.9
+    _, zs, _ = su.evolve(m, e, 8, theta, 3, per_site=True)
+    for q in range(0, m, 17):
+        assert abs(zs[2, q] - lightcone_z(m, e, theta, q, 3)) < 1e-12
+
+
+def test_truncation_changes_result_and_conserves_norm():
+    """D < 2^n truncates: the result departs from the exact value; lambda stays unit-norm."""
+    theta = 1.0
+    _, zs, peps = su.evolve(M127, E127, 2, theta, 3, per_site=True)
+    ref = np.array([lightcone_z(M127, E127, theta, q, 3) for q in range(M127)])
+    assert np.abs(zs[2] - ref).max() > 1e-4
+    assert np.allclose(np.linalg.norm(peps.lam, axis=1), 1.0, atol=1e-13)
+
+
+# ------------------------------------------------------------------ planted mistakes
+def _tree_error(cls):
+    """Max deviation of <Z_i> and of lambda_e from the state vector (3 steps, D = 8)."""
+    m, e, _ = TREE16
+    peps = cls(m, e, 8)
+    err = 0.0
+    g = nx.Graph([tuple(map(int, x)) for x in e])
+    for n, psi in enumerate(sv.kicked_ising_states(m, e, 0.7, 3)):
+        peps.step(0.7)
+        err = max(err, float(np.abs(peps.expect_z() - sv.z_expectations(psi)).max()))
+        for k, (a, b) in enumerate(e):
+            h = g.copy(); h.remove_edge(int(a), int(b))
+            s = sv.schmidt_values(psi, nx.node_connected_component(h, int(a)))[:8]
+            lam = np.zeros(8); lam[:len(s)] = s
+            err = max(err, float(np.abs(peps.lambdas()[k] - lam).max()))
+    return err
+
+
+def test_unmodified_oracle_is_exact_on_the_tree():
+    assert _tree_error(su.GPEPS) < 1e-12
+
+
+def test_planted_mistake_no_absorb():
+    class Bad(su.GPEPS):
+        def _absorb(self, i, skip):
+            return self.gamma[i]
+    assert _tree_error(Bad) > 1e-6
+
+
+def test_planted_mistake_no_strip():
+    class Bad(su.GPEPS):
+        def _strip(self, T, i, skip):
+            return T
+    assert _tree_error(Bad) > 1e-6
+
+
+def test_planted_mistake_readout_sqrt_lambda():
+    class Bad(su.GPEPS):
+        def expect_z(self):
+            saved = self.lam
+            self.lam = np.sqrt(saved)
+            try:
+                return su.GPEPS.expect_z(self)
+            finally:
+                self.lam = saved
+    assert _tree_error(Bad) > 1e-6
+
+
+def test_planted_mistake_transposed_gate_phase():
+    class Bad(su.GPEPS):
+        def __init__(self, *a, **k):
+            super().__init__(*a, **k)
+            z = np.array([1.0, -1.0])
+            self.g = np.exp(1j * math.pi / 4 * np.add.outer(z, np.zeros(2)))   # single-site phase only
+    assert _tree_error(Bad) > 1e-6
+
+
+def test_planted_mistake_zz_before_kick():
+    """A trailing ZZ layer commutes with Z_q, so only the lambda spectra can catch this one."""
+    class Bad(su.GPEPS):
+        def step(self, theta):
+            for c in range(self.n_colours):
+                self.zz_layer(c)
+            self.kick(theta)
+    assert _tree_error(Bad) > 1e-6
