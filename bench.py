@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the simple-update Trotter step (bond updates/s) on one GB300 per rank.
+
+Workload (default ``heavyhex_mix_d32``): one batch of the 127-, 433- and
+1121-qubit heavy-hex lattices (1968 bond updates per Trotter step), bond
+dimension D = 32, theta_h = 0.7, started from |0...0>, synthetic (the lattices
+stand in for the processors' coupling maps).  A step is one Trotter step of
+the whole batch: kick, three colour classes of bond updates, mean-field <Z>.
+
+``--impl gpeps`` (default) times the CUDA library: W warm-up steps, then K
+steps replayed from the captured step graph, bracketed by CUDA events on the
+library's stream; the state (>= 307 MB) is larger than L2, so no flush is
+needed.  It also reports the complex128 path on the same batch, per-kernel
+times of the dominant kernel against the FP64 ALU roofline, an end-to-end
+number through the public API with host buffers, and the FP64 CPU oracle
+timed on a bounded sample.  ``--impl reference`` times the oracle alone.
+
+Multi-GPU (torchrun): replicas only.  Every rank evolves its own copy of the
+batch; there is no collective on the data path; value = all ranks' bond
+updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "bond updates/s at D=32 (mixed vs FP64 plain, |d<Z>|<=1e-4); % of roofline"
+FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 (vector) rate; measured 1197 by an FMA loop
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpeps", choices=["gpeps", "reference"])
+    ap.add_argument("--workload", default="heavyhex_mix_d32")
+    ap.add_argument("--dtype", default="mixed", choices=["mixed", "c128"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi sampler (200 ms) running while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons, power = [], [], set(), []
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                power.append(float(r[3]))
+            except ValueError:
+                pass
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows),
+                "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------ algorithmic counts
+def bond_kernel_flops(w, sweeps_per_bond):
+    """FP64 flops of the bond-eigenproblem launch per bond (n = 2 D for the 2D x 2D bond matrix):
+    rho formation 2 (n D^2 + n^2 D) complex MACs, Jacobi sweeps of (n-1) rounds with
+    n/2 (n/2 + 1)/2 two-sided 2x2 block rotations (72 flops) and n^2/2 eigenvector
+    rotations (18 flops), and the Y matrices 2 D^2 n complex MACs; 8 flops per complex MAC."""
+    D = w.D
+    n = 2 * D
+    m = n // 2
+    form = 2 * (n * D * D + n * n * D) * 8
+    sweep = (n - 1) * (m * (m + 1) // 2 * 72 + n * m * 18)
+    ymat = 2 * D * D * n * 8
+    return form + sweeps_per_bond * sweep + ymat
+
+
+def step_bytes(graphs, D, elt):
+    """Algorithmic HBM bytes of one Trotter step: every bond reads and writes both site
+    tensors once (its larger end twice: Gram and update pass), the readout reads every
+    tensor once; lambda vectors are negligible."""
+    tot = 0
+    for n, edges in graphs:
+        import numpy as np
+        deg = np.bincount(np.asarray(edges).ravel(), minlength=n)
+        size = {int(d): 2 * D ** int(d) * elt for d in set(deg.tolist())}
+        for a, b in edges:
+            sa, sb = size[int(deg[a])], size[int(deg[b])]
+            big, small = max(sa, sb), min(sa, sb)
+            tot += 3 * big + 2 * small
+        tot += sum(size[int(d)] for d in deg)
+    return tot
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_oracle(w, seconds_cap=30.0, min_steps=1):
+    """The FP64 oracle on a bounded sample: the first lattice of the batch, whole Trotter
+    steps from |0...0> until ``seconds_cap`` (at least ``min_steps``)."""
+    from oracle.su import GPEPS as OraclePEPS
+    from workloads import kick_angles
+    (n, edges) = w.graphs()[0]
+    th = kick_angles(w)[0]
+    peps = OraclePEPS(n, edges, w.D)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < min_steps or (time.perf_counter() - t0 < seconds_cap * 0.5 and steps < w.steps):
+        peps.step(th)
+        peps.expect_z()
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": len(edges) * steps / dt, "unit": "bond updates/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{n}-qubit lattice of the batch, D={w.D}, {steps} Trotter steps from |0...0> "
+                      f"({len(edges) * steps} bond updates, numpy/LAPACK FP64, default BLAS threads)",
+            "seconds": dt, "steps": steps}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpeps(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2309_15642_gb300 import _build
+    _build.build()
+    from paper_2309_15642_gb300 import GPEPS
+    from workloads import kick_angles, workload
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = workload(args.workload)
+    graphs = w.graphs()
+    theta = [float(t[0]) for t in kick_angles(w)]
+    K, W = args.steps, args.warmup
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+
+    def timed(dtype, K, W):
+        g = GPEPS(graphs, w.D, dtype=dtype, device=str(dev))
+        g.reset()
+        th = torch.tensor(theta, dtype=torch.float64, device=dev)
+        out = torch.empty((max(K, 1), g.n_instances), dtype=torch.float64, device=dev)
+        g.step(W, th)
+        torch.cuda.synchronize(dev)
+        if dist:
+            tdist.barrier()
+        clocks = Clocks(local_rank) if rank == 0 else None
+        if clocks:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(g.stream)
+        g.step(K, th, out=out)
+        e1.record(g.stream)
+        e1.synchronize()
+        torch.cuda.synchronize(dev)
+        ck = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            ms = float(t.item())
+        flags = g.status()
+        return g, th, out, ms, ck, flags
+
+    g, th, out, ms, clocks, flags = timed(args.dtype, K, W)
+    bonds_step = g.bonds_per_step
+    value = world * bonds_step * K / (ms * 1e-3)
+    mean_last = out[K - 1].cpu().numpy().tolist() if K else []
+
+    # per-kernel durations of profiled steps right after the timed region
+    prof = {"gram": [], "bond": [], "update": []}
+    s0, b0 = g.sweeps()
+    for _ in range(args.profile_steps):
+        g.kick(th)
+        for c in range(g.n_colours):
+            t3 = g.zz_layer_profiled(c)
+            for k, v in zip(("gram", "bond", "update"), t3):
+                prof[k].append(v)
+        g.expect_z()
+    s1, b1 = g.sweeps()
+    sweeps_per_bond = (s1 - s0) / max(b1 - b0, 1)
+    layer_ms = {k: sum(v) / max(args.profile_steps, 1) for k, v in prof.items()}   # per step, all colours
+    bond_launch_ms = sum(prof["bond"]) / max(len(prof["bond"]), 1)
+    bonds_per_launch = bonds_step / g.n_colours
+    flops_launch = bond_kernel_flops(w, sweeps_per_bond) * bonds_per_launch
+    achieved = flops_launch / (bond_launch_ms * 1e-3) / 1e9
+    roofline = {"kernel": "bond_kernel (2D x 2D bond eigenproblem, FP64 Jacobi)", "bound": "alu",
+                "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                "peak_source": "nominal FP64 1.25 TFLOP/s of the GB300 (no FP64 figure in MEASURED_PEAKS.json)",
+                "sweeps_per_bond": sweeps_per_bond, "launch_ms": bond_launch_ms,
+                "per_step_ms": layer_ms}
+    elt = 8 if args.dtype == "mixed" else 16
+    sb = step_bytes(graphs, w.D, elt)
+    hbm = {"algorithmic_bytes_per_step": sb, "achieved_gbs_whole_step": sb / (ms / K * 1e-3) / 1e9}
+
+    # end to end through the public API with host buffers
+    th_host = torch.tensor(theta, dtype=torch.float64).pin_memory()
+    res_host = torch.empty(g.n_instances, dtype=torch.float64).pin_memory()
+    th_dev = torch.empty_like(th_host, device=dev)
+    res_dev = torch.empty((1, g.n_instances), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+    Ke = max(min(K, 10), 1)
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        th_dev.copy_(th_host, non_blocking=True)
+        g.step(1, th_dev, out=res_dev)
+        res_host.copy_(res_dev[0], non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * bonds_step * Ke / e2e_s, "unit": "bond updates/s",
+           "h2d_bytes_per_step": th_host.numel() * 8, "d2h_bytes_per_step": res_host.numel() * 8}
+    g.close()
+
+    plain = None
+    if not args.no_plain and args.dtype == "mixed":
+        Kp, Wp = max(min(K, 10), 1), max(min(W, 3), 1)
+        gp, _, outp, msp, _, flp = timed("c128", Kp, Wp)
+        plain = {"dtype": "c128", "value": world * bonds_step * Kp / (msp * 1e-3), "unit": "bond updates/s",
+                 "ms_per_step": msp / Kp, "steps": Kp, "warmup": Wp, "flags": flp}
+        gp.close()
+    return dict(value=value, ms=ms, bonds_step=bonds_step, clocks=clocks, flags=flags, roofline=roofline,
+                e2e=e2e, plain=plain, hbm=hbm, mean_last=mean_last, w=w)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    from workloads import workload
+    w = workload(args.workload)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        K, W = args.steps, args.warmup
+        # each step: one Trotter step of the oracle on the 127-qubit lattice of the batch
+        from oracle.su import GPEPS as OraclePEPS
+        from workloads import kick_angles
+        (n, edges) = w.graphs()[0]
+        th = kick_angles(w)[0]
+        peps = OraclePEPS(n, edges, w.D)
+        for _ in range(W):
+            peps.step(th)
+            peps.expect_z()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            peps.step(th)
+            peps.expect_z()
+        dt = time.perf_counter() - t0
+        v = len(edges) * K / dt
+        sample = f"{n}-qubit lattice of the batch, D={w.D}, one Trotter step per step (numpy/LAPACK FP64)"
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": v, "unit": "bond updates/s", "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": dt / max(K, 1) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "lattices": [list(l) for l in w.lattices], "D": w.D,
+                       "theta": list(w.theta), "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "bond updates/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "bond updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    r = run_gpeps(args, rank, world, local_rank)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle(w)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": r["value"], "unit": "bond updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64+f64" if args.dtype == "mixed" else "c128", "data": "synthetic",
+            "config": {"workload": w.name, "lattices": [list(l) for l in w.lattices], "D": w.D,
+                       "theta": list(w.theta), "bonds_per_step": r["bonds_step"],
+                       "trotter_steps_per_s": world * 1e3 * args.steps / r["ms"] / world,
+                       "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{world}",
+                       "timed_steps": f"{args.warmup + 1}..{args.warmup + args.steps} from |0...0>"},
+            "roofline": r["roofline"], "hbm": r["hbm"], "clocks": r["clocks"], "e2e": r["e2e"],
+            "plain_c128": r["plain"], "cpu_baseline": cpu,
+            "gpu_launches": (1 + 3 * 3 + 2) * args.steps, "device_flags": r["flags"],
+            "mean_z_last_step": r["mean_last"],
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

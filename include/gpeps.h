@@ -1,0 +1,178 @@
+/*
+ * gpeps.h -- C ABI of the GB300 (sm_103a) simple-update Trotter evolution of
+ * the kicked Ising circuit on heavy-hexagon graph PEPS.
+ *
+ * The method (paper, sections "Model" and "Method", Eqs. 1-3): a graph PEPS
+ * with one tensor Gamma_i per qubit (physical dimension 2, one virtual leg of
+ * dimension D per coupler) and one weight vector lambda_e per coupler is
+ * evolved by U(theta_h) = (prod_edges exp(i pi/4 Z_i Z_j)) (prod_i exp(-i theta_h X_i / 2))
+ * with the *simple update* of tensors, truncating every bond to D ("chi" in the
+ * paper), and read out with a *mean-field* approximation of the environment.
+ *
+ * Conventions for every entry point
+ *   - Every function returns an int status: GPEPS_OK (0) or a GPEPS_E* code.
+ *     gpeps_error_string() names it.  No entry point aborts or traps.
+ *   - All GPU work is enqueued asynchronously on the stream given to
+ *     gpeps_create (NULL = legacy default stream) unless stated otherwise.
+ *   - Device memory is owned by the caller: gpeps_query_workspace() reports the
+ *     two sizes, the caller allocates them (e.g. torch tensors) and passes them
+ *     to gpeps_bind().  The handle owns only host metadata and, after the first
+ *     gpeps_step(), one instantiated CUDA graph.  The library never calls
+ *     cudaMalloc.
+ *   - "host" pointers are read (or written) before the call returns; "device"
+ *     pointers must stay valid until the enqueued work has finished.
+ *   - Errors found on the device (Jacobi sweep cap, NaN/Inf, vanishing norm)
+ *     set bits in a device flag word; gpeps_status() synchronises the stream
+ *     and returns them.  Device code never traps and every loop is bounded.
+ *
+ * Scope: graphs in which every edge has an end of degree <= 2 and every vertex
+ * has degree <= 3 (true of the heavy-hex lattices of the paper, Fig. 1);
+ * 1 <= D <= 32.
+ */
+#ifndef GPEPS_H
+#define GPEPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GPEPS_OK 0
+#define GPEPS_EINVAL 1   /* bad argument: graph, D, dtype, colour, pointer, call order */
+#define GPEPS_ECUDA 2    /* a CUDA runtime call failed (the message is kept, see gpeps_last_cuda_error) */
+#define GPEPS_ENOCONV 3  /* device flag: a Jacobi eigensolver hit its sweep cap (results still written) */
+#define GPEPS_ENUMERIC 4 /* device flag: NaN/Inf or a vanishing bond spectrum */
+#define GPEPS_ENOMEM 5   /* host allocation failed */
+
+/* device flag bits returned by gpeps_status */
+#define GPEPS_FLAG_NOCONV 1
+#define GPEPS_FLAG_NUMERIC 2
+
+/* storage / arithmetic of the evolution */
+#define GPEPS_C128 0       /* complex128 tensors; every product and the eigensolver in FP64 */
+#define GPEPS_MIXED_C64 1  /* complex64 tensors; Gram/contract products in FP32; bond
+                              eigensolver, lambda renormalisation and lambda^-1 in FP64 */
+
+/*
+ * One coupling graph.  edges: host, int32[2*n_edges], pairs (a, b) with
+ * 0 <= a, b < n_qubits, a != b, no duplicates.  colour: host, int8[n_edges]
+ * giving the update class of every edge (each class must be a matching), or
+ * NULL for the library's greedy first-fit colouring over edges sorted by
+ * (smaller label, larger label).  The paper does not fix an update order; the
+ * ZZ gates of Eq. 2 commute, so only truncated results depend on it.
+ */
+typedef struct {
+  int32_t n_qubits;
+  int32_t n_edges;
+  const int32_t* edges;
+  const int8_t* colour;
+} gpeps_graph;
+
+typedef struct gpeps_handle gpeps_handle;
+
+/*
+ * Create a batch of n_instances independent gPEPS, instance k living on
+ * graphs[k] (the same graph may be passed for several instances, e.g. a sweep
+ * of theta_h).  D: bond dimension (paper's chi, section "Method").  dtype:
+ * GPEPS_C128 or GPEPS_MIXED_C64.  stream: a cudaStream_t or NULL.  The graph
+ * arrays are copied; *out receives the handle (free with gpeps_destroy).
+ * Errors: GPEPS_EINVAL for a malformed graph, a colouring that is not a
+ * matching, a vertex of degree > 3, an edge joining two degree-3 vertices,
+ * D outside [1, 32] or an unknown dtype.
+ */
+int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int32_t dtype,
+                 void* stream, gpeps_handle** out);
+
+/*
+ * Bytes of the two caller-owned device buffers.  state: every Gamma_i (complex,
+ * physical index outermost, legs in sorted-neighbour order, last leg fastest)
+ * and every lambda_e (float64[D]).  work: kick angles, bond work lists,
+ * per-bond scratch, <Z> outputs and the flag word.  Both need 256-byte
+ * alignment (cudaMalloc and torch give it).
+ */
+int gpeps_query_workspace(const gpeps_handle* h, size_t* state_bytes, size_t* work_bytes);
+
+/* Attach the two device buffers (sizes from gpeps_query_workspace) and upload
+ * the work lists; enqueues copies on the stream.  Re-binding invalidates a
+ * captured step graph.  Errors: GPEPS_EINVAL for NULL or misaligned pointers. */
+int gpeps_bind(gpeps_handle* h, void* d_state, void* d_work);
+
+/* Product state |0...0> of Eq. 3 on every instance: Gamma_i[0,0,...,0] = 1,
+ * lambda_e = (1, 0, ..., 0), no pending kick; clears the flag word. */
+int gpeps_reset(gpeps_handle* h);
+
+/*
+ * Kick: apply exp(-i theta X_i / 2) (Eq. 2, single-site factor) to every qubit
+ * of every instance.  theta: device float64, [n_instances] when per_qubit == 0,
+ * else [total qubits] in instance-then-label order.  The rotation is not
+ * applied to the tensors here: it is accumulated per site and fused into the
+ * next bond update that touches the site (and applied on the fly by
+ * gpeps_expect_z while still pending).
+ */
+int gpeps_kick(gpeps_handle* h, const double* theta, int32_t per_qubit);
+
+/*
+ * Simple update (section "Method") with the gate exp(i pi/4 Z_i Z_j) of Eq. 2
+ * on every edge of colour class `colour` of every instance; the edges of a
+ * class are independent and run concurrently.  Per bond: absorb the lambda of
+ * the other legs, reduce both site tensors, apply the gate, solve the 2D x 2D
+ * bond eigenproblem, keep the D largest Schmidt values, renormalise lambda to
+ * unit 2-norm and strip lambda^-1 (pseudo-inverse below 1e-13 max(lambda)).
+ * Errors: GPEPS_EINVAL for colour outside [0, n_colours).
+ */
+int gpeps_zz_layer(gpeps_handle* h, int32_t colour);
+
+/*
+ * Same work as gpeps_zz_layer, with CUDA events recorded on the handle's
+ * stream around its three launches; synchronises and writes the durations in
+ * milliseconds to host ms[3]: [0] Gram partials of the larger ends, [1] bond
+ * eigenproblems (one CTA per bond), [2] update of the larger ends.
+ */
+int gpeps_zz_layer_profiled(gpeps_handle* h, int32_t colour, float* ms);
+
+/* Number of colour classes (the largest over the instances). */
+int gpeps_n_colours(const gpeps_handle* h, int32_t* n_colours);
+
+/*
+ * Mean-field <Z_i> (section "Method"; App. B): psi_i = Gamma_i with lambda on
+ * every leg, p_s = sum |psi_i[s,...]|^2, <Z_i> = (p_0 - p_1)/(p_0 + p_1), pending
+ * kicks applied on the fly.  d_z: device float64[total qubits] or NULL;
+ * d_mean: device float64[n_instances] (mean over the instance's qubits) or NULL.
+ */
+int gpeps_expect_z(gpeps_handle* h, double* d_z, double* d_mean);
+
+/*
+ * n_steps Trotter steps U(theta) of Eq. 2: kick with theta (device, as in
+ * gpeps_kick), then every colour class in increasing order, then the mean
+ * <Z> of every instance into d_mean_per_step[t * n_instances + k] (device
+ * float64, or NULL).  One step is captured once as a CUDA graph and replayed.
+ */
+int gpeps_step(gpeps_handle* h, int32_t n_steps, const double* theta, int32_t per_qubit,
+               double* d_mean_per_step);
+
+/* Synchronise the stream and return the device flag word (GPEPS_FLAG_* bits)
+ * in *flags; also returns GPEPS_ECUDA if a CUDA error is pending. */
+int gpeps_status(gpeps_handle* h, int32_t* flags);
+
+/* Copy lambda of edge `edge` (index into that instance's edge list) of
+ * instance `instance` to host out[D], sorted in decreasing order; synchronises. */
+int gpeps_lambda(gpeps_handle* h, int32_t instance, int32_t edge, double* out);
+
+/* Totals of the batch: qubits, edges, bond updates per Trotter step. */
+int gpeps_sizes(const gpeps_handle* h, int64_t* total_qubits, int64_t* total_edges);
+
+/* Counters of the device-side work of the last synchronised layer calls:
+ * Jacobi sweeps summed over bonds since the last reset (int64). Synchronises. */
+int gpeps_sweeps(gpeps_handle* h, int64_t* total_sweeps, int64_t* total_bonds);
+
+int gpeps_destroy(gpeps_handle* h);
+const char* gpeps_error_string(int status);
+const char* gpeps_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPEPS_H */

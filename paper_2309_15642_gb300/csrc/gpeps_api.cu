@@ -1,0 +1,607 @@
+// Host side of the C ABI declared in include/gpeps.h: graph validation, edge
+// colouring, per-colour bond work lists, caller-owned buffer layout, launches
+// and the per-step CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "gpeps.h"
+#include "gpeps_internal.cuh"
+
+using namespace gpeps;
+
+namespace {
+
+thread_local std::string g_last_cuda;
+
+int cuda_fail(cudaError_t e, const char* where) {
+  g_last_cuda = std::string(where) + ": " + cudaGetErrorString(e);
+  return GPEPS_ECUDA;
+}
+
+#define GP_CUDA(call)                                       \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct ColourPlan {
+  std::vector<BondDesc> bonds;
+  std::vector<TileDesc> tiles;
+  size_t w_bonds = 0, w_tiles = 0;  // byte offsets in the work buffer
+  int n_parts = 0;
+};
+
+struct InstGraph {
+  int n = 0;
+  std::vector<std::pair<int, int>> edges;  // as given
+  std::vector<int> colour;
+  std::vector<std::vector<int>> nb;        // sorted neighbours
+  std::vector<std::vector<int>> nb_edge;   // edge index of each neighbour
+};
+
+int64_t ipow(int64_t b, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+}  // namespace
+
+struct gpeps_handle {
+  int D = 0, dtype = 0, n_inst = 0;
+  size_t elt = 0;  // bytes per complex element
+  cudaStream_t stream = nullptr;
+  std::vector<InstGraph> g;
+  int64_t total_sites = 0, total_edges = 0;
+  std::vector<int32_t> inst_site0, inst_edge0, site_inst;
+  std::vector<int64_t> site_off;
+  std::vector<SiteDesc> sites;
+  int64_t n_gamma = 0;  // complex elements of all Gamma
+  std::vector<ColourPlan> colours;
+  int max_parts = 0, max_bonds = 0;
+  JacobiParams jp{};
+  // buffer layout (bytes)
+  size_t state_bytes = 0, work_bytes = 0;
+  size_t s_lam = 0, s_gamma = 0;
+  size_t w_pending = 0, w_flags = 0, w_sweeps = 0, w_z = 0, w_mean = 0, w_sites = 0, w_inst_site0 = 0,
+         w_site_inst = 0, w_site_off = 0, w_partials = 0, w_Y = 0, w_theta_a = 0;
+  char* d_state = nullptr;
+  char* d_work = nullptr;
+  bool bound = false;
+  int64_t bonds_since_reset = 0;
+  // captured step
+  cudaGraphExec_t step_exec = nullptr;
+  const double* step_theta = nullptr;
+  int step_per_qubit = -1;
+
+  double* lam() const { return reinterpret_cast<double*>(d_state + s_lam); }
+  void* gamma() const { return d_state + s_gamma; }
+  double* pending() const { return reinterpret_cast<double*>(d_work + w_pending); }
+  int* flags() const { return reinterpret_cast<int*>(d_work + w_flags); }
+  unsigned long long* sweeps() const { return reinterpret_cast<unsigned long long*>(d_work + w_sweeps); }
+  double* z() const { return reinterpret_cast<double*>(d_work + w_z); }
+  double* mean() const { return reinterpret_cast<double*>(d_work + w_mean); }
+  template <typename P>
+  P* at(size_t off) const {
+    return reinterpret_cast<P*>(d_work + off);
+  }
+};
+
+namespace {
+
+int validate_and_colour(const gpeps_graph& gr, InstGraph& ig) {
+  if (gr.n_qubits < 1 || gr.n_edges < 0) return GPEPS_EINVAL;
+  if (gr.n_edges > 0 && gr.edges == nullptr) return GPEPS_EINVAL;
+  ig.n = gr.n_qubits;
+  ig.nb.assign(ig.n, {});
+  ig.edges.resize(gr.n_edges);
+  std::vector<std::pair<int, int>> seen;
+  seen.reserve(gr.n_edges);
+  for (int e = 0; e < gr.n_edges; ++e) {
+    const int a = gr.edges[2 * e], b = gr.edges[2 * e + 1];
+    if (a < 0 || b < 0 || a >= ig.n || b >= ig.n || a == b) return GPEPS_EINVAL;
+    ig.edges[e] = {a, b};
+    seen.emplace_back(std::min(a, b), std::max(a, b));
+    ig.nb[a].push_back(b);
+    ig.nb[b].push_back(a);
+  }
+  std::sort(seen.begin(), seen.end());
+  if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return GPEPS_EINVAL;
+  for (int v = 0; v < ig.n; ++v) {
+    if (ig.nb[v].size() > 3) return GPEPS_EINVAL;
+    std::sort(ig.nb[v].begin(), ig.nb[v].end());
+  }
+  for (auto& e : ig.edges)
+    if (ig.nb[e.first].size() == 3 && ig.nb[e.second].size() == 3) return GPEPS_EINVAL;
+  // edge index of each leg
+  ig.nb_edge.assign(ig.n, {});
+  for (int v = 0; v < ig.n; ++v) ig.nb_edge[v].assign(ig.nb[v].size(), -1);
+  for (int e = 0; e < gr.n_edges; ++e) {
+    const int a = ig.edges[e].first, b = ig.edges[e].second;
+    const int pa = (int)(std::find(ig.nb[a].begin(), ig.nb[a].end(), b) - ig.nb[a].begin());
+    const int pb = (int)(std::find(ig.nb[b].begin(), ig.nb[b].end(), a) - ig.nb[b].begin());
+    ig.nb_edge[a][pa] = e;
+    ig.nb_edge[b][pb] = e;
+  }
+  ig.colour.assign(gr.n_edges, -1);
+  if (gr.colour) {
+    for (int e = 0; e < gr.n_edges; ++e) {
+      if (gr.colour[e] < 0) return GPEPS_EINVAL;
+      ig.colour[e] = gr.colour[e];
+    }
+  } else {
+    // greedy first-fit over edges sorted by (smaller label, larger label)
+    std::vector<int> order(gr.n_edges);
+    for (int e = 0; e < gr.n_edges; ++e) order[e] = e;
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+      auto kx = std::make_pair(std::min(ig.edges[x].first, ig.edges[x].second),
+                               std::max(ig.edges[x].first, ig.edges[x].second));
+      auto ky = std::make_pair(std::min(ig.edges[y].first, ig.edges[y].second),
+                               std::max(ig.edges[y].first, ig.edges[y].second));
+      return kx < ky;
+    });
+    std::vector<unsigned> used(ig.n, 0u);  // colour bitmask per vertex
+    for (int e : order) {
+      const int a = ig.edges[e].first, b = ig.edges[e].second;
+      const unsigned taken = used[a] | used[b];
+      int c = 0;
+      while (taken & (1u << c)) ++c;
+      ig.colour[e] = c;
+      used[a] |= 1u << c;
+      used[b] |= 1u << c;
+    }
+  }
+  // every class must be a matching
+  std::vector<std::vector<int>> touched(ig.n);
+  for (int e = 0; e < gr.n_edges; ++e) {
+    for (int v : {ig.edges[e].first, ig.edges[e].second}) {
+      for (int c : touched[v])
+        if (c == ig.colour[e]) return GPEPS_EINVAL;
+      touched[v].push_back(ig.colour[e]);
+    }
+  }
+  return GPEPS_OK;
+}
+
+SideDesc side_desc(const gpeps_handle* h, int inst, int v, int nbr) {
+  const InstGraph& ig = h->g[inst];
+  const int D = h->D;
+  const int d = (int)ig.nb[v].size();
+  const int p = (int)(std::find(ig.nb[v].begin(), ig.nb[v].end(), nbr) - ig.nb[v].begin());
+  auto stride = [&](int q) { return (int32_t)ipow(D, d - 1 - q); };
+  SideDesc sd{};
+  const int gsite = h->inst_site0[inst] + v;
+  sd.off = h->site_off[gsite];
+  sd.site = gsite;
+  sd.str_s = (int32_t)ipow(D, d);
+  sd.str_k = stride(p);
+  sd.rows = (int32_t)ipow(D, d - 1);
+  std::vector<int> others;
+  for (int q = 0; q < d; ++q)
+    if (q != p) others.push_back(q);
+  const int e0 = h->inst_edge0[inst];
+  sd.lam_o1 = sd.lam_o2 = -1;
+  sd.str_o1 = sd.str_o2 = 0;
+  sd.n2 = 1;
+  if (others.size() == 2) {
+    sd.str_o1 = stride(others[0]);
+    sd.lam_o1 = (e0 + ig.nb_edge[v][others[0]]) * D;
+    sd.str_o2 = stride(others[1]);
+    sd.lam_o2 = (e0 + ig.nb_edge[v][others[1]]) * D;
+    sd.n2 = D;
+  } else if (others.size() == 1) {
+    sd.str_o2 = stride(others[0]);
+    sd.lam_o2 = (e0 + ig.nb_edge[v][others[0]]) * D;
+    sd.n2 = D;
+  }
+  return sd;
+}
+
+struct PhaseEvents {
+  cudaEvent_t ev[4];
+};
+
+template <typename T>
+int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr) {
+  ColourPlan& cp = h->colours[c];
+  const int nt = (int)cp.tiles.size(), nbd = (int)cp.bonds.size();
+  if (nbd == 0) return GPEPS_OK;
+  const TileDesc* tiles = h->at<TileDesc>(cp.w_tiles);
+  const BondDesc* bonds = h->at<BondDesc>(cp.w_bonds);
+  void* partials = h->d_work + h->w_partials;
+  void* Y = h->d_work + h->w_Y;
+  double* theta_a = h->at<double>(h->w_theta_a);
+  if (pe) GP_CUDA(cudaEventRecord(pe->ev[0], h->stream));
+  GP_CUDA(Launch<T>::gram(tiles, nt, bonds, h->gamma(), h->lam(), h->pending(), partials, h->D, h->stream));
+  if (pe) GP_CUDA(cudaEventRecord(pe->ev[1], h->stream));
+  GP_CUDA(Launch<T>::bond(bonds, nbd, partials, h->gamma(), h->lam(), h->pending(), Y, theta_a, h->flags(),
+                          h->sweeps(), h->D, h->jp, h->stream));
+  if (pe) GP_CUDA(cudaEventRecord(pe->ev[2], h->stream));
+  GP_CUDA(Launch<T>::update(tiles, nt, bonds, h->gamma(), h->lam(), Y, theta_a, h->D, h->stream));
+  if (pe) GP_CUDA(cudaEventRecord(pe->ev[3], h->stream));
+  h->bonds_since_reset += nbd;
+  return GPEPS_OK;
+}
+
+int layer(gpeps_handle* h, int c, PhaseEvents* pe = nullptr) {
+  return h->dtype == GPEPS_C128 ? layer_impl<double>(h, c, pe) : layer_impl<float>(h, c, pe);
+}
+
+int kick_impl(gpeps_handle* h, const double* theta, int per_qubit) {
+  const int n = (int)h->total_sites;
+  cudaError_t e = h->dtype == GPEPS_C128
+                      ? Launch<double>::kick(h->pending(), theta, h->at<int32_t>(h->w_site_inst), n, per_qubit,
+                                             h->stream)
+                      : Launch<float>::kick(h->pending(), theta, h->at<int32_t>(h->w_site_inst), n, per_qubit,
+                                            h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "kick");
+  return GPEPS_OK;
+}
+
+int readout_impl(gpeps_handle* h) {
+  const int n = (int)h->total_sites;
+  cudaError_t e =
+      h->dtype == GPEPS_C128
+          ? Launch<double>::readout(h->at<SiteDesc>(h->w_sites), n, h->gamma(), h->lam(), h->pending(), h->z(),
+                                    h->D, h->stream)
+          : Launch<float>::readout(h->at<SiteDesc>(h->w_sites), n, h->gamma(), h->lam(), h->pending(), h->z(),
+                                   h->D, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "readout");
+  e = launch_mean(h->z(), h->at<int32_t>(h->w_inst_site0), h->n_inst, h->mean(), h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "mean");
+  return GPEPS_OK;
+}
+
+int one_step(gpeps_handle* h, const double* theta, int per_qubit) {
+  int st = kick_impl(h, theta, per_qubit);
+  if (st) return st;
+  for (int c = 0; c < (int)h->colours.size(); ++c) {
+    st = layer(h, c);
+    if (st) return st;
+  }
+  return readout_impl(h);
+}
+
+void drop_graph(gpeps_handle* h) {
+  if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
+  h->step_exec = nullptr;
+  h->step_theta = nullptr;
+  h->step_per_qubit = -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int32_t dtype, void* stream,
+                 gpeps_handle** out) {
+  if (!out || !graphs || n_instances < 1) return GPEPS_EINVAL;
+  *out = nullptr;
+  if (D < 1 || D > kMaxD) return GPEPS_EINVAL;
+  if (dtype != GPEPS_C128 && dtype != GPEPS_MIXED_C64) return GPEPS_EINVAL;
+  gpeps_handle* h = new (std::nothrow) gpeps_handle();
+  if (!h) return GPEPS_ENOMEM;
+  h->D = D;
+  h->dtype = dtype;
+  h->n_inst = n_instances;
+  h->elt = dtype == GPEPS_C128 ? 16 : 8;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->g.resize(n_instances);
+  for (int k = 0; k < n_instances; ++k) {
+    const int st = validate_and_colour(graphs[k], h->g[k]);
+    if (st) {
+      delete h;
+      return st;
+    }
+  }
+  // sites, offsets
+  h->inst_site0.assign(n_instances + 1, 0);
+  h->inst_edge0.assign(n_instances + 1, 0);
+  for (int k = 0; k < n_instances; ++k) {
+    h->inst_site0[k + 1] = h->inst_site0[k] + h->g[k].n;
+    h->inst_edge0[k + 1] = h->inst_edge0[k] + (int)h->g[k].edges.size();
+  }
+  h->total_sites = h->inst_site0[n_instances];
+  h->total_edges = h->inst_edge0[n_instances];
+  h->site_off.resize(h->total_sites);
+  h->site_inst.resize(h->total_sites);
+  h->sites.resize(h->total_sites);
+  int64_t off = 0;
+  for (int k = 0; k < n_instances; ++k) {
+    for (int v = 0; v < h->g[k].n; ++v) {
+      const int gs = h->inst_site0[k] + v;
+      const int d = (int)h->g[k].nb[v].size();
+      h->site_off[gs] = off;
+      h->site_inst[gs] = k;
+      SiteDesc sd{};
+      sd.off = off;
+      sd.deg = d;
+      for (int q = 0; q < 3; ++q) sd.lam[q] = q < d ? (h->inst_edge0[k] + h->g[k].nb_edge[v][q]) * D : -1;
+      h->sites[gs] = sd;
+      off += 2 * ipow(D, d);
+    }
+  }
+  h->n_gamma = off;
+  // colour plans
+  int ncol = 0;
+  for (auto& ig : h->g)
+    for (int c : ig.colour) ncol = std::max(ncol, c + 1);
+  h->colours.resize(ncol);
+  for (int c = 0; c < ncol; ++c) {
+    ColourPlan& cp = h->colours[c];
+    for (int k = 0; k < n_instances; ++k) {
+      const InstGraph& ig = h->g[k];
+      for (int e = 0; e < (int)ig.edges.size(); ++e) {
+        if (ig.colour[e] != c) continue;
+        int u = ig.edges[e].first, v = ig.edges[e].second;
+        const int du = (int)ig.nb[u].size(), dv = (int)ig.nb[v].size();
+        // end a: more legs (ties: smaller label); end b carries the eigenproblem
+        int a = u, b = v;
+        if (dv > du || (dv == du && v < u)) std::swap(a, b);
+        BondDesc bd{};
+        bd.a = side_desc(h, k, a, b);
+        bd.b = side_desc(h, k, b, a);
+        bd.lam_e = (h->inst_edge0[k] + e) * D;
+        bd.part0 = cp.n_parts;
+        bd.n_parts = (bd.a.rows + kTileRows - 1) / kTileRows;
+        for (int p = 0; p < bd.n_parts; ++p) {
+          TileDesc t{};
+          t.bond = (int)cp.bonds.size();
+          t.row0 = p * kTileRows;
+          t.nrows = std::min(kTileRows, bd.a.rows - t.row0);
+          t.part = cp.n_parts + p;
+          cp.tiles.push_back(t);
+        }
+        cp.n_parts += bd.n_parts;
+        cp.bonds.push_back(bd);
+      }
+    }
+    h->max_parts = std::max(h->max_parts, cp.n_parts);
+    h->max_bonds = std::max(h->max_bonds, (int)cp.bonds.size());
+  }
+  // Jacobi thresholds: the bond matrix carries FP64 rounding (C128) or the
+  // FP32 rounding of its Gram inputs (mixed); eigenvalues below that level are noise.
+  h->jp.tol = 1e-15;
+  h->jp.floor_rel = 1e-14;
+  h->jp.ev_cut = dtype == GPEPS_C128 ? 1e-14 : 1e-7;
+  h->jp.max_sweeps = 40;
+  // layouts
+  size_t s = 0;
+  h->s_lam = s;
+  s = align256(s + (size_t)h->total_edges * D * sizeof(double));
+  h->s_gamma = s;
+  s = align256(s + (size_t)h->n_gamma * h->elt);
+  h->state_bytes = std::max<size_t>(s, 256);
+  size_t w = 0;
+  auto carve = [&](size_t bytes) {
+    const size_t o = w;
+    w = align256(w + std::max<size_t>(bytes, 1));
+    return o;
+  };
+  h->w_pending = carve(h->total_sites * sizeof(double));
+  h->w_flags = carve(sizeof(int) * 4);
+  h->w_sweeps = carve(sizeof(unsigned long long));
+  h->w_z = carve(h->total_sites * sizeof(double));
+  h->w_mean = carve(n_instances * sizeof(double));
+  h->w_sites = carve(h->total_sites * sizeof(SiteDesc));
+  h->w_inst_site0 = carve((n_instances + 1) * sizeof(int32_t));
+  h->w_site_inst = carve(h->total_sites * sizeof(int32_t));
+  h->w_site_off = carve(h->total_sites * sizeof(int64_t));
+  for (auto& cp : h->colours) {
+    cp.w_bonds = carve(cp.bonds.size() * sizeof(BondDesc));
+    cp.w_tiles = carve(cp.tiles.size() * sizeof(TileDesc));
+  }
+  h->w_partials = carve((size_t)h->max_parts * 2 * D * D * h->elt);
+  h->w_Y = carve((size_t)h->max_bonds * 2 * D * D * h->elt);
+  h->w_theta_a = carve((size_t)h->max_bonds * sizeof(double));
+  h->work_bytes = w;
+  *out = h;
+  return GPEPS_OK;
+}
+
+int gpeps_query_workspace(const gpeps_handle* h, size_t* state_bytes, size_t* work_bytes) {
+  if (!h || !state_bytes || !work_bytes) return GPEPS_EINVAL;
+  *state_bytes = h->state_bytes;
+  *work_bytes = h->work_bytes;
+  return GPEPS_OK;
+}
+
+int gpeps_bind(gpeps_handle* h, void* d_state, void* d_work) {
+  if (!h || !d_state || !d_work) return GPEPS_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_state) & 255) || (reinterpret_cast<uintptr_t>(d_work) & 255))
+    return GPEPS_EINVAL;
+  drop_graph(h);
+  h->d_state = static_cast<char*>(d_state);
+  h->d_work = static_cast<char*>(d_work);
+  GP_CUDA(h->dtype == GPEPS_C128 ? Launch<double>::init() : Launch<float>::init());
+  auto up = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(h->d_work + off, src, bytes, cudaMemcpyHostToDevice, h->stream);
+  };
+  GP_CUDA(up(h->w_sites, h->sites.data(), h->sites.size() * sizeof(SiteDesc)));
+  GP_CUDA(up(h->w_inst_site0, h->inst_site0.data(), h->inst_site0.size() * sizeof(int32_t)));
+  GP_CUDA(up(h->w_site_inst, h->site_inst.data(), h->site_inst.size() * sizeof(int32_t)));
+  GP_CUDA(up(h->w_site_off, h->site_off.data(), h->site_off.size() * sizeof(int64_t)));
+  for (auto& cp : h->colours) {
+    GP_CUDA(up(cp.w_bonds, cp.bonds.data(), cp.bonds.size() * sizeof(BondDesc)));
+    GP_CUDA(up(cp.w_tiles, cp.tiles.data(), cp.tiles.size() * sizeof(TileDesc)));
+  }
+  GP_CUDA(cudaMemsetAsync(h->d_work + h->w_flags, 0, sizeof(int) * 4, h->stream));
+  GP_CUDA(cudaMemsetAsync(h->d_work + h->w_sweeps, 0, sizeof(unsigned long long), h->stream));
+  GP_CUDA(cudaMemsetAsync(h->d_work + h->w_pending, 0, h->total_sites * sizeof(double), h->stream));
+  // host vectors are pageable: the copies above have been staged when they return
+  h->bound = true;
+  return GPEPS_OK;
+}
+
+int gpeps_reset(gpeps_handle* h) {
+  if (!h || !h->bound) return GPEPS_EINVAL;
+  const int64_t* so = h->at<int64_t>(h->w_site_off);
+  cudaError_t e = h->dtype == GPEPS_C128
+                      ? Launch<double>::reset(h->gamma(), h->lam(), h->n_gamma, h->total_edges, h->D, so,
+                                              (int)h->total_sites, h->pending(), h->stream)
+                      : Launch<float>::reset(h->gamma(), h->lam(), h->n_gamma, h->total_edges, h->D, so,
+                                             (int)h->total_sites, h->pending(), h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reset");
+  GP_CUDA(cudaMemsetAsync(h->d_work + h->w_flags, 0, sizeof(int) * 4, h->stream));
+  GP_CUDA(cudaMemsetAsync(h->d_work + h->w_sweeps, 0, sizeof(unsigned long long), h->stream));
+  h->bonds_since_reset = 0;
+  return GPEPS_OK;
+}
+
+int gpeps_kick(gpeps_handle* h, const double* theta, int32_t per_qubit) {
+  if (!h || !h->bound || !theta) return GPEPS_EINVAL;
+  return kick_impl(h, theta, per_qubit ? 1 : 0);
+}
+
+int gpeps_zz_layer(gpeps_handle* h, int32_t colour) {
+  if (!h || !h->bound) return GPEPS_EINVAL;
+  if (colour < 0 || colour >= (int)h->colours.size()) return GPEPS_EINVAL;
+  return layer(h, colour);
+}
+
+int gpeps_zz_layer_profiled(gpeps_handle* h, int32_t colour, float* ms) {
+  if (!h || !h->bound || !ms) return GPEPS_EINVAL;
+  if (colour < 0 || colour >= (int)h->colours.size()) return GPEPS_EINVAL;
+  PhaseEvents pe{};
+  for (int i = 0; i < 4; ++i) GP_CUDA(cudaEventCreate(&pe.ev[i]));
+  int st = layer(h, colour, &pe);
+  cudaError_t e = cudaEventSynchronize(pe.ev[3]);
+  for (int i = 0; i < 3 && st == GPEPS_OK && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[i], pe.ev[i], pe.ev[i + 1]);
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(pe.ev[i]);
+  if (st) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "gpeps_zz_layer_profiled");
+  return GPEPS_OK;
+}
+
+int gpeps_n_colours(const gpeps_handle* h, int32_t* n_colours) {
+  if (!h || !n_colours) return GPEPS_EINVAL;
+  *n_colours = (int32_t)h->colours.size();
+  return GPEPS_OK;
+}
+
+int gpeps_expect_z(gpeps_handle* h, double* d_z, double* d_mean) {
+  if (!h || !h->bound) return GPEPS_EINVAL;
+  const int st = readout_impl(h);
+  if (st) return st;
+  if (d_z)
+    GP_CUDA(cudaMemcpyAsync(d_z, h->z(), h->total_sites * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  if (d_mean)
+    GP_CUDA(cudaMemcpyAsync(d_mean, h->mean(), h->n_inst * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  return GPEPS_OK;
+}
+
+int gpeps_step(gpeps_handle* h, int32_t n_steps, const double* theta, int32_t per_qubit,
+               double* d_mean_per_step) {
+  if (!h || !h->bound || !theta || n_steps < 0) return GPEPS_EINVAL;
+  per_qubit = per_qubit ? 1 : 0;
+  const int64_t nbonds_step = [&] {
+    int64_t s = 0;
+    for (auto& cp : h->colours) s += (int64_t)cp.bonds.size();
+    return s;
+  }();
+  const bool use_graph = h->stream != nullptr;
+  if (use_graph && (h->step_exec == nullptr || h->step_theta != theta || h->step_per_qubit != per_qubit)) {
+    drop_graph(h);
+    GP_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t saved = h->bonds_since_reset;
+    const int st = one_step(h, theta, per_qubit);
+    h->bonds_since_reset = saved;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
+    if (st) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ec != cudaSuccess) return cuda_fail(ec, "cudaStreamEndCapture");
+    const cudaError_t ei = cudaGraphInstantiate(&h->step_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      h->step_exec = nullptr;
+      return cuda_fail(ei, "cudaGraphInstantiate");
+    }
+    h->step_theta = theta;
+    h->step_per_qubit = per_qubit;
+  }
+  for (int t = 0; t < n_steps; ++t) {
+    if (use_graph) {
+      GP_CUDA(cudaGraphLaunch(h->step_exec, h->stream));
+      h->bonds_since_reset += nbonds_step;
+    } else {
+      const int st = one_step(h, theta, per_qubit);
+      if (st) return st;
+    }
+    if (d_mean_per_step)
+      GP_CUDA(cudaMemcpyAsync(d_mean_per_step + (int64_t)t * h->n_inst, h->mean(), h->n_inst * sizeof(double),
+                              cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return GPEPS_OK;
+}
+
+int gpeps_status(gpeps_handle* h, int32_t* flags) {
+  if (!h || !h->bound || !flags) return GPEPS_EINVAL;
+  GP_CUDA(cudaStreamSynchronize(h->stream));
+  int f = 0;
+  GP_CUDA(cudaMemcpy(&f, h->flags(), sizeof(int), cudaMemcpyDeviceToHost));
+  *flags = f;
+  return GPEPS_OK;
+}
+
+int gpeps_lambda(gpeps_handle* h, int32_t instance, int32_t edge, double* out) {
+  if (!h || !h->bound || !out || instance < 0 || instance >= h->n_inst) return GPEPS_EINVAL;
+  if (edge < 0 || edge >= (int)h->g[instance].edges.size()) return GPEPS_EINVAL;
+  GP_CUDA(cudaStreamSynchronize(h->stream));
+  GP_CUDA(cudaMemcpy(out, h->lam() + (int64_t)(h->inst_edge0[instance] + edge) * h->D, h->D * sizeof(double),
+                     cudaMemcpyDeviceToHost));
+  std::sort(out, out + h->D, [](double x, double y) { return x > y; });
+  return GPEPS_OK;
+}
+
+int gpeps_sizes(const gpeps_handle* h, int64_t* total_qubits, int64_t* total_edges) {
+  if (!h) return GPEPS_EINVAL;
+  if (total_qubits) *total_qubits = h->total_sites;
+  if (total_edges) *total_edges = h->total_edges;
+  return GPEPS_OK;
+}
+
+int gpeps_sweeps(gpeps_handle* h, int64_t* total_sweeps, int64_t* total_bonds) {
+  if (!h || !h->bound) return GPEPS_EINVAL;
+  GP_CUDA(cudaStreamSynchronize(h->stream));
+  unsigned long long s = 0;
+  GP_CUDA(cudaMemcpy(&s, h->sweeps(), sizeof(s), cudaMemcpyDeviceToHost));
+  if (total_sweeps) *total_sweeps = (int64_t)s;
+  if (total_bonds) *total_bonds = h->bonds_since_reset;
+  return GPEPS_OK;
+}
+
+int gpeps_destroy(gpeps_handle* h) {
+  if (!h) return GPEPS_EINVAL;
+  drop_graph(h);
+  delete h;
+  return GPEPS_OK;
+}
+
+const char* gpeps_error_string(int status) {
+  switch (status) {
+    case GPEPS_OK: return "ok";
+    case GPEPS_EINVAL: return "invalid argument";
+    case GPEPS_ECUDA: return "CUDA runtime error";
+    case GPEPS_ENOCONV: return "Jacobi eigensolver hit its sweep cap";
+    case GPEPS_ENUMERIC: return "non-finite or vanishing bond spectrum";
+    case GPEPS_ENOMEM: return "host allocation failed";
+    default: return "unknown status";
+  }
+}
+
+const char* gpeps_last_cuda_error(void) { return g_last_cuda.c_str(); }
+
+}  // extern "C"

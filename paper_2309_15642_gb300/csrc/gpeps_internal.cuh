@@ -1,0 +1,88 @@
+// Internal device-side data structures of the gPEPS simple-update library.
+//
+// Site tensors live in one state buffer, each Gamma_i as [s][leg0][leg1][leg2]
+// (physical index outermost, legs in sorted-neighbour order, last leg fastest),
+// followed by lambda_e as float64[D] per edge.  A bond update views each end as
+// a matrix A[(other legs), (s, k)] through the strides of a SideDesc.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gpeps {
+
+constexpr int kMaxD = 32;          // bond dimension limit of this build
+constexpr int kTileRows = 64;      // rows of a big-side tile (Gram and update launches)
+constexpr int kThreads = 256;      // threads of every CTA
+constexpr double kLambdaCut = 1e-13;  // pseudo-inverse threshold relative to max(lambda)
+
+// One end of a bond seen as a matrix: row r = (r1, r2) runs over the other legs,
+// column (s, k) over the physical index and the bond leg.
+struct SideDesc {
+  int64_t off;      // element offset of Gamma in the tensor area of the state
+  int32_t rows;     // D^(deg-1)
+  int32_t n2;       // extent of the faster other leg (1 if none)
+  int32_t str_s;    // element stride of the physical index
+  int32_t str_k;    // element stride of the bond leg
+  int32_t str_o1;   // element stride of the slower other leg (0 if none)
+  int32_t str_o2;   // element stride of the faster other leg (0 if none)
+  int32_t lam_o1;   // lambda offset (float64 elements) of the slower other leg, -1 if none
+  int32_t lam_o2;   // lambda offset of the faster other leg, -1 if none
+  int32_t site;     // global site index (kick angles)
+  int32_t pad;
+};
+
+// Bond (a, b): a is the end with more rows (Gram + update launches), b the end
+// whose (row, s) space carries the bond eigenproblem (2 * b.rows <= 2D).
+struct BondDesc {
+  SideDesc a;
+  SideDesc b;
+  int32_t lam_e;    // lambda offset of the bond itself
+  int32_t part0;    // first Gram-partial slot of side a
+  int32_t n_parts;  // row tiles of side a
+  int32_t pad;
+};
+
+struct TileDesc {
+  int32_t bond;     // index into the colour class's bond list
+  int32_t row0;     // first row of side a in this tile
+  int32_t nrows;    // rows in this tile (<= kTileRows)
+  int32_t part;     // Gram-partial slot written by this tile
+};
+
+struct SiteDesc {
+  int64_t off;      // element offset of Gamma
+  int32_t deg;
+  int32_t lam[3];   // lambda offsets of the legs in leg order (-1 past deg)
+};
+
+struct JacobiParams {
+  double tol;        // relative off-diagonal threshold |a_pq| <= tol sqrt(a_pp a_qq)
+  double floor_rel;  // absolute threshold |a_pq| <= floor_rel * trace
+  double ev_cut;     // eigenvalues <= ev_cut * max eigenvalue are dropped (lambda = 0)
+  int max_sweeps;
+  int pad;
+};
+
+// Launchers (su_kernels.cu).  T = float for GPEPS_MIXED_C64, double for GPEPS_C128.
+template <typename T>
+struct Launch {
+  static cudaError_t init();
+  static cudaError_t reset(void* gamma, double* lam, int64_t n_gamma, int64_t n_lam_edges, int D,
+                           const int64_t* d_site_off, int n_sites, double* pending, cudaStream_t st);
+  static cudaError_t kick(double* pending, const double* theta, const int32_t* site_inst, int n_sites,
+                          int per_qubit, cudaStream_t st);
+  static cudaError_t gram(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, const void* gamma,
+                          const double* lam, const double* pending, void* partials, int D, cudaStream_t st);
+  static cudaError_t bond(const BondDesc* bonds, int n_bonds, const void* partials, void* gamma, double* lam,
+                          double* pending, void* Y, double* theta_a, int* flags,
+                          unsigned long long* sweeps, int D, JacobiParams jp, cudaStream_t st);
+  static cudaError_t update(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, void* gamma,
+                            const double* lam, const void* Y, const double* theta_a, int D, cudaStream_t st);
+  static cudaError_t readout(const SiteDesc* sites, int n_sites, const void* gamma, const double* lam,
+                             const double* pending, double* z, int D, cudaStream_t st);
+};
+
+cudaError_t launch_mean(const double* z, const int32_t* inst_site0, int n_inst, double* mean, cudaStream_t st);
+size_t bond_smem_bytes(int D, int n);
+
+}  // namespace gpeps

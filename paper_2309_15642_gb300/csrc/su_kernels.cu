@@ -1,0 +1,765 @@
+// CUDA kernels of the simple-update Trotter step (sm_103a).
+//
+// One bond update (paper, section "Method": simple update; gate of Eq. 2) is
+// split over three batched launches per colour class:
+//
+//   gram    per row tile of the big end a: kick (Eq. 2, single-site factor) and
+//           lambda of the other legs fused on load, partial Gram blocks
+//           G_s[k][l] = sum_r conj(A[r][s][k]) A[r][s][l]          (T arithmetic)
+//   bond    per bond: reduced density matrix of the small end b,
+//           rho[x][y] = sum_s conj(g(s,t_x)) g(s,t_y) sum_{k,l} conj(F[x][k]) lam_k G_s[k][l] lam_l F[y][l]
+//           with x = (row of b, t), F = kicked A_b; its Hermitian eigenproblem by
+//           parallel cyclic Jacobi in FP64; keep the D largest eigenvalues
+//           (Schmidt values s^2), lambda' = s / ||s||, Gamma_b' = conj(V) / lambda_other
+//           (pseudo-inverse), and the small matrices
+//           Y_s[k][k'] = lam_k sum_x F[x][k] g(s,t_x) V[x][k'] / s_k'
+//   update  per row tile of a: Gamma_a'[r][s][k'] = sum_k A~[r][s][k] Y_s[k][k'] in place
+//           (A~ = kicked Gamma_a without lambda: the lambda absorbed into the
+//           Gram cancels against the lambda^-1 strip; rows whose lambda is below
+//           the pseudo-inverse cut are zeroed).
+//
+// This is the textbook QR + SVD simple update rewritten around Gram matrices:
+// the singular values and vectors of the gated two-site matrix are those of
+// the eigenproblem of rho, so no panel QR is ever formed, and the only FP64
+// work is the 2D x 2D bond eigenproblem (and, in complex128 mode, the products).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "gpeps_internal.cuh"
+
+namespace gpeps {
+
+template <typename T> struct vec2;
+template <> struct vec2<float> { using type = float2; };
+template <> struct vec2<double> { using type = double2; };
+
+template <typename T>
+using V2 = typename vec2<T>::type;
+
+template <typename T>
+__device__ __forceinline__ V2<T> mk(T x, T y) {
+  V2<T> r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+
+// acc += conj(a) * b
+template <typename T>
+__device__ __forceinline__ void fma_conj(V2<T>& acc, V2<T> a, V2<T> b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+
+// acc += a * b
+template <typename T>
+__device__ __forceinline__ void fma_c(V2<T>& acc, V2<T> a, V2<T> b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// exp(-i theta X / 2) applied to the pair (g0, g1) of physical components.
+template <typename T>
+__device__ __forceinline__ void kick2(T c, T s, V2<T> g0, V2<T> g1, V2<T>& a0, V2<T>& a1) {
+  a0 = mk<T>(c * g0.x + s * g1.y, c * g0.y - s * g1.x);
+  a1 = mk<T>(s * g0.y + c * g1.x, -s * g0.x + c * g1.y);
+}
+
+struct RowPos {
+  int r1, r2;
+};
+__device__ __forceinline__ RowPos row_pos(const SideDesc& sd, int r) {
+  RowPos p;
+  p.r1 = r / sd.n2;
+  p.r2 = r - p.r1 * sd.n2;
+  return p;
+}
+__device__ __forceinline__ int64_t elem(const SideDesc& sd, int s, RowPos p, int k) {
+  return sd.off + (int64_t)s * sd.str_s + (int64_t)p.r1 * sd.str_o1 + (int64_t)p.r2 * sd.str_o2 +
+         (int64_t)k * sd.str_k;
+}
+__device__ __forceinline__ double row_weight(const SideDesc& sd, const double* lam, RowPos p) {
+  double w = 1.0;
+  if (sd.lam_o1 >= 0) w *= lam[sd.lam_o1 + p.r1];
+  if (sd.lam_o2 >= 0) w *= lam[sd.lam_o2 + p.r2];
+  return w;
+}
+
+// ---------------------------------------------------------------- reset / kick
+template <typename T>
+__global__ void reset_kernel(V2<T>* gamma, double* lam, const int64_t* site_off, int n_sites,
+                             int64_t n_edges, int D, double* pending) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n_sites) {
+    gamma[site_off[i]] = mk<T>((T)1, (T)0);
+    pending[i] = 0.0;
+  }
+  if (i < n_edges) lam[i * D] = 1.0;
+}
+
+__global__ void kick_kernel(double* pending, const double* theta, const int32_t* site_inst, int n_sites,
+                            int per_qubit) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_sites) pending[i] += per_qubit ? theta[i] : theta[site_inst[i]];
+}
+
+// ---------------------------------------------------------------- Gram partials
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    gram_kernel(const TileDesc* __restrict__ tiles, const BondDesc* __restrict__ bonds,
+                const V2<T>* __restrict__ gamma, const double* __restrict__ lam,
+                const double* __restrict__ pending, V2<T>* __restrict__ partials, int D) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V2<T>* A = reinterpret_cast<V2<T>*>(smem_raw);  // [nrows][2D+1]
+  const TileDesc t = tiles[blockIdx.x];
+  const SideDesc sa = bonds[t.bond].a;
+  const int ld = 2 * D + 1;
+  const double th = pending[sa.site];
+  const T c = (T)cos(0.5 * th), s = (T)sin(0.5 * th);
+  const int nel = t.nrows * D;
+  for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+    int r, k;
+    if (sa.str_k == 1) {
+      r = idx / D;
+      k = idx - r * D;
+    } else {
+      k = idx / t.nrows;
+      r = idx - k * t.nrows;
+    }
+    const RowPos p = row_pos(sa, t.row0 + r);
+    const int64_t e = elem(sa, 0, p, k);
+    const T w = (T)row_weight(sa, lam, p);
+    V2<T> a0, a1;
+    kick2<T>(c, s, gamma[e], gamma[e + sa.str_s], a0, a1);
+    A[r * ld + k] = mk<T>(a0.x * w, a0.y * w);
+    A[r * ld + D + k] = mk<T>(a1.x * w, a1.y * w);
+  }
+  __syncthreads();
+  const int D2 = D * D;
+  const int nout = 2 * D2;
+  V2<T>* out = partials + (int64_t)t.part * nout;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    const int sidx = o / D2;
+    const int kl = o - sidx * D2;
+    const int k = kl / D;
+    const int l = kl - k * D;
+    const V2<T>* ck = A + sidx * D + k;
+    const V2<T>* cl = A + sidx * D + l;
+    V2<T> acc = mk<T>(0, 0);
+    for (int r = 0; r < t.nrows; ++r) fma_conj<T>(acc, ck[r * ld], cl[r * ld]);
+    out[o] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- bond eigenproblem
+// Shared-memory layout of bond_kernel for a bond whose small end has nb rows
+// (n = 2 nb): every double2 array first, then doubles, then ints.
+struct BondSmem {
+  int n, D;
+  size_t off_F, off_RHO, off_X, off_re, off_lamo, off_ev, off_sv, off_rc, off_rs, off_int, total;
+  __host__ __device__ BondSmem(int D_, int n_) : n(n_), D(D_) {
+    const size_t c16 = 16, c8 = 8;
+    const int m = n / 2;
+    size_t x = (size_t)2 * D * D + (size_t)n * D;
+    if ((size_t)n * n > x) x = (size_t)n * n;
+    off_F = 0;
+    off_RHO = off_F + (size_t)n * D * c16;
+    off_X = off_RHO + (size_t)n * (n + 1) * c16;
+    off_re = off_X + x * c16;
+    off_lamo = off_re + (size_t)m * c16;
+    off_ev = off_lamo + (size_t)D * c8;
+    off_sv = off_ev + (size_t)n * c8;
+    off_rc = off_sv + (size_t)D * c8;
+    off_rs = off_rc + (size_t)m * c8;
+    off_int = off_rs + (size_t)m * c8 + 8 * c8;  // 8 scalar doubles after rs
+    total = off_int + (size_t)(n + 2 * m + 8) * 4;
+  }
+};
+
+size_t bond_smem_bytes(int D, int n) { return BondSmem(D, n).total; }
+
+// Parallel cyclic Jacobi for the Hermitian n x n matrix A (row stride lda) in
+// shared memory, accumulating V (row stride ldv) = product of rotations.  The
+// (n-1) rounds of a sweep use the round-robin pairing, so the n/2 rotations of
+// a round are disjoint and applied together: A <- J^dagger A J block by block
+// (upper blocks computed, lower blocks mirrored), V <- V J.  Rotation of pair
+// (p, q) (Golub & Van Loan, Alg. 8.4.1, sym.schur2, after a diagonal phase that
+// makes a_pq real): J = [[c, s], [-s e, c e]], e = conj(a_pq)/|a_pq|.  A pair is
+// skipped when |a_pq| <= max(tol sqrt(a_pp a_qq), floor).  Returns the sweeps
+// run; max_sweeps + 1 means the cap was hit.
+__device__ int jacobi_hermitian(double2* A, int lda, double2* V, int ldv, int n, const JacobiParams& jp,
+                                double floor_abs, double* rc, double* rs, double2* re, int* rp, int* rq,
+                                int* iflag) {
+  const int m = n / 2;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - (idx / n) * n;
+    V[i * ldv + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < jp.max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) iflag[0] = 0;
+    __syncthreads();
+    for (int r = 0; r < n - 1; ++r) {
+      for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        int p, q;
+        if (k == 0) {
+          p = r;
+          q = n - 1;
+        } else {
+          p = (r + k) % (n - 1);
+          q = (r - k + (n - 1)) % (n - 1);
+        }
+        if (p > q) {
+          const int tmp = p;
+          p = q;
+          q = tmp;
+        }
+        const double app = A[p * lda + p].x, aqq = A[q * lda + q].x;
+        const double2 apq = A[p * lda + q];
+        const double g = hypot(apq.x, apq.y);
+        double cs = 1.0, sn = 0.0;
+        double2 e = make_double2(1.0, 0.0);
+        if (g > floor_abs && g > jp.tol * sqrt(fabs(app * aqq))) {
+          const double zeta = (aqq - app) / (2.0 * g);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          cs = 1.0 / sqrt(1.0 + t * t);
+          sn = t * cs;
+          e = make_double2(apq.x / g, -apq.y / g);
+          iflag[0] = 1;
+        }
+        rp[k] = p;
+        rq[k] = q;
+        rc[k] = cs;
+        rs[k] = sn;
+        re[k] = e;
+      }
+      __syncthreads();
+      // A <- J^dagger A J on the upper blocks (a <= b), lower blocks mirrored
+      for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+        const int a = idx / m, b = idx - (idx / m) * m;
+        if (a > b) continue;
+        const bool rot_a = rs[a] != 0.0, rot_b = rs[b] != 0.0;
+        if (!rot_a && !rot_b) continue;
+        const int pa = rp[a], qa = rq[a], pb = rp[b], qb = rq[b];
+        const double ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
+        const double2 ea = re[a], eb = re[b];
+        const double2 b00 = A[pa * lda + pb], b01 = A[pa * lda + qb];
+        const double2 b10 = A[qa * lda + pb], b11 = A[qa * lda + qb];
+        // T = B J_b
+        const double2 b01e = cmul(b01, eb), b11e = cmul(b11, eb);
+        const double2 t00 = csub(cscale(b00, cb), cscale(b01e, sb));
+        const double2 t01 = cadd(cscale(b00, sb), cscale(b01e, cb));
+        const double2 t10 = csub(cscale(b10, cb), cscale(b11e, sb));
+        const double2 t11 = cadd(cscale(b10, sb), cscale(b11e, cb));
+        // B' = J_a^dagger T, J_a^dagger = [[c, -s conj(e)], [s, c conj(e)]]
+        const double2 ce = cconj(ea);
+        const double2 u10 = cmul(t10, ce), u11 = cmul(t11, ce);
+        double2 n00 = csub(cscale(t00, ca), cscale(u10, sa));
+        double2 n01 = csub(cscale(t01, ca), cscale(u11, sa));
+        double2 n10 = cadd(cscale(t00, sa), cscale(u10, ca));
+        double2 n11 = cadd(cscale(t01, sa), cscale(u11, ca));
+        if (a == b) {
+          n00.y = 0.0;
+          n11.y = 0.0;
+          n01 = make_double2(0.0, 0.0);
+          n10 = make_double2(0.0, 0.0);
+        }
+        A[pa * lda + pb] = n00;
+        A[pa * lda + qb] = n01;
+        A[qa * lda + pb] = n10;
+        A[qa * lda + qb] = n11;
+        if (a < b) {
+          A[pb * lda + pa] = cconj(n00);
+          A[qb * lda + pa] = cconj(n01);
+          A[pb * lda + qa] = cconj(n10);
+          A[qb * lda + qa] = cconj(n11);
+        }
+      }
+      // V <- V J
+      for (int idx = threadIdx.x; idx < n * m; idx += blockDim.x) {
+        const int i = idx / m, k = idx - (idx / m) * m;
+        const double sn = rs[k];
+        if (sn == 0.0) continue;
+        const double cs = rc[k];
+        const int p = rp[k], q = rq[k];
+        const double2 vp = V[i * ldv + p];
+        const double2 vqe = cmul(V[i * ldv + q], re[k]);
+        V[i * ldv + p] = csub(cscale(vp, cs), cscale(vqe, sn));
+        V[i * ldv + q] = cadd(cscale(vp, sn), cscale(vqe, cs));
+      }
+      __syncthreads();
+    }
+    const int done = (iflag[0] == 0);
+    __syncthreads();
+    if (done) return sweep + 1;
+  }
+  return jp.max_sweeps + 1;
+}
+
+// A bond whose spectrum is not usable (NaN/Inf or zero norm) is left as it
+// was: Y = identity so that the update launch only applies the pending kick
+// to end a, lambda and end b untouched; the flag word reports it.
+template <typename T>
+__device__ void bond_fail(const BondDesc& bd, V2<T>* Yout, double* theta_a, double* pending, int* flags, int D) {
+  const int D2 = D * D;
+  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
+    const int kl = o % D2;
+    Yout[(int64_t)blockIdx.x * 2 * D2 + o] = mk<T>((T)((kl / D) == (kl % D) ? 1 : 0), (T)0);
+  }
+  if (threadIdx.x == 0) {
+    atomicOr(flags, 2);
+    theta_a[blockIdx.x] = pending[bd.a.site];
+    pending[bd.a.site] = 0.0;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    bond_kernel(const BondDesc* __restrict__ bonds, const V2<T>* __restrict__ partials, V2<T>* gamma,
+                double* lam, double* pending, V2<T>* __restrict__ Yout, double* __restrict__ theta_a,
+                int* flags, unsigned long long* sweeps_out, int D, JacobiParams jp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BondDesc bd = bonds[blockIdx.x];
+  const SideDesc sb = bd.b;
+  const int nb = sb.rows;
+  const int n = 2 * nb;
+  const int m = n / 2;
+  const int D2 = D * D;
+  const BondSmem L(D, n);
+  double2* F = reinterpret_cast<double2*>(smem_raw + L.off_F);      // [n][D]
+  double2* RHO = reinterpret_cast<double2*>(smem_raw + L.off_RHO);  // [n][n+1]
+  double2* X = reinterpret_cast<double2*>(smem_raw + L.off_X);
+  double2* Cs = X;           // [2][D][D]
+  double2* H = X + 2 * D2;   // [n][D]
+  double2* Vm = X;           // [n][n] after rho is formed
+  double2* re = reinterpret_cast<double2*>(smem_raw + L.off_re);
+  double* lamo = reinterpret_cast<double*>(smem_raw + L.off_lamo);  // old lambda of the bond
+  double* ev = reinterpret_cast<double*>(smem_raw + L.off_ev);
+  double* sv = reinterpret_cast<double*>(smem_raw + L.off_sv);
+  double* rc = reinterpret_cast<double*>(smem_raw + L.off_rc);
+  double* rs = reinterpret_cast<double*>(smem_raw + L.off_rs);
+  double* scal = rs + m;  // [0] trace, [1] norm, [2] max lambda_other, [3] ev max
+  int* order = reinterpret_cast<int*>(smem_raw + L.off_int);
+  int* rp = order + n;
+  int* rq = rp + m;
+  int* iflag = rq + m;
+  const int ldr = n + 1;
+
+  // old lambda of the bond; Gram blocks with lambda on both sides, summed in FP64
+  for (int k = threadIdx.x; k < D; k += blockDim.x) lamo[k] = lam[bd.lam_e + k];
+  __syncthreads();
+  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int p = 0; p < bd.n_parts; ++p) {
+      const V2<T> v = partials[(int64_t)(bd.part0 + p) * 2 * D2 + o];
+      acc.x += (double)v.x;
+      acc.y += (double)v.y;
+    }
+    const int kl = o % D2;
+    const int k = kl / D, l = kl - (kl / D) * D;
+    Cs[o] = cscale(acc, lamo[k] * lamo[l]);
+  }
+  // F[(row, t)][k]: kicked Gamma_b with the lambda of its other legs
+  {
+    const double th = pending[sb.site];
+    const double c = cos(0.5 * th), s = sin(0.5 * th);
+    for (int idx = threadIdx.x; idx < nb * D; idx += blockDim.x) {
+      const int rj = idx / D, k = idx - (idx / D) * D;
+      const RowPos p = row_pos(sb, rj);
+      const int64_t e = elem(sb, 0, p, k);
+      const V2<T> g0 = gamma[e], g1 = gamma[e + sb.str_s];
+      double2 a0, a1;
+      kick2<double>(c, s, make_double2(g0.x, g0.y), make_double2(g1.x, g1.y), a0, a1);
+      const double w = row_weight(sb, lam, p);
+      F[(rj * 2 + 0) * D + k] = cscale(a0, w);
+      F[(rj * 2 + 1) * D + k] = cscale(a1, w);
+    }
+  }
+  for (int idx = threadIdx.x; idx < n * ldr; idx += blockDim.x) RHO[idx] = make_double2(0.0, 0.0);
+  __syncthreads();
+  // rho = sum_s phase(s) o (conj(F) C_s F^T)
+  for (int sidx = 0; sidx < 2; ++sidx) {
+    const double2* C = Cs + sidx * D2;
+    for (int idx = threadIdx.x; idx < n * D; idx += blockDim.x) {
+      const int x = idx / D, l = idx - (idx / D) * D;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = 0; k < D; ++k) fma_conj<double>(acc, F[x * D + k], C[k * D + l]);
+      H[x * D + l] = acc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int x = idx / n, y = idx - (idx / n) * n;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int l = 0; l < D; ++l) fma_c<double>(acc, H[x * D + l], F[y * D + l]);
+      const int tx = x & 1, ty = y & 1;
+      double2 v;
+      if (tx == ty) {
+        v = acc;
+      } else if (sidx == ty) {  // +i
+        v = make_double2(-acc.y, acc.x);
+      } else {  // -i
+        v = make_double2(acc.y, -acc.x);
+      }
+      RHO[x * ldr + y] = cadd(RHO[x * ldr + y], v);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += RHO[i * ldr + i].x;
+    scal[0] = tr;
+  }
+  __syncthreads();
+  const double trace = scal[0];
+  if (!(trace > 0.0) || !isfinite(trace)) {
+    bond_fail<T>(bd, Yout, theta_a, pending, flags, D);
+    return;
+  }
+  const int sweeps =
+      jacobi_hermitian(RHO, ldr, Vm, n, n, jp, jp.floor_rel * trace, rc, rs, re, rp, rq, iflag);
+  if (threadIdx.x == 0) {
+    if (sweeps > jp.max_sweeps) atomicOr(flags, 1);
+    atomicAdd(sweeps_out, (unsigned long long)(sweeps > jp.max_sweeps ? jp.max_sweeps : sweeps));
+  }
+  // eigenvalues sorted in decreasing order (ties by index)
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ev[i] = RHO[i * ldr + i].x;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int rank = 0;
+    const double vi = ev[i];
+    for (int j = 0; j < n; ++j) rank += (ev[j] > vi) || (ev[j] == vi && j < i);
+    order[rank] = i;
+  }
+  __syncthreads();
+  const int keep = n < D ? n : D;
+  if (threadIdx.x == 0) {
+    const double emax = ev[order[0]];
+    double nrm2 = 0.0;
+    for (int kk = 0; kk < D; ++kk) {
+      double sval = 0.0;
+      if (kk < keep) {
+        const double e = ev[order[kk]];
+        if (e > jp.ev_cut * emax && e > 0.0) sval = sqrt(e);
+      }
+      sv[kk] = sval;
+      nrm2 += sval * sval;
+    }
+    scal[1] = sqrt(nrm2);
+    double mx = 0.0;
+    const int lo = sb.lam_o1 >= 0 ? sb.lam_o1 : sb.lam_o2;
+    if (lo >= 0)
+      for (int k = 0; k < D; ++k) mx = fmax(mx, lam[lo + k]);
+    scal[2] = mx;
+  }
+  __syncthreads();
+  const double nrm = scal[1];
+  if (!(nrm > 0.0) || !isfinite(nrm)) {
+    bond_fail<T>(bd, Yout, theta_a, pending, flags, D);
+    return;
+  }
+  // Y_s[k][kk] = lam_k sum_x F[x][k] g(s, t_x) V[x][order[kk]] / sv[kk]
+  const double r2 = 0.70710678118654752440;
+  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
+    const int sidx = o / D2;
+    const int kl = o - sidx * D2;
+    const int k = kl / D, kk = kl - (kl / D) * D;
+    double2 acc = make_double2(0.0, 0.0);
+    if (sv[kk] > 0.0) {
+      const int col = order[kk];
+      for (int x = 0; x < n; ++x) {
+        const double2 fv = F[x * D + k];
+        const double2 g = make_double2(r2, (sidx == (x & 1)) ? r2 : -r2);
+        fma_c<double>(acc, cmul(fv, g), Vm[x * n + col]);
+      }
+      acc = cscale(acc, lamo[k] / sv[kk]);
+    }
+    Yout[(int64_t)blockIdx.x * 2 * D2 + o] = mk<T>((T)acc.x, (T)acc.y);
+  }
+  // Gamma_b'[t][row][kk] = conj(V[(row, t)][order[kk]]) / lambda_other(row)
+  {
+    const double mx = scal[2];
+    for (int idx = threadIdx.x; idx < n * D; idx += blockDim.x) {
+      const int x = idx / D, kk = idx - (idx / D) * D;
+      const int rj = x >> 1, t = x & 1;
+      const RowPos p = row_pos(sb, rj);
+      double winv = 1.0;
+      const int lo = sb.lam_o1 >= 0 ? sb.lam_o1 : sb.lam_o2;
+      if (lo >= 0) {
+        const double lv = lam[lo + (sb.lam_o1 >= 0 ? p.r1 : p.r2)];
+        winv = lv > kLambdaCut * mx ? 1.0 / lv : 0.0;
+      }
+      double2 v = make_double2(0.0, 0.0);
+      if (sv[kk] > 0.0) v = cscale(cconj(Vm[x * n + order[kk]]), winv);
+      gamma[elem(sb, t, p, kk)] = mk<T>((T)v.x, (T)v.y);
+    }
+  }
+  __syncthreads();
+  // new lambda of the bond; kick angles consumed
+  for (int kk = threadIdx.x; kk < D; kk += blockDim.x) lam[bd.lam_e + kk] = sv[kk] / nrm;
+  if (threadIdx.x == 0) {
+    theta_a[blockIdx.x] = pending[bd.a.site];
+    pending[bd.a.site] = 0.0;
+    pending[sb.site] = 0.0;
+  }
+}
+
+// ---------------------------------------------------------------- big-end update
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    update_kernel(const TileDesc* __restrict__ tiles, const BondDesc* __restrict__ bonds, V2<T>* gamma,
+                  const double* __restrict__ lam, const V2<T>* __restrict__ Y,
+                  const double* __restrict__ theta_a, int D) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const TileDesc t = tiles[blockIdx.x];
+  const SideDesc sa = bonds[t.bond].a;
+  const int D2 = D * D;
+  V2<T>* Ys = reinterpret_cast<V2<T>*>(smem_raw);  // [2][D][D]
+  V2<T>* A = Ys + 2 * D2;                          // tile, layout chosen for the write order
+  const size_t a_elems_r = (size_t)t.nrows * (2 * D + 1), a_elems_c = (size_t)(2 * D) * (t.nrows + 1);
+  float* mask = reinterpret_cast<float*>(A + (a_elems_r > a_elems_c ? a_elems_r : a_elems_c));
+  __shared__ double cut[2];
+  const bool kfast = sa.str_k == 1;
+  // kfast: A[r][(2D+1)] with (s, k) inside; else A[(s, k)][nrows+1] with r inside
+  const int ldr = 2 * D + 1, ldc = t.nrows + 1;
+  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) Ys[o] = Y[(int64_t)t.bond * 2 * D2 + o];
+  if (threadIdx.x < 2) {
+    const int lo = threadIdx.x == 0 ? sa.lam_o1 : sa.lam_o2;
+    double mx = 0.0;
+    if (lo >= 0)
+      for (int k = 0; k < D; ++k) mx = fmax(mx, lam[lo + k]);
+    cut[threadIdx.x] = kLambdaCut * mx;
+  }
+  const double th = theta_a[t.bond];
+  const T c = (T)cos(0.5 * th), s = (T)sin(0.5 * th);
+  const int nel = t.nrows * D;
+  for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+    int r, k;
+    if (kfast) {
+      r = idx / D;
+      k = idx - r * D;
+    } else {
+      k = idx / t.nrows;
+      r = idx - k * t.nrows;
+    }
+    const RowPos p = row_pos(sa, t.row0 + r);
+    const int64_t e = elem(sa, 0, p, k);
+    V2<T> a0, a1;
+    kick2<T>(c, s, gamma[e], gamma[e + sa.str_s], a0, a1);
+    if (kfast) {
+      A[r * ldr + k] = a0;
+      A[r * ldr + D + k] = a1;
+    } else {
+      A[k * ldc + r] = a0;
+      A[(D + k) * ldc + r] = a1;
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < t.nrows; r += blockDim.x) {
+    const RowPos p = row_pos(sa, t.row0 + r);
+    bool ok = true;
+    if (sa.lam_o1 >= 0) ok = ok && lam[sa.lam_o1 + p.r1] > cut[0];
+    if (sa.lam_o2 >= 0) ok = ok && lam[sa.lam_o2 + p.r2] > cut[1];
+    mask[r] = ok ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const int nout = t.nrows * 2 * D;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    int r, sidx, kk;
+    if (kfast) {  // kk fastest
+      r = o / (2 * D);
+      const int rem = o - r * 2 * D;
+      sidx = rem / D;
+      kk = rem - sidx * D;
+    } else {  // r fastest
+      const int col = o / t.nrows;
+      r = o - col * t.nrows;
+      sidx = col / D;
+      kk = col - sidx * D;
+    }
+    V2<T> acc = mk<T>(0, 0);
+    const V2<T>* Yc = Ys + sidx * D2 + kk;
+    if (kfast) {
+      const V2<T>* Ar = A + r * ldr + sidx * D;
+      for (int k = 0; k < D; ++k) fma_c<T>(acc, Ar[k], Yc[k * D]);
+    } else {
+      const V2<T>* Ar = A + (sidx * D) * ldc + r;
+      for (int k = 0; k < D; ++k) fma_c<T>(acc, Ar[k * ldc], Yc[k * D]);
+    }
+    const T mk_ = (T)mask[r];
+    const RowPos p = row_pos(sa, t.row0 + r);
+    gamma[elem(sa, sidx, p, kk)] = mk<T>(acc.x * mk_, acc.y * mk_);
+  }
+}
+
+// ---------------------------------------------------------------- readout
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    readout_kernel(const SiteDesc* __restrict__ sites, const V2<T>* __restrict__ gamma,
+                   const double* __restrict__ lam, const double* __restrict__ pending, double* __restrict__ z,
+                   int D) {
+  const SiteDesc sd = sites[blockIdx.x];
+  int nel = 1;
+  for (int q = 0; q < sd.deg; ++q) nel *= D;
+  const double th = pending[blockIdx.x];
+  const double c = cos(0.5 * th), s = sin(0.5 * th);
+  double p0 = 0.0, p1 = 0.0;
+  for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+    double w = 1.0;
+    int rest = idx;
+    for (int q = sd.deg - 1; q >= 0; --q) {
+      const int l = rest % D;
+      rest /= D;
+      const double lv = lam[sd.lam[q] + l];
+      w *= lv * lv;
+    }
+    const V2<T> g0 = gamma[sd.off + idx], g1 = gamma[sd.off + nel + idx];
+    double2 a0, a1;
+    kick2<double>(c, s, make_double2(g0.x, g0.y), make_double2(g1.x, g1.y), a0, a1);
+    p0 += w * (a0.x * a0.x + a0.y * a0.y);
+    p1 += w * (a1.x * a1.x + a1.y * a1.y);
+  }
+  __shared__ double red[2][kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) {
+    p0 += __shfl_down_sync(0xffffffffu, p0, off);
+    p1 += __shfl_down_sync(0xffffffffu, p1, off);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[0][warp] = p0;
+    red[1][warp] = p1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      s0 += red[0][w];
+      s1 += red[1][w];
+    }
+    z[blockIdx.x] = (s0 - s1) / (s0 + s1);
+  }
+}
+
+__global__ void mean_kernel(const double* __restrict__ z, const int32_t* __restrict__ inst_site0,
+                            double* __restrict__ mean) {
+  const int k = blockIdx.x;
+  const int s0 = inst_site0[k], s1 = inst_site0[k + 1];
+  double acc = 0.0;
+  for (int i = s0 + threadIdx.x; i < s1; i += blockDim.x) acc += z[i];
+  __shared__ double red[kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    mean[k] = s / (double)(s1 - s0);
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+static size_t gram_smem(int D) { return (size_t)kTileRows * (2 * D + 1) * 16; }
+static size_t update_smem(int D, size_t elt) {
+  const size_t r = (size_t)kTileRows * (2 * D + 1), c = (size_t)(kTileRows + 1) * 2 * D;
+  return (size_t)2 * D * D * elt + (r > c ? r : c) * elt + (size_t)kTileRows * 4 + 64;
+}
+
+// Opt in to the dynamic shared memory of the largest supported D (called once
+// per handle before any launch, outside stream capture).
+template <typename T>
+cudaError_t Launch<T>::init() {
+  cudaError_t e = cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)gram_smem(kMaxD));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(bond_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bond_smem_bytes(kMaxD, 2 * kMaxD));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)update_smem(kMaxD, sizeof(V2<T>)));
+}
+
+template <typename T>
+cudaError_t Launch<T>::reset(void* gamma, double* lam, int64_t n_gamma, int64_t n_lam_edges, int D,
+                             const int64_t* d_site_off, int n_sites, double* pending, cudaStream_t st) {
+  cudaError_t err = cudaMemsetAsync(gamma, 0, (size_t)n_gamma * sizeof(V2<T>), st);
+  if (err != cudaSuccess) return err;
+  err = cudaMemsetAsync(lam, 0, (size_t)n_lam_edges * D * sizeof(double), st);
+  if (err != cudaSuccess) return err;
+  const int64_t n = n_sites > n_lam_edges ? n_sites : n_lam_edges;
+  if (n == 0) return cudaSuccess;
+  reset_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(static_cast<V2<T>*>(gamma), lam, d_site_off,
+                                                                 n_sites, n_lam_edges, D, pending);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::kick(double* pending, const double* theta, const int32_t* site_inst, int n_sites,
+                            int per_qubit, cudaStream_t st) {
+  if (n_sites == 0) return cudaSuccess;
+  kick_kernel<<<(n_sites + 255) / 256, 256, 0, st>>>(pending, theta, site_inst, n_sites, per_qubit);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::gram(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, const void* gamma,
+                            const double* lam, const double* pending, void* partials, int D, cudaStream_t st) {
+  if (n_tiles == 0) return cudaSuccess;
+  const size_t sm = (size_t)kTileRows * (2 * D + 1) * sizeof(V2<T>);
+  gram_kernel<T><<<n_tiles, kThreads, sm, st>>>(tiles, bonds, static_cast<const V2<T>*>(gamma), lam, pending,
+                                                 static_cast<V2<T>*>(partials), D);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::bond(const BondDesc* bonds, int n_bonds, const void* partials, void* gamma, double* lam,
+                            double* pending, void* Y, double* theta_a, int* flags, unsigned long long* sweeps,
+                            int D, JacobiParams jp, cudaStream_t st) {
+  if (n_bonds == 0) return cudaSuccess;
+  const size_t sm = bond_smem_bytes(D, 2 * D);
+  bond_kernel<T><<<n_bonds, kThreads, sm, st>>>(bonds, static_cast<const V2<T>*>(partials),
+                                                 static_cast<V2<T>*>(gamma), lam, pending,
+                                                 static_cast<V2<T>*>(Y), theta_a, flags, sweeps, D, jp);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::update(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, void* gamma,
+                              const double* lam, const void* Y, const double* theta_a, int D, cudaStream_t st) {
+  if (n_tiles == 0) return cudaSuccess;
+  const size_t sm = update_smem(D, sizeof(V2<T>));
+  update_kernel<T><<<n_tiles, kThreads, sm, st>>>(tiles, bonds, static_cast<V2<T>*>(gamma), lam,
+                                                   static_cast<const V2<T>*>(Y), theta_a, D);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::readout(const SiteDesc* sites, int n_sites, const void* gamma, const double* lam,
+                               const double* pending, double* z, int D, cudaStream_t st) {
+  if (n_sites == 0) return cudaSuccess;
+  readout_kernel<T><<<n_sites, kThreads, 0, st>>>(sites, static_cast<const V2<T>*>(gamma), lam, pending, z, D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mean(const double* z, const int32_t* inst_site0, int n_inst, double* mean, cudaStream_t st) {
+  if (n_inst == 0) return cudaSuccess;
+  mean_kernel<<<n_inst, kThreads, 0, st>>>(z, inst_site0, mean);
+  return cudaGetLastError();
+}
+
+template struct Launch<float>;
+template struct Launch<double>;
+
+}  // namespace gpeps

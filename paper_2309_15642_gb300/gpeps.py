@@ -1,0 +1,160 @@
+"""Thin Python binding of the C ABI: the same calls, with torch for device memory and streams.
+
+Every step of the evolution runs in ``libgpeps.so``; this module only packs
+arguments, allocates the two caller-owned device buffers as torch tensors and
+orders the library's stream against torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import GPEPS_C128, GPEPS_MIXED_C64, GraphC, check
+
+DTYPES = {"c128": GPEPS_C128, "mixed": GPEPS_MIXED_C64}
+
+
+class GPEPS:
+    """A batch of graph PEPS, one per graph in ``graphs`` (list of ``(n_qubits, edges)``).
+
+    ``dtype``: ``"c128"`` (FP64 everywhere) or ``"mixed"`` (complex64 tensors,
+    FP32 Gram/contract products, FP64 bond eigensolver and lambda).
+    ``colours``: optional list (one int8 array per graph) of edge colour classes.
+    """
+
+    def __init__(self, graphs, D, dtype="mixed", device="cuda:0", colours=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("GPEPS needs a CUDA device; there is no CPU path")
+        self.lib = _abi.load()
+        self.device = torch.device(device)
+        self.D = int(D)
+        self.dtype = dtype
+        self.n_instances = len(graphs)
+        self._keep = []
+        arr = (GraphC * self.n_instances)()
+        for k, (n, edges) in enumerate(graphs):
+            e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+            self._keep.append(e)
+            arr[k].n_qubits = int(n)
+            arr[k].n_edges = int(e.shape[0])
+            arr[k].edges = e.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            if colours is not None and colours[k] is not None:
+                c = np.ascontiguousarray(np.asarray(colours[k], dtype=np.int8))
+                self._keep.append(c)
+                arr[k].colour = c.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
+            else:
+                arr[k].colour = None
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.Stream(self.device)
+        h = ctypes.c_void_p()
+        check(self.lib.gpeps_create(ctypes.cast(arr, ctypes.c_void_p), self.n_instances, self.D,
+                                    DTYPES[dtype], ctypes.c_void_p(self.stream.cuda_stream),
+                                    ctypes.byref(h)), "gpeps_create")
+        self.h = h
+        sb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+        check(self.lib.gpeps_query_workspace(self.h, ctypes.byref(sb), ctypes.byref(wb)), "gpeps_query_workspace")
+        self.state_bytes, self.work_bytes = sb.value, wb.value
+        self.state = torch.empty(self.state_bytes, dtype=torch.uint8, device=self.device)
+        self.work = torch.empty(self.work_bytes, dtype=torch.uint8, device=self.device)
+        check(self.lib.gpeps_bind(self.h, ctypes.c_void_p(self.state.data_ptr()),
+                                  ctypes.c_void_p(self.work.data_ptr())), "gpeps_bind")
+        q, e = ctypes.c_int64(), ctypes.c_int64()
+        check(self.lib.gpeps_sizes(self.h, ctypes.byref(q), ctypes.byref(e)), "gpeps_sizes")
+        self.total_qubits, self.total_edges = q.value, e.value
+        nc = ctypes.c_int32()
+        check(self.lib.gpeps_n_colours(self.h, ctypes.byref(nc)), "gpeps_n_colours")
+        self.n_colours = nc.value
+        self.bonds_per_step = self.total_edges
+
+    # -------------------------------------------------------------- stream order
+    def _after_torch(self):
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def _before_torch(self):
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def _theta(self, theta, per_qubit):
+        t = torch.as_tensor(theta, dtype=torch.float64)
+        if t.device != self.device:
+            t = t.to(self.device)
+        t = t.contiguous()
+        n = self.total_qubits if per_qubit else self.n_instances
+        if t.numel() != n:
+            raise ValueError(f"theta must have {n} entries (per_qubit={per_qubit})")
+        return t
+
+    # -------------------------------------------------------------- the C calls
+    def reset(self):
+        self._after_torch()
+        check(self.lib.gpeps_reset(self.h), "gpeps_reset")
+
+    def kick(self, theta, per_qubit=False):
+        t = self._theta(theta, per_qubit)
+        self._after_torch()
+        check(self.lib.gpeps_kick(self.h, ctypes.c_void_p(t.data_ptr()), int(bool(per_qubit))), "gpeps_kick")
+        t.record_stream(self.stream)
+
+    def zz_layer(self, colour):
+        check(self.lib.gpeps_zz_layer(self.h, int(colour)), "gpeps_zz_layer")
+
+    def zz_layer_profiled(self, colour):
+        """Run colour class ``colour`` with events around its three launches; returns ms[3]
+        (Gram partials, bond eigenproblems, larger-end update)."""
+        ms = (ctypes.c_float * 3)()
+        check(self.lib.gpeps_zz_layer_profiled(self.h, int(colour), ms), "gpeps_zz_layer_profiled")
+        return [float(x) for x in ms]
+
+    def expect_z(self):
+        """Return ``(z[total_qubits], mean[n_instances])`` as float64 CUDA tensors."""
+        z = torch.empty(self.total_qubits, dtype=torch.float64, device=self.device)
+        m = torch.empty(self.n_instances, dtype=torch.float64, device=self.device)
+        self._after_torch()
+        check(self.lib.gpeps_expect_z(self.h, ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(m.data_ptr())),
+              "gpeps_expect_z")
+        self._before_torch()
+        return z, m
+
+    def step(self, n_steps, theta, per_qubit=False, out=None):
+        """Run ``n_steps`` Trotter steps; returns the mean <Z> per step and instance."""
+        t = self._theta(theta, per_qubit)
+        if out is None:
+            out = torch.empty((n_steps, self.n_instances), dtype=torch.float64, device=self.device)
+        self._after_torch()
+        check(self.lib.gpeps_step(self.h, int(n_steps), ctypes.c_void_p(t.data_ptr()), int(bool(per_qubit)),
+                                  ctypes.c_void_p(out.data_ptr())), "gpeps_step")
+        self._before_torch()
+        self._last_theta = t  # the captured graph reads this buffer
+        return out
+
+    def status(self):
+        f = ctypes.c_int32()
+        check(self.lib.gpeps_status(self.h, ctypes.byref(f)), "gpeps_status")
+        return f.value
+
+    def lambdas(self, instance, edge):
+        out = (ctypes.c_double * self.D)()
+        check(self.lib.gpeps_lambda(self.h, int(instance), int(edge), out), "gpeps_lambda")
+        return np.array(out[:], dtype=np.float64)
+
+    def sweeps(self):
+        s, b = ctypes.c_int64(), ctypes.c_int64()
+        check(self.lib.gpeps_sweeps(self.h, ctypes.byref(s), ctypes.byref(b)), "gpeps_sweeps")
+        return s.value, b.value
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            self.stream.synchronize()
+            self.lib.gpeps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,63 @@
+"""Write the oracle's expected values for the larger workloads (calls only ``oracle/``).
+
+    python tests/golden/make_oracle_golden.py eagle_sweep16_d16
+    python tests/golden/make_oracle_golden.py heavyhex_mix_d32
+
+Each run writes ``tests/golden/oracle_<workload>.json``: the mean <Z> of every
+instance after every Trotter step, the per-qubit <Z> after a few sampled steps
+and the sorted lambda spectra of a few sampled edges.  The oracle is the plain
+FP64 simple update of ``oracle/su.py`` (greedy colouring, same inputs as the
+GPU tests from ``workloads``).
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import numpy as np  # noqa: E402
+
+from oracle.su import GPEPS  # noqa: E402
+from workloads import kick_angles, workload  # noqa: E402
+
+SAMPLE_STEPS = {"eagle_sweep16_d16": [1, 4, 5, 10, 20], "heavyhex_mix_d32": [1, 5, 6, 10, 25, 50]}
+
+
+def sampled_edges(n_edges, k=8):
+    return sorted(set(np.linspace(0, n_edges - 1, k).astype(int).tolist()))
+
+
+def run(name, steps=None):
+    w = workload(name)
+    steps = steps or w.steps
+    thetas = kick_angles(w)
+    sample = [s for s in SAMPLE_STEPS.get(name, [steps]) if s <= steps]
+    out = {"workload": name, "D": w.D, "steps": steps, "instances": []}
+    t0 = time.time()
+    for k, ((n, edges), th) in enumerate(zip(w.graphs(), thetas)):
+        peps = GPEPS(n, edges, w.D)
+        inst = {"n_qubits": int(n), "theta": float(th[0]) if w.per_qubit_seed is None else None,
+                "mean_z": [], "z": {}, "lambda": {}}
+        ed = sampled_edges(len(edges))
+        for t in range(1, steps + 1):
+            peps.step(th)
+            z = peps.expect_z()
+            inst["mean_z"].append(float(z.mean()))
+            if t in sample:
+                inst["z"][str(t)] = [float(v) for v in z]
+                lam = peps.lambdas()
+                inst["lambda"][str(t)] = {str(e): [float(v) for v in lam[e]] for e in ed}
+            print(f"{name} instance {k} step {t} mean {z.mean():.12f} ({time.time() - t0:.0f}s)", flush=True)
+        out["instances"].append(inst)
+    path = os.path.join(HERE, f"oracle_{name}.json")
+    with open(path, "w") as f:
+        json.dump(out, f)
+    print("wrote", path)
+
+
+if __name__ == "__main__":
+    run(sys.argv[1], int(sys.argv[2]) if len(sys.argv) > 2 else None)

@@ -1,0 +1,212 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle and the exact pins.
+
+Tolerances: |d<Z>| <= 1e-10 for the complex128 path and <= 1e-4 for the mixed
+path (complex64 tensors, FP64 bond eigensolver).  lambda spectra: the GPU
+obtains Schmidt values as square roots of eigenvalues of a Gram-type matrix,
+so a value is resolved only down to ~sqrt(eps) of the largest: entries are
+compared to 1e-6 (c128) / 2e-3 (mixed) absolute, and to 1e-9 (c128) where the
+oracle's value exceeds 1e-3.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import statevector as sv
+from oracle import su
+from oracle.lightcone import lightcone_z
+from workloads import EAGLE, OSPREY, heavy_hex, induced_subgraph, kick_angles, workload
+
+from ._gpu_util import run_layers, run_step, split
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-10, "mixed": 1e-4}
+M127, E127 = heavy_hex(*EAGLE)
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def oracle_run(n, e, D, theta, steps):
+    peps = su.GPEPS(n, e, D)
+    zs = []
+    for _ in range(steps):
+        peps.step(theta)
+        zs.append(peps.expect_z())
+    return np.array(zs), peps
+
+
+def lam_check(gpu_lam, orc_lam, dtype):
+    d = np.abs(gpu_lam - orc_lam)
+    assert d.max() < (1e-6 if dtype == "c128" else 2e-3), d.max()
+    if dtype == "c128":
+        big = orc_lam > 1e-3
+        assert d[big].max() < 1e-9 if big.any() else True
+
+
+@pytest.mark.parametrize("dtype", ["c128", "mixed"])
+def test_eagle_d4_matches_oracle(dtype):
+    """127 qubits, D=4, theta=0.6, 5 steps: per-qubit <Z> after every step and lambda."""
+    zg, mg, g = run_layers([(M127, E127)], 4, dtype, [0.6], 5)
+    zo, peps = oracle_run(M127, E127, 4, 0.6, 5)
+    assert np.abs(zg - zo).max() < TOL[dtype]
+    assert np.abs(mg[:, 0] - zo.mean(axis=1)).max() < TOL[dtype]
+    lam = np.array([g.lambdas(0, e) for e in range(len(E127))])
+    lam_check(lam, peps.lambdas(), dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "mixed"])
+def test_tree_fragment_exact(dtype):
+    """16-qubit tree, D = 2^n: the GPU result equals the brute-force state vector."""
+    m, e, _ = induced_subgraph(E127, range(16))
+    zg, _, _ = run_layers([(m, e)], 32, dtype, [0.6], 5)
+    ref = sv.kicked_ising_z(m, e, 0.6, 5)
+    assert np.abs(zg - ref).max() < TOL[dtype]
+
+
+def test_full_lattice_lightcone_exact():
+    """127 qubits, D=16, 4 steps: every qubit equals its exact light-cone value."""
+    theta = 0.6
+    zg, _, _ = run_layers([(M127, E127)], 16, "c128", [theta], 4)
+    for n in (1, 2, 3, 4):
+        ref = np.array([lightcone_z(M127, E127, theta, q, n) for q in range(M127)])
+        assert np.abs(zg[n - 1] - ref).max() < 1e-10
+
+
+@pytest.mark.parametrize("dtype", ["c128", "mixed"])
+def test_invariants(dtype):
+    for theta, f in ((0.0, lambda n: 1.0), (math.pi, lambda n: (-1.0) ** n)):
+        zg, _, _ = run_layers([(M127, E127)], 4, dtype, [theta], 3)
+        for n in range(3):
+            assert np.abs(zg[n] - f(n + 1)).max() < TOL[dtype]
+    zg, _, _ = run_layers([(M127, E127)], 16, dtype, [math.pi / 2], 4)
+    assert np.abs(zg).max() < TOL[dtype]
+
+
+@pytest.mark.parametrize("D", [1, 2, 5, 7])
+def test_ragged_bond_dimensions(D):
+    zg, _, g = run_layers([(M127, E127)], D, "c128", [0.9], 4)
+    zo, peps = oracle_run(M127, E127, D, 0.9, 4)
+    assert np.abs(zg - zo).max() < 1e-10
+    lam = np.array([g.lambdas(0, e) for e in range(len(E127))])
+    lam_check(lam, peps.lambdas(), "c128")
+
+
+def test_small_graphs():
+    """Isolated qubit (kick only: <Z> = cos(n theta)), a coupled pair (cos, cos^2), a star."""
+    th = 0.77
+    zg, _, _ = run_layers([(1, np.zeros((0, 2), int))], 4, "c128", [th], 3)
+    assert np.allclose(zg[:, 0], [math.cos(th), math.cos(2 * th), math.cos(3 * th)], atol=1e-12)
+    zg, _, _ = run_layers([(2, [[0, 1]])], 4, "c128", [th], 2)
+    assert abs(zg[0, 0] - math.cos(th)) < 1e-12 and abs(zg[1, 0] - math.cos(th) ** 2) < 1e-12
+    star = (4, [[0, 1], [0, 2], [0, 3]])
+    zg, _, _ = run_layers([star], 8, "c128", [th], 3)
+    ref = sv.kicked_ising_z(4, np.array(star[1]), th, 3)
+    assert np.abs(zg - ref).max() < 1e-10
+
+
+def test_per_qubit_angles_and_batch():
+    """Per-qubit kick angles (seeded, as in the gradient workload) on a batch of two lattices."""
+    w = workload("eagle_grad_d16")
+    th = kick_angles(w)[0]
+    m2, e2 = heavy_hex(3, 11)
+    th2 = np.linspace(0.4, 1.2, m2)
+    graphs = [(M127, E127), (m2, e2)]
+    zg, mg, _ = run_layers(graphs, 8, "c128", np.concatenate([th, th2]), 4, per_qubit=True)
+    z1, z2 = split(zg, graphs)
+    o1, _ = oracle_run(M127, E127, 8, th, 4)
+    o2, _ = oracle_run(m2, e2, 8, th2, 4)
+    assert np.abs(z1 - o1).max() < 1e-10 and np.abs(z2 - o2).max() < 1e-10
+    assert np.abs(mg[:, 1] - o2.mean(axis=1)).max() < 1e-10
+
+
+def test_explicit_colouring_and_pending_kick_readout():
+    from oracle.graph import greedy_colouring
+    col = greedy_colouring(E127)
+    za, _, _ = run_layers([(M127, E127)], 4, "c128", [0.5], 2)
+    zb, _, _ = run_layers([(M127, E127)], 4, "c128", [0.5], 2, colours=[col])
+    assert np.array_equal(za, zb)
+    # a kick still pending is applied on the fly by the readout
+    from ._gpu_util import gpu_lib
+    import torch
+    g = gpu_lib()([(M127, E127)], 4, dtype="c128")
+    g.reset()
+    g.kick(torch.tensor([0.3], dtype=torch.float64, device="cuda"))
+    z, _ = g.expect_z()
+    assert np.abs(z.cpu().numpy() - math.cos(0.3)).max() < 1e-14
+
+
+@pytest.mark.parametrize("dtype", ["c128", "mixed"])
+def test_graph_replay_equals_explicit_calls(dtype):
+    _, mg, _ = run_layers([(M127, E127)], 8, dtype, [0.7], 6)
+    ms, _ = run_step([(M127, E127)], 8, dtype, [0.7], 6)
+    assert np.array_equal(mg, ms)
+
+
+def _golden(name):
+    path = os.path.join(GOLD, f"oracle_{name}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not generated")
+    return json.load(open(path))
+
+
+def _is_clifford_tie(theta, step, D):
+    """theta = pi/2 is Clifford: every Schmidt spectrum is flat, so once 2^step > D the
+    truncation cut falls inside a degenerate multiplet and several results are correct."""
+    return abs(theta - math.pi / 2) < 1e-12 and 2 ** step > D
+
+
+@pytest.mark.parametrize("dtype", ["mixed", "c128"])
+def test_theta_sweep_16_instances(dtype):
+    """16 instances, theta evenly spaced in [0, pi/2], D=16, 20 steps, one batch."""
+    gold = _golden("eagle_sweep16_d16")
+    w = workload("eagle_sweep16_d16")
+    graphs = w.graphs()
+    theta = [th[0] for th in kick_angles(w)]
+    means, g = run_step(graphs, w.D, dtype, theta, w.steps)
+    ref = np.array([inst["mean_z"] for inst in gold["instances"]]).T
+    for k in range(len(theta)):
+        for t in range(w.steps):
+            if _is_clifford_tie(theta[k], t + 1, w.D):
+                # a correct truncation of a flat spectrum: stays small, not pinned
+                assert abs(means[t, k]) < 0.05
+                continue
+            assert abs(means[t, k] - ref[t, k]) < TOL[dtype], (k, t)
+    z, _ = g.expect_z()
+    zi = split(z.cpu().numpy(), graphs)
+    for k, inst in enumerate(gold["instances"]):
+        if _is_clifford_tie(theta[k], w.steps, w.D):
+            continue
+        assert np.abs(zi[k] - np.array(inst["z"][str(w.steps)])).max() < TOL[dtype]
+        for e, lam in inst["lambda"][str(w.steps)].items():
+            lam_check(g.lambdas(k, int(e)), np.array(lam), dtype)
+
+
+@pytest.mark.parametrize("dtype", ["mixed", "c128"])
+def test_heavyhex_mix_d32_full_size(dtype):
+    """127 + 433 + 1121 qubits in one batch, D=32, theta=0.7, 50 steps (the benchmark workload)."""
+    gold = _golden("heavyhex_mix_d32")
+    w = workload("heavyhex_mix_d32")
+    graphs = w.graphs()
+    theta = [0.7] * 3
+    from ._gpu_util import gpu_lib
+    import torch
+    g = gpu_lib()(graphs, w.D, dtype=dtype)
+    g.reset()
+    th = torch.tensor(theta, dtype=torch.float64, device="cuda")
+    samples = sorted(int(s) for s in gold["instances"][0]["z"])
+    done, means = 0, []
+    for s in samples:
+        means.append(g.step(s - done, th).cpu().numpy())
+        done = s
+        z, _ = g.expect_z()
+        zi = split(z.cpu().numpy(), graphs)
+        for k, inst in enumerate(gold["instances"]):
+            assert np.abs(zi[k] - np.array(inst["z"][str(s)])).max() < TOL[dtype], (s, k)
+            for e, lam in inst["lambda"][str(s)].items():
+                lam_check(g.lambdas(k, int(e)), np.array(lam), dtype)
+    means = np.concatenate(means)
+    ref = np.array([inst["mean_z"] for inst in gold["instances"]]).T
+    assert np.abs(means - ref).max() < TOL[dtype]
+    assert g.status() == 0
