@@ -108,18 +108,23 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ algorithmic counts
-def bond_kernel_flops(w, sweeps_per_bond):
-    """FP64 flops of the bond-eigenproblem launch per bond (n = 2 D for the 2D x 2D bond matrix):
-    rho formation 2 (n D^2 + n^2 D) complex MACs, Jacobi sweeps of (n-1) rounds with
-    n/2 (n/2 + 1)/2 two-sided 2x2 block rotations (72 flops) and n^2/2 eigenvector
-    rotations (18 flops), and the Y matrices 2 D^2 n complex MACs; 8 flops per complex MAC."""
+def bond_kernel_flops(w, sweeps64, sweeps32):
+    """(FP64, FP32) flops of the bond-eigenproblem launch per bond, n = 2D (8 flops per
+    complex MAC): rho formation 2 (n D^2 + n(n+1)/2 D) MACs; Cholesky-QR of the FP32
+    eigenvectors n^3/2 + n^3/6 + n^3/2 MACs; rho' = V^dagger rho V 3 n^3/2 MACs; Y matrices
+    2 D^2 n MACs; a Jacobi sweep is (n-1) rounds of n/2 (n/2+1)/2 two-sided 2x2 block
+    rotations (72 flops) and n^2/2 eigenvector rotations (18 flops), counted for every
+    pair (an upper bound: converged pairs are skipped)."""
     D = w.D
     n = 2 * D
     m = n // 2
-    form = 2 * (n * D * D + n * n * D) * 8
+    mac = 8
+    form = 2 * (n * D * D + n * (n + 1) // 2 * D) * mac
+    orth = (n ** 3 // 2 + n ** 3 // 6 + n ** 3 // 2) * mac
+    rot = (3 * n ** 3 // 2) * mac
+    ymat = 2 * D * D * n * mac
     sweep = (n - 1) * (m * (m + 1) // 2 * 72 + n * m * 18)
-    ymat = 2 * D * D * n * 8
-    return form + sweeps_per_bond * sweep + ymat
+    return form + orth + rot + ymat + sweeps64 * sweep, sweeps32 * sweep
 
 
 def step_bytes(graphs, D, elt):
@@ -216,7 +221,8 @@ def run_gpeps(args, rank, world, local_rank):
 
     # per-kernel durations of profiled steps right after the timed region
     prof = {"gram": [], "bond": [], "update": []}
-    s0, b0 = g.sweeps()
+    s0, q0, b0 = g.sweeps()
+    c0 = g.bond_phase_cycles()
     for _ in range(args.profile_steps):
         g.kick(th)
         for c in range(g.n_colours):
@@ -224,18 +230,26 @@ def run_gpeps(args, rank, world, local_rank):
             for k, v in zip(("gram", "bond", "update"), t3):
                 prof[k].append(v)
         g.expect_z()
-    s1, b1 = g.sweeps()
+    s1, q1, b1 = g.sweeps()
+    c1 = g.bond_phase_cycles()
+    phase_names = ["rho", "fp32_jacobi", "fp64_orthonormalise", "rotate_and_fp32_levels", "fp64_jacobi",
+                   "epilogue"]
+    phase_cycles = {k: (b - a) / max(b1 - b0, 1) for k, a, b in zip(phase_names, c0, c1)}
     sweeps_per_bond = (s1 - s0) / max(b1 - b0, 1)
+    sweeps32_per_bond = (q1 - q0) / max(b1 - b0, 1)
     layer_ms = {k: sum(v) / max(args.profile_steps, 1) for k, v in prof.items()}   # per step, all colours
     bond_launch_ms = sum(prof["bond"]) / max(len(prof["bond"]), 1)
     bonds_per_launch = bonds_step / g.n_colours
-    flops_launch = bond_kernel_flops(w, sweeps_per_bond) * bonds_per_launch
+    f64, f32 = bond_kernel_flops(w, sweeps_per_bond, sweeps32_per_bond)
+    flops_launch = f64 * bonds_per_launch
     achieved = flops_launch / (bond_launch_ms * 1e-3) / 1e9
     roofline = {"kernel": "bond_kernel (2D x 2D bond eigenproblem, FP64 Jacobi)", "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
                 "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
                 "peak_source": "nominal FP64 1.25 TFLOP/s of the GB300 (no FP64 figure in MEASURED_PEAKS.json)",
-                "sweeps_per_bond": sweeps_per_bond, "launch_ms": bond_launch_ms,
+                "fp64_sweeps_per_bond": sweeps_per_bond, "fp32_sweeps_per_bond": sweeps32_per_bond,
+                "fp32_gflops": f32 * bonds_per_launch / (bond_launch_ms * 1e-3) / 1e9,
+                "launch_ms": bond_launch_ms, "cycles_per_bond_by_phase": phase_cycles,
                 "per_step_ms": layer_ms}
     elt = 8 if args.dtype == "mixed" else 16
     sb = step_bytes(graphs, w.D, elt)

@@ -121,6 +121,7 @@ int gpeps_kick(gpeps_handle* h, const double* theta, int32_t per_qubit);
  * the other legs, reduce both site tensors, apply the gate, solve the 2D x 2D
  * bond eigenproblem, keep the D largest Schmidt values, renormalise lambda to
  * unit 2-norm and strip lambda^-1 (pseudo-inverse below 1e-13 max(lambda)).
+ * Every Schmidt value with a positive squared value is kept (up to D).
  * Errors: GPEPS_EINVAL for colour outside [0, n_colours).
  */
 int gpeps_zz_layer(gpeps_handle* h, int32_t colour);
@@ -164,9 +165,18 @@ int gpeps_lambda(gpeps_handle* h, int32_t instance, int32_t edge, double* out);
 /* Totals of the batch: qubits, edges, bond updates per Trotter step. */
 int gpeps_sizes(const gpeps_handle* h, int64_t* total_qubits, int64_t* total_edges);
 
-/* Counters of the device-side work of the last synchronised layer calls:
- * Jacobi sweeps summed over bonds since the last reset (int64). Synchronises. */
-int gpeps_sweeps(gpeps_handle* h, int64_t* total_sweeps, int64_t* total_bonds);
+/* Work counters since the last gpeps_reset, summed over bonds: FP64 Jacobi
+ * sweeps, FP32 warm-start sweeps, and bond updates launched.  Host pointers
+ * (any may be NULL); synchronises. */
+int gpeps_sweeps(gpeps_handle* h, int64_t* sweeps64, int64_t* sweeps32, int64_t* total_bonds);
+
+/* SM cycles spent in the phases of the bond-eigenproblem kernel since the last
+ * gpeps_reset, summed over bonds (clock64 of one thread per CTA), host
+ * int64[6]: [0] reduced density matrix, [1] first FP32 Jacobi level, [2] FP64
+ * re-orthonormalisation of the FP32 eigenvectors, [3] V^dagger rho V and the
+ * further FP32 levels on small-eigenvalue blocks, [4] FP64 Jacobi sweeps,
+ * [5] truncation, Y matrices and the smaller end.  Synchronises. */
+int gpeps_bond_phase_cycles(gpeps_handle* h, int64_t* cycles);
 
 int gpeps_destroy(gpeps_handle* h);
 const char* gpeps_error_string(int status);

@@ -26,7 +26,8 @@ SIGNATURES = {
     "gpeps_status": (c_int, [c_void_p, POINTER(c_int32)]),
     "gpeps_lambda": (c_int, [c_void_p, c_int32, c_int32, POINTER(c_double)]),
     "gpeps_sizes": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
-    "gpeps_sweeps": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
+    "gpeps_sweeps": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
+    "gpeps_bond_phase_cycles": (c_int, [c_void_p, POINTER(c_int64)]),
     "gpeps_destroy": (c_int, [c_void_p]),
     "gpeps_error_string": (c_char_p, [c_int]),
     "gpeps_last_cuda_error": (c_char_p, []),

@@ -72,7 +72,7 @@ struct gpeps_handle {
   // buffer layout (bytes)
   size_t state_bytes = 0, work_bytes = 0;
   size_t s_lam = 0, s_gamma = 0;
-  size_t w_pending = 0, w_flags = 0, w_sweeps = 0, w_z = 0, w_mean = 0, w_sites = 0, w_inst_site0 = 0,
+  size_t w_pending = 0, w_flags = 0, w_sweeps = 0, w_cycles = 0, w_z = 0, w_mean = 0, w_sites = 0, w_inst_site0 = 0,
          w_site_inst = 0, w_site_off = 0, w_partials = 0, w_Y = 0, w_theta_a = 0;
   char* d_state = nullptr;
   char* d_work = nullptr;
@@ -88,6 +88,7 @@ struct gpeps_handle {
   double* pending() const { return reinterpret_cast<double*>(d_work + w_pending); }
   int* flags() const { return reinterpret_cast<int*>(d_work + w_flags); }
   unsigned long long* sweeps() const { return reinterpret_cast<unsigned long long*>(d_work + w_sweeps); }
+  unsigned long long* cycles() const { return reinterpret_cast<unsigned long long*>(d_work + w_cycles); }
   double* z() const { return reinterpret_cast<double*>(d_work + w_z); }
   double* mean() const { return reinterpret_cast<double*>(d_work + w_mean); }
   template <typename P>
@@ -224,7 +225,7 @@ int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr) {
   GP_CUDA(Launch<T>::gram(tiles, nt, bonds, h->gamma(), h->lam(), h->pending(), partials, h->D, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[1], h->stream));
   GP_CUDA(Launch<T>::bond(bonds, nbd, partials, h->gamma(), h->lam(), h->pending(), Y, theta_a, h->flags(),
-                          h->sweeps(), h->D, h->jp, h->stream));
+                          h->sweeps(), h->cycles(), h->D, h->jp, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[2], h->stream));
   GP_CUDA(Launch<T>::update(tiles, nt, bonds, h->gamma(), h->lam(), Y, theta_a, h->D, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[3], h->stream));
@@ -371,9 +372,15 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   // Jacobi thresholds: the bond matrix carries FP64 rounding (C128) or the
   // FP32 rounding of its Gram inputs (mixed); eigenvalues below that level are noise.
   h->jp.tol = 1e-15;
-  h->jp.floor_rel = 1e-14;
-  h->jp.ev_cut = dtype == GPEPS_C128 ? 1e-14 : 1e-7;
+  // FP64 sweeps stop at |a_pq| <= floor_rel * trace: 2 eps for complex128 (the
+  // entries of rho carry ~eps * trace rounding), coarser for the mixed path
+  // whose rho carries FP32 rounding of its inputs
+  h->jp.floor_rel = dtype == GPEPS_C128 ? 4.4e-16 : 2e-15;
+  h->jp.tol32 = 1e-6;
+  h->jp.floor32 = 2e-7;
+  h->jp.ev_cut = 0.0;
   h->jp.max_sweeps = 40;
+  h->jp.max_sweeps32 = 20;
   // layouts
   size_t s = 0;
   h->s_lam = s;
@@ -389,7 +396,8 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   };
   h->w_pending = carve(h->total_sites * sizeof(double));
   h->w_flags = carve(sizeof(int) * 4);
-  h->w_sweeps = carve(sizeof(unsigned long long));
+  h->w_sweeps = carve(4 * sizeof(unsigned long long));
+  h->w_cycles = carve(kPhases * sizeof(unsigned long long));
   h->w_z = carve(h->total_sites * sizeof(double));
   h->w_mean = carve(n_instances * sizeof(double));
   h->w_sites = carve(h->total_sites * sizeof(SiteDesc));
@@ -453,7 +461,8 @@ int gpeps_reset(gpeps_handle* h) {
                                              (int)h->total_sites, h->pending(), h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "reset");
   GP_CUDA(cudaMemsetAsync(h->d_work + h->w_flags, 0, sizeof(int) * 4, h->stream));
-  GP_CUDA(cudaMemsetAsync(h->d_work + h->w_sweeps, 0, sizeof(unsigned long long), h->stream));
+  GP_CUDA(cudaMemsetAsync(h->d_work + h->w_sweeps, 0, 4 * sizeof(unsigned long long), h->stream));
+  GP_CUDA(cudaMemsetAsync(h->d_work + h->w_cycles, 0, kPhases * sizeof(unsigned long long), h->stream));
   h->bonds_since_reset = 0;
   return GPEPS_OK;
 }
@@ -573,13 +582,23 @@ int gpeps_sizes(const gpeps_handle* h, int64_t* total_qubits, int64_t* total_edg
   return GPEPS_OK;
 }
 
-int gpeps_sweeps(gpeps_handle* h, int64_t* total_sweeps, int64_t* total_bonds) {
+int gpeps_sweeps(gpeps_handle* h, int64_t* sweeps64, int64_t* sweeps32, int64_t* total_bonds) {
   if (!h || !h->bound) return GPEPS_EINVAL;
   GP_CUDA(cudaStreamSynchronize(h->stream));
-  unsigned long long s = 0;
-  GP_CUDA(cudaMemcpy(&s, h->sweeps(), sizeof(s), cudaMemcpyDeviceToHost));
-  if (total_sweeps) *total_sweeps = (int64_t)s;
+  unsigned long long s[2] = {0, 0};
+  GP_CUDA(cudaMemcpy(s, h->sweeps(), sizeof(s), cudaMemcpyDeviceToHost));
+  if (sweeps64) *sweeps64 = (int64_t)s[0];
+  if (sweeps32) *sweeps32 = (int64_t)s[1];
   if (total_bonds) *total_bonds = h->bonds_since_reset;
+  return GPEPS_OK;
+}
+
+int gpeps_bond_phase_cycles(gpeps_handle* h, int64_t* cycles) {
+  if (!h || !h->bound || !cycles) return GPEPS_EINVAL;
+  GP_CUDA(cudaStreamSynchronize(h->stream));
+  unsigned long long c[kPhases];
+  GP_CUDA(cudaMemcpy(c, h->cycles(), sizeof(c), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < kPhases; ++i) cycles[i] = (int64_t)c[i];
   return GPEPS_OK;
 }
 

@@ -14,6 +14,10 @@ constexpr int kMaxD = 32;          // bond dimension limit of this build
 constexpr int kTileRows = 64;      // rows of a big-side tile (Gram and update launches)
 constexpr int kThreads = 256;      // threads of every CTA
 constexpr double kLambdaCut = 1e-13;  // pseudo-inverse threshold relative to max(lambda)
+constexpr int kPhases = 6;            // phases of the bond kernel with SM-cycle counters
+constexpr int kExtraLevels = 2;       // FP32 warm-start levels after the first (small-eigenvalue blocks)
+constexpr double kLevelRatio = 1e-5;  // a level takes the diagonals below this fraction of the last scale
+constexpr double kNoiseRel = 1e-15;   // ... and above this fraction of the trace (FP64 rounding noise)
 
 // One end of a bond seen as a matrix: row r = (r1, r2) runs over the other legs,
 // column (s, k) over the physical index and the bond leg.
@@ -56,11 +60,13 @@ struct SiteDesc {
 };
 
 struct JacobiParams {
-  double tol;        // relative off-diagonal threshold |a_pq| <= tol sqrt(a_pp a_qq)
-  double floor_rel;  // absolute threshold |a_pq| <= floor_rel * trace
+  double tol;        // FP64 sweeps: relative off-diagonal threshold |a_pq| <= tol sqrt(a_pp a_qq)
+  double floor_rel;  // FP64 sweeps: absolute threshold |a_pq| <= floor_rel * trace
+  double tol32;      // FP32 warm-start sweeps: the same two thresholds
+  double floor32;
   double ev_cut;     // eigenvalues <= ev_cut * max eigenvalue are dropped (lambda = 0)
-  int max_sweeps;
-  int pad;
+  int max_sweeps;    // FP64 cap (hitting it sets GPEPS_FLAG_NOCONV)
+  int max_sweeps32;  // FP32 cap (hitting it only costs FP64 sweeps)
 };
 
 // Launchers (su_kernels.cu).  T = float for GPEPS_MIXED_C64, double for GPEPS_C128.
@@ -75,7 +81,8 @@ struct Launch {
                           const double* lam, const double* pending, void* partials, int D, cudaStream_t st);
   static cudaError_t bond(const BondDesc* bonds, int n_bonds, const void* partials, void* gamma, double* lam,
                           double* pending, void* Y, double* theta_a, int* flags,
-                          unsigned long long* sweeps, int D, JacobiParams jp, cudaStream_t st);
+                          unsigned long long* sweeps, unsigned long long* cycles, int D, JacobiParams jp,
+                          cudaStream_t st);
   static cudaError_t update(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, void* gamma,
                             const double* lam, const void* Y, const double* theta_a, int D, cudaStream_t st);
   static cudaError_t readout(const SiteDesc* sites, int n_sites, const void* gamma, const double* lam,

@@ -165,52 +165,121 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------- bond eigenproblem
+template <typename T>
+__device__ __forceinline__ V2<T> c_mul(V2<T> a, V2<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ V2<T> c_conj(V2<T> a) {
+  return mk<T>(a.x, -a.y);
+}
+template <typename T>
+__device__ __forceinline__ V2<T> c_scale(V2<T> a, T s) {
+  return mk<T>(a.x * s, a.y * s);
+}
+template <typename T>
+__device__ __forceinline__ V2<T> c_add(V2<T> a, V2<T> b) {
+  return mk<T>(a.x + b.x, a.y + b.y);
+}
+template <typename T>
+__device__ __forceinline__ V2<T> c_sub(V2<T> a, V2<T> b) {
+  return mk<T>(a.x - b.x, a.y - b.y);
+}
+
 // Shared-memory layout of bond_kernel for a bond whose small end has nb rows
-// (n = 2 nb): every double2 array first, then doubles, then ints.
+// (n = 2 nb).  Three large regions of complex doubles:
+//   R    [n][n+1]                 the bond matrix rho, later V^dagger rho V
+//   Vr   max(n*n, 2D^2 + n*D)     Gram blocks C_s and H while rho is formed, then V
+//   X    max(n*(n+1), n*D)        F; then the FP32 copies rho32 [n][n+1] and V32 [n][n];
+//                                 then the Gram/Cholesky factor of V; then rho V; then F again
+// followed by the small arrays (rotations of both precisions, eigenvalues, indices).
 struct BondSmem {
-  int n, D;
-  size_t off_F, off_RHO, off_X, off_re, off_lamo, off_ev, off_sv, off_rc, off_rs, off_int, total;
-  __host__ __device__ BondSmem(int D_, int n_) : n(n_), D(D_) {
-    const size_t c16 = 16, c8 = 8;
+  size_t off_R, off_V, off_X, off_re, off_re32, off_lamo, off_ev, off_sv, off_rc, off_rs, off_scal, off_rc32,
+      off_rs32, off_int, total;
+  __host__ __device__ BondSmem(int D, int n) {
     const int m = n / 2;
-    size_t x = (size_t)2 * D * D + (size_t)n * D;
-    if ((size_t)n * n > x) x = (size_t)n * n;
-    off_F = 0;
-    off_RHO = off_F + (size_t)n * D * c16;
-    off_X = off_RHO + (size_t)n * (n + 1) * c16;
-    off_re = off_X + x * c16;
-    off_lamo = off_re + (size_t)m * c16;
-    off_ev = off_lamo + (size_t)D * c8;
-    off_sv = off_ev + (size_t)n * c8;
-    off_rc = off_sv + (size_t)D * c8;
-    off_rs = off_rc + (size_t)m * c8;
-    off_int = off_rs + (size_t)m * c8 + 8 * c8;  // 8 scalar doubles after rs
+    size_t v = (size_t)n * n;
+    if ((size_t)2 * D * D + (size_t)n * D > v) v = (size_t)2 * D * D + (size_t)n * D;
+    size_t x = (size_t)n * (n + 1);
+    if ((size_t)n * D > x) x = (size_t)n * D;
+    off_R = 0;
+    off_V = off_R + (size_t)n * (n + 1) * 16;
+    off_X = off_V + v * 16;
+    off_re = off_X + x * 16;
+    off_re32 = off_re + (size_t)m * 16;
+    off_lamo = off_re32 + (size_t)((m + 1) / 2) * 16;
+    off_ev = off_lamo + (size_t)D * 8;
+    off_sv = off_ev + (size_t)n * 8;
+    off_rc = off_sv + (size_t)D * 8;
+    off_rs = off_rc + (size_t)m * 8;
+    off_scal = off_rs + (size_t)m * 8;
+    off_rc32 = off_scal + 8 * 8;
+    off_rs32 = off_rc32 + (size_t)((m + 1) / 2) * 8;
+    off_int = off_rs32 + (size_t)((m + 1) / 2) * 8;
     total = off_int + (size_t)(n + 2 * m + 8) * 4;
   }
 };
 
 size_t bond_smem_bytes(int D, int n) { return BondSmem(D, n).total; }
 
+// Rotation of the pair (p, q) (Golub & Van Loan, Alg. 8.4.1, sym.schur2, after
+// the diagonal phase that makes a_pq real): J = [[c, s], [-s e, c e]],
+// e = conj(a_pq)/|a_pq|.  Returns false (identity) when the pair is converged.
+__device__ __forceinline__ bool rotation(float app, float aqq, float2 apq, float tol, float floor_abs, float& c,
+                                         float& s, float2& e) {
+  const float g2 = apq.x * apq.x + apq.y * apq.y;
+  if (!(g2 > floor_abs * floor_abs && g2 > tol * tol * fabsf(app * aqq))) return false;
+  const float ig = rsqrtf(g2);
+  const float zeta = (aqq - app) * (0.5f * ig);
+  const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  c = rsqrtf(1.f + t * t);
+  s = t * c;
+  e = make_float2(apq.x * ig, -apq.y * ig);
+  return true;
+}
+// FP64 version: the angle is taken in FP32 (accurate to ~1e-7, enough for the
+// sweep to shrink a_pq by that factor) and (c, s) and e are normalised in FP64
+// by two Newton steps, so J is unitary to FP64 rounding without FP64 divides
+// or square roots.
+__device__ __forceinline__ bool rotation(double app, double aqq, double2 apq, double tol, double floor_abs,
+                                         double& c, double& s, double2& e) {
+  const double g2 = apq.x * apq.x + apq.y * apq.y;
+  if (!(g2 > floor_abs * floor_abs && g2 > tol * tol * fabs(app * aqq))) return false;
+  const float g2f = (float)g2;
+  const float igf = rsqrtf(g2f);
+  const float zeta = (float)(aqq - app) * (0.5f * igf);
+  const float tf = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  const double t = (double)tf;
+  const double u = 1.0 + t * t;
+  double cc = (double)rsqrtf((float)u);
+  cc = cc * (1.5 - 0.5 * u * cc * cc);
+  cc = cc * (1.5 - 0.5 * u * cc * cc);
+  double ig = (double)igf;
+  ig = ig * (1.5 - 0.5 * g2 * ig * ig);
+  ig = ig * (1.5 - 0.5 * g2 * ig * ig);
+  c = cc;
+  s = t * cc;
+  e = make_double2(apq.x * ig, -apq.y * ig);
+  return true;
+}
+
 // Parallel cyclic Jacobi for the Hermitian n x n matrix A (row stride lda) in
-// shared memory, accumulating V (row stride ldv) = product of rotations.  The
-// (n-1) rounds of a sweep use the round-robin pairing, so the n/2 rotations of
-// a round are disjoint and applied together: A <- J^dagger A J block by block
-// (upper blocks computed, lower blocks mirrored), V <- V J.  Rotation of pair
-// (p, q) (Golub & Van Loan, Alg. 8.4.1, sym.schur2, after a diagonal phase that
-// makes a_pq real): J = [[c, s], [-s e, c e]], e = conj(a_pq)/|a_pq|.  A pair is
-// skipped when |a_pq| <= max(tol sqrt(a_pp a_qq), floor).  Returns the sweeps
-// run; max_sweeps + 1 means the cap was hit.
-__device__ int jacobi_hermitian(double2* A, int lda, double2* V, int ldv, int n, const JacobiParams& jp,
-                                double floor_abs, double* rc, double* rs, double2* re, int* rp, int* rq,
-                                int* iflag) {
+// shared memory, accumulating V (row stride ldv) <- V * product of rotations
+// (V is initialised by the caller).  The (n-1) rounds of a sweep use the
+// round-robin pairing, so the n/2 rotations of a round are disjoint and applied
+// together: A <- J^dagger A J on 2x2 blocks (a, b) enumerated circulantly
+// (b = a + d mod m, each unordered pair once; block (b, a) is the mirror),
+// V <- V J.  A pair is skipped when |a_pq| <= max(tol sqrt(a_pp a_qq), floor_abs).
+// With kExact the off-diagonal of a rotated diagonal block is set to zero (the
+// FP32 angle is exact for FP32 arithmetic); the FP64 sweeps keep the computed
+// residual instead.  Returns the sweeps run; max_sweeps + 1 = cap hit.
+template <typename R, bool kExact>
+__device__ int jacobi_hermitian(V2<R>* A, int lda, V2<R>* V, int ldv, int n, R tol, R floor_abs, int max_sweeps,
+                                R* rc, R* rs, V2<R>* re, int* rp, int* rq, int* iflag) {
   const int m = n / 2;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx - (idx / n) * n;
-    V[i * ldv + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-  }
-  __syncthreads();
+  const int nd = m / 2 + 1;  // circulant offsets d = 0..m/2
   int sweep = 0;
-  for (; sweep < jp.max_sweeps; ++sweep) {
+  for (; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) iflag[0] = 0;
     __syncthreads();
     for (int r = 0; r < n - 1; ++r) {
@@ -228,19 +297,9 @@ __device__ int jacobi_hermitian(double2* A, int lda, double2* V, int ldv, int n,
           p = q;
           q = tmp;
         }
-        const double app = A[p * lda + p].x, aqq = A[q * lda + q].x;
-        const double2 apq = A[p * lda + q];
-        const double g = hypot(apq.x, apq.y);
-        double cs = 1.0, sn = 0.0;
-        double2 e = make_double2(1.0, 0.0);
-        if (g > floor_abs && g > jp.tol * sqrt(fabs(app * aqq))) {
-          const double zeta = (aqq - app) / (2.0 * g);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          cs = 1.0 / sqrt(1.0 + t * t);
-          sn = t * cs;
-          e = make_double2(apq.x / g, -apq.y / g);
-          iflag[0] = 1;
-        }
+        R cs = 1, sn = 0;
+        V2<R> e = mk<R>(1, 0);
+        if (rotation(A[p * lda + p].x, A[q * lda + q].x, A[p * lda + q], tol, floor_abs, cs, sn, e)) iflag[0] = 1;
         rp[k] = p;
         rq[k] = q;
         rc[k] = cs;
@@ -248,58 +307,58 @@ __device__ int jacobi_hermitian(double2* A, int lda, double2* V, int ldv, int n,
         re[k] = e;
       }
       __syncthreads();
-      // A <- J^dagger A J on the upper blocks (a <= b), lower blocks mirrored
-      for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-        const int a = idx / m, b = idx - (idx / m) * m;
-        if (a > b) continue;
-        const bool rot_a = rs[a] != 0.0, rot_b = rs[b] != 0.0;
-        if (!rot_a && !rot_b) continue;
+      for (int idx = threadIdx.x; idx < nd * m; idx += blockDim.x) {
+        const int d = idx / m, a = idx - (idx / m) * m;
+        if (2 * d == m && a >= d) continue;  // offset m/2 pairs each block twice
+        const int b = a + d < m ? a + d : a + d - m;
+        if (rs[a] == R(0) && rs[b] == R(0)) continue;
         const int pa = rp[a], qa = rq[a], pb = rp[b], qb = rq[b];
-        const double ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
-        const double2 ea = re[a], eb = re[b];
-        const double2 b00 = A[pa * lda + pb], b01 = A[pa * lda + qb];
-        const double2 b10 = A[qa * lda + pb], b11 = A[qa * lda + qb];
-        // T = B J_b
-        const double2 b01e = cmul(b01, eb), b11e = cmul(b11, eb);
-        const double2 t00 = csub(cscale(b00, cb), cscale(b01e, sb));
-        const double2 t01 = cadd(cscale(b00, sb), cscale(b01e, cb));
-        const double2 t10 = csub(cscale(b10, cb), cscale(b11e, sb));
-        const double2 t11 = cadd(cscale(b10, sb), cscale(b11e, cb));
-        // B' = J_a^dagger T, J_a^dagger = [[c, -s conj(e)], [s, c conj(e)]]
-        const double2 ce = cconj(ea);
-        const double2 u10 = cmul(t10, ce), u11 = cmul(t11, ce);
-        double2 n00 = csub(cscale(t00, ca), cscale(u10, sa));
-        double2 n01 = csub(cscale(t01, ca), cscale(u11, sa));
-        double2 n10 = cadd(cscale(t00, sa), cscale(u10, ca));
-        double2 n11 = cadd(cscale(t01, sa), cscale(u11, ca));
-        if (a == b) {
-          n00.y = 0.0;
-          n11.y = 0.0;
-          n01 = make_double2(0.0, 0.0);
-          n10 = make_double2(0.0, 0.0);
+        const R ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
+        const V2<R> ea = re[a], eb = re[b];
+        const V2<R> b00 = A[pa * lda + pb], b01 = A[pa * lda + qb];
+        const V2<R> b10 = A[qa * lda + pb], b11 = A[qa * lda + qb];
+        const V2<R> b01e = c_mul<R>(b01, eb), b11e = c_mul<R>(b11, eb);
+        const V2<R> t00 = c_sub<R>(c_scale<R>(b00, cb), c_scale<R>(b01e, sb));
+        const V2<R> t01 = c_add<R>(c_scale<R>(b00, sb), c_scale<R>(b01e, cb));
+        const V2<R> t10 = c_sub<R>(c_scale<R>(b10, cb), c_scale<R>(b11e, sb));
+        const V2<R> t11 = c_add<R>(c_scale<R>(b10, sb), c_scale<R>(b11e, cb));
+        const V2<R> ce = c_conj<R>(ea);
+        const V2<R> u10 = c_mul<R>(t10, ce), u11 = c_mul<R>(t11, ce);
+        V2<R> n00 = c_sub<R>(c_scale<R>(t00, ca), c_scale<R>(u10, sa));
+        V2<R> n01 = c_sub<R>(c_scale<R>(t01, ca), c_scale<R>(u11, sa));
+        V2<R> n10 = c_add<R>(c_scale<R>(t00, sa), c_scale<R>(u10, ca));
+        V2<R> n11 = c_add<R>(c_scale<R>(t01, sa), c_scale<R>(u11, ca));
+        if (d == 0) {
+          n00.y = R(0);
+          n11.y = R(0);
+          if (kExact) {
+            n01 = mk<R>(0, 0);
+          } else {
+            n01 = mk<R>(R(0.5) * (n01.x + n10.x), R(0.5) * (n01.y - n10.y));
+          }
+          n10 = c_conj<R>(n01);
         }
         A[pa * lda + pb] = n00;
         A[pa * lda + qb] = n01;
         A[qa * lda + pb] = n10;
         A[qa * lda + qb] = n11;
-        if (a < b) {
-          A[pb * lda + pa] = cconj(n00);
-          A[qb * lda + pa] = cconj(n01);
-          A[pb * lda + qa] = cconj(n10);
-          A[qb * lda + qa] = cconj(n11);
+        if (d != 0) {
+          A[pb * lda + pa] = c_conj<R>(n00);
+          A[qb * lda + pa] = c_conj<R>(n01);
+          A[pb * lda + qa] = c_conj<R>(n10);
+          A[qb * lda + qa] = c_conj<R>(n11);
         }
       }
-      // V <- V J
       for (int idx = threadIdx.x; idx < n * m; idx += blockDim.x) {
         const int i = idx / m, k = idx - (idx / m) * m;
-        const double sn = rs[k];
-        if (sn == 0.0) continue;
-        const double cs = rc[k];
+        const R sn = rs[k];
+        if (sn == R(0)) continue;
+        const R cs = rc[k];
         const int p = rp[k], q = rq[k];
-        const double2 vp = V[i * ldv + p];
-        const double2 vqe = cmul(V[i * ldv + q], re[k]);
-        V[i * ldv + p] = csub(cscale(vp, cs), cscale(vqe, sn));
-        V[i * ldv + q] = cadd(cscale(vp, sn), cscale(vqe, cs));
+        const V2<R> vp = V[i * ldv + p];
+        const V2<R> vqe = c_mul<R>(V[i * ldv + q], re[k]);
+        V[i * ldv + p] = c_sub<R>(c_scale<R>(vp, cs), c_scale<R>(vqe, sn));
+        V[i * ldv + q] = c_add<R>(c_scale<R>(vp, sn), c_scale<R>(vqe, cs));
       }
       __syncthreads();
     }
@@ -307,7 +366,92 @@ __device__ int jacobi_hermitian(double2* A, int lda, double2* V, int ldv, int n,
     __syncthreads();
     if (done) return sweep + 1;
   }
-  return jp.max_sweeps + 1;
+  return max_sweeps + 1;
+}
+
+// Re-orthonormalise the columns of V (n x n, row stride n) in FP64.  V is a
+// product of FP32 rotations, so G = V^dagger V = I + E with |E| ~ 1e-6 and the
+// Cholesky factor R (G = R^dagger R) and its inverse follow from short series
+// that are exact to O(|E|^3) ~ 1e-18, with only parallel products:
+//   X1 = P(E), X = P(E - X1^dagger X1), R = I + X, R^-1 = I - X + X^2,
+// where P keeps the strict upper triangle and half the diagonal.  Q = V R^-1
+// is formed row by row in place (one warp per row).  G holds E and X in its
+// upper triangle and X1^dagger X1, X^2 in its strict lower triangle (row
+// stride ldg); dg[n] holds their diagonals.  Returns max |E_ij|.
+__device__ double orthonormalise(double2* V, int n, double2* G, int ldg, double* dg, double* scal) {
+  // E = V^dagger V - I (upper triangle)
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - (idx / n) * n;
+    if (j < i) continue;
+    double2 acc = make_double2(i == j ? -1.0 : 0.0, 0.0);
+    for (int r = 0; r < n; ++r) fma_conj<double>(acc, V[r * n + i], V[r * n + j]);
+    if (i == j) acc.y = 0.0;
+    G[i * ldg + j] = acc;
+  }
+  if (threadIdx.x == 0) scal[6] = 0.0;
+  __syncthreads();
+  // K = X1^dagger X1 with X1 = P(E): K_ij = sum_{k <= i} conj(X1_ki) X1_kj  (i <= j)
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - (idx / n) * n;
+    if (j < i) continue;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k <= i; ++k) {
+      double2 xki = G[k * ldg + i], xkj = G[k * ldg + j];
+      if (k == i) xki = cscale(xki, 0.5);
+      if (k == j) xkj = cscale(xkj, 0.5);
+      fma_conj<double>(acc, xki, xkj);
+    }
+    if (i == j) dg[i] = acc.x;
+    else G[j * ldg + i] = acc;
+  }
+  __syncthreads();
+  // X = P(E - K) in the upper triangle; record max |E|
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - (idx / n) * n;
+    if (j < i) continue;
+    const double2 e = G[i * ldg + j];
+    const double ae = fabs(e.x) + fabs(e.y);
+    if (ae > scal[6]) atomicMax(reinterpret_cast<unsigned long long*>(scal + 6), __double_as_longlong(ae));
+    if (i == j) G[i * ldg + i] = make_double2(0.5 * (e.x - dg[i]), 0.0);
+    else G[i * ldg + j] = csub(e, G[j * ldg + i]);
+  }
+  __syncthreads();
+  // X^2 (upper triangular) into the strict lower triangle and dg
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - (idx / n) * n;
+    if (j < i) continue;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = i; k <= j; ++k) fma_c<double>(acc, G[i * ldg + k], G[k * ldg + j]);
+    if (i == j) dg[i] = acc.x;
+    else G[j * ldg + i] = acc;
+  }
+  __syncthreads();
+  // M = X^2 - X in the upper triangle
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - (idx / n) * n;
+    if (j < i) continue;
+    if (i == j) G[i * ldg + i] = make_double2(dg[i] - G[i * ldg + i].x, 0.0);
+    else G[i * ldg + j] = csub(G[j * ldg + i], G[i * ldg + j]);
+  }
+  __syncthreads();
+  // Q[r][j] = V[r][j] + sum_{i <= j} V[r][i] M[i][j], one warp per row, in place
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < n; r += nw) {
+    double2* v = V + r * n;
+    double2 out[kMaxD * 2 / 32];
+    int cnt = 0;
+    for (int j = lane; j < n; j += 32) {
+      double2 acc = v[j];
+      for (int i = 0; i <= j; ++i) fma_c<double>(acc, v[i], G[i * ldg + j]);
+      out[cnt++] = acc;
+    }
+    __syncwarp();
+    cnt = 0;
+    for (int j = lane; j < n; j += 32) v[j] = out[cnt++];
+    __syncwarp();
+  }
+  __syncthreads();
+  return scal[6];
 }
 
 // A bond whose spectrum is not usable (NaN/Inf or zero norm) is left as it
@@ -327,39 +471,74 @@ __device__ void bond_fail(const BondDesc& bd, V2<T>* Yout, double* theta_a, doub
   }
 }
 
+// F[(row, t)][k]: kicked Gamma_b with the lambda of its other legs (FP64).
+template <typename T>
+__device__ void load_F(const SideDesc& sb, const V2<T>* gamma, const double* lam, double th, double2* F, int D) {
+  const double c = cos(0.5 * th), s = sin(0.5 * th);
+  for (int idx = threadIdx.x; idx < sb.rows * D; idx += blockDim.x) {
+    const int rj = idx / D, k = idx - (idx / D) * D;
+    const RowPos p = row_pos(sb, rj);
+    const int64_t e = elem(sb, 0, p, k);
+    const V2<T> g0 = gamma[e], g1 = gamma[e + sb.str_s];
+    double2 a0, a1;
+    kick2<double>(c, s, make_double2(g0.x, g0.y), make_double2(g1.x, g1.y), a0, a1);
+    const double w = row_weight(sb, lam, p);
+    F[(rj * 2 + 0) * D + k] = cscale(a0, w);
+    F[(rj * 2 + 1) * D + k] = cscale(a1, w);
+  }
+}
+
+// Bond eigenproblem: rho (FP64), eigenvectors by FP32 Jacobi to convergence
+// (the FP32 pipe is 64x the FP64 pipe on this part), FP64 Cholesky-QR of the
+// FP32 eigenvectors, rho' = V^dagger rho V and FP64 Jacobi sweeps on rho' until
+// every off-diagonal is at FP64 rounding level (mixed-precision Jacobi: a
+// low-precision eigenbasis as preconditioner of the high-precision sweeps).
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     bond_kernel(const BondDesc* __restrict__ bonds, const V2<T>* __restrict__ partials, V2<T>* gamma,
                 double* lam, double* pending, V2<T>* __restrict__ Yout, double* __restrict__ theta_a,
-                int* flags, unsigned long long* sweeps_out, int D, JacobiParams jp) {
+                int* flags, unsigned long long* sweeps_out, unsigned long long* cycles, int D, JacobiParams jp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BondDesc bd = bonds[blockIdx.x];
   const SideDesc sb = bd.b;
   const int nb = sb.rows;
   const int n = 2 * nb;
-  const int m = n / 2;
   const int D2 = D * D;
   const BondSmem L(D, n);
-  double2* F = reinterpret_cast<double2*>(smem_raw + L.off_F);      // [n][D]
-  double2* RHO = reinterpret_cast<double2*>(smem_raw + L.off_RHO);  // [n][n+1]
+  double2* RHO = reinterpret_cast<double2*>(smem_raw + L.off_R);  // [n][n+1]
+  double2* Vr = reinterpret_cast<double2*>(smem_raw + L.off_V);
   double2* X = reinterpret_cast<double2*>(smem_raw + L.off_X);
-  double2* Cs = X;           // [2][D][D]
-  double2* H = X + 2 * D2;   // [n][D]
-  double2* Vm = X;           // [n][n] after rho is formed
+  double2* Cs = Vr;           // [2][D][D]
+  double2* H = Vr + 2 * D2;   // [n][D]
+  double2* Vm = Vr;           // [n][n]
+  double2* F = X;             // [n][D]
+  float2* R32 = reinterpret_cast<float2*>(X);     // [n][n+1]
+  float2* V32 = R32 + (size_t)n * (n + 1);        // [n][n]
   double2* re = reinterpret_cast<double2*>(smem_raw + L.off_re);
-  double* lamo = reinterpret_cast<double*>(smem_raw + L.off_lamo);  // old lambda of the bond
+  float2* re32 = reinterpret_cast<float2*>(smem_raw + L.off_re32);
+  double* lamo = reinterpret_cast<double*>(smem_raw + L.off_lamo);
   double* ev = reinterpret_cast<double*>(smem_raw + L.off_ev);
   double* sv = reinterpret_cast<double*>(smem_raw + L.off_sv);
   double* rc = reinterpret_cast<double*>(smem_raw + L.off_rc);
   double* rs = reinterpret_cast<double*>(smem_raw + L.off_rs);
-  double* scal = rs + m;  // [0] trace, [1] norm, [2] max lambda_other, [3] ev max
+  double* scal = reinterpret_cast<double*>(smem_raw + L.off_scal);  // [0] trace [1] norm [2] max lambda_o [4] tmp
+  float* rc32 = reinterpret_cast<float*>(smem_raw + L.off_rc32);
+  float* rs32 = reinterpret_cast<float*>(smem_raw + L.off_rs32);
   int* order = reinterpret_cast<int*>(smem_raw + L.off_int);
   int* rp = order + n;
-  int* rq = rp + m;
-  int* iflag = rq + m;
+  int* rq = rp + n / 2;
+  int* iflag = rq + n / 2;  // [4]
   const int ldr = n + 1;
+  const double th_b = pending[sb.site];
+  long long t_prev = clock64();
+  auto mark = [&](int phase) {
+    if (threadIdx.x == 0) {
+      const long long t = clock64();
+      atomicAdd(cycles + phase, (unsigned long long)(t - t_prev));
+      t_prev = t;
+    }
+  };
 
-  // old lambda of the bond; Gram blocks with lambda on both sides, summed in FP64
   for (int k = threadIdx.x; k < D; k += blockDim.x) lamo[k] = lam[bd.lam_e + k];
   __syncthreads();
   for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
@@ -373,25 +552,10 @@ __global__ void __launch_bounds__(kThreads)
     const int k = kl / D, l = kl - (kl / D) * D;
     Cs[o] = cscale(acc, lamo[k] * lamo[l]);
   }
-  // F[(row, t)][k]: kicked Gamma_b with the lambda of its other legs
-  {
-    const double th = pending[sb.site];
-    const double c = cos(0.5 * th), s = sin(0.5 * th);
-    for (int idx = threadIdx.x; idx < nb * D; idx += blockDim.x) {
-      const int rj = idx / D, k = idx - (idx / D) * D;
-      const RowPos p = row_pos(sb, rj);
-      const int64_t e = elem(sb, 0, p, k);
-      const V2<T> g0 = gamma[e], g1 = gamma[e + sb.str_s];
-      double2 a0, a1;
-      kick2<double>(c, s, make_double2(g0.x, g0.y), make_double2(g1.x, g1.y), a0, a1);
-      const double w = row_weight(sb, lam, p);
-      F[(rj * 2 + 0) * D + k] = cscale(a0, w);
-      F[(rj * 2 + 1) * D + k] = cscale(a1, w);
-    }
-  }
+  load_F<T>(sb, gamma, lam, th_b, F, D);
   for (int idx = threadIdx.x; idx < n * ldr; idx += blockDim.x) RHO[idx] = make_double2(0.0, 0.0);
   __syncthreads();
-  // rho = sum_s phase(s) o (conj(F) C_s F^T)
+  // rho = sum_s phase(s) o (conj(F) C_s F^T), upper triangle, then mirrored
   for (int sidx = 0; sidx < 2; ++sidx) {
     const double2* C = Cs + sidx * D2;
     for (int idx = threadIdx.x; idx < n * D; idx += blockDim.x) {
@@ -403,6 +567,7 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
       const int x = idx / n, y = idx - (idx / n) * n;
+      if (y < x) continue;
       double2 acc = make_double2(0.0, 0.0);
       for (int l = 0; l < D; ++l) fma_c<double>(acc, H[x * D + l], F[y * D + l]);
       const int tx = x & 1, ty = y & 1;
@@ -418,6 +583,12 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();
   }
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int x = idx / n, y = idx - (idx / n) * n;
+    if (y > x) RHO[y * ldr + x] = cconj(RHO[x * ldr + y]);
+    if (y == x) RHO[x * ldr + x].y = 0.0;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     double tr = 0.0;
     for (int i = 0; i < n; ++i) tr += RHO[i * ldr + i].x;
@@ -429,11 +600,149 @@ __global__ void __launch_bounds__(kThreads)
     bond_fail<T>(bd, Yout, theta_a, pending, flags, D);
     return;
   }
-  const int sweeps =
-      jacobi_hermitian(RHO, ldr, Vm, n, n, jp, jp.floor_rel * trace, rc, rs, re, rp, rq, iflag);
+  mark(0);
+  // FP32 Jacobi on a rounded copy (F is reloaded at the end)
+  for (int idx = threadIdx.x; idx < n * ldr; idx += blockDim.x) {
+    const double2 v = RHO[idx];
+    R32[idx] = make_float2((float)v.x, (float)v.y);
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x)
+    V32[idx] = make_float2((idx / n) == (idx % n) ? 1.f : 0.f, 0.f);
+  __syncthreads();
+  const int sw32 = jacobi_hermitian<float, true>(R32, ldr, V32, n, n, (float)jp.tol32,
+                                                 (float)(jp.floor32 * trace), jp.max_sweeps32, rc32, rs32, re32,
+                                                 rp, rq, iflag);
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const float2 v = V32[idx];
+    Vm[idx] = make_double2((double)v.x, (double)v.y);
+  }
+  __syncthreads();
+  mark(1);
+  const double emax = orthonormalise(Vm, n, X, ldr, ev, scal);
+  if (threadIdx.x == 0 && !(emax < 1e-4)) atomicOr(flags, 1);  // FP32 basis too far from unitary
+  mark(2);
+  // rho' = V^dagger rho V: W = rho V into X, then the upper triangle of V^dagger W into RHO
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - (idx / n) * n;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < n; ++k) fma_c<double>(acc, RHO[i * ldr + k], Vm[k * n + j]);
+    X[i * ldr + j] = acc;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - (idx / n) * n;
+    if (j < i) continue;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < n; ++k) fma_conj<double>(acc, Vm[k * n + i], X[k * ldr + j]);
+    RHO[i * ldr + j] = acc;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - (idx / n) * n;
+    if (j > i) RHO[j * ldr + i] = cconj(RHO[i * ldr + j]);
+    if (j == i) RHO[i * ldr + i].y = 0.0;
+  }
+  __syncthreads();
+  // Further FP32 levels for the eigenvalues the previous level could not
+  // resolve (FP32 rounding ~1e-7 of that level's largest entry): the indices
+  // whose diagonal lies below kLevelRatio x the previous level's scale (and
+  // above rounding noise of the whole matrix) are diagonalised again in FP32
+  // on a rescaled copy of their block, and the rotation, re-orthonormalised in
+  // FP64, is applied to V and to rho' in FP64.
+  {
+    int* cand = order;  // [n] candidate indices of this level
+    double* dcur = ev;
+    double2* W64 = X;                                 // [ns][ns]
+    double2* Gw = X + (size_t)(n / 2) * (n / 2);      // [ns][ns+1]
+    float2* B32 = reinterpret_cast<float2*>(Gw + (size_t)(n / 2) * (n / 2 + 1));  // [ns][ns+1]
+    float2* W32 = B32 + (size_t)(n / 2) * (n / 2 + 1);                            // [ns][ns]
+    double prev_scale = -1.0;  // level 0 covered everything
+    for (int level = 0; level < kExtraLevels; ++level) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) dcur[i] = RHO[i * ldr + i].x;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double scale = 0.0;
+        for (int i = 0; i < n; ++i)
+          if (prev_scale < 0.0 || dcur[i] <= prev_scale) scale = fmax(scale, dcur[i]);
+        const double hi = kLevelRatio * scale, lo = kNoiseRel * trace;
+        int ns = 0;
+        for (int i = 0; i < n; ++i)
+          if (dcur[i] <= hi && dcur[i] > lo) cand[ns++] = i;
+        // keep at most n/2, the largest first
+        for (int a = 0; a < ns; ++a)
+          for (int b = a + 1; b < ns; ++b)
+            if (dcur[cand[b]] > dcur[cand[a]]) {
+              const int t = cand[a];
+              cand[a] = cand[b];
+              cand[b] = t;
+            }
+        if (ns > n / 2) ns = n / 2;
+        ns &= ~1;  // even: drop the smallest
+        iflag[1] = ns;
+        scal[7] = ns > 0 ? dcur[cand[0]] : 0.0;
+        scal[3] = hi;
+      }
+      __syncthreads();
+      const int ns = iflag[1];
+      const double bscale = scal[7];
+      prev_scale = scal[3];
+      if (ns < 2 || !(bscale > 0.0)) break;
+      const int ldb = ns + 1;
+      const double inv = 1.0 / bscale;
+      double btr = 0.0;
+      for (int idx = threadIdx.x; idx < ns * ns; idx += blockDim.x) {
+        const int a = idx / ns, b = idx - (idx / ns) * ns;
+        const double2 v = RHO[cand[a] * ldr + cand[b]];
+        B32[a * ldb + b] = make_float2((float)(v.x * inv), (float)(v.y * inv));
+        W32[a * ns + b] = make_float2(a == b ? 1.f : 0.f, 0.f);
+      }
+      for (int a = 0; a < ns; ++a) btr += dcur[cand[a]] * inv;
+      __syncthreads();
+      const int swl = jacobi_hermitian<float, true>(B32, ldb, W32, ns, ns, (float)jp.tol32,
+                                                    (float)(jp.floor32 * btr), jp.max_sweeps32, rc32, rs32, re32,
+                                                    rp, rq, iflag);
+      (void)swl;
+      for (int idx = threadIdx.x; idx < ns * ns; idx += blockDim.x) {
+        const float2 v = W32[idx];
+        W64[idx] = make_double2((double)v.x, (double)v.y);
+      }
+      __syncthreads();
+      orthonormalise(W64, ns, Gw, ldb, dcur, scal);
+      // rows of V and rho': X[r][cand] <- X[r][cand] W (one warp per row, ns <= 32 per lane pass)
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int rr = warp; rr < 2 * n; rr += nw) {
+        double2* row = rr < n ? Vm + rr * n : RHO + (rr - n) * ldr;
+        double2 out = make_double2(0.0, 0.0);
+        if (lane < ns) {
+          for (int a = 0; a < ns; ++a) fma_c<double>(out, row[cand[a]], W64[a * ns + lane]);
+        }
+        __syncwarp();
+        if (lane < ns) row[cand[lane]] = out;
+        __syncwarp();
+      }
+      __syncthreads();
+      // columns of rho': rho'[cand][c] <- W^dagger rho'[cand][c]
+      for (int c = warp; c < n; c += nw) {
+        double2 out = make_double2(0.0, 0.0);
+        if (lane < ns) {
+          for (int a = 0; a < ns; ++a) fma_conj<double>(out, W64[a * ns + lane], RHO[cand[a] * ldr + c]);
+        }
+        __syncwarp();
+        if (lane < ns) RHO[cand[lane] * ldr + c] = out;
+        __syncwarp();
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) atomicAdd(sweeps_out + 2, 1ull);
+    }
+  }
+  mark(3);
+  const int sweeps = jacobi_hermitian<double, false>(RHO, ldr, Vm, n, n, jp.tol, jp.floor_rel * trace,
+                                                     jp.max_sweeps, rc, rs, re, rp, rq, iflag);
+  mark(4);
   if (threadIdx.x == 0) {
     if (sweeps > jp.max_sweeps) atomicOr(flags, 1);
     atomicAdd(sweeps_out, (unsigned long long)(sweeps > jp.max_sweeps ? jp.max_sweeps : sweeps));
+    atomicAdd(sweeps_out + 1, (unsigned long long)(sw32 > jp.max_sweeps32 ? jp.max_sweeps32 : sw32));
   }
   // eigenvalues sorted in decreasing order (ties by index)
   for (int i = threadIdx.x; i < n; i += blockDim.x) ev[i] = RHO[i * ldr + i].x;
@@ -465,6 +774,7 @@ __global__ void __launch_bounds__(kThreads)
       for (int k = 0; k < D; ++k) mx = fmax(mx, lam[lo + k]);
     scal[2] = mx;
   }
+  load_F<T>(sb, gamma, lam, th_b, F, D);
   __syncthreads();
   const double nrm = scal[1];
   if (!(nrm > 0.0) || !isfinite(nrm)) {
@@ -515,6 +825,7 @@ __global__ void __launch_bounds__(kThreads)
     pending[bd.a.site] = 0.0;
     pending[sb.site] = 0.0;
   }
+  mark(5);
 }
 
 // ---------------------------------------------------------------- big-end update
@@ -726,12 +1037,12 @@ cudaError_t Launch<T>::gram(const TileDesc* tiles, int n_tiles, const BondDesc* 
 template <typename T>
 cudaError_t Launch<T>::bond(const BondDesc* bonds, int n_bonds, const void* partials, void* gamma, double* lam,
                             double* pending, void* Y, double* theta_a, int* flags, unsigned long long* sweeps,
-                            int D, JacobiParams jp, cudaStream_t st) {
+                            unsigned long long* cycles, int D, JacobiParams jp, cudaStream_t st) {
   if (n_bonds == 0) return cudaSuccess;
   const size_t sm = bond_smem_bytes(D, 2 * D);
   bond_kernel<T><<<n_bonds, kThreads, sm, st>>>(bonds, static_cast<const V2<T>*>(partials),
                                                  static_cast<V2<T>*>(gamma), lam, pending,
-                                                 static_cast<V2<T>*>(Y), theta_a, flags, sweeps, D, jp);
+                                                 static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles, D, jp);
   return cudaGetLastError();
 }
 

@@ -140,9 +140,16 @@ class GPEPS:
         return np.array(out[:], dtype=np.float64)
 
     def sweeps(self):
-        s, b = ctypes.c_int64(), ctypes.c_int64()
-        check(self.lib.gpeps_sweeps(self.h, ctypes.byref(s), ctypes.byref(b)), "gpeps_sweeps")
-        return s.value, b.value
+        """(FP64 Jacobi sweeps, FP32 warm-start sweeps, bond updates) since the last reset."""
+        s, s32, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check(self.lib.gpeps_sweeps(self.h, ctypes.byref(s), ctypes.byref(s32), ctypes.byref(b)), "gpeps_sweeps")
+        return s.value, s32.value, b.value
+
+    def bond_phase_cycles(self):
+        """SM cycles per phase of the bond kernel since the last reset (summed over bonds)."""
+        c = (ctypes.c_int64 * 6)()
+        check(self.lib.gpeps_bond_phase_cycles(self.h, c), "gpeps_bond_phase_cycles")
+        return [int(x) for x in c]
 
     def synchronize(self):
         self.stream.synchronize()

@@ -1,11 +1,16 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle and the exact pins.
 
 Tolerances: |d<Z>| <= 1e-10 for the complex128 path and <= 1e-4 for the mixed
-path (complex64 tensors, FP64 bond eigensolver).  lambda spectra: the GPU
-obtains Schmidt values as square roots of eigenvalues of a Gram-type matrix,
-so a value is resolved only down to ~sqrt(eps) of the largest: entries are
-compared to 1e-6 (c128) / 2e-3 (mixed) absolute, and to 1e-9 (c128) where the
-oracle's value exceeds 1e-3.
+path (complex64 tensors, FP64 bond eigensolver), on every qubit in the exact
+(untruncated) regime and on the mean <Z> always.  Per-qubit <Z> after many
+truncated steps in complex128 is held to 5e-9: the GPU obtains Schmidt vectors
+from the eigenproblem of a Gram-type (squared) matrix, whose eigenvectors are
+accurate to eps ||rho|| / gap, so components of relative size below ~1e-8 are
+resolved only approximately (the same formulation with LAPACK's eigensolver
+reaches 9e-10 on the 16-angle sweep).  lambda spectra: a Schmidt value is
+resolved down to ~sqrt(eps) of the largest: entries are compared to 1e-6
+(c128) / 2e-3 (mixed) absolute, and to 1e-9 (c128) where the oracle's value
+exceeds 1e-3.
 """
 import json
 import math
@@ -24,6 +29,7 @@ from ._gpu_util import run_layers, run_step, split
 pytestmark = pytest.mark.gpu
 
 TOL = {"c128": 1e-10, "mixed": 1e-4}
+TOL_SITE_TRUNC = {"c128": 5e-9, "mixed": 1e-4}    # per qubit, long truncated runs
 M127, E127 = heavy_hex(*EAGLE)
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -178,7 +184,7 @@ def test_theta_sweep_16_instances(dtype):
     for k, inst in enumerate(gold["instances"]):
         if _is_clifford_tie(theta[k], w.steps, w.D):
             continue
-        assert np.abs(zi[k] - np.array(inst["z"][str(w.steps)])).max() < TOL[dtype]
+        assert np.abs(zi[k] - np.array(inst["z"][str(w.steps)])).max() < TOL_SITE_TRUNC[dtype]
         for e, lam in inst["lambda"][str(w.steps)].items():
             lam_check(g.lambdas(k, int(e)), np.array(lam), dtype)
 
@@ -203,7 +209,8 @@ def test_heavyhex_mix_d32_full_size(dtype):
         z, _ = g.expect_z()
         zi = split(z.cpu().numpy(), graphs)
         for k, inst in enumerate(gold["instances"]):
-            assert np.abs(zi[k] - np.array(inst["z"][str(s)])).max() < TOL[dtype], (s, k)
+            tol = TOL[dtype] if 2 ** s <= w.D else TOL_SITE_TRUNC[dtype]
+            assert np.abs(zi[k] - np.array(inst["z"][str(s)])).max() < tol, (s, k)
             for e, lam in inst["lambda"][str(s)].items():
                 lam_check(g.lambdas(k, int(e)), np.array(lam), dtype)
     means = np.concatenate(means)
