@@ -183,7 +183,7 @@ def test_theta_sweep_16_instances(dtype):
     zi = split(z.cpu().numpy(), graphs)
     for k, inst in enumerate(gold["instances"]):
         if _is_clifford_tie(theta[k], w.steps, w.D):
-            continue
+            continue   # <Z> and lambda of a truncated flat spectrum are not unique
         assert np.abs(zi[k] - np.array(inst["z"][str(w.steps)])).max() < TOL_SITE_TRUNC[dtype]
         for e, lam in inst["lambda"][str(w.steps)].items():
             lam_check(g.lambdas(k, int(e)), np.array(lam), dtype)
