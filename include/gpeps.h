@@ -162,6 +162,22 @@ int gpeps_status(gpeps_handle* h, int32_t* flags);
  * instance `instance` to host out[D], sorted in decreasing order; synchronises. */
 int gpeps_lambda(gpeps_handle* h, int32_t instance, int32_t edge, double* out);
 
+/*
+ * Layout of the state buffer, for reading, checkpointing or writing tensors.
+ * gpeps_site_layout: byte offset of Gamma of site `site` of instance
+ * `instance` inside the state buffer, its degree, and its neighbours in leg
+ * order (host int32[3], -1 past the degree).  Gamma is complex (16 bytes per
+ * element for GPEPS_C128, 8 for GPEPS_MIXED_C64), laid out [s][leg0][leg1][leg2]
+ * with the physical index s in {0, 1} outermost and the last leg fastest,
+ * 2 * D^deg elements.  gpeps_lambda_layout: byte offset of lambda (float64[D])
+ * of edge `edge`.  Host-only; the handle need not be bound.  Saving the state
+ * buffer after a full Trotter step (no kick pending) and copying it back into
+ * a bound handle of the same graphs, D and dtype restores the evolution.
+ */
+int gpeps_site_layout(const gpeps_handle* h, int32_t instance, int32_t site, int64_t* byte_offset, int32_t* deg,
+                      int32_t* neighbours);
+int gpeps_lambda_layout(const gpeps_handle* h, int32_t instance, int32_t edge, int64_t* byte_offset);
+
 /* Totals of the batch: qubits, edges, bond updates per Trotter step. */
 int gpeps_sizes(const gpeps_handle* h, int64_t* total_qubits, int64_t* total_edges);
 

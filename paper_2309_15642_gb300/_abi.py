@@ -25,6 +25,9 @@ SIGNATURES = {
     "gpeps_step": (c_int, [c_void_p, c_int32, c_void_p, c_int32, c_void_p]),
     "gpeps_status": (c_int, [c_void_p, POINTER(c_int32)]),
     "gpeps_lambda": (c_int, [c_void_p, c_int32, c_int32, POINTER(c_double)]),
+    "gpeps_site_layout": (c_int, [c_void_p, c_int32, c_int32, POINTER(c_int64), POINTER(c_int32),
+                                  POINTER(c_int32)]),
+    "gpeps_lambda_layout": (c_int, [c_void_p, c_int32, c_int32, POINTER(c_int64)]),
     "gpeps_sizes": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
     "gpeps_sweeps": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
     "gpeps_bond_phase_cycles": (c_int, [c_void_p, POINTER(c_int64)]),

@@ -575,6 +575,26 @@ int gpeps_lambda(gpeps_handle* h, int32_t instance, int32_t edge, double* out) {
   return GPEPS_OK;
 }
 
+int gpeps_site_layout(const gpeps_handle* h, int32_t instance, int32_t site, int64_t* byte_offset, int32_t* deg,
+                      int32_t* neighbours) {
+  if (!h || instance < 0 || instance >= h->n_inst) return GPEPS_EINVAL;
+  if (site < 0 || site >= h->g[instance].n) return GPEPS_EINVAL;
+  const int gs = h->inst_site0[instance] + site;
+  const auto& nb = h->g[instance].nb[site];
+  if (byte_offset) *byte_offset = (int64_t)h->s_gamma + h->site_off[gs] * (int64_t)h->elt;
+  if (deg) *deg = (int32_t)nb.size();
+  if (neighbours)
+    for (int q = 0; q < 3; ++q) neighbours[q] = q < (int)nb.size() ? nb[q] : -1;
+  return GPEPS_OK;
+}
+
+int gpeps_lambda_layout(const gpeps_handle* h, int32_t instance, int32_t edge, int64_t* byte_offset) {
+  if (!h || !byte_offset || instance < 0 || instance >= h->n_inst) return GPEPS_EINVAL;
+  if (edge < 0 || edge >= (int)h->g[instance].edges.size()) return GPEPS_EINVAL;
+  *byte_offset = (int64_t)h->s_lam + (int64_t)(h->inst_edge0[instance] + edge) * h->D * (int64_t)sizeof(double);
+  return GPEPS_OK;
+}
+
 int gpeps_sizes(const gpeps_handle* h, int64_t* total_qubits, int64_t* total_edges) {
   if (!h) return GPEPS_EINVAL;
   if (total_qubits) *total_qubits = h->total_sites;

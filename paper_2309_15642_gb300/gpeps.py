@@ -151,6 +151,42 @@ class GPEPS:
         check(self.lib.gpeps_bond_phase_cycles(self.h, c), "gpeps_bond_phase_cycles")
         return [int(x) for x in c]
 
+    # -------------------------------------------------------------- state access
+    def site_tensor(self, instance, site):
+        """View of Gamma of a site inside the state buffer: complex tensor [2] + [D] * deg, and
+        the site's neighbours in leg order."""
+        off, deg = ctypes.c_int64(), ctypes.c_int32()
+        nb = (ctypes.c_int32 * 3)()
+        check(self.lib.gpeps_site_layout(self.h, int(instance), int(site), ctypes.byref(off), ctypes.byref(deg),
+                                         nb), "gpeps_site_layout")
+        cdt = torch.complex128 if self.dtype == "c128" else torch.complex64
+        esz = 16 if self.dtype == "c128" else 8
+        n = 2 * self.D ** deg.value
+        t = self.state[off.value: off.value + n * esz].view(cdt).view([2] + [self.D] * deg.value)
+        return t, [x for x in nb[:deg.value]]
+
+    def lambda_tensor(self, instance, edge):
+        """View of lambda (float64[D], unsorted) of an edge inside the state buffer."""
+        off = ctypes.c_int64()
+        check(self.lib.gpeps_lambda_layout(self.h, int(instance), int(edge), ctypes.byref(off)),
+              "gpeps_lambda_layout")
+        return self.state[off.value: off.value + self.D * 8].view(torch.float64)
+
+    def save_state(self):
+        """Host copy of the whole state (every Gamma and lambda): a checkpoint taken after a
+        full Trotter step, when no kick is pending."""
+        self.stream.synchronize()
+        return self.state.cpu().clone()
+
+    def load_state(self, saved):
+        """Restore a checkpoint of :meth:`save_state` (same graphs, D and dtype)."""
+        if saved.numel() != self.state.numel():
+            raise ValueError("checkpoint of another layout")
+        self._after_torch()
+        with torch.cuda.stream(self.stream):
+            self.state.copy_(saved.to(self.device, non_blocking=False))
+        self.stream.synchronize()
+
     def synchronize(self):
         self.stream.synchronize()
 

@@ -122,3 +122,35 @@ def test_product_path_fails_loudly_without_gpu():
     from paper_2309_15642_gb300 import GPEPS
     with pytest.raises(RuntimeError):
         GPEPS([(3, [[0, 1], [1, 2]])], 2)
+
+
+def test_state_layout_host_only(abi):
+    """Site and lambda offsets tile the state buffer without overlap (no GPU needed)."""
+    lib = abi.load()
+    n, e = heavy_hex(*EAGLE)
+    D = 3
+    for dtype, elt in ((0, 16), (1, 8)):
+        st, h = _create(abi, [(n, e), (n, e)], D=D, dtype=dtype)
+        assert st == 0
+        spans = []
+        for inst in range(2):
+            for v in range(n):
+                off, deg = ctypes.c_int64(), ctypes.c_int32()
+                nb = (ctypes.c_int32 * 3)()
+                assert lib.gpeps_site_layout(h, inst, v, ctypes.byref(off), ctypes.byref(deg), nb) == 0
+                d = int(np.count_nonzero(e == v))
+                assert deg.value == d
+                assert list(nb[:d]) == sorted(int(b if a == v else a) for a, b in e if v in (a, b))
+                spans.append((off.value, off.value + 2 * D ** d * elt))
+            for k in range(len(e)):
+                off = ctypes.c_int64()
+                assert lib.gpeps_lambda_layout(h, inst, k, ctypes.byref(off)) == 0
+                spans.append((off.value, off.value + D * 8))
+        spans.sort()
+        assert all(a[1] <= b[0] for a, b in zip(spans[:-1], spans[1:]))
+        sb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+        lib.gpeps_query_workspace(h, ctypes.byref(sb), ctypes.byref(wb))
+        assert spans[-1][1] <= sb.value
+        off = ctypes.c_int64()
+        assert lib.gpeps_lambda_layout(h, 2, 0, ctypes.byref(off)) == abi.GPEPS_EINVAL
+        lib.gpeps_destroy(h)

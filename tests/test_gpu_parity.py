@@ -217,3 +217,30 @@ def test_heavyhex_mix_d32_full_size(dtype):
     ref = np.array([inst["mean_z"] for inst in gold["instances"]]).T
     assert np.abs(means - ref).max() < TOL[dtype]
     assert g.status() == 0
+
+
+def test_checkpoint_restore_and_readout_on_gpu_state():
+    """(1) save_state after step 3, two more steps, restore, the same two steps: identical
+    <Z>.  (2) the oracle's mean-field readout applied to the GPU's own tensors equals the
+    readout kernel."""
+    import torch
+    from ._gpu_util import gpu_lib
+    g = gpu_lib()([(M127, E127)], 8, dtype="c128")
+    g.reset()
+    th = torch.tensor([0.9], dtype=torch.float64, device="cuda")
+    g.step(3, th)
+    saved = g.save_state()
+    a = g.step(2, th).cpu().numpy()
+    za, _ = g.expect_z()
+    g.load_state(saved)
+    b = g.step(2, th).cpu().numpy()
+    zb, _ = g.expect_z()
+    assert np.array_equal(a, b) and torch.equal(za, zb)
+    peps = su.GPEPS(M127, E127, 8)
+    for v in range(M127):
+        t, nb = g.site_tensor(0, v)
+        assert nb == peps.nb[v]
+        peps.gamma[v] = t.cpu().numpy().astype(np.complex128)
+    for k in range(len(E127)):
+        peps.lam[k] = g.lambda_tensor(0, k).cpu().numpy()
+    assert np.abs(peps.expect_z() - zb.cpu().numpy()).max() < 1e-12
