@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--dtype", default="mixed", choices=["mixed", "c128"])
     ap.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--profile-steps", type=int, default=2)
+    ap.add_argument("--profile-steps", type=int, default=2, help="profiled steps after the timed region (>= 1)")
     return ap.parse_args()
 
 
@@ -286,6 +286,7 @@ def run_gpeps(args, rank, world, local_rank):
 
 def main():
     args = parse()
+    args.profile_steps = max(args.profile_steps, 1)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
