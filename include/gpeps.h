@@ -194,6 +194,43 @@ int gpeps_sweeps(gpeps_handle* h, int64_t* sweeps64, int64_t* sweeps32, int64_t*
  * [5] truncation, Y matrices and the smaller end.  Synchronises. */
 int gpeps_bond_phase_cycles(gpeps_handle* h, int64_t* cycles);
 
+/*
+ * One simple-update bond step on two caller-owned site tensors, allocating
+ * nothing.  The paper has no counterpart: this is a variant of the batched
+ * layer for callers that cannot allocate device memory once they run, e.g. a
+ * host framework that owns every device allocation through its own pool and
+ * does not let libraries call cudaMalloc/cudaFree (which also synchronise the
+ * device), or a latency-critical loop that must not pay for an allocation.
+ *
+ * Same arithmetic as gpeps_zz_layer for one bond: kick, absorb, gate, bond
+ * eigenproblem, truncation to D, renormalisation, lambda^-1 strip.
+ *   D, dtype      as in gpeps_create (1 <= D <= 32).
+ *   gamma_a/b     device, the two site tensors (layout of gpeps_site_layout:
+ *                 [s][leg0][leg1][leg2], last leg fastest), updated in place;
+ *                 aligned to their element size, distinct.
+ *   deg_a/b       degrees (1..3, not both 3); leg_a/b: position of the bond leg.
+ *   lam           device float64[5][D]: row 0 lambda of the bond (replaced by
+ *                 the new one, unsorted), rows 1-2 lambda of a's other legs in
+ *                 leg order, rows 3-4 those of b (rows past the degree unused).
+ *   theta         host float64[2] or NULL: kick angles exp(-i theta X/2) applied
+ *                 to a and b before the gate (0 = none).
+ *   stream        cudaStream_t or NULL; flags_out: host or NULL; when given the
+ *                 call synchronises the stream and stores the GPEPS_FLAG_* bits.
+ * Scratch: a file-scope device array of GPEPS_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading this library holds until the process exits; enough for D <= 32
+ * in either dtype (larger sizes return GPEPS_EINVAL).  The first call on a
+ * device, with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress) and opts the kernels in to their shared memory; make
+ * that first call before any stream capture.  Every call shares the array and
+ * it keeps the last call's contents: calls whose work overlaps on the GPU (on
+ * different streams, or from several threads) race and must be serialised by
+ * the caller.  No cudaMalloc, cudaFree or allocating library call is made.
+ */
+#define GPEPS_NOALLOC_SCRATCH_BYTES (1u << 20)
+int gpeps_bond_update_noalloc(int32_t D, int32_t dtype, void* gamma_a, int32_t deg_a, int32_t leg_a,
+                              void* gamma_b, int32_t deg_b, int32_t leg_b, double* lam, const double* theta,
+                              void* stream, int32_t* flags_out);
+
 int gpeps_destroy(gpeps_handle* h);
 const char* gpeps_error_string(int status);
 const char* gpeps_last_cuda_error(void);
