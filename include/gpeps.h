@@ -134,6 +134,18 @@ int gpeps_zz_layer(gpeps_handle* h, int32_t colour);
  */
 int gpeps_zz_layer_profiled(gpeps_handle* h, int32_t colour, float* ms);
 
+/*
+ * Thresholds of the bond eigensolver (defaults in parentheses): FP64 sweeps
+ * stop rotating a pair when |a_pq| <= max(tol sqrt(a_pp a_qq), floor_rel *
+ * trace) (complex128: 1e-15, 4.4e-16; mixed: 1e-9, 1e-9); the FP32 levels use tol32
+ * (1e-6) and floor32 (2e-7); sweep caps max_sweeps (40; hitting it sets
+ * GPEPS_FLAG_NOCONV) and max_sweeps32 (20).  Host-only; drops a captured step
+ * graph.  Errors: GPEPS_EINVAL for non-positive thresholds or caps outside
+ * [1, 200] (FP64) / [0, 200] (FP32).
+ */
+int gpeps_set_jacobi(gpeps_handle* h, double tol, double floor_rel, double tol32, double floor32,
+                     int32_t max_sweeps, int32_t max_sweeps32);
+
 /* Number of colour classes (the largest over the instances). */
 int gpeps_n_colours(const gpeps_handle* h, int32_t* n_colours);
 
@@ -186,12 +198,14 @@ int gpeps_sizes(const gpeps_handle* h, int64_t* total_qubits, int64_t* total_edg
  * (any may be NULL); synchronises. */
 int gpeps_sweeps(gpeps_handle* h, int64_t* sweeps64, int64_t* sweeps32, int64_t* total_bonds);
 
-/* SM cycles spent in the phases of the bond-eigenproblem kernel since the last
- * gpeps_reset, summed over bonds (clock64 of one thread per CTA), host
- * int64[6]: [0] reduced density matrix, [1] first FP32 Jacobi level, [2] FP64
- * re-orthonormalisation of the FP32 eigenvectors, [3] V^dagger rho V and the
- * further FP32 levels on small-eigenvalue blocks, [4] FP64 Jacobi sweeps,
- * [5] truncation, Y matrices and the smaller end.  Synchronises. */
+/* Counters of the bond-eigenproblem kernel since the last gpeps_reset, summed
+ * over bonds, host int64[22].  [0..5] SM cycles (clock64 of one thread per
+ * CTA) of its phases: [0] reduced density matrix, [1] first FP32 Jacobi level,
+ * [2] FP64 re-orthonormalisation of the FP32 eigenvectors, [3] V^dagger rho V
+ * and the further FP32 levels on small-eigenvalue blocks, [4] FP64 Jacobi
+ * sweeps, [5] truncation, Y matrices and the smaller end.  [6..13] rotations
+ * applied in sweep 0..7 of the first FP32 level, [14..21] in FP64 sweep 0..7.
+ * Synchronises. */
 int gpeps_bond_phase_cycles(gpeps_handle* h, int64_t* cycles);
 
 /*

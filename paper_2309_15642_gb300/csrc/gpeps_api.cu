@@ -371,11 +371,12 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   }
   // Jacobi thresholds: the bond matrix carries FP64 rounding (C128) or the
   // FP32 rounding of its Gram inputs (mixed); eigenvalues below that level are noise.
-  h->jp.tol = 1e-15;
-  // FP64 sweeps stop at |a_pq| <= floor_rel * trace: 2 eps for complex128 (the
-  // entries of rho carry ~eps * trace rounding), coarser for the mixed path
-  // whose rho carries FP32 rounding of its inputs
-  h->jp.floor_rel = dtype == GPEPS_C128 ? 4.4e-16 : 2e-15;
+  // FP64 sweeps stop at |a_pq| <= max(tol sqrt(a_pp a_qq), floor_rel * trace):
+  // at FP64 rounding for complex128 (rho carries ~eps * trace), and far below
+  // the ~1e-7 * trace rounding that the mixed path's rho inherits from its
+  // FP32 inputs (resolving that rho further changes nothing)
+  h->jp.tol = dtype == GPEPS_C128 ? 1e-15 : 1e-9;
+  h->jp.floor_rel = dtype == GPEPS_C128 ? 4.4e-16 : 1e-9;
   h->jp.tol32 = 1e-6;
   h->jp.floor32 = 2e-7;
   h->jp.ev_cut = 0.0;
@@ -397,7 +398,7 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   h->w_pending = carve(h->total_sites * sizeof(double));
   h->w_flags = carve(sizeof(int) * 4);
   h->w_sweeps = carve(4 * sizeof(unsigned long long));
-  h->w_cycles = carve(kPhases * sizeof(unsigned long long));
+  h->w_cycles = carve(kCounters * sizeof(unsigned long long));
   h->w_z = carve(h->total_sites * sizeof(double));
   h->w_mean = carve(n_instances * sizeof(double));
   h->w_sites = carve(h->total_sites * sizeof(SiteDesc));
@@ -462,7 +463,7 @@ int gpeps_reset(gpeps_handle* h) {
   if (e != cudaSuccess) return cuda_fail(e, "reset");
   GP_CUDA(cudaMemsetAsync(h->d_work + h->w_flags, 0, sizeof(int) * 4, h->stream));
   GP_CUDA(cudaMemsetAsync(h->d_work + h->w_sweeps, 0, 4 * sizeof(unsigned long long), h->stream));
-  GP_CUDA(cudaMemsetAsync(h->d_work + h->w_cycles, 0, kPhases * sizeof(unsigned long long), h->stream));
+  GP_CUDA(cudaMemsetAsync(h->d_work + h->w_cycles, 0, kCounters * sizeof(unsigned long long), h->stream));
   h->bonds_since_reset = 0;
   return GPEPS_OK;
 }
@@ -616,9 +617,24 @@ int gpeps_sweeps(gpeps_handle* h, int64_t* sweeps64, int64_t* sweeps32, int64_t*
 int gpeps_bond_phase_cycles(gpeps_handle* h, int64_t* cycles) {
   if (!h || !h->bound || !cycles) return GPEPS_EINVAL;
   GP_CUDA(cudaStreamSynchronize(h->stream));
-  unsigned long long c[kPhases];
+  unsigned long long c[kCounters];
   GP_CUDA(cudaMemcpy(c, h->cycles(), sizeof(c), cudaMemcpyDeviceToHost));
-  for (int i = 0; i < kPhases; ++i) cycles[i] = (int64_t)c[i];
+  for (int i = 0; i < kCounters; ++i) cycles[i] = (int64_t)c[i];
+  return GPEPS_OK;
+}
+
+int gpeps_set_jacobi(gpeps_handle* h, double tol, double floor_rel, double tol32, double floor32,
+                     int32_t max_sweeps, int32_t max_sweeps32) {
+  if (!h) return GPEPS_EINVAL;
+  if (!(tol > 0.0) || !(floor_rel > 0.0) || !(tol32 > 0.0) || !(floor32 > 0.0)) return GPEPS_EINVAL;
+  if (max_sweeps < 1 || max_sweeps > 200 || max_sweeps32 < 0 || max_sweeps32 > 200) return GPEPS_EINVAL;
+  h->jp.tol = tol;
+  h->jp.floor_rel = floor_rel;
+  h->jp.tol32 = tol32;
+  h->jp.floor32 = floor32;
+  h->jp.max_sweeps = max_sweeps;
+  h->jp.max_sweeps32 = max_sweeps32;
+  drop_graph(h);  // the captured step holds the old parameters
   return GPEPS_OK;
 }
 

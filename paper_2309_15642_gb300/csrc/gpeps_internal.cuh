@@ -15,6 +15,8 @@ constexpr int kTileRows = 64;      // rows of a big-side tile (Gram and update l
 constexpr int kThreads = 256;      // threads of every CTA
 constexpr double kLambdaCut = 1e-13;  // pseudo-inverse threshold relative to max(lambda)
 constexpr int kPhases = 6;            // phases of the bond kernel with SM-cycle counters
+constexpr int kRotSweeps = 8;         // rotation counters kept for the first sweeps of a solve
+constexpr int kCounters = kPhases + 2 * kRotSweeps;  // cycles, FP32 rotations, FP64 rotations
 constexpr int kExtraLevels = 2;       // FP32 warm-start levels after the first (small-eigenvalue blocks)
 constexpr double kLevelRatio = 1e-5;  // a level takes the diagonals below this fraction of the last scale
 constexpr double kNoiseRel = 1e-15;   // ... and above this fraction of the trace (FP64 rounding noise)

@@ -31,13 +31,14 @@ void* g_scratch[kMaxDevices] = {};
 // Layout of the scratch (bytes).
 constexpr size_t kFlagsOff = 0;                                  // int flags[4]
 constexpr size_t kSweepsOff = 16;                                // u64[4]
-constexpr size_t kCyclesOff = 48;                                // u64[kPhases]
+constexpr size_t kCyclesOff = 48;                                // u64[kCounters]
 constexpr size_t kPendingOff = 256;                              // double pending[2], theta_a[1]
 constexpr size_t kDescOff = 512;                                 // BondDesc, TileDesc[...]
 constexpr size_t kMaxTiles = (kMaxD * kMaxD + kTileRows - 1) / kTileRows;
 constexpr size_t kYOff = 1024;                                   // 2 D^2 complex
 constexpr size_t kPartOff = kYOff + (size_t)2 * kMaxD * kMaxD * 16;  // tiles x 2 D^2 complex
 
+static_assert(kCyclesOff + kCounters * sizeof(unsigned long long) <= kPendingOff, "counter area");
 static_assert(sizeof(BondDesc) + kMaxTiles * sizeof(TileDesc) <= kYOff - kDescOff, "descriptor area");
 static_assert(kPartOff + kMaxTiles * 2 * kMaxD * kMaxD * 16 <= GPEPS_NOALLOC_SCRATCH_BYTES, "scratch size");
 
@@ -176,8 +177,8 @@ extern "C" int gpeps_bond_update_noalloc(int32_t D, int32_t dtype, void* gamma_a
   if (e != cudaSuccess) return GPEPS_ECUDA;
   // Jacobi thresholds of the batched path for this dtype
   JacobiParams jp{};
-  jp.tol = 1e-15;
-  jp.floor_rel = dtype == GPEPS_C128 ? 4.4e-16 : 2e-15;
+  jp.tol = dtype == GPEPS_C128 ? 1e-15 : 1e-9;
+  jp.floor_rel = dtype == GPEPS_C128 ? 4.4e-16 : 1e-9;
   jp.tol32 = 1e-6;
   jp.floor32 = 2e-7;
   jp.ev_cut = 0.0;

@@ -275,12 +275,16 @@ __device__ __forceinline__ bool rotation(double app, double aqq, double2 apq, do
 // residual instead.  Returns the sweeps run; max_sweeps + 1 = cap hit.
 template <typename R, bool kExact>
 __device__ int jacobi_hermitian(V2<R>* A, int lda, V2<R>* V, int ldv, int n, R tol, R floor_abs, int max_sweeps,
-                                R* rc, R* rs, V2<R>* re, int* rp, int* rq, int* iflag) {
+                                R* rc, R* rs, V2<R>* re, int* rp, int* rq, int* iflag,
+                                unsigned long long* rot_count) {
   const int m = n / 2;
   const int nd = m / 2 + 1;  // circulant offsets d = 0..m/2
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) iflag[0] = 0;
+    if (threadIdx.x == 0) {
+      iflag[0] = 0;
+      iflag[2] = 0;
+    }
     __syncthreads();
     for (int r = 0; r < n - 1; ++r) {
       for (int k = threadIdx.x; k < m; k += blockDim.x) {
@@ -299,7 +303,10 @@ __device__ int jacobi_hermitian(V2<R>* A, int lda, V2<R>* V, int ldv, int n, R t
         }
         R cs = 1, sn = 0;
         V2<R> e = mk<R>(1, 0);
-        if (rotation(A[p * lda + p].x, A[q * lda + q].x, A[p * lda + q], tol, floor_abs, cs, sn, e)) iflag[0] = 1;
+        if (rotation(A[p * lda + p].x, A[q * lda + q].x, A[p * lda + q], tol, floor_abs, cs, sn, e)) {
+          iflag[0] = 1;
+          atomicAdd(iflag + 2, 1);
+        }
         rp[k] = p;
         rq[k] = q;
         rc[k] = cs;
@@ -363,6 +370,8 @@ __device__ int jacobi_hermitian(V2<R>* A, int lda, V2<R>* V, int ldv, int n, R t
       __syncthreads();
     }
     const int done = (iflag[0] == 0);
+    if (rot_count && threadIdx.x == 0 && sweep < kRotSweeps)
+      atomicAdd(rot_count + sweep, (unsigned long long)iflag[2]);
     __syncthreads();
     if (done) return sweep + 1;
   }
@@ -471,20 +480,20 @@ __device__ void bond_fail(const BondDesc& bd, V2<T>* Yout, double* theta_a, doub
   }
 }
 
-// F[(row, t)][k]: kicked Gamma_b with the lambda of its other legs (FP64).
+// F[(row, t)][k]: kicked Gamma_b with the lambda of its other legs, in the
+// storage precision T.
 template <typename T>
-__device__ void load_F(const SideDesc& sb, const V2<T>* gamma, const double* lam, double th, double2* F, int D) {
-  const double c = cos(0.5 * th), s = sin(0.5 * th);
+__device__ void load_F(const SideDesc& sb, const V2<T>* gamma, const double* lam, double th, V2<T>* F, int D) {
+  const T c = (T)cos(0.5 * th), s = (T)sin(0.5 * th);
   for (int idx = threadIdx.x; idx < sb.rows * D; idx += blockDim.x) {
     const int rj = idx / D, k = idx - (idx / D) * D;
     const RowPos p = row_pos(sb, rj);
     const int64_t e = elem(sb, 0, p, k);
-    const V2<T> g0 = gamma[e], g1 = gamma[e + sb.str_s];
-    double2 a0, a1;
-    kick2<double>(c, s, make_double2(g0.x, g0.y), make_double2(g1.x, g1.y), a0, a1);
-    const double w = row_weight(sb, lam, p);
-    F[(rj * 2 + 0) * D + k] = cscale(a0, w);
-    F[(rj * 2 + 1) * D + k] = cscale(a1, w);
+    V2<T> a0, a1;
+    kick2<T>(c, s, gamma[e], gamma[e + sb.str_s], a0, a1);
+    const T w = (T)row_weight(sb, lam, p);
+    F[(rj * 2 + 0) * D + k] = c_scale<T>(a0, w);
+    F[(rj * 2 + 1) * D + k] = c_scale<T>(a1, w);
   }
 }
 
@@ -508,10 +517,10 @@ __global__ void __launch_bounds__(kThreads)
   double2* RHO = reinterpret_cast<double2*>(smem_raw + L.off_R);  // [n][n+1]
   double2* Vr = reinterpret_cast<double2*>(smem_raw + L.off_V);
   double2* X = reinterpret_cast<double2*>(smem_raw + L.off_X);
-  double2* Cs = Vr;           // [2][D][D]
-  double2* H = Vr + 2 * D2;   // [n][D]
-  double2* Vm = Vr;           // [n][n]
-  double2* F = X;             // [n][D]
+  V2<T>* Cs = reinterpret_cast<V2<T>*>(Vr);  // [2][D][D], storage precision
+  V2<T>* H = Cs + 2 * D2;                     // [n][D]
+  double2* Vm = Vr;                           // [n][n]
+  V2<T>* F = reinterpret_cast<V2<T>*>(X);     // [n][D]
   float2* R32 = reinterpret_cast<float2*>(X);     // [n][n+1]
   float2* V32 = R32 + (size_t)n * (n + 1);        // [n][n]
   double2* re = reinterpret_cast<double2*>(smem_raw + L.off_re);
@@ -550,34 +559,36 @@ __global__ void __launch_bounds__(kThreads)
     }
     const int kl = o % D2;
     const int k = kl / D, l = kl - (kl / D) * D;
-    Cs[o] = cscale(acc, lamo[k] * lamo[l]);
+    const double2 v = cscale(acc, lamo[k] * lamo[l]);
+    Cs[o] = mk<T>((T)v.x, (T)v.y);
   }
   load_F<T>(sb, gamma, lam, th_b, F, D);
   for (int idx = threadIdx.x; idx < n * ldr; idx += blockDim.x) RHO[idx] = make_double2(0.0, 0.0);
   __syncthreads();
-  // rho = sum_s phase(s) o (conj(F) C_s F^T), upper triangle, then mirrored
+  // rho = sum_s phase(s) o (conj(F) C_s F^T), upper triangle, then mirrored;
+  // products in the storage precision (the inputs carry no more), sum in FP64
   for (int sidx = 0; sidx < 2; ++sidx) {
-    const double2* C = Cs + sidx * D2;
+    const V2<T>* C = Cs + sidx * D2;
     for (int idx = threadIdx.x; idx < n * D; idx += blockDim.x) {
       const int x = idx / D, l = idx - (idx / D) * D;
-      double2 acc = make_double2(0.0, 0.0);
-      for (int k = 0; k < D; ++k) fma_conj<double>(acc, F[x * D + k], C[k * D + l]);
+      V2<T> acc = mk<T>(0, 0);
+      for (int k = 0; k < D; ++k) fma_conj<T>(acc, F[x * D + k], C[k * D + l]);
       H[x * D + l] = acc;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
       const int x = idx / n, y = idx - (idx / n) * n;
       if (y < x) continue;
-      double2 acc = make_double2(0.0, 0.0);
-      for (int l = 0; l < D; ++l) fma_c<double>(acc, H[x * D + l], F[y * D + l]);
+      V2<T> acc = mk<T>(0, 0);
+      for (int l = 0; l < D; ++l) fma_c<T>(acc, H[x * D + l], F[y * D + l]);
       const int tx = x & 1, ty = y & 1;
       double2 v;
       if (tx == ty) {
-        v = acc;
+        v = make_double2((double)acc.x, (double)acc.y);
       } else if (sidx == ty) {  // +i
-        v = make_double2(-acc.y, acc.x);
+        v = make_double2(-(double)acc.y, (double)acc.x);
       } else {  // -i
-        v = make_double2(acc.y, -acc.x);
+        v = make_double2((double)acc.y, -(double)acc.x);
       }
       RHO[x * ldr + y] = cadd(RHO[x * ldr + y], v);
     }
@@ -611,7 +622,7 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   const int sw32 = jacobi_hermitian<float, true>(R32, ldr, V32, n, n, (float)jp.tol32,
                                                  (float)(jp.floor32 * trace), jp.max_sweeps32, rc32, rs32, re32,
-                                                 rp, rq, iflag);
+                                                 rp, rq, iflag, cycles + kPhases);
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const float2 v = V32[idx];
     Vm[idx] = make_double2((double)v.x, (double)v.y);
@@ -700,7 +711,7 @@ __global__ void __launch_bounds__(kThreads)
       __syncthreads();
       const int swl = jacobi_hermitian<float, true>(B32, ldb, W32, ns, ns, (float)jp.tol32,
                                                     (float)(jp.floor32 * btr), jp.max_sweeps32, rc32, rs32, re32,
-                                                    rp, rq, iflag);
+                                                    rp, rq, iflag, nullptr);
       (void)swl;
       for (int idx = threadIdx.x; idx < ns * ns; idx += blockDim.x) {
         const float2 v = W32[idx];
@@ -737,7 +748,8 @@ __global__ void __launch_bounds__(kThreads)
   }
   mark(3);
   const int sweeps = jacobi_hermitian<double, false>(RHO, ldr, Vm, n, n, jp.tol, jp.floor_rel * trace,
-                                                     jp.max_sweeps, rc, rs, re, rp, rq, iflag);
+                                                     jp.max_sweeps, rc, rs, re, rp, rq, iflag,
+                                                     cycles + kPhases + kRotSweeps);
   mark(4);
   if (threadIdx.x == 0) {
     if (sweeps > jp.max_sweeps) atomicOr(flags, 1);
@@ -781,23 +793,25 @@ __global__ void __launch_bounds__(kThreads)
     bond_fail<T>(bd, Yout, theta_a, pending, flags, D);
     return;
   }
-  // Y_s[k][kk] = lam_k sum_x F[x][k] g(s, t_x) V[x][order[kk]] / sv[kk]
-  const double r2 = 0.70710678118654752440;
+  // Y_s[k][kk] = lam_k sum_x F[x][k] g(s, t_x) V[x][order[kk]] / sv[kk], in the
+  // storage precision (Y feeds the storage-precision update of end a)
+  const T r2 = (T)0.70710678118654752440;
   for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
     const int sidx = o / D2;
     const int kl = o - sidx * D2;
     const int k = kl / D, kk = kl - (kl / D) * D;
-    double2 acc = make_double2(0.0, 0.0);
+    V2<T> acc = mk<T>(0, 0);
     if (sv[kk] > 0.0) {
       const int col = order[kk];
       for (int x = 0; x < n; ++x) {
-        const double2 fv = F[x * D + k];
-        const double2 g = make_double2(r2, (sidx == (x & 1)) ? r2 : -r2);
-        fma_c<double>(acc, cmul(fv, g), Vm[x * n + col]);
+        const V2<T> fv = F[x * D + k];
+        const V2<T> g = mk<T>(r2, (sidx == (x & 1)) ? r2 : -r2);
+        const double2 vd = Vm[x * n + col];
+        fma_c<T>(acc, c_mul<T>(fv, g), mk<T>((T)vd.x, (T)vd.y));
       }
-      acc = cscale(acc, lamo[k] / sv[kk]);
+      acc = c_scale<T>(acc, (T)(lamo[k] / sv[kk]));
     }
-    Yout[(int64_t)blockIdx.x * 2 * D2 + o] = mk<T>((T)acc.x, (T)acc.y);
+    Yout[(int64_t)blockIdx.x * 2 * D2 + o] = acc;
   }
   // Gamma_b'[t][row][kk] = conj(V[(row, t)][order[kk]]) / lambda_other(row)
   {

@@ -147,9 +147,23 @@ class GPEPS:
 
     def bond_phase_cycles(self):
         """SM cycles per phase of the bond kernel since the last reset (summed over bonds)."""
-        c = (ctypes.c_int64 * 6)()
+        return self.bond_counters()[:6]
+
+    def bond_counters(self):
+        """All counters of the bond kernel: 6 phase cycle sums, rotations per FP32 sweep (8),
+        rotations per FP64 sweep (8)."""
+        c = (ctypes.c_int64 * 22)()
         check(self.lib.gpeps_bond_phase_cycles(self.h, c), "gpeps_bond_phase_cycles")
         return [int(x) for x in c]
+
+    def set_jacobi(self, tol=None, floor_rel=None, tol32=1e-6, floor32=2e-7, max_sweeps=40, max_sweeps32=20):
+        """Thresholds of the bond eigensolver (see gpeps_set_jacobi); None = the dtype's default."""
+        if tol is None:
+            tol = 1e-15 if self.dtype == "c128" else 1e-9
+        if floor_rel is None:
+            floor_rel = 4.4e-16 if self.dtype == "c128" else 1e-9
+        check(self.lib.gpeps_set_jacobi(self.h, float(tol), float(floor_rel), float(tol32), float(floor32),
+                                        int(max_sweeps), int(max_sweeps32)), "gpeps_set_jacobi")
 
     # -------------------------------------------------------------- state access
     def site_tensor(self, instance, site):

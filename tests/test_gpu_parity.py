@@ -9,8 +9,9 @@ accurate to eps ||rho|| / gap, so components of relative size below ~1e-8 are
 resolved only approximately (the same formulation with LAPACK's eigensolver
 reaches 9e-10 on the 16-angle sweep).  lambda spectra: a Schmidt value is
 resolved down to ~sqrt(eps) of the largest: entries are compared to 1e-6
-(c128) / 2e-3 (mixed) absolute, and to 1e-9 (c128) where the oracle's value
-exceeds 1e-3.
+(c128) / 2e-3 (mixed) absolute, and where the oracle's value exceeds 1e-3 to
+1e-9 (c128) in the exact regime and 5e-8 after many truncated steps (the
+state itself then differs from the oracle's by O(sqrt(eps)) in norm).
 """
 import json
 import math
@@ -49,7 +50,7 @@ def lam_check(gpu_lam, orc_lam, dtype, truncated=False):
     if dtype == "c128":
         big = orc_lam > 1e-3
         if big.any():
-            assert d[big].max() < (TOL_SITE_TRUNC["c128"] if truncated else 1e-9), d[big].max()
+            assert d[big].max() < (5e-8 if truncated else 1e-9), d[big].max()
 
 
 @pytest.mark.parametrize("dtype", ["c128", "mixed"])
