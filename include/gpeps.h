@@ -190,6 +190,33 @@ int gpeps_site_layout(const gpeps_handle* h, int32_t instance, int32_t site, int
                       int32_t* neighbours);
 int gpeps_lambda_layout(const gpeps_handle* h, int32_t instance, int32_t edge, int64_t* byte_offset);
 
+/*
+ * Gradient of L = sum_i c_i <Z_i> after n_steps Trotter steps with respect to
+ * per-qubit kick angles theta_i (the same angles at every step), by a
+ * hand-written reverse mode of the simple update (no counterpart in the
+ * paper).  complex128 handles with D <= 16 only.
+ *
+ * The forward applies the kicks exp(-i theta_i X_i / 2) explicitly, then the
+ * colour classes; Schmidt values whose square is <= 1e-14 of the largest are
+ * zero in both directions.  The reverse is first-order perturbation theory of
+ * the bond eigenproblem over all its eigenvectors with Lorentzian broadening
+ * 1/(e_k - e_j) -> (e_k - e_j) / ((e_k - e_j)^2 + (1e-12 e_max)^2), chained
+ * through the Gram, update, lambda renormalisation and lambda^-1 steps, the
+ * kicks and the mean-field readout.  Checkpoints: the state every ckpt_every
+ * steps; each segment is recomputed with one state snapshot per colour class.
+ *   theta:   device float64[total qubits] (instance-then-label order)
+ *   dL_dz:   device float64[total qubits] (the weights c_i), or NULL for the
+ *            forward alone
+ *   z_out:   device float64[total qubits] or NULL: <Z_i> after n_steps
+ *   dtheta:  device float64[total qubits] (required with dL_dz): dL/dtheta_i
+ *   d_grad_work: device, 256-byte aligned, >= gpeps_query_grad_workspace bytes
+ * The handle's state is left at a recomputed intermediate state.  Errors:
+ * GPEPS_EINVAL (dtype, D, sizes, pointers).
+ */
+int gpeps_query_grad_workspace(const gpeps_handle* h, int32_t n_steps, int32_t ckpt_every, size_t* bytes);
+int gpeps_grad(gpeps_handle* h, const double* theta, int32_t n_steps, int32_t ckpt_every, const double* dL_dz,
+               double* z_out, double* dtheta, void* d_grad_work, size_t grad_work_bytes);
+
 /* Totals of the batch: qubits, edges, bond updates per Trotter step. */
 int gpeps_sizes(const gpeps_handle* h, int64_t* total_qubits, int64_t* total_edges);
 

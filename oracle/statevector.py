@@ -30,14 +30,17 @@ def _zz_diagonal(m, edges, sign):
 
 
 def kicked_ising_states(m, edges, theta, steps, zz_sign=+1.0):
-    """Yield the state tensor (shape (2,)*m) after each Trotter step."""
-    th = np.broadcast_to(np.asarray(theta, dtype=np.float64), (m,))
+    """Yield the state tensor (shape (2,)*m) after each Trotter step.
+
+    ``theta``: scalar, per qubit (m,), or per step and qubit (steps, m)."""
+    th = np.asarray(theta, dtype=np.float64)
+    th = th if th.ndim == 2 else np.broadcast_to(th, (m,))[None, :].repeat(steps, axis=0)
     psi = np.zeros((2,) * m, dtype=np.complex128)
     psi[(0,) * m] = 1.0
     phase = _zz_diagonal(m, edges, zz_sign)
-    for _ in range(steps):
+    for t in range(steps):
         for q in range(m):
-            psi = np.moveaxis(np.tensordot(_rx(th[q]), psi, axes=(1, q)), 0, q)
+            psi = np.moveaxis(np.tensordot(_rx(th[t, q]), psi, axes=(1, q)), 0, q)
         psi = psi * phase
         yield psi
 

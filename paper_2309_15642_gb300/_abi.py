@@ -29,6 +29,9 @@ SIGNATURES = {
     "gpeps_site_layout": (c_int, [c_void_p, c_int32, c_int32, POINTER(c_int64), POINTER(c_int32),
                                   POINTER(c_int32)]),
     "gpeps_lambda_layout": (c_int, [c_void_p, c_int32, c_int32, POINTER(c_int64)]),
+    "gpeps_query_grad_workspace": (c_int, [c_void_p, c_int32, c_int32, POINTER(c_size_t)]),
+    "gpeps_grad": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                           c_size_t]),
     "gpeps_sizes": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
     "gpeps_sweeps": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
     "gpeps_bond_phase_cycles": (c_int, [c_void_p, POINTER(c_int64)]),

@@ -212,7 +212,7 @@ struct PhaseEvents {
 };
 
 template <typename T>
-int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr) {
+int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr, void* vsave = nullptr) {
   ColourPlan& cp = h->colours[c];
   const int nt = (int)cp.tiles.size(), nbd = (int)cp.bonds.size();
   if (nbd == 0) return GPEPS_OK;
@@ -225,7 +225,7 @@ int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr) {
   GP_CUDA(Launch<T>::gram(tiles, nt, bonds, h->gamma(), h->lam(), h->pending(), partials, h->D, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[1], h->stream));
   GP_CUDA(Launch<T>::bond(bonds, nbd, partials, h->gamma(), h->lam(), h->pending(), Y, theta_a, h->flags(),
-                          h->sweeps(), h->cycles(), h->D, h->jp, h->stream));
+                          h->sweeps(), h->cycles(), vsave, h->D, h->jp, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[2], h->stream));
   GP_CUDA(Launch<T>::update(tiles, nt, bonds, h->gamma(), h->lam(), Y, theta_a, h->D, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[3], h->stream));
@@ -233,8 +233,8 @@ int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr) {
   return GPEPS_OK;
 }
 
-int layer(gpeps_handle* h, int c, PhaseEvents* pe = nullptr) {
-  return h->dtype == GPEPS_C128 ? layer_impl<double>(h, c, pe) : layer_impl<float>(h, c, pe);
+int layer(gpeps_handle* h, int c, PhaseEvents* pe = nullptr, void* vsave = nullptr) {
+  return h->dtype == GPEPS_C128 ? layer_impl<double>(h, c, pe, vsave) : layer_impl<float>(h, c, pe, vsave);
 }
 
 int kick_impl(gpeps_handle* h, const double* theta, int per_qubit) {
@@ -635,6 +635,152 @@ int gpeps_set_jacobi(gpeps_handle* h, double tol, double floor_rel, double tol32
   h->jp.max_sweeps = max_sweeps;
   h->jp.max_sweeps32 = max_sweeps32;
   drop_graph(h);  // the captured step holds the old parameters
+  return GPEPS_OK;
+}
+
+namespace {
+
+struct GradLayout {
+  size_t ckpt = 0, snaps = 0, adj = 0, partG = 0, partY = 0, Gbar = 0, Ybuf = 0, vsave = 0, vslot = 0, total = 0;
+  int n_ckpt = 0, n_snap = 0;
+};
+
+GradLayout grad_layout(const gpeps_handle* h, int n_steps, int k) {
+  GradLayout L;
+  const size_t sb = h->state_bytes;
+  const int nc = (int)h->colours.size();
+  L.n_ckpt = (n_steps + k - 1) / k;
+  L.n_snap = nc * k;
+  size_t o = 0;
+  L.ckpt = o;
+  o += (size_t)L.n_ckpt * sb;
+  L.snaps = o;
+  o += (size_t)L.n_snap * sb;
+  L.adj = o;
+  o += sb;
+  const size_t blk = (size_t)2 * h->D * h->D * 16;
+  L.partG = o;
+  o += align256((size_t)h->max_parts * blk);
+  L.partY = o;
+  o += align256((size_t)h->max_parts * blk);
+  L.Gbar = o;
+  o += align256((size_t)h->max_bonds * blk);
+  L.Ybuf = o;
+  o += align256((size_t)h->max_bonds * blk);
+  // forward eigenvectors of every bond of every layer of a segment (2D x 2D + 2D complex per bond)
+  const size_t nm = 2 * (size_t)h->D;
+  L.vslot = align256((size_t)h->max_bonds * (nm * nm + nm) * 16);
+  L.vsave = o;
+  o += (size_t)L.n_snap * L.vslot;
+  L.total = o;
+  return L;
+}
+
+int grad_check(const gpeps_handle* h, int n_steps, int k) {
+  if (!h || h->dtype != GPEPS_C128 || h->D > kMaxGradD || n_steps < 0 || k < 1) return GPEPS_EINVAL;
+  return GPEPS_OK;
+}
+
+JacobiParams grad_jacobi(const gpeps_handle* h) {
+  JacobiParams jp = h->jp;
+  jp.ev_cut = 1e-14;  // Schmidt values <= 1e-7 of the largest are zero in both directions
+  return jp;
+}
+
+}  // namespace
+
+int gpeps_query_grad_workspace(const gpeps_handle* h, int32_t n_steps, int32_t ckpt_every, size_t* bytes) {
+  if (!bytes) return GPEPS_EINVAL;
+  const int st = grad_check(h, n_steps, ckpt_every);
+  if (st) return st;
+  *bytes = grad_layout(h, n_steps, ckpt_every).total;
+  return GPEPS_OK;
+}
+
+int gpeps_grad(gpeps_handle* h, const double* theta, int32_t n_steps, int32_t ckpt_every, const double* dL_dz,
+               double* z_out, double* dtheta, void* d_grad_work, size_t grad_work_bytes) {
+  int st = grad_check(h, n_steps, ckpt_every);
+  if (st) return st;
+  if (!h->bound || !theta || !d_grad_work || (reinterpret_cast<uintptr_t>(d_grad_work) & 255)) return GPEPS_EINVAL;
+  if (dL_dz && !dtheta) return GPEPS_EINVAL;
+  const int k = ckpt_every;
+  const GradLayout L = grad_layout(h, n_steps, k);
+  if (grad_work_bytes < L.total) return GPEPS_EINVAL;
+  char* gw = static_cast<char*>(d_grad_work);
+  const size_t sb = h->state_bytes;
+  const int nc = (int)h->colours.size();
+  const int n_sites = (int)h->total_sites;
+  const SiteDesc* sites = h->at<SiteDesc>(h->w_sites);
+  cudaStream_t s = h->stream;
+  const JacobiParams jp = grad_jacobi(h);
+  const JacobiParams saved_jp = h->jp;
+  GP_CUDA(Adjoint::init());
+  GP_CUDA(Launch<double>::init());
+  auto state_of = [&](char* base) { return std::make_pair(static_cast<void*>(base + h->s_gamma),
+                                                          reinterpret_cast<double*>(base + h->s_lam)); };
+  auto copy_state = [&](char* dst, const char* src) -> cudaError_t {
+    return cudaMemcpyAsync(dst, src, sb, cudaMemcpyDeviceToDevice, s);
+  };
+  // forward layers of the gradient path: pending kicks are zero (kicks applied explicitly)
+  auto fwd_layer = [&](int c, void* vsave) -> int {
+    h->jp = jp;
+    const int r = layer(h, c, nullptr, vsave);
+    h->jp = saved_jp;
+    return r;
+  };
+  // ---- forward with checkpoints
+  st = gpeps_reset(h);
+  if (st) return st;
+  for (int t = 0; t < n_steps; ++t) {
+    if (t % k == 0) GP_CUDA(copy_state(gw + L.ckpt + (size_t)(t / k) * sb, h->d_state));
+    GP_CUDA(Adjoint::apply_kick(sites, n_sites, h->gamma(), theta, h->D, s));
+    for (int c = 0; c < nc; ++c) {
+      st = fwd_layer(c, nullptr);
+      if (st) return st;
+    }
+  }
+  st = readout_impl(h);
+  if (st) return st;
+  if (z_out) GP_CUDA(cudaMemcpyAsync(z_out, h->z(), n_sites * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (!dL_dz) return GPEPS_OK;
+  // ---- reverse
+  char* adj = gw + L.adj;
+  GP_CUDA(cudaMemsetAsync(adj, 0, sb, s));
+  GP_CUDA(cudaMemsetAsync(dtheta, 0, n_sites * sizeof(double), s));
+  {
+    auto cur = state_of(h->d_state);
+    auto ad = state_of(adj);
+    GP_CUDA(Adjoint::readout(sites, n_sites, cur.first, cur.second, dL_dz, ad.first, ad.second, h->D, s));
+  }
+  for (int seg = L.n_ckpt - 1; seg >= 0; --seg) {
+    const int t0 = seg * k, t1 = std::min(n_steps, t0 + k);
+    GP_CUDA(copy_state(h->d_state, gw + L.ckpt + (size_t)seg * sb));
+    for (int t = t0; t < t1; ++t) {
+      GP_CUDA(Adjoint::apply_kick(sites, n_sites, h->gamma(), theta, h->D, s));
+      for (int c = 0; c < nc; ++c) {
+        const size_t slot = (size_t)((t - t0) * nc + c);
+        GP_CUDA(copy_state(gw + L.snaps + slot * sb, h->d_state));
+        st = fwd_layer(c, gw + L.vsave + slot * L.vslot);
+        if (st) return st;
+      }
+    }
+    for (int t = t1 - 1; t >= t0; --t) {
+      for (int c = nc - 1; c >= 0; --c) {
+        ColourPlan& cp = h->colours[c];
+        char* snap = gw + L.snaps + (size_t)((t - t0) * nc + c) * sb;
+        auto in = state_of(snap);
+        auto ad = state_of(adj);
+        GP_CUDA(Adjoint::layer(h->at<TileDesc>(cp.w_tiles), (int)cp.tiles.size(), h->at<BondDesc>(cp.w_bonds),
+                               (int)cp.bonds.size(), in.first, in.second, ad.first, ad.second, gw + L.partG,
+                               gw + L.partY, gw + L.Gbar, gw + L.Ybuf,
+                               gw + L.vsave + (size_t)((t - t0) * nc + c) * L.vslot, h->D, jp, s));
+      }
+      char* snap0 = gw + L.snaps + (size_t)((t - t0) * nc) * sb;
+      auto post = state_of(snap0);
+      auto ad = state_of(adj);
+      GP_CUDA(Adjoint::kick(sites, n_sites, post.first, ad.first, theta, dtheta, h->D, s));
+    }
+  }
   return GPEPS_OK;
 }
 

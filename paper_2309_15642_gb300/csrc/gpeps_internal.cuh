@@ -83,12 +83,28 @@ struct Launch {
                           const double* lam, const double* pending, void* partials, int D, cudaStream_t st);
   static cudaError_t bond(const BondDesc* bonds, int n_bonds, const void* partials, void* gamma, double* lam,
                           double* pending, void* Y, double* theta_a, int* flags,
-                          unsigned long long* sweeps, unsigned long long* cycles, int D, JacobiParams jp,
-                          cudaStream_t st);
+                          unsigned long long* sweeps, unsigned long long* cycles, void* vsave, int D,
+                          JacobiParams jp, cudaStream_t st);
   static cudaError_t update(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, void* gamma,
                             const double* lam, const void* Y, const double* theta_a, int D, cudaStream_t st);
   static cudaError_t readout(const SiteDesc* sites, int n_sites, const void* gamma, const double* lam,
                              const double* pending, double* z, int D, cudaStream_t st);
+};
+
+constexpr int kMaxGradD = 16;  // bond dimension limit of the reverse mode (shared memory of its bond kernel)
+
+// Reverse mode (complex128 only), su_kernels.cu.
+struct Adjoint {
+  static cudaError_t init();
+  static cudaError_t layer(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, int n_bonds, const void* gamma,
+                           const double* lam, void* gbar, double* lbar, void* partG, void* partY, void* Gbar,
+                           void* Ybuf, const void* vsave, int D, JacobiParams jp, cudaStream_t st);
+  static cudaError_t apply_kick(const SiteDesc* sites, int n_sites, void* gamma, const double* theta, int D,
+                                cudaStream_t st);
+  static cudaError_t kick(const SiteDesc* sites, int n_sites, const void* gamma_post, void* gbar,
+                          const double* theta, double* dtheta, int D, cudaStream_t st);
+  static cudaError_t readout(const SiteDesc* sites, int n_sites, const void* gamma, const double* lam,
+                             const double* cz, void* gbar, double* lbar, int D, cudaStream_t st);
 };
 
 cudaError_t launch_mean(const double* z, const int32_t* inst_site0, int n_inst, double* mean, cudaStream_t st);

@@ -117,7 +117,8 @@ int run(char* scratch, int D, void* base, const BondDesc& bd, int n_tiles, doubl
   void* partials = scratch + kPartOff;
   cudaError_t e = Launch<T>::gram(tiles, n_tiles, bonds, base, lam, pending, partials, D, st);
   if (e == cudaSuccess)
-    e = Launch<T>::bond(bonds, 1, partials, base, lam, pending, Y, theta_a, flags, sweeps, cycles, D, jp, st);
+    e = Launch<T>::bond(bonds, 1, partials, base, lam, pending, Y, theta_a, flags, sweeps, cycles, nullptr, D, jp,
+                        st);
   if (e == cudaSuccess) e = Launch<T>::update(tiles, n_tiles, bonds, base, lam, Y, theta_a, D, st);
   (void)bd;
   return e == cudaSuccess ? GPEPS_OK : GPEPS_ECUDA;

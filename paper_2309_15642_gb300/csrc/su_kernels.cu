@@ -463,156 +463,29 @@ __device__ double orthonormalise(double2* V, int n, double2* G, int ldg, double*
   return scal[6];
 }
 
-// A bond whose spectrum is not usable (NaN/Inf or zero norm) is left as it
-// was: Y = identity so that the update launch only applies the pending kick
-// to end a, lambda and end b untouched; the flag word reports it.
-template <typename T>
-__device__ void bond_fail(const BondDesc& bd, V2<T>* Yout, double* theta_a, double* pending, int* flags, int D) {
-  const int D2 = D * D;
-  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
-    const int kl = o % D2;
-    Yout[(int64_t)blockIdx.x * 2 * D2 + o] = mk<T>((T)((kl / D) == (kl % D) ? 1 : 0), (T)0);
-  }
-  if (threadIdx.x == 0) {
-    atomicOr(flags, 2);
-    theta_a[blockIdx.x] = pending[bd.a.site];
-    pending[bd.a.site] = 0.0;
-  }
-}
-
-// F[(row, t)][k]: kicked Gamma_b with the lambda of its other legs, in the
-// storage precision T.
-template <typename T>
-__device__ void load_F(const SideDesc& sb, const V2<T>* gamma, const double* lam, double th, V2<T>* F, int D) {
-  const T c = (T)cos(0.5 * th), s = (T)sin(0.5 * th);
-  for (int idx = threadIdx.x; idx < sb.rows * D; idx += blockDim.x) {
-    const int rj = idx / D, k = idx - (idx / D) * D;
-    const RowPos p = row_pos(sb, rj);
-    const int64_t e = elem(sb, 0, p, k);
-    V2<T> a0, a1;
-    kick2<T>(c, s, gamma[e], gamma[e + sb.str_s], a0, a1);
-    const T w = (T)row_weight(sb, lam, p);
-    F[(rj * 2 + 0) * D + k] = c_scale<T>(a0, w);
-    F[(rj * 2 + 1) * D + k] = c_scale<T>(a1, w);
-  }
-}
-
-// Bond eigenproblem: rho (FP64), eigenvectors by FP32 Jacobi to convergence
-// (the FP32 pipe is 64x the FP64 pipe on this part), FP64 Cholesky-QR of the
-// FP32 eigenvectors, rho' = V^dagger rho V and FP64 Jacobi sweeps on rho' until
-// every off-diagonal is at FP64 rounding level (mixed-precision Jacobi: a
-// low-precision eigenbasis as preconditioner of the high-precision sweeps).
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-    bond_kernel(const BondDesc* __restrict__ bonds, const V2<T>* __restrict__ partials, V2<T>* gamma,
-                double* lam, double* pending, V2<T>* __restrict__ Yout, double* __restrict__ theta_a,
-                int* flags, unsigned long long* sweeps_out, unsigned long long* cycles, int D, JacobiParams jp) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const BondDesc bd = bonds[blockIdx.x];
-  const SideDesc sb = bd.b;
-  const int nb = sb.rows;
-  const int n = 2 * nb;
-  const int D2 = D * D;
-  const BondSmem L(D, n);
-  double2* RHO = reinterpret_cast<double2*>(smem_raw + L.off_R);  // [n][n+1]
-  double2* Vr = reinterpret_cast<double2*>(smem_raw + L.off_V);
-  double2* X = reinterpret_cast<double2*>(smem_raw + L.off_X);
-  V2<T>* Cs = reinterpret_cast<V2<T>*>(Vr);  // [2][D][D], storage precision
-  V2<T>* H = Cs + 2 * D2;                     // [n][D]
-  double2* Vm = Vr;                           // [n][n]
-  V2<T>* F = reinterpret_cast<V2<T>*>(X);     // [n][D]
-  float2* R32 = reinterpret_cast<float2*>(X);     // [n][n+1]
-  float2* V32 = R32 + (size_t)n * (n + 1);        // [n][n]
-  double2* re = reinterpret_cast<double2*>(smem_raw + L.off_re);
-  float2* re32 = reinterpret_cast<float2*>(smem_raw + L.off_re32);
-  double* lamo = reinterpret_cast<double*>(smem_raw + L.off_lamo);
-  double* ev = reinterpret_cast<double*>(smem_raw + L.off_ev);
-  double* sv = reinterpret_cast<double*>(smem_raw + L.off_sv);
-  double* rc = reinterpret_cast<double*>(smem_raw + L.off_rc);
-  double* rs = reinterpret_cast<double*>(smem_raw + L.off_rs);
-  double* scal = reinterpret_cast<double*>(smem_raw + L.off_scal);  // [0] trace [1] norm [2] max lambda_o [4] tmp
-  float* rc32 = reinterpret_cast<float*>(smem_raw + L.off_rc32);
-  float* rs32 = reinterpret_cast<float*>(smem_raw + L.off_rs32);
-  int* order = reinterpret_cast<int*>(smem_raw + L.off_int);
-  int* rp = order + n;
-  int* rq = rp + n / 2;
-  int* iflag = rq + n / 2;  // [4]
+// Mixed-precision Jacobi eigensolver of the Hermitian n x n matrix RHO (FP64,
+// row stride n+1, trace > 0) in shared memory: FP32 sweeps to convergence on a
+// rounded copy, FP64 re-orthonormalisation of their eigenvectors, rho' =
+// V^dagger rho V in FP64, further FP32 levels on rescaled small-eigenvalue
+// blocks, FP64 sweeps to the thresholds of jp.  On return RHO is diagonal (the
+// eigenvalues) and Vm [n][n] holds the eigenvectors.  X is scratch of
+// max(n(n+1), n D) complex doubles; the small arrays as in bond_kernel.
+// Returns the FP64 sweeps (max_sweeps + 1 = cap hit).
+__device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, double trace, const JacobiParams& jp,
+                         double2* re, float2* re32, double* ev, double* rc, double* rs, double* scal, float* rc32,
+                         float* rs32, int* order, int* rp, int* rq, int* iflag, unsigned long long* sweeps_out,
+                         unsigned long long* cycles, int* flags, long long& t_prev) {
   const int ldr = n + 1;
-  const double th_b = pending[sb.site];
-  long long t_prev = clock64();
+  float2* R32 = reinterpret_cast<float2*>(X);  // [n][n+1]
+  float2* V32 = R32 + (size_t)n * (n + 1);     // [n][n]
   auto mark = [&](int phase) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && cycles) {
       const long long t = clock64();
       atomicAdd(cycles + phase, (unsigned long long)(t - t_prev));
       t_prev = t;
     }
   };
-
-  for (int k = threadIdx.x; k < D; k += blockDim.x) lamo[k] = lam[bd.lam_e + k];
-  __syncthreads();
-  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
-    for (int p = 0; p < bd.n_parts; ++p) {
-      const V2<T> v = partials[(int64_t)(bd.part0 + p) * 2 * D2 + o];
-      acc.x += (double)v.x;
-      acc.y += (double)v.y;
-    }
-    const int kl = o % D2;
-    const int k = kl / D, l = kl - (kl / D) * D;
-    const double2 v = cscale(acc, lamo[k] * lamo[l]);
-    Cs[o] = mk<T>((T)v.x, (T)v.y);
-  }
-  load_F<T>(sb, gamma, lam, th_b, F, D);
-  for (int idx = threadIdx.x; idx < n * ldr; idx += blockDim.x) RHO[idx] = make_double2(0.0, 0.0);
-  __syncthreads();
-  // rho = sum_s phase(s) o (conj(F) C_s F^T), upper triangle, then mirrored;
-  // products in the storage precision (the inputs carry no more), sum in FP64
-  for (int sidx = 0; sidx < 2; ++sidx) {
-    const V2<T>* C = Cs + sidx * D2;
-    for (int idx = threadIdx.x; idx < n * D; idx += blockDim.x) {
-      const int x = idx / D, l = idx - (idx / D) * D;
-      V2<T> acc = mk<T>(0, 0);
-      for (int k = 0; k < D; ++k) fma_conj<T>(acc, F[x * D + k], C[k * D + l]);
-      H[x * D + l] = acc;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      const int x = idx / n, y = idx - (idx / n) * n;
-      if (y < x) continue;
-      V2<T> acc = mk<T>(0, 0);
-      for (int l = 0; l < D; ++l) fma_c<T>(acc, H[x * D + l], F[y * D + l]);
-      const int tx = x & 1, ty = y & 1;
-      double2 v;
-      if (tx == ty) {
-        v = make_double2((double)acc.x, (double)acc.y);
-      } else if (sidx == ty) {  // +i
-        v = make_double2(-(double)acc.y, (double)acc.x);
-      } else {  // -i
-        v = make_double2((double)acc.y, -(double)acc.x);
-      }
-      RHO[x * ldr + y] = cadd(RHO[x * ldr + y], v);
-    }
-    __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int x = idx / n, y = idx - (idx / n) * n;
-    if (y > x) RHO[y * ldr + x] = cconj(RHO[x * ldr + y]);
-    if (y == x) RHO[x * ldr + x].y = 0.0;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += RHO[i * ldr + i].x;
-    scal[0] = tr;
-  }
-  __syncthreads();
-  const double trace = scal[0];
-  if (!(trace > 0.0) || !isfinite(trace)) {
-    bond_fail<T>(bd, Yout, theta_a, pending, flags, D);
-    return;
-  }
-  mark(0);
-  // FP32 Jacobi on a rounded copy (F is reloaded at the end)
+  // FP32 Jacobi on a rounded copy
   for (int idx = threadIdx.x; idx < n * ldr; idx += blockDim.x) {
     const double2 v = RHO[idx];
     R32[idx] = make_float2((float)v.x, (float)v.y);
@@ -622,7 +495,7 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   const int sw32 = jacobi_hermitian<float, true>(R32, ldr, V32, n, n, (float)jp.tol32,
                                                  (float)(jp.floor32 * trace), jp.max_sweeps32, rc32, rs32, re32,
-                                                 rp, rq, iflag, cycles + kPhases);
+                                                 rp, rq, iflag, cycles ? cycles + kPhases : nullptr);
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const float2 v = V32[idx];
     Vm[idx] = make_double2((double)v.x, (double)v.y);
@@ -749,13 +622,166 @@ __global__ void __launch_bounds__(kThreads)
   mark(3);
   const int sweeps = jacobi_hermitian<double, false>(RHO, ldr, Vm, n, n, jp.tol, jp.floor_rel * trace,
                                                      jp.max_sweeps, rc, rs, re, rp, rq, iflag,
-                                                     cycles + kPhases + kRotSweeps);
+                                                     cycles ? cycles + kPhases + kRotSweeps : nullptr);
   mark(4);
   if (threadIdx.x == 0) {
     if (sweeps > jp.max_sweeps) atomicOr(flags, 1);
     atomicAdd(sweeps_out, (unsigned long long)(sweeps > jp.max_sweeps ? jp.max_sweeps : sweeps));
     atomicAdd(sweeps_out + 1, (unsigned long long)(sw32 > jp.max_sweeps32 ? jp.max_sweeps32 : sw32));
   }
+  return sweeps;
+}
+
+// A bond whose spectrum is not usable (NaN/Inf or zero norm) is left as it
+// was: Y = identity so that the update launch only applies the pending kick
+// to end a, lambda and end b untouched; the flag word reports it.
+template <typename T>
+__device__ void bond_fail(const BondDesc& bd, V2<T>* Yout, double* theta_a, double* pending, int* flags, int D) {
+  const int D2 = D * D;
+  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
+    const int kl = o % D2;
+    Yout[(int64_t)blockIdx.x * 2 * D2 + o] = mk<T>((T)((kl / D) == (kl % D) ? 1 : 0), (T)0);
+  }
+  if (threadIdx.x == 0) {
+    atomicOr(flags, 2);
+    theta_a[blockIdx.x] = pending[bd.a.site];
+    pending[bd.a.site] = 0.0;
+  }
+}
+
+// F[(row, t)][k]: kicked Gamma_b with the lambda of its other legs, in the
+// storage precision T.
+template <typename T>
+__device__ void load_F(const SideDesc& sb, const V2<T>* gamma, const double* lam, double th, V2<T>* F, int D) {
+  const T c = (T)cos(0.5 * th), s = (T)sin(0.5 * th);
+  for (int idx = threadIdx.x; idx < sb.rows * D; idx += blockDim.x) {
+    const int rj = idx / D, k = idx - (idx / D) * D;
+    const RowPos p = row_pos(sb, rj);
+    const int64_t e = elem(sb, 0, p, k);
+    V2<T> a0, a1;
+    kick2<T>(c, s, gamma[e], gamma[e + sb.str_s], a0, a1);
+    const T w = (T)row_weight(sb, lam, p);
+    F[(rj * 2 + 0) * D + k] = c_scale<T>(a0, w);
+    F[(rj * 2 + 1) * D + k] = c_scale<T>(a1, w);
+  }
+}
+
+// Bond eigenproblem: rho (FP64), eigenvectors by FP32 Jacobi to convergence
+// (the FP32 pipe is 64x the FP64 pipe on this part), FP64 Cholesky-QR of the
+// FP32 eigenvectors, rho' = V^dagger rho V and FP64 Jacobi sweeps on rho' until
+// every off-diagonal is at FP64 rounding level (mixed-precision Jacobi: a
+// low-precision eigenbasis as preconditioner of the high-precision sweeps).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    bond_kernel(const BondDesc* __restrict__ bonds, const V2<T>* __restrict__ partials, V2<T>* gamma,
+                double* lam, double* pending, V2<T>* __restrict__ Yout, double* __restrict__ theta_a,
+                int* flags, unsigned long long* sweeps_out, unsigned long long* cycles, double2* vsave, int D,
+                JacobiParams jp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BondDesc bd = bonds[blockIdx.x];
+  const SideDesc sb = bd.b;
+  const int nb = sb.rows;
+  const int n = 2 * nb;
+  const int D2 = D * D;
+  const BondSmem L(D, n);
+  double2* RHO = reinterpret_cast<double2*>(smem_raw + L.off_R);  // [n][n+1]
+  double2* Vr = reinterpret_cast<double2*>(smem_raw + L.off_V);
+  double2* X = reinterpret_cast<double2*>(smem_raw + L.off_X);
+  V2<T>* Cs = reinterpret_cast<V2<T>*>(Vr);  // [2][D][D], storage precision
+  V2<T>* H = Cs + 2 * D2;                     // [n][D]
+  double2* Vm = Vr;                           // [n][n]
+  V2<T>* F = reinterpret_cast<V2<T>*>(X);     // [n][D]
+  double2* re = reinterpret_cast<double2*>(smem_raw + L.off_re);
+  float2* re32 = reinterpret_cast<float2*>(smem_raw + L.off_re32);
+  double* lamo = reinterpret_cast<double*>(smem_raw + L.off_lamo);
+  double* ev = reinterpret_cast<double*>(smem_raw + L.off_ev);
+  double* sv = reinterpret_cast<double*>(smem_raw + L.off_sv);
+  double* rc = reinterpret_cast<double*>(smem_raw + L.off_rc);
+  double* rs = reinterpret_cast<double*>(smem_raw + L.off_rs);
+  double* scal = reinterpret_cast<double*>(smem_raw + L.off_scal);  // [0] trace [1] norm [2] max lambda_o [4] tmp
+  float* rc32 = reinterpret_cast<float*>(smem_raw + L.off_rc32);
+  float* rs32 = reinterpret_cast<float*>(smem_raw + L.off_rs32);
+  int* order = reinterpret_cast<int*>(smem_raw + L.off_int);
+  int* rp = order + n;
+  int* rq = rp + n / 2;
+  int* iflag = rq + n / 2;  // [4]
+  const int ldr = n + 1;
+  const double th_b = pending[sb.site];
+  long long t_prev = clock64();
+  auto mark = [&](int phase) {
+    if (threadIdx.x == 0) {
+      const long long t = clock64();
+      atomicAdd(cycles + phase, (unsigned long long)(t - t_prev));
+      t_prev = t;
+    }
+  };
+
+  for (int k = threadIdx.x; k < D; k += blockDim.x) lamo[k] = lam[bd.lam_e + k];
+  __syncthreads();
+  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int p = 0; p < bd.n_parts; ++p) {
+      const V2<T> v = partials[(int64_t)(bd.part0 + p) * 2 * D2 + o];
+      acc.x += (double)v.x;
+      acc.y += (double)v.y;
+    }
+    const int kl = o % D2;
+    const int k = kl / D, l = kl - (kl / D) * D;
+    const double2 v = cscale(acc, lamo[k] * lamo[l]);
+    Cs[o] = mk<T>((T)v.x, (T)v.y);
+  }
+  load_F<T>(sb, gamma, lam, th_b, F, D);
+  for (int idx = threadIdx.x; idx < n * ldr; idx += blockDim.x) RHO[idx] = make_double2(0.0, 0.0);
+  __syncthreads();
+  // rho = sum_s phase(s) o (conj(F) C_s F^T), upper triangle, then mirrored;
+  // products in the storage precision (the inputs carry no more), sum in FP64
+  for (int sidx = 0; sidx < 2; ++sidx) {
+    const V2<T>* C = Cs + sidx * D2;
+    for (int idx = threadIdx.x; idx < n * D; idx += blockDim.x) {
+      const int x = idx / D, l = idx - (idx / D) * D;
+      V2<T> acc = mk<T>(0, 0);
+      for (int k = 0; k < D; ++k) fma_conj<T>(acc, F[x * D + k], C[k * D + l]);
+      H[x * D + l] = acc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int x = idx / n, y = idx - (idx / n) * n;
+      if (y < x) continue;
+      V2<T> acc = mk<T>(0, 0);
+      for (int l = 0; l < D; ++l) fma_c<T>(acc, H[x * D + l], F[y * D + l]);
+      const int tx = x & 1, ty = y & 1;
+      double2 v;
+      if (tx == ty) {
+        v = make_double2((double)acc.x, (double)acc.y);
+      } else if (sidx == ty) {  // +i
+        v = make_double2(-(double)acc.y, (double)acc.x);
+      } else {  // -i
+        v = make_double2((double)acc.y, -(double)acc.x);
+      }
+      RHO[x * ldr + y] = cadd(RHO[x * ldr + y], v);
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int x = idx / n, y = idx - (idx / n) * n;
+    if (y > x) RHO[y * ldr + x] = cconj(RHO[x * ldr + y]);
+    if (y == x) RHO[x * ldr + x].y = 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += RHO[i * ldr + i].x;
+    scal[0] = tr;
+  }
+  __syncthreads();
+  const double trace = scal[0];
+  if (!(trace > 0.0) || !isfinite(trace)) {
+    bond_fail<T>(bd, Yout, theta_a, pending, flags, D);
+    return;
+  }
+  mark(0);
+  eig_mixed(RHO, Vm, X, n, D, trace, jp, re, re32, ev, rc, rs, scal, rc32, rs32, order, rp, rq, iflag, sweeps_out,
+            cycles, flags, t_prev);
   // eigenvalues sorted in decreasing order (ties by index)
   for (int i = threadIdx.x; i < n; i += blockDim.x) ev[i] = RHO[i * ldr + i].x;
   __syncthreads();
@@ -766,6 +792,15 @@ __global__ void __launch_bounds__(kThreads)
     order[rank] = i;
   }
   __syncthreads();
+  if (vsave) {  // sorted eigenvectors and eigenvalues for the reverse mode (slot of 2D x 2D + 2D)
+    const int nm = 2 * D;
+    double2* vs = vsave + (int64_t)blockIdx.x * (nm * nm + nm);
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int x = idx / n, j = idx - (idx / n) * n;
+      vs[x * n + j] = Vm[x * n + order[j]];
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) vs[n * n + j] = make_double2(ev[order[j]], 0.0);
+  }
   const int keep = n < D ? n : D;
   if (threadIdx.x == 0) {
     const double emax = ev[order[0]];
@@ -1051,12 +1086,13 @@ cudaError_t Launch<T>::gram(const TileDesc* tiles, int n_tiles, const BondDesc* 
 template <typename T>
 cudaError_t Launch<T>::bond(const BondDesc* bonds, int n_bonds, const void* partials, void* gamma, double* lam,
                             double* pending, void* Y, double* theta_a, int* flags, unsigned long long* sweeps,
-                            unsigned long long* cycles, int D, JacobiParams jp, cudaStream_t st) {
+                            unsigned long long* cycles, void* vsave, int D, JacobiParams jp, cudaStream_t st) {
   if (n_bonds == 0) return cudaSuccess;
   const size_t sm = bond_smem_bytes(D, 2 * D);
   bond_kernel<T><<<n_bonds, kThreads, sm, st>>>(bonds, static_cast<const V2<T>*>(partials),
                                                  static_cast<V2<T>*>(gamma), lam, pending,
-                                                 static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles, D, jp);
+                                                 static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles,
+                                                 static_cast<double2*>(vsave), D, jp);
   return cudaGetLastError();
 }
 
@@ -1086,5 +1122,705 @@ cudaError_t launch_mean(const double* z, const int32_t* inst_site0, int n_inst, 
 
 template struct Launch<float>;
 template struct Launch<double>;
+
+// ============================================================================
+// Reverse mode (gradient of a weighted sum of <Z_i> with respect to the kick
+// angles), complex128, D <= kMaxGradD.  Convention: for a real loss L and a
+// complex variable z, zbar = dL/dRe z + i dL/dIm z; for z = a w with a fixed,
+// wbar = conj(a) zbar.  The forward of the gradient path applies the kicks
+// explicitly (no kick is fused into a bond) and treats Schmidt values whose
+// square is <= jp.ev_cut of the largest as zero, in both directions.
+//
+// One colour layer is reversed by three launches that mirror the forward:
+//   adj_tile    per tile of the larger end a: the Gram partials of the forward
+//               and Ybar_s = sum_r conj(A~[r][s][k]) Gbar'[r][s][l]
+//   adj_bond    per bond: recompute the bond eigenproblem, then
+//               Gbar_b' -> Vbar, w_b-bar;  Ybar -> lambda-bar, Vbar, sbar, Fbar;
+//               lambda'-bar -> sbar;  sbar -> Ebar = sbar / 2s;
+//               (Ebar, Vbar) -> rhobar = (M + M^H)/2,
+//               M = V (diag(Ebar) + K) V^H, K_kj = (vbar_k^H v_j) (e_k - e_j) /
+//               ((e_k - e_j)^2 + eps^2) over every eigenvector j (Lorentzian-
+//               broadened first-order perturbation theory);
+//               rho = sum_s B_s^H C_s B_s (B_s = F^T diag g(s,.)) ->
+//               Cbar_s = B_s rhobar B_s^H, Bbar_s = 2 C_s B_s rhobar -> Fbar;
+//               C_s = Lambda G_s Lambda -> Gbar_s, lambda-bar;  F -> Gbar_b, w_b-bar
+//   adj_update  per tile of a: A~bar = mask (Gbar' Y_s^H) + 2 w^2 A~ Gbar_s,
+//               w-bar -> lambda-bar of a's other legs
+// ============================================================================
+
+struct AdjSmem {
+  size_t off_R, off_V, off_X, off_F, off_Gs, off_Cs, off_Yb, off_Ym, off_Vb, off_Fb, off_M, off_T1, off_re,
+      off_re32, off_lamo, off_ev, off_sv, off_rc, off_rs, off_scal, off_lbe, off_svb, off_eb, off_wbb, off_rc32,
+      off_rs32, off_int, total;
+  __host__ __device__ AdjSmem(int D, int n) {
+    const int m = n / 2;
+    size_t x = (size_t)n * (n + 1);
+    if ((size_t)n * D > x) x = (size_t)n * D;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+      const size_t r = o;
+      o += (bytes + 15) & ~(size_t)15;
+      return r;
+    };
+    off_R = take((size_t)n * (n + 1) * 16);
+    off_V = take((size_t)n * n * 16);
+    off_X = take(x * 16);
+    off_F = take((size_t)n * D * 16);
+    off_Gs = take((size_t)2 * D * D * 16);
+    off_Cs = take((size_t)2 * D * D * 16);
+    off_Yb = take((size_t)2 * D * D * 16);
+    off_Ym = take((size_t)2 * D * D * 16);
+    off_Vb = take((size_t)n * D * 16);
+    off_Fb = take((size_t)n * D * 16);
+    // M holds K and M (n x n) and Cbar_s (D x D); T1 holds Xbar (D x D) and B_s rhobar (D x n)
+    off_M = take((size_t)(n * n > D * D ? n * n : D * D) * 16);
+    off_T1 = take((size_t)(D * n > D * D ? D * n : D * D) * 16);
+    off_re = take((size_t)m * 16);
+    off_re32 = take((size_t)m * 8);
+    off_lamo = take((size_t)D * 8);
+    off_ev = take((size_t)n * 8);
+    off_sv = take((size_t)D * 8);
+    off_rc = take((size_t)m * 8);
+    off_rs = take((size_t)m * 8);
+    off_scal = take(8 * 8);
+    off_lbe = take((size_t)D * 8);
+    off_svb = take((size_t)D * 8);
+    off_eb = take((size_t)n * 8);
+    off_wbb = take((size_t)n * 8);
+    off_rc32 = take((size_t)m * 4);
+    off_rs32 = take((size_t)m * 4);
+    off_int = take((size_t)(n + 2 * m + 8) * 4);
+    total = o;
+  }
+};
+
+size_t adj_bond_smem_bytes(int D, int n) { return AdjSmem(D, n).total; }
+
+// Gram partials (as the forward) and Ybar partials of the larger end, per tile.
+__global__ void __launch_bounds__(kThreads)
+    adj_tile_kernel(const TileDesc* __restrict__ tiles, const BondDesc* __restrict__ bonds,
+                    const double2* __restrict__ gamma, const double* __restrict__ lam,
+                    const double2* __restrict__ gbar, double2* __restrict__ partG, double2* __restrict__ partY,
+                    int D) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const TileDesc t = tiles[blockIdx.x];
+  const SideDesc sa = bonds[t.bond].a;
+  const int ld = 2 * D + 1;
+  double2* At = reinterpret_cast<double2*>(smem_raw);  // [nrows][2D+1]
+  double2* Gb = At + (size_t)t.nrows * ld;              // [nrows][2D+1]
+  double* w = reinterpret_cast<double*>(Gb + (size_t)t.nrows * ld);
+  __shared__ double cut[2];
+  if (threadIdx.x < 2) {
+    const int lo = threadIdx.x == 0 ? sa.lam_o1 : sa.lam_o2;
+    double mx = 0.0;
+    if (lo >= 0)
+      for (int k = 0; k < D; ++k) mx = fmax(mx, lam[lo + k]);
+    cut[threadIdx.x] = kLambdaCut * mx;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < t.nrows; r += blockDim.x) {
+    const RowPos p = row_pos(sa, t.row0 + r);
+    w[r] = row_weight(sa, lam, p);
+  }
+  for (int idx = threadIdx.x; idx < t.nrows * D; idx += blockDim.x) {
+    int r, k;
+    if (sa.str_k == 1) {
+      r = idx / D;
+      k = idx - r * D;
+    } else {
+      k = idx / t.nrows;
+      r = idx - k * t.nrows;
+    }
+    const RowPos p = row_pos(sa, t.row0 + r);
+    bool ok = true;
+    if (sa.lam_o1 >= 0) ok = ok && lam[sa.lam_o1 + p.r1] > cut[0];
+    if (sa.lam_o2 >= 0) ok = ok && lam[sa.lam_o2 + p.r2] > cut[1];
+    const int64_t e = elem(sa, 0, p, k);
+    At[r * ld + k] = gamma[e];
+    At[r * ld + D + k] = gamma[e + sa.str_s];
+    Gb[r * ld + k] = ok ? gbar[e] : make_double2(0.0, 0.0);
+    Gb[r * ld + D + k] = ok ? gbar[e + sa.str_s] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const int D2 = D * D;
+  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
+    const int sidx = o / D2, kl = o - (o / D2) * D2, k = kl / D, l = kl - (kl / D) * D;
+    double2 g = make_double2(0.0, 0.0), y = make_double2(0.0, 0.0);
+    for (int r = 0; r < t.nrows; ++r) {
+      const double2 ak = At[r * ld + sidx * D + k];
+      const double ww = w[r] * w[r];
+      fma_conj<double>(g, cscale(ak, ww), At[r * ld + sidx * D + l]);
+      fma_conj<double>(y, ak, Gb[r * ld + sidx * D + l]);
+    }
+    partG[(int64_t)t.part * 2 * D2 + o] = g;
+    partY[(int64_t)t.part * 2 * D2 + o] = y;
+  }
+}
+
+__device__ __forceinline__ double2 phase_g(int sidx, int t) {
+  const double r2 = 0.70710678118654752440;
+  return make_double2(r2, sidx == t ? r2 : -r2);
+}
+
+__global__ void __launch_bounds__(kThreads)
+    adj_bond_kernel(const BondDesc* __restrict__ bonds, const double2* __restrict__ partG,
+                    const double2* __restrict__ partY, const double2* __restrict__ gamma,
+                    const double* __restrict__ lam, double2* gbar, double* lbar, double2* __restrict__ Gbar_out,
+                    double2* __restrict__ Y_out, const double2* __restrict__ vsave, int D, JacobiParams jp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BondDesc bd = bonds[blockIdx.x];
+  const SideDesc sb = bd.b;
+  const int nb = sb.rows, n = 2 * nb, D2 = D * D, ldr = n + 1;
+  const AdjSmem L(D, n);
+  double2* RHO = reinterpret_cast<double2*>(smem_raw + L.off_R);
+  double2* Vm = reinterpret_cast<double2*>(smem_raw + L.off_V);
+  double2* X = reinterpret_cast<double2*>(smem_raw + L.off_X);
+  double2* F = reinterpret_cast<double2*>(smem_raw + L.off_F);
+  double2* Gs = reinterpret_cast<double2*>(smem_raw + L.off_Gs);
+  double2* Cs = reinterpret_cast<double2*>(smem_raw + L.off_Cs);
+  double2* Yb = reinterpret_cast<double2*>(smem_raw + L.off_Yb);
+  double2* Ym = reinterpret_cast<double2*>(smem_raw + L.off_Ym);
+  double2* Vb = reinterpret_cast<double2*>(smem_raw + L.off_Vb);  // [n][D] Vbar of the kept columns
+  double2* Fb = reinterpret_cast<double2*>(smem_raw + L.off_Fb);  // [n][D]
+  double2* Mm = reinterpret_cast<double2*>(smem_raw + L.off_M);   // [n][n] or [D][D]
+  double2* T1 = reinterpret_cast<double2*>(smem_raw + L.off_T1);  // [D][n] or [D][D]
+  double* lamo = reinterpret_cast<double*>(smem_raw + L.off_lamo);
+  double* ev = reinterpret_cast<double*>(smem_raw + L.off_ev);
+  double* sv = reinterpret_cast<double*>(smem_raw + L.off_sv);
+  double* scal = reinterpret_cast<double*>(smem_raw + L.off_scal);
+  double* lbe = reinterpret_cast<double*>(smem_raw + L.off_lbe);
+  double* svb = reinterpret_cast<double*>(smem_raw + L.off_svb);
+  double* eb = reinterpret_cast<double*>(smem_raw + L.off_eb);
+  double* wbb = reinterpret_cast<double*>(smem_raw + L.off_wbb);
+  int* order = reinterpret_cast<int*>(smem_raw + L.off_int);
+
+  // ---- forward recomputation
+  for (int k = threadIdx.x; k < D; k += blockDim.x) {
+    lamo[k] = lam[bd.lam_e + k];
+    lbe[k] = 0.0;
+    svb[k] = 0.0;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) wbb[i] = 0.0;
+  __syncthreads();
+  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
+    double2 g = make_double2(0.0, 0.0), y = make_double2(0.0, 0.0);
+    for (int p = 0; p < bd.n_parts; ++p) {
+      g = cadd(g, partG[(int64_t)(bd.part0 + p) * 2 * D2 + o]);
+      y = cadd(y, partY[(int64_t)(bd.part0 + p) * 2 * D2 + o]);
+    }
+    const int kl = o % D2, k = kl / D, l = kl - (kl / D) * D;
+    Gs[o] = g;
+    Cs[o] = cscale(g, lamo[k] * lamo[l]);
+    Yb[o] = y;
+  }
+  load_F<double>(sb, gamma, lam, 0.0, F, D);
+  // the forward's eigenvectors (sorted by decreasing eigenvalue) and eigenvalues: the
+  // output adjoints are expressed in the forward's gauge, so the same V must be used
+  {
+    const int nm = 2 * D;
+    const double2* vs = vsave + (int64_t)blockIdx.x * (nm * nm + nm);
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Vm[idx] = vs[idx];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      ev[j] = vs[n * n + j].x;
+      order[j] = j;
+    }
+  }
+  __syncthreads();
+  const int kmax = n < D ? n : D;
+  if (threadIdx.x == 0) {
+    const double emax = ev[order[0]];
+    double nrm2 = 0.0;
+    for (int kk = 0; kk < D; ++kk) {
+      double sval = 0.0;
+      if (kk < kmax) {
+        const double e = ev[order[kk]];
+        if (e > jp.ev_cut * emax && e > 0.0) sval = sqrt(e);
+      }
+      sv[kk] = sval;
+      nrm2 += sval * sval;
+    }
+    scal[1] = sqrt(nrm2);
+    double mx = 0.0;
+    const int lo = sb.lam_o1 >= 0 ? sb.lam_o1 : sb.lam_o2;
+    if (lo >= 0)
+      for (int k = 0; k < D; ++k) mx = fmax(mx, lam[lo + k]);
+    scal[2] = mx;
+    scal[3] = emax;
+  }
+  __syncthreads();
+  const double nrm = scal[1], lmx = scal[2], emax = scal[3];
+  // forward Y (FP64) for the update adjoint
+  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
+    const int sidx = o / D2, kl = o - (o / D2) * D2, k = kl / D, kk = kl - (kl / D) * D;
+    double2 acc = make_double2(0.0, 0.0);
+    if (sv[kk] > 0.0) {
+      for (int x = 0; x < n; ++x) fma_c<double>(acc, cmul(F[x * D + k], phase_g(sidx, x & 1)), Vm[x * n + order[kk]]);
+      acc = cscale(acc, lamo[k] / sv[kk]);
+    }
+    Ym[o] = acc;
+    Y_out[(int64_t)blockIdx.x * 2 * D2 + o] = acc;
+  }
+  // ---- reverse
+  // Gamma_b' = conj(V_D) / w_b: Vbar and w_b-bar
+  for (int idx = threadIdx.x; idx < n * D; idx += blockDim.x) {
+    const int x = idx / D, kk = idx - (idx / D) * D;
+    const int rj = x >> 1, t = x & 1;
+    const RowPos p = row_pos(sb, rj);
+    double winv = 1.0;
+    const int lo = sb.lam_o1 >= 0 ? sb.lam_o1 : sb.lam_o2;
+    if (lo >= 0) {
+      const double lv = lam[lo + (sb.lam_o1 >= 0 ? p.r1 : p.r2)];
+      winv = lv > kLambdaCut * lmx ? 1.0 / lv : 0.0;
+    }
+    double2 vb = make_double2(0.0, 0.0);
+    if (sv[kk] > 0.0) {
+      const double2 g = gbar[elem(sb, t, p, kk)];
+      vb = cscale(cconj(g), winv);
+    }
+    Vb[x * D + kk] = vb;
+  }
+  __syncthreads();
+  if (threadIdx.x < nb) {
+    const int rj = threadIdx.x;
+    const RowPos p = row_pos(sb, rj);
+    const int lo = sb.lam_o1 >= 0 ? sb.lam_o1 : sb.lam_o2;
+    if (lo >= 0) {
+      const double lv = lam[lo + (sb.lam_o1 >= 0 ? p.r1 : p.r2)];
+      if (lv > kLambdaCut * lmx) {
+        double acc = 0.0;
+        for (int t = 0; t < 2; ++t)
+          for (int kk = 0; kk < D; ++kk)
+            if (sv[kk] > 0.0) {
+              const double2 g = gbar[elem(sb, t, p, kk)];
+              const double2 v = Vm[(rj * 2 + t) * n + order[kk]];
+              acc += g.x * v.x - g.y * v.y;  // Re(conj(gbar) conj(V)) = Re(gbar V) with conj both
+            }
+        wbb[rj] += -acc / (lv * lv);
+      }
+    }
+  }
+  for (int idx = threadIdx.x; idx < n * D; idx += blockDim.x) Fb[idx] = make_double2(0.0, 0.0);
+  __syncthreads();
+  // Y_s = Lambda B_s V_D / s
+  for (int sidx = 0; sidx < 2; ++sidx) {
+    // lambda_e-bar (per k) and Xbar = lambda_k Ybar / s into T1[k][kk]
+    for (int k = threadIdx.x; k < D; k += blockDim.x) {
+      double acc = 0.0;
+      for (int kk = 0; kk < D; ++kk) {
+        if (!(sv[kk] > 0.0)) continue;
+        const double2 yb = Yb[sidx * D2 + k * D + kk], ym = Ym[sidx * D2 + k * D + kk];
+        // X[k][kk] = Ym * s / lambda_k: Re(conj(Yb) X) / s = Re(conj(Yb) Ym) / lambda_k
+        if (lamo[k] > 0.0) acc += (yb.x * ym.x + yb.y * ym.y) / lamo[k];
+      }
+      lbe[k] += acc;
+    }
+    for (int kk = threadIdx.x; kk < D; kk += blockDim.x) {
+      if (!(sv[kk] > 0.0)) continue;
+      double acc = 0.0;
+      for (int k = 0; k < D; ++k) {
+        const double2 yb = Yb[sidx * D2 + k * D + kk], ym = Ym[sidx * D2 + k * D + kk];
+        acc += yb.x * ym.x + yb.y * ym.y;
+      }
+      svb[kk] -= acc / sv[kk];
+    }
+    for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
+      const int k = idx / D, kk = idx - (idx / D) * D;
+      T1[k * D + kk] = sv[kk] > 0.0 ? cscale(Yb[sidx * D2 + k * D + kk], lamo[k] / sv[kk]) : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    // Vbar[x][kk] += sum_k conj(B_s[k][x]) Xbar[k][kk];  Fbar[x][k] += conj(g) sum_kk Xbar[k][kk] conj(V[x][kk])
+    for (int idx = threadIdx.x; idx < n * D; idx += blockDim.x) {
+      const int x = idx / D, c = idx - (idx / D) * D;
+      const double2 g = phase_g(sidx, x & 1);
+      double2 vb = make_double2(0.0, 0.0), fb = make_double2(0.0, 0.0);
+      for (int k = 0; k < D; ++k) fma_conj<double>(vb, cmul(F[x * D + k], g), T1[k * D + c]);
+      for (int kk = 0; kk < D; ++kk)
+        if (sv[kk] > 0.0) fma_c<double>(fb, T1[c * D + kk], cconj(Vm[x * n + order[kk]]));
+      Vb[x * D + c] = cadd(Vb[x * D + c], vb);
+      Fb[x * D + c] = cadd(Fb[x * D + c], cmul(cconj(g), fb));
+    }
+    __syncthreads();
+  }
+  // lambda' = s / ||s||
+  if (threadIdx.x == 0) {
+    double dot = 0.0;
+    for (int kk = 0; kk < D; ++kk)
+      if (sv[kk] > 0.0) dot += (sv[kk] / nrm) * lbar[bd.lam_e + kk];
+    for (int kk = 0; kk < D; ++kk)
+      if (sv[kk] > 0.0) {
+        svb[kk] += (lbar[bd.lam_e + kk] - (sv[kk] / nrm) * dot) / nrm;
+      }
+    for (int j = 0; j < n; ++j) eb[j] = 0.0;
+    for (int kk = 0; kk < D && kk < n; ++kk)
+      if (sv[kk] > 0.0) eb[kk] = svb[kk] / (2.0 * sv[kk]);
+  }
+  __syncthreads();
+  // eigen adjoint.  Sorted columns: v_j = V[:, order[j]].  Q[kk][j] = vbar_kk^H v_j (kk kept),
+  // K = Q o Fm;  T = V_sorted (diag(Ebar) + K) in X [n][n];  M = T V_sorted^H in Mm.
+  const double eps2 = (1e-12 * emax) * (1e-12 * emax);
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int kk = idx / n, j = idx - (idx / n) * n;
+    double2 q = make_double2(0.0, 0.0);
+    if (kk < D && sv[kk] > 0.0 && j != kk) {
+      for (int x = 0; x < n; ++x) fma_conj<double>(q, Vb[x * D + kk], Vm[x * n + order[j]]);
+      const double d = ev[order[kk]] - ev[order[j]];
+      q = cscale(q, d / (d * d + eps2));
+    }
+    Mm[kk * n + j] = q;  // K
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int x = idx / n, j = idx - (idx / n) * n;
+    double2 acc = cscale(Vm[x * n + order[j]], eb[j]);
+    for (int kk = 0; kk < D && kk < n; ++kk) fma_c<double>(acc, Vm[x * n + order[kk]], Mm[kk * n + j]);
+    X[x * n + j] = acc;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int x = idx / n, y = idx - (idx / n) * n;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = 0; j < n; ++j) fma_c<double>(acc, X[x * n + j], cconj(Vm[y * n + order[j]]));
+    Mm[x * n + y] = acc;
+  }
+  __syncthreads();
+  // rhobar = (M + M^H)/2 into RHO (the forward rho is no longer needed)
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int x = idx / n, y = idx - (idx / n) * n;
+    const double2 a = Mm[x * n + y], b = Mm[y * n + x];
+    RHO[x * ldr + y] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+  }
+  __syncthreads();
+  for (int sidx = 0; sidx < 2; ++sidx) {
+    // T1 = B_s rhobar  [D][n]
+    for (int idx = threadIdx.x; idx < D * n; idx += blockDim.x) {
+      const int k = idx / n, y = idx - (idx / n) * n;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int x = 0; x < n; ++x) fma_c<double>(acc, cmul(F[x * D + k], phase_g(sidx, x & 1)), RHO[x * ldr + y]);
+      T1[k * n + y] = acc;
+    }
+    __syncthreads();
+    // Cbar_s[k][l] = sum_y T1[k][y] conj(B_s[l][y]) -> Gbar_s = Lambda Cbar Lambda, lambda-bar
+    for (int idx = threadIdx.x; idx < D2; idx += blockDim.x) {
+      const int k = idx / D, l = idx - (idx / D) * D;
+      double2 cb = make_double2(0.0, 0.0);
+      for (int y = 0; y < n; ++y) fma_c<double>(cb, T1[k * n + y], cconj(cmul(F[y * D + l], phase_g(sidx, y & 1))));
+      Gbar_out[(int64_t)blockIdx.x * 2 * D2 + sidx * D2 + idx] = cscale(cb, lamo[k] * lamo[l]);
+      Mm[idx] = cb;  // Cbar_s, reused below
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < D; k += blockDim.x) {
+      double acc = 0.0;
+      for (int l = 0; l < D; ++l) {
+        const double2 cb = Mm[k * D + l], g = Gs[sidx * D2 + k * D + l];
+        acc += (cb.x * g.x + cb.y * g.y) * lamo[l];
+      }
+      lbe[k] += 2.0 * acc;
+    }
+    // Bbar_s = 2 C_s T1 -> Fbar[x][k] += conj(g(s,t_x)) Bbar_s[k][x]
+    for (int idx = threadIdx.x; idx < n * D; idx += blockDim.x) {
+      const int x = idx / D, k = idx - (idx / D) * D;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int l = 0; l < D; ++l) fma_c<double>(acc, Cs[sidx * D2 + k * D + l], T1[l * n + x]);
+      Fb[x * D + k] = cadd(Fb[x * D + k], cmul(cconj(phase_g(sidx, x & 1)), cscale(acc, 2.0)));
+    }
+    __syncthreads();
+  }
+  // F = w_b Gamma_b: Gamma_b-bar, w_b-bar; write back
+  for (int idx = threadIdx.x; idx < nb * D; idx += blockDim.x) {
+    const int rj = idx / D, k = idx - (idx / D) * D;
+    const RowPos p = row_pos(sb, rj);
+    const double w = row_weight(sb, lam, p);
+    for (int t = 0; t < 2; ++t) {
+      const int64_t e = elem(sb, t, p, k);
+      gbar[e] = cscale(Fb[(rj * 2 + t) * D + k], w);
+    }
+  }
+  if (threadIdx.x < nb) {
+    const int rj = threadIdx.x;
+    const RowPos p = row_pos(sb, rj);
+    double acc = wbb[rj];
+    for (int t = 0; t < 2; ++t)
+      for (int k = 0; k < D; ++k) {
+        const double2 fb = Fb[(rj * 2 + t) * D + k], g = gamma[elem(sb, t, p, k)];
+        acc += fb.x * g.x + fb.y * g.y;
+      }
+    if (sb.lam_o1 >= 0 && sb.lam_o2 >= 0) {
+      atomicAdd(lbar + sb.lam_o1 + p.r1, acc * lam[sb.lam_o2 + p.r2]);
+      atomicAdd(lbar + sb.lam_o2 + p.r2, acc * lam[sb.lam_o1 + p.r1]);
+    } else if (sb.lam_o2 >= 0) {
+      atomicAdd(lbar + sb.lam_o2 + p.r2, acc);
+    } else if (sb.lam_o1 >= 0) {
+      atomicAdd(lbar + sb.lam_o1 + p.r1, acc);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < D; k += blockDim.x) lbar[bd.lam_e + k] = lbe[k];
+}
+
+// A~bar = mask (Gbar' Y_s^H) + 2 w^2 A~ Gbar_s (in place over Gbar'), w-bar -> lambda-bar of a's other legs.
+__global__ void __launch_bounds__(kThreads)
+    adj_update_kernel(const TileDesc* __restrict__ tiles, const BondDesc* __restrict__ bonds,
+                      const double2* __restrict__ gamma, const double* __restrict__ lam, double2* gbar, double* lbar,
+                      const double2* __restrict__ Gbar_in, const double2* __restrict__ Y_in, int D) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const TileDesc t = tiles[blockIdx.x];
+  const SideDesc sa = bonds[t.bond].a;
+  const int ld = 2 * D + 1, D2 = D * D;
+  double2* Ys = reinterpret_cast<double2*>(smem_raw);  // [2][D][D]
+  double2* Gg = Ys + 2 * D2;                           // [2][D][D]
+  double2* At = Gg + 2 * D2;                           // [nrows][2D+1]
+  double2* Gb = At + (size_t)t.nrows * ld;             // [nrows][2D+1]
+  double* w = reinterpret_cast<double*>(Gb + (size_t)t.nrows * ld);
+  double* wb = w + t.nrows;
+  __shared__ double cut[2];
+  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
+    Ys[o] = Y_in[(int64_t)t.bond * 2 * D2 + o];
+    Gg[o] = Gbar_in[(int64_t)t.bond * 2 * D2 + o];
+  }
+  if (threadIdx.x < 2) {
+    const int lo = threadIdx.x == 0 ? sa.lam_o1 : sa.lam_o2;
+    double mx = 0.0;
+    if (lo >= 0)
+      for (int k = 0; k < D; ++k) mx = fmax(mx, lam[lo + k]);
+    cut[threadIdx.x] = kLambdaCut * mx;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < t.nrows; r += blockDim.x) {
+    const RowPos p = row_pos(sa, t.row0 + r);
+    w[r] = row_weight(sa, lam, p);
+    wb[r] = 0.0;
+  }
+  for (int idx = threadIdx.x; idx < t.nrows * D; idx += blockDim.x) {
+    int r, k;
+    if (sa.str_k == 1) {
+      r = idx / D;
+      k = idx - r * D;
+    } else {
+      k = idx / t.nrows;
+      r = idx - k * t.nrows;
+    }
+    const RowPos p = row_pos(sa, t.row0 + r);
+    bool ok = true;
+    if (sa.lam_o1 >= 0) ok = ok && lam[sa.lam_o1 + p.r1] > cut[0];
+    if (sa.lam_o2 >= 0) ok = ok && lam[sa.lam_o2 + p.r2] > cut[1];
+    const int64_t e = elem(sa, 0, p, k);
+    At[r * ld + k] = gamma[e];
+    At[r * ld + D + k] = gamma[e + sa.str_s];
+    Gb[r * ld + k] = ok ? gbar[e] : make_double2(0.0, 0.0);
+    Gb[r * ld + D + k] = ok ? gbar[e + sa.str_s] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < t.nrows * 2 * D; o += blockDim.x) {
+    const int r = o / (2 * D), rem = o - r * 2 * D, sidx = rem / D, k = rem - sidx * D;
+    double2 y = make_double2(0.0, 0.0), a = make_double2(0.0, 0.0);
+    for (int l = 0; l < D; ++l) {
+      fma_c<double>(y, Gb[r * ld + sidx * D + l], cconj(Ys[sidx * D2 + k * D + l]));
+      fma_c<double>(a, At[r * ld + sidx * D + l], Gg[sidx * D2 + l * D + k]);
+    }
+    a = cscale(a, 2.0 * w[r]);  // Abar[r][s][k] (the adjoint of A = w A~)
+    const double2 at = At[r * ld + sidx * D + k];
+    atomicAdd(wb + r, a.x * at.x + a.y * at.y);
+    const double2 out = cadd(y, cscale(a, w[r]));
+    const RowPos p = row_pos(sa, t.row0 + r);
+    gbar[elem(sa, sidx, p, k)] = out;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < t.nrows; r += blockDim.x) {
+    const RowPos p = row_pos(sa, t.row0 + r);
+    const double v = wb[r];
+    if (sa.lam_o1 >= 0 && sa.lam_o2 >= 0) {
+      atomicAdd(lbar + sa.lam_o1 + p.r1, v * lam[sa.lam_o2 + p.r2]);
+      atomicAdd(lbar + sa.lam_o2 + p.r2, v * lam[sa.lam_o1 + p.r1]);
+    } else if (sa.lam_o2 >= 0) {
+      atomicAdd(lbar + sa.lam_o2 + p.r2, v);
+    } else if (sa.lam_o1 >= 0) {
+      atomicAdd(lbar + sa.lam_o1 + p.r1, v);
+    }
+  }
+}
+
+// Explicit kick of every site: Gamma_i <- exp(-i theta_i X / 2) Gamma_i (one CTA per site).
+__global__ void apply_kick_kernel(const SiteDesc* __restrict__ sites, double2* gamma, const double* __restrict__ theta,
+                                  int D) {
+  const SiteDesc sd = sites[blockIdx.x];
+  int nel = 1;
+  for (int q = 0; q < sd.deg; ++q) nel *= D;
+  const double th = theta[blockIdx.x];
+  const double c = cos(0.5 * th), s = sin(0.5 * th);
+  for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+    double2 a0, a1;
+    kick2<double>(c, s, gamma[sd.off + idx], gamma[sd.off + nel + idx], a0, a1);
+    gamma[sd.off + idx] = a0;
+    gamma[sd.off + nel + idx] = a1;
+  }
+}
+
+// Reverse of the explicit kick: thetabar_i += Re <Gbar, (-i/2) X Gamma_post>, Gbar <- R^H Gbar.
+__global__ void adj_kick_kernel(const SiteDesc* __restrict__ sites, const double2* __restrict__ gamma_post,
+                                double2* gbar, const double* __restrict__ theta, double* dtheta, int D) {
+  const SiteDesc sd = sites[blockIdx.x];
+  int nel = 1;
+  for (int q = 0; q < sd.deg; ++q) nel *= D;
+  const double th = theta[blockIdx.x];
+  const double c = cos(0.5 * th), s = sin(0.5 * th);
+  double acc = 0.0;
+  for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+    const double2 g0 = gbar[sd.off + idx], g1 = gbar[sd.off + nel + idx];
+    const double2 p0 = gamma_post[sd.off + idx], p1 = gamma_post[sd.off + nel + idx];
+    // (-i/2) X Gamma_post: component 0 <- (-i/2) p1, component 1 <- (-i/2) p0
+    acc += g0.x * (0.5 * p1.y) + g0.y * (-0.5 * p1.x) + g1.x * (0.5 * p0.y) + g1.y * (-0.5 * p0.x);
+    // R^H = [[c, i s], [i s, c]]
+    gbar[sd.off + idx] = make_double2(c * g0.x - s * g1.y, c * g0.y + s * g1.x);
+    gbar[sd.off + nel + idx] = make_double2(-s * g0.y + c * g1.x, s * g0.x + c * g1.y);
+  }
+  __shared__ double red[kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+    dtheta[blockIdx.x] += v;
+  }
+}
+
+// Reverse of the mean-field readout for L = sum_i c_i <Z_i>: Gbar_i (written) and
+// lambda-bar (accumulated) of every leg.  One CTA per site.
+__global__ void adj_readout_kernel(const SiteDesc* __restrict__ sites, const double2* __restrict__ gamma,
+                                   const double* __restrict__ lam, const double* __restrict__ cz, double2* gbar,
+                                   double* lbar, int D) {
+  const SiteDesc sd = sites[blockIdx.x];
+  int nel = 1;
+  for (int q = 0; q < sd.deg; ++q) nel *= D;
+  __shared__ double red[2][kThreads / 32];
+  __shared__ double pz[2];
+  __shared__ double lb[3][kMaxD];
+  for (int i = threadIdx.x; i < 3 * kMaxD; i += blockDim.x) lb[i / kMaxD][i % kMaxD] = 0.0;
+  double p0 = 0.0, p1 = 0.0;
+  for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+    double w = 1.0;
+    int rest = idx;
+    for (int q = sd.deg - 1; q >= 0; --q) {
+      const double lv = lam[sd.lam[q] + rest % D];
+      w *= lv * lv;
+      rest /= D;
+    }
+    const double2 g0 = gamma[sd.off + idx], g1 = gamma[sd.off + nel + idx];
+    p0 += w * (g0.x * g0.x + g0.y * g0.y);
+    p1 += w * (g1.x * g1.x + g1.y * g1.y);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    p0 += __shfl_down_sync(0xffffffffu, p0, off);
+    p1 += __shfl_down_sync(0xffffffffu, p1, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = p0;
+    red[1][threadIdx.x >> 5] = p1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      s0 += red[0][w];
+      s1 += red[1][w];
+    }
+    const double c = cz[blockIdx.x], den = (s0 + s1) * (s0 + s1);
+    pz[0] = c * 2.0 * s1 / den;   // d<Z>/dp0
+    pz[1] = -c * 2.0 * s0 / den;  // d<Z>/dp1
+  }
+  __syncthreads();
+  const double dz0 = pz[0], dz1 = pz[1];
+  for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+    int li[3] = {0, 0, 0};
+    int rest = idx;
+    for (int q = sd.deg - 1; q >= 0; --q) {
+      li[q] = rest % D;
+      rest /= D;
+    }
+    double l2[3] = {1.0, 1.0, 1.0};
+    double w = 1.0;
+    for (int q = 0; q < sd.deg; ++q) {
+      const double lv = lam[sd.lam[q] + li[q]];
+      l2[q] = lv * lv;
+      w *= l2[q];
+    }
+    const double2 g0 = gamma[sd.off + idx], g1 = gamma[sd.off + nel + idx];
+    gbar[sd.off + idx] = cscale(g0, 2.0 * dz0 * w);
+    gbar[sd.off + nel + idx] = cscale(g1, 2.0 * dz1 * w);
+    const double m = dz0 * (g0.x * g0.x + g0.y * g0.y) + dz1 * (g1.x * g1.x + g1.y * g1.y);
+    for (int q = 0; q < sd.deg; ++q) {
+      double other = 1.0;
+      for (int q2 = 0; q2 < sd.deg; ++q2)
+        if (q2 != q) other *= l2[q2];
+      atomicAdd(&lb[q][li[q]], m * 2.0 * lam[sd.lam[q] + li[q]] * other);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < sd.deg * D; i += blockDim.x) {
+    const int q = i / D, l = i - (i / D) * D;
+    atomicAdd(lbar + sd.lam[q] + l, lb[q][l]);
+  }
+}
+
+static size_t adj_tile_smem(int D) { return (size_t)2 * kTileRows * (2 * D + 1) * 16 + (size_t)kTileRows * 8; }
+static size_t adj_update_smem(int D) {
+  return (size_t)4 * D * D * 16 + (size_t)2 * kTileRows * (2 * D + 1) * 16 + (size_t)2 * kTileRows * 8;
+}
+
+cudaError_t Adjoint::init() {
+  cudaError_t e = cudaFuncSetAttribute(adj_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)adj_tile_smem(kMaxGradD));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(adj_bond_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)adj_bond_smem_bytes(kMaxGradD, 2 * kMaxGradD));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(adj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)adj_update_smem(kMaxGradD));
+}
+
+cudaError_t Adjoint::layer(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, int n_bonds, const void* gamma,
+                           const double* lam, void* gbar, double* lbar, void* partG, void* partY, void* Gbar,
+                           void* Ybuf, const void* vsave, int D, JacobiParams jp, cudaStream_t st) {
+  if (n_bonds == 0) return cudaSuccess;
+  const double2* g = static_cast<const double2*>(gamma);
+  adj_tile_kernel<<<n_tiles, kThreads, adj_tile_smem(D), st>>>(tiles, bonds, g, lam, static_cast<double2*>(gbar),
+                                                                static_cast<double2*>(partG),
+                                                                static_cast<double2*>(partY), D);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  adj_bond_kernel<<<n_bonds, kThreads, adj_bond_smem_bytes(D, 2 * D), st>>>(
+      bonds, static_cast<const double2*>(partG), static_cast<const double2*>(partY), g, lam,
+      static_cast<double2*>(gbar), lbar, static_cast<double2*>(Gbar), static_cast<double2*>(Ybuf),
+      static_cast<const double2*>(vsave), D, jp);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  adj_update_kernel<<<n_tiles, kThreads, adj_update_smem(D), st>>>(tiles, bonds, g, lam, static_cast<double2*>(gbar),
+                                                                    lbar, static_cast<const double2*>(Gbar),
+                                                                    static_cast<const double2*>(Ybuf), D);
+  return cudaGetLastError();
+}
+
+cudaError_t Adjoint::apply_kick(const SiteDesc* sites, int n_sites, void* gamma, const double* theta, int D,
+                                cudaStream_t st) {
+  if (n_sites == 0) return cudaSuccess;
+  apply_kick_kernel<<<n_sites, kThreads, 0, st>>>(sites, static_cast<double2*>(gamma), theta, D);
+  return cudaGetLastError();
+}
+
+cudaError_t Adjoint::kick(const SiteDesc* sites, int n_sites, const void* gamma_post, void* gbar,
+                          const double* theta, double* dtheta, int D, cudaStream_t st) {
+  if (n_sites == 0) return cudaSuccess;
+  adj_kick_kernel<<<n_sites, kThreads, 0, st>>>(sites, static_cast<const double2*>(gamma_post),
+                                                 static_cast<double2*>(gbar), theta, dtheta, D);
+  return cudaGetLastError();
+}
+
+cudaError_t Adjoint::readout(const SiteDesc* sites, int n_sites, const void* gamma, const double* lam,
+                             const double* cz, void* gbar, double* lbar, int D, cudaStream_t st) {
+  if (n_sites == 0) return cudaSuccess;
+  adj_readout_kernel<<<n_sites, kThreads, 0, st>>>(sites, static_cast<const double2*>(gamma), lam, cz,
+                                                    static_cast<double2*>(gbar), lbar, D);
+  return cudaGetLastError();
+}
 
 }  // namespace gpeps

@@ -165,6 +165,31 @@ class GPEPS:
         check(self.lib.gpeps_set_jacobi(self.h, float(tol), float(floor_rel), float(tol32), float(floor32),
                                         int(max_sweeps), int(max_sweeps32)), "gpeps_set_jacobi")
 
+    # -------------------------------------------------------------- gradient
+    def grad(self, theta, n_steps, ckpt_every=5, dL_dz=None):
+        """Gradient path (complex128, D <= 16): returns ``(z, dtheta)`` with z = <Z_i> after
+        ``n_steps`` steps from |0...0> with per-qubit kick angles ``theta`` and, when the weights
+        ``dL_dz`` are given, dtheta = d(sum_i dL_dz_i <Z_i>)/dtheta (else None)."""
+        t = self._theta(theta, per_qubit=True)
+        nbytes = ctypes.c_size_t()
+        check(self.lib.gpeps_query_grad_workspace(self.h, int(n_steps), int(ckpt_every), ctypes.byref(nbytes)),
+              "gpeps_query_grad_workspace")
+        work = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=self.device)
+        z = torch.empty(self.total_qubits, dtype=torch.float64, device=self.device)
+        w = dth = None
+        if dL_dz is not None:
+            w = torch.as_tensor(dL_dz, dtype=torch.float64).to(self.device).contiguous()
+            dth = torch.empty(self.total_qubits, dtype=torch.float64, device=self.device)
+        self._after_torch()
+        check(self.lib.gpeps_grad(self.h, ctypes.c_void_p(t.data_ptr()), int(n_steps), int(ckpt_every),
+                                  ctypes.c_void_p(w.data_ptr()) if w is not None else None,
+                                  ctypes.c_void_p(z.data_ptr()),
+                                  ctypes.c_void_p(dth.data_ptr()) if dth is not None else None,
+                                  ctypes.c_void_p(work.data_ptr()), nbytes.value), "gpeps_grad")
+        self._before_torch()
+        self.stream.synchronize()
+        return z, dth
+
     # -------------------------------------------------------------- state access
     def site_tensor(self, instance, site):
         """View of Gamma of a site inside the state buffer: complex tensor [2] + [D] * deg, and
@@ -215,3 +240,22 @@ class GPEPS:
             self.close()
         except Exception:
             pass
+
+
+class KickedIsingZ(torch.autograd.Function):
+    """<Z_i> after ``n_steps`` Trotter steps as a differentiable function of the per-qubit kick
+    angles: ``z = KickedIsingZ.apply(theta, g, n_steps, ckpt_every)``; backward runs the
+    library's reverse mode (checkpointed, recomputing each segment)."""
+
+    @staticmethod
+    def forward(ctx, theta, g, n_steps, ckpt_every=5):
+        z, _ = g.grad(theta.detach(), n_steps, ckpt_every)
+        ctx.save_for_backward(theta.detach())
+        ctx.g, ctx.n_steps, ctx.ckpt_every = g, n_steps, ckpt_every
+        return z
+
+    @staticmethod
+    def backward(ctx, grad_z):
+        (theta,) = ctx.saved_tensors
+        _, dth = ctx.g.grad(theta, ctx.n_steps, ctx.ckpt_every, dL_dz=grad_z.detach())
+        return dth.to(theta.dtype), None, None, None

@@ -59,5 +59,29 @@ def run(name, steps=None):
     print("wrote", path)
 
 
+GRAD_QUBITS = [0, 13, 37, 62, 100, 126]
+
+
+def run_grad(name):
+    """Oracle gradient (central differences, h = 1e-5) of the mean <Z> after all steps with
+    respect to a few per-qubit kick angles."""
+    from oracle.gradient import fd_gradient, oracle_loss
+    w = workload(name)
+    (n, edges), th = w.graphs()[0], kick_angles(w)[0]
+    weights = np.full(n, 1.0 / n)
+    t0 = time.time()
+    loss = oracle_loss(n, edges, w.D, th, w.steps, weights)
+    g = fd_gradient(n, edges, w.D, th, w.steps, weights, h=1e-5, qubits=GRAD_QUBITS)
+    out = {"workload": name, "D": w.D, "steps": w.steps, "h": 1e-5, "loss": loss,
+           "dloss_dtheta": {str(q): v for q, v in g.items()}}
+    path = os.path.join(HERE, f"oracle_{name}.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print("wrote", path, f"({time.time() - t0:.0f}s)")
+
+
 if __name__ == "__main__":
-    run(sys.argv[1], int(sys.argv[2]) if len(sys.argv) > 2 else None)
+    if workload(sys.argv[1]).per_qubit_seed is not None:
+        run_grad(sys.argv[1])
+    else:
+        run(sys.argv[1], int(sys.argv[2]) if len(sys.argv) > 2 else None)

@@ -185,3 +185,26 @@ def test_planted_mistake_zz_before_kick():
                 self.zz_layer(c)
             self.kick(theta)
     assert _tree_error(Bad) > 1e-6
+
+
+def test_oracle_gradient_matches_parameter_shift_on_a_tree():
+    """Exact regime: central differences of the oracle equal the parameter-shift derivative
+    of the state vector (a second, independent derivative)."""
+    from oracle.gradient import fd_gradient, parameter_shift_gradient
+    m, e, _ = TREE16
+    rng = np.random.default_rng(7)
+    theta = rng.uniform(0.5, 0.9, m)
+    w = np.full(m, 1.0 / m)
+    steps = 3
+    ps = parameter_shift_gradient(m, e, theta, steps, w)
+    fd = fd_gradient(m, e, 8, theta, steps, w, qubits=[0, 3, 4, 9, 14, 15])
+    for q, v in fd.items():
+        assert abs(v - ps[q]) < 1e-8 * max(1.0, abs(ps[q])), (q, v, ps[q])
+
+
+def test_parameter_shift_single_qubit_closed_form():
+    """One qubit: <Z> = cos(n theta), d/dtheta = -n sin(n theta)."""
+    from oracle.gradient import parameter_shift_gradient
+    th = 0.41
+    g = parameter_shift_gradient(1, np.zeros((0, 2), int), [th], 3, np.ones(1))
+    assert abs(g[0] + 3 * math.sin(3 * th)) < 1e-13
