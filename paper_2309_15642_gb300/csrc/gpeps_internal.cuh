@@ -12,7 +12,8 @@ namespace gpeps {
 
 constexpr int kMaxD = 32;          // bond dimension limit of this build
 constexpr int kTileRows = 64;      // rows of a big-side tile (Gram and update launches)
-constexpr int kThreads = 256;      // threads of every CTA
+constexpr int kThreads = 256;      // threads of the streaming and readout CTAs
+constexpr int kBondThreads = 512;  // threads of the bond-eigenproblem CTA (one CTA per SM: more warps hide FP64 latency)
 constexpr double kLambdaCut = 1e-13;  // pseudo-inverse threshold relative to max(lambda)
 constexpr int kPhases = 6;            // phases of the bond kernel with SM-cycle counters
 constexpr int kRotSweeps = 8;         // rotation counters kept for the first sweeps of a solve

@@ -672,7 +672,7 @@ __device__ void load_F(const SideDesc& sb, const V2<T>* gamma, const double* lam
 // every off-diagonal is at FP64 rounding level (mixed-precision Jacobi: a
 // low-precision eigenbasis as preconditioner of the high-precision sweeps).
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kBondThreads)
     bond_kernel(const BondDesc* __restrict__ bonds, const V2<T>* __restrict__ partials, V2<T>* gamma,
                 double* lam, double* pending, V2<T>* __restrict__ Yout, double* __restrict__ theta_a,
                 int* flags, unsigned long long* sweeps_out, unsigned long long* cycles, double2* vsave, int D,
@@ -1089,7 +1089,7 @@ cudaError_t Launch<T>::bond(const BondDesc* bonds, int n_bonds, const void* part
                             unsigned long long* cycles, void* vsave, int D, JacobiParams jp, cudaStream_t st) {
   if (n_bonds == 0) return cudaSuccess;
   const size_t sm = bond_smem_bytes(D, 2 * D);
-  bond_kernel<T><<<n_bonds, kThreads, sm, st>>>(bonds, static_cast<const V2<T>*>(partials),
+  bond_kernel<T><<<n_bonds, kBondThreads, sm, st>>>(bonds, static_cast<const V2<T>*>(partials),
                                                  static_cast<V2<T>*>(gamma), lam, pending,
                                                  static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles,
                                                  static_cast<double2*>(vsave), D, jp);
