@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile-steps", type=int, default=2, help="profiled steps after the timed region (>= 1)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule and thresholds")
     return ap.parse_args()
 
 
@@ -167,6 +168,20 @@ def cpu_oracle(w, seconds_cap=30.0, min_steps=1):
             "seconds": dt, "steps": steps}
 
 
+def golden_parity(w, means, W, K):
+    """max |mean <Z> - oracle| over the timed steps W+1..W+K, from the committed oracle values."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_{w.name}.json")
+    if not os.path.exists(path):
+        return None
+    gold = json.load(open(path))
+    ref = np.array([inst["mean_z"] for inst in gold["instances"]]).T      # [steps, instances]
+    if W + K > ref.shape[0]:
+        return None
+    d = float(np.abs(means[:K] - ref[W:W + K]).max())
+    return {"max_abs_dmean_z": d, "steps": f"{W + 1}..{W + K}", "reference": "FP64 CPU oracle (committed values)"}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpeps(args, rank, world, local_rank):
     import numpy as np
@@ -186,8 +201,13 @@ def run_gpeps(args, rank, world, local_rank):
     if dist:
         import torch.distributed as tdist
 
-    def timed(dtype, K, W):
+    def timed(dtype, K, W, tune):
         g = GPEPS(graphs, w.D, dtype=dtype, device=str(dev))
+        tuning = None
+        if tune:
+            from paper_2309_15642_gb300.autotune import autotune
+            best, table = autotune(g, theta)
+            tuning = {"chosen": best, "candidates": table}
         g.reset()
         th = torch.tensor(theta, dtype=torch.float64, device=dev)
         out = torch.empty((max(K, 1), g.n_instances), dtype=torch.float64, device=dev)
@@ -212,9 +232,9 @@ def run_gpeps(args, rank, world, local_rank):
             tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
             ms = float(t.item())
         flags = g.status()
-        return g, th, out, ms, ck, flags
+        return g, th, out, ms, ck, flags, tuning
 
-    g, th, out, ms, clocks, flags = timed(args.dtype, K, W)
+    g, th, out, ms, clocks, flags, tuning = timed(args.dtype, K, W, not args.no_autotune)
     bonds_step = g.bonds_per_step
     value = world * bonds_step * K / (ms * 1e-3)
     mean_last = out[K - 1].cpu().numpy().tolist() if K else []
@@ -276,12 +296,15 @@ def run_gpeps(args, rank, world, local_rank):
     plain = None
     if not args.no_plain and args.dtype == "mixed":
         Kp, Wp = max(min(K, 10), 1), max(min(W, 3), 1)
-        gp, _, outp, msp, _, flp = timed("c128", Kp, Wp)
+        gp, _, outp, msp, _, flp, tunp = timed("c128", Kp, Wp, not args.no_autotune)
         plain = {"dtype": "c128", "value": world * bonds_step * Kp / (msp * 1e-3), "unit": "bond updates/s",
-                 "ms_per_step": msp / Kp, "steps": Kp, "warmup": Wp, "flags": flp}
+                 "ms_per_step": msp / Kp, "steps": Kp, "warmup": Wp, "flags": flp,
+                 "schedule": (tunp or {}).get("chosen"),
+                 "parity": golden_parity(w, outp.cpu().numpy(), Wp, Kp)}
         gp.close()
+    parity = golden_parity(w, out.cpu().numpy(), W, K)
     return dict(value=value, ms=ms, bonds_step=bonds_step, clocks=clocks, flags=flags, roofline=roofline,
-                e2e=e2e, plain=plain, hbm=hbm, mean_last=mean_last, w=w)
+                e2e=e2e, plain=plain, hbm=hbm, mean_last=mean_last, w=w, tuning=tuning, parity=parity)
 
 
 def main():
@@ -345,7 +368,8 @@ def main():
                        "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{world}",
                        "timed_steps": f"{args.warmup + 1}..{args.warmup + args.steps} from |0...0>"},
             "roofline": r["roofline"], "hbm": r["hbm"], "clocks": r["clocks"], "e2e": r["e2e"],
-            "plain_c128": r["plain"], "cpu_baseline": cpu,
+            "plain_c128": r["plain"], "cpu_baseline": cpu, "parity": r["parity"],
+            "tuning": (r["tuning"] or {}).get("chosen"),
             "gpu_launches": (1 + 3 * 3 + 2) * args.steps, "device_flags": r["flags"],
             "mean_z_last_step": r["mean_last"],
         }

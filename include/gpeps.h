@@ -146,6 +146,14 @@ int gpeps_zz_layer_profiled(gpeps_handle* h, int32_t colour, float* ms);
 int gpeps_set_jacobi(gpeps_handle* h, double tol, double floor_rel, double tol32, double floor32,
                      int32_t max_sweeps, int32_t max_sweeps32);
 
+/*
+ * Schedule of the bond eigenproblems: persistent = 0 launches one CTA per bond
+ * (default); 1 launches one CTA per SM that takes bonds from a work queue in
+ * the work buffer.  Either way the bonds of a colour class run largest first.
+ * Host-only; drops a captured step graph.  Errors: GPEPS_EINVAL for other values.
+ */
+int gpeps_set_schedule(gpeps_handle* h, int32_t persistent);
+
 /* Number of colour classes (the largest over the instances). */
 int gpeps_n_colours(const gpeps_handle* h, int32_t* n_colours);
 

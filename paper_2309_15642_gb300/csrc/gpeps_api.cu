@@ -72,11 +72,13 @@ struct gpeps_handle {
   // buffer layout (bytes)
   size_t state_bytes = 0, work_bytes = 0;
   size_t s_lam = 0, s_gamma = 0;
-  size_t w_pending = 0, w_flags = 0, w_sweeps = 0, w_cycles = 0, w_z = 0, w_mean = 0, w_sites = 0, w_inst_site0 = 0,
+  size_t w_pending = 0, w_flags = 0, w_sweeps = 0, w_cycles = 0, w_queue = 0, w_z = 0, w_mean = 0, w_sites = 0, w_inst_site0 = 0,
          w_site_inst = 0, w_site_off = 0, w_partials = 0, w_Y = 0, w_theta_a = 0;
   char* d_state = nullptr;
   char* d_work = nullptr;
   bool bound = false;
+  bool persistent = false;  // bond eigenproblems from a work queue (one CTA per SM)
+  int n_sms = 0;
   int64_t bonds_since_reset = 0;
   // captured step
   cudaGraphExec_t step_exec = nullptr;
@@ -225,7 +227,8 @@ int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr, void* vsave = 
   GP_CUDA(Launch<T>::gram(tiles, nt, bonds, h->gamma(), h->lam(), h->pending(), partials, h->D, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[1], h->stream));
   GP_CUDA(Launch<T>::bond(bonds, nbd, partials, h->gamma(), h->lam(), h->pending(), Y, theta_a, h->flags(),
-                          h->sweeps(), h->cycles(), vsave, h->D, h->jp, h->stream));
+                          h->sweeps(), h->cycles(), vsave, h->D, h->jp, h->stream,
+                          h->persistent ? h->at<unsigned int>(h->w_queue) : nullptr, h->n_sms));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[2], h->stream));
   GP_CUDA(Launch<T>::update(tiles, nt, bonds, h->gamma(), h->lam(), Y, theta_a, h->D, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[3], h->stream));
@@ -352,19 +355,28 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
         bd.a = side_desc(h, k, a, b);
         bd.b = side_desc(h, k, b, a);
         bd.lam_e = (h->inst_edge0[k] + e) * D;
-        bd.part0 = cp.n_parts;
-        bd.n_parts = (bd.a.rows + kTileRows - 1) / kTileRows;
-        for (int p = 0; p < bd.n_parts; ++p) {
-          TileDesc t{};
-          t.bond = (int)cp.bonds.size();
-          t.row0 = p * kTileRows;
-          t.nrows = std::min(kTileRows, bd.a.rows - t.row0);
-          t.part = cp.n_parts + p;
-          cp.tiles.push_back(t);
-        }
-        cp.n_parts += bd.n_parts;
         cp.bonds.push_back(bd);
       }
+    }
+    // largest bond eigenproblems (and larger ends) first: the last CTAs of a launch,
+    // and the tail of the persistent work queue, are the cheap ones
+    std::stable_sort(cp.bonds.begin(), cp.bonds.end(), [](const BondDesc& x, const BondDesc& y) {
+      if (x.b.rows != y.b.rows) return x.b.rows > y.b.rows;
+      return x.a.rows > y.a.rows;
+    });
+    for (int bi = 0; bi < (int)cp.bonds.size(); ++bi) {
+      BondDesc& bd = cp.bonds[bi];
+      bd.part0 = cp.n_parts;
+      bd.n_parts = (bd.a.rows + kTileRows - 1) / kTileRows;
+      for (int p = 0; p < bd.n_parts; ++p) {
+        TileDesc t{};
+        t.bond = bi;
+        t.row0 = p * kTileRows;
+        t.nrows = std::min(kTileRows, bd.a.rows - t.row0);
+        t.part = cp.n_parts + p;
+        cp.tiles.push_back(t);
+      }
+      cp.n_parts += bd.n_parts;
     }
     h->max_parts = std::max(h->max_parts, cp.n_parts);
     h->max_bonds = std::max(h->max_bonds, (int)cp.bonds.size());
@@ -399,6 +411,7 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   h->w_flags = carve(sizeof(int) * 4);
   h->w_sweeps = carve(4 * sizeof(unsigned long long));
   h->w_cycles = carve(kCounters * sizeof(unsigned long long));
+  h->w_queue = carve(sizeof(unsigned int));
   h->w_z = carve(h->total_sites * sizeof(double));
   h->w_mean = carve(n_instances * sizeof(double));
   h->w_sites = carve(h->total_sites * sizeof(SiteDesc));
@@ -432,6 +445,11 @@ int gpeps_bind(gpeps_handle* h, void* d_state, void* d_work) {
   h->d_state = static_cast<char*>(d_state);
   h->d_work = static_cast<char*>(d_work);
   GP_CUDA(h->dtype == GPEPS_C128 ? Launch<double>::init() : Launch<float>::init());
+  {
+    int dev = 0;
+    GP_CUDA(cudaGetDevice(&dev));
+    GP_CUDA(cudaDeviceGetAttribute(&h->n_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
   auto up = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
     if (bytes == 0) return cudaSuccess;
     return cudaMemcpyAsync(h->d_work + off, src, bytes, cudaMemcpyHostToDevice, h->stream);
@@ -490,6 +508,13 @@ int gpeps_zz_layer_profiled(gpeps_handle* h, int32_t colour, float* ms) {
   for (int i = 0; i < 4; ++i) cudaEventDestroy(pe.ev[i]);
   if (st) return st;
   if (e != cudaSuccess) return cuda_fail(e, "gpeps_zz_layer_profiled");
+  return GPEPS_OK;
+}
+
+int gpeps_set_schedule(gpeps_handle* h, int32_t persistent) {
+  if (!h || (persistent != 0 && persistent != 1)) return GPEPS_EINVAL;
+  h->persistent = persistent == 1;
+  drop_graph(h);
   return GPEPS_OK;
 }
 

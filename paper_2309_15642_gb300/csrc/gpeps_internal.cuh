@@ -85,7 +85,7 @@ struct Launch {
   static cudaError_t bond(const BondDesc* bonds, int n_bonds, const void* partials, void* gamma, double* lam,
                           double* pending, void* Y, double* theta_a, int* flags,
                           unsigned long long* sweeps, unsigned long long* cycles, void* vsave, int D,
-                          JacobiParams jp, cudaStream_t st);
+                          JacobiParams jp, cudaStream_t st, unsigned int* queue = nullptr, int n_ctas = 0);
   static cudaError_t update(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, void* gamma,
                             const double* lam, const void* Y, const double* theta_a, int D, cudaStream_t st);
   static cudaError_t readout(const SiteDesc* sites, int n_sites, const void* gamma, const double* lam,

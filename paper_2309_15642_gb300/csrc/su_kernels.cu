@@ -636,15 +636,16 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
 // was: Y = identity so that the update launch only applies the pending kick
 // to end a, lambda and end b untouched; the flag word reports it.
 template <typename T>
-__device__ void bond_fail(const BondDesc& bd, V2<T>* Yout, double* theta_a, double* pending, int* flags, int D) {
+__device__ void bond_fail(int bi, const BondDesc& bd, V2<T>* Yout, double* theta_a, double* pending, int* flags,
+                          int D) {
   const int D2 = D * D;
   for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
     const int kl = o % D2;
-    Yout[(int64_t)blockIdx.x * 2 * D2 + o] = mk<T>((T)((kl / D) == (kl % D) ? 1 : 0), (T)0);
+    Yout[(int64_t)bi * 2 * D2 + o] = mk<T>((T)((kl / D) == (kl % D) ? 1 : 0), (T)0);
   }
   if (threadIdx.x == 0) {
     atomicOr(flags, 2);
-    theta_a[blockIdx.x] = pending[bd.a.site];
+    theta_a[bi] = pending[bd.a.site];
     pending[bd.a.site] = 0.0;
   }
 }
@@ -672,13 +673,12 @@ __device__ void load_F(const SideDesc& sb, const V2<T>* gamma, const double* lam
 // every off-diagonal is at FP64 rounding level (mixed-precision Jacobi: a
 // low-precision eigenbasis as preconditioner of the high-precision sweeps).
 template <typename T>
-__global__ void __launch_bounds__(kBondThreads)
-    bond_kernel(const BondDesc* __restrict__ bonds, const V2<T>* __restrict__ partials, V2<T>* gamma,
+__device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T>* __restrict__ partials, V2<T>* gamma,
                 double* lam, double* pending, V2<T>* __restrict__ Yout, double* __restrict__ theta_a,
                 int* flags, unsigned long long* sweeps_out, unsigned long long* cycles, double2* vsave, int D,
                 JacobiParams jp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const BondDesc bd = bonds[blockIdx.x];
+  const BondDesc bd = bonds[bi];
   const SideDesc sb = bd.b;
   const int nb = sb.rows;
   const int n = 2 * nb;
@@ -776,7 +776,7 @@ __global__ void __launch_bounds__(kBondThreads)
   __syncthreads();
   const double trace = scal[0];
   if (!(trace > 0.0) || !isfinite(trace)) {
-    bond_fail<T>(bd, Yout, theta_a, pending, flags, D);
+    bond_fail<T>(bi, bd, Yout, theta_a, pending, flags, D);
     return;
   }
   mark(0);
@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(kBondThreads)
   __syncthreads();
   if (vsave) {  // sorted eigenvectors and eigenvalues for the reverse mode (slot of 2D x 2D + 2D)
     const int nm = 2 * D;
-    double2* vs = vsave + (int64_t)blockIdx.x * (nm * nm + nm);
+    double2* vs = vsave + (int64_t)bi * (nm * nm + nm);
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
       const int x = idx / n, j = idx - (idx / n) * n;
       vs[x * n + j] = Vm[x * n + order[j]];
@@ -825,7 +825,7 @@ __global__ void __launch_bounds__(kBondThreads)
   __syncthreads();
   const double nrm = scal[1];
   if (!(nrm > 0.0) || !isfinite(nrm)) {
-    bond_fail<T>(bd, Yout, theta_a, pending, flags, D);
+    bond_fail<T>(bi, bd, Yout, theta_a, pending, flags, D);
     return;
   }
   // Y_s[k][kk] = lam_k sum_x F[x][k] g(s, t_x) V[x][order[kk]] / sv[kk], in the
@@ -846,7 +846,7 @@ __global__ void __launch_bounds__(kBondThreads)
       }
       acc = c_scale<T>(acc, (T)(lamo[k] / sv[kk]));
     }
-    Yout[(int64_t)blockIdx.x * 2 * D2 + o] = acc;
+    Yout[(int64_t)bi * 2 * D2 + o] = acc;
   }
   // Gamma_b'[t][row][kk] = conj(V[(row, t)][order[kk]]) / lambda_other(row)
   {
@@ -870,11 +870,43 @@ __global__ void __launch_bounds__(kBondThreads)
   // new lambda of the bond; kick angles consumed
   for (int kk = threadIdx.x; kk < D; kk += blockDim.x) lam[bd.lam_e + kk] = sv[kk] / nrm;
   if (threadIdx.x == 0) {
-    theta_a[blockIdx.x] = pending[bd.a.site];
+    theta_a[bi] = pending[bd.a.site];
     pending[bd.a.site] = 0.0;
     pending[sb.site] = 0.0;
   }
   mark(5);
+}
+
+// One CTA per bond.
+template <typename T>
+__global__ void __launch_bounds__(kBondThreads, 1)
+    bond_kernel(const BondDesc* __restrict__ bonds, const V2<T>* __restrict__ partials, V2<T>* gamma, double* lam,
+                double* pending, V2<T>* __restrict__ Yout, double* __restrict__ theta_a, int* flags,
+                unsigned long long* sweeps_out, unsigned long long* cycles, double2* vsave, int D, JacobiParams jp) {
+  bond_body<T>(blockIdx.x, bonds, partials, gamma, lam, pending, Yout, theta_a, flags, sweeps_out, cycles, vsave, D,
+               jp);
+}
+
+// Persistent form: one CTA per SM takes bonds from a work queue (bonds are
+// ordered by decreasing size, so the large ones go first and the small ones
+// fill the tail).  The queue counter is zeroed before every launch.
+template <typename T>
+__global__ void __launch_bounds__(kBondThreads, 1)
+    bond_kernel_persistent(int n_bonds, unsigned int* queue, const BondDesc* __restrict__ bonds,
+                           const V2<T>* __restrict__ partials, V2<T>* gamma, double* lam, double* pending,
+                           V2<T>* __restrict__ Yout, double* __restrict__ theta_a, int* flags,
+                           unsigned long long* sweeps_out, unsigned long long* cycles, double2* vsave, int D,
+                           JacobiParams jp) {
+  __shared__ int next;
+  for (;;) {
+    if (threadIdx.x == 0) next = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int bi = next;
+    __syncthreads();
+    if (bi >= n_bonds) break;
+    bond_body<T>(bi, bonds, partials, gamma, lam, pending, Yout, theta_a, flags, sweeps_out, cycles, vsave, D, jp);
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------- big-end update
@@ -1047,6 +1079,9 @@ cudaError_t Launch<T>::init() {
   e = cudaFuncSetAttribute(bond_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bond_smem_bytes(kMaxD, 2 * kMaxD));
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(bond_kernel_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bond_smem_bytes(kMaxD, 2 * kMaxD));
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)update_smem(kMaxD, sizeof(V2<T>)));
 }
@@ -1086,9 +1121,19 @@ cudaError_t Launch<T>::gram(const TileDesc* tiles, int n_tiles, const BondDesc* 
 template <typename T>
 cudaError_t Launch<T>::bond(const BondDesc* bonds, int n_bonds, const void* partials, void* gamma, double* lam,
                             double* pending, void* Y, double* theta_a, int* flags, unsigned long long* sweeps,
-                            unsigned long long* cycles, void* vsave, int D, JacobiParams jp, cudaStream_t st) {
+                            unsigned long long* cycles, void* vsave, int D, JacobiParams jp, cudaStream_t st,
+                            unsigned int* queue, int n_ctas) {
   if (n_bonds == 0) return cudaSuccess;
   const size_t sm = bond_smem_bytes(D, 2 * D);
+  if (queue) {
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    const int grid = n_ctas < n_bonds ? n_ctas : n_bonds;
+    bond_kernel_persistent<T><<<grid, kBondThreads, sm, st>>>(
+        n_bonds, queue, bonds, static_cast<const V2<T>*>(partials), static_cast<V2<T>*>(gamma), lam, pending,
+        static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles, static_cast<double2*>(vsave), D, jp);
+    return cudaGetLastError();
+  }
   bond_kernel<T><<<n_bonds, kBondThreads, sm, st>>>(bonds, static_cast<const V2<T>*>(partials),
                                                  static_cast<V2<T>*>(gamma), lam, pending,
                                                  static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles,

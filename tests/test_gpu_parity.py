@@ -246,3 +246,35 @@ def test_checkpoint_restore_and_readout_on_gpu_state():
     for k in range(len(E127)):
         peps.lam[k] = g.lambda_tensor(0, k).cpu().numpy()
     assert np.abs(peps.expect_z() - zb.cpu().numpy()).max() < 1e-12
+
+
+def test_persistent_schedule_is_bit_identical():
+    """The work-queue schedule changes which SM runs a bond, not its arithmetic."""
+    import torch
+    from ._gpu_util import gpu_lib
+    outs = []
+    for persistent in (0, 1):
+        g = gpu_lib()([(M127, E127), heavy_hex(*OSPREY)], 8, dtype="mixed")
+        g.set_schedule(persistent)
+        g.reset()
+        m = g.step(6, torch.tensor([0.7, 0.9], dtype=torch.float64, device="cuda"))
+        z, _ = g.expect_z()
+        outs.append((m.cpu().numpy(), z.cpu().numpy()))
+        assert g.status() == 0
+        g.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_autotuned_setting_stays_within_tolerance():
+    """The autotuner's choice, run from |0...0>, still matches the oracle (127 q, D = 8)."""
+    import torch
+    from paper_2309_15642_gb300.autotune import autotune, candidates
+    from ._gpu_util import gpu_lib
+    g = gpu_lib()([(M127, E127)], 8, dtype="mixed")
+    best, table = autotune(g, [0.9], warm_steps=4, steps=3)
+    assert any(all(best.get(k) == c.get(k) for k in c) for c in candidates("mixed")) or best.get("persistent") == 0
+    assert any(t["accepted"] for t in table)
+    means = g.step(6, torch.tensor([0.9], dtype=torch.float64, device="cuda")).cpu().numpy()[:, 0]
+    zo, _ = oracle_run(M127, E127, 8, 0.9, 6)
+    assert np.abs(means - zo.mean(axis=1)).max() < TOL["mixed"]
+    g.close()
