@@ -237,26 +237,31 @@ __device__ __forceinline__ bool rotation(float app, float aqq, float2 apq, float
   e = make_float2(apq.x * ig, -apq.y * ig);
   return true;
 }
-// FP64 version: the angle is taken in FP32 (accurate to ~1e-7, enough for the
-// sweep to shrink a_pq by that factor) and (c, s) and e are normalised in FP64
-// by two Newton steps, so J is unitary to FP64 rounding without FP64 divides
-// or square roots.
+// FP64 version: the angle is taken in FP32 and refined by one FP64 Newton step,
+// and (c, s) and e are normalised in FP64 by two Newton steps, so J is unitary
+// to FP64 rounding without FP64 divides or square roots.
 __device__ __forceinline__ bool rotation(double app, double aqq, double2 apq, double tol, double floor_abs,
                                          double& c, double& s, double2& e) {
   const double g2 = apq.x * apq.x + apq.y * apq.y;
   if (!(g2 > floor_abs * floor_abs && g2 > tol * tol * fabs(app * aqq))) return false;
   const float g2f = (float)g2;
   const float igf = rsqrtf(g2f);
-  const float zeta = (float)(aqq - app) * (0.5f * igf);
-  const float tf = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-  const double t = (double)tf;
+  double ig = (double)igf;
+  ig = ig * (1.5 - 0.5 * g2 * ig * ig);
+  ig = ig * (1.5 - 0.5 * g2 * ig * ig);
+  const float zetaf = (float)(aqq - app) * (0.5f * igf);
+  const float tf = copysignf(1.f, zetaf) / (fabsf(zetaf) + sqrtf(1.f + zetaf * zetaf));
+  // one Newton step on t^2 + 2 zeta t - 1 = 0 in FP64 (the FP32 reciprocal of the
+  // derivative suffices): the angle becomes FP64-accurate, so a rotation zeroes
+  // a_pq to rounding instead of shrinking it by the FP32 angle error
+  const double zeta = (aqq - app) * (0.5 * ig);
+  double t = (double)tf;
+  const double f = fma(t, t, fma(2.0 * zeta, t, -1.0));
+  t -= f * (double)__frcp_rn((float)(2.0 * (t + zeta)));
   const double u = 1.0 + t * t;
   double cc = (double)rsqrtf((float)u);
   cc = cc * (1.5 - 0.5 * u * cc * cc);
   cc = cc * (1.5 - 0.5 * u * cc * cc);
-  double ig = (double)igf;
-  ig = ig * (1.5 - 0.5 * g2 * ig * ig);
-  ig = ig * (1.5 - 0.5 * g2 * ig * ig);
   c = cc;
   s = t * cc;
   e = make_double2(apq.x * ig, -apq.y * ig);
@@ -378,6 +383,21 @@ __device__ int jacobi_hermitian(V2<R>* A, int lda, V2<R>* V, int ldv, int n, R t
   return max_sweeps + 1;
 }
 
+// Bijection from [0, n(n+1)/2) onto the upper triangle i <= j of an n x n
+// matrix (n even): row r is paired with row n-1-r (lengths n-r and r+1), so a
+// loop over the triangle keeps every lane busy.
+__device__ __forceinline__ void upper_index(int idx, int n, int& i, int& j) {
+  const int w = n + 1;
+  const int r = idx / w, c = idx - (idx / w) * w;
+  if (c < n - r) {
+    i = r;
+    j = r + c;
+  } else {
+    i = n - 1 - r;
+    j = i + (c - (n - r));
+  }
+}
+
 // Re-orthonormalise the columns of V (n x n, row stride n) in FP64.  V is a
 // product of FP32 rotations, so G = V^dagger V = I + E with |E| ~ 1e-6 and the
 // Cholesky factor R (G = R^dagger R) and its inverse follow from short series
@@ -389,9 +409,9 @@ __device__ int jacobi_hermitian(V2<R>* A, int lda, V2<R>* V, int ldv, int n, R t
 // stride ldg); dg[n] holds their diagonals.  Returns max |E_ij|.
 __device__ double orthonormalise(double2* V, int n, double2* G, int ldg, double* dg, double* scal) {
   // E = V^dagger V - I (upper triangle)
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx - (idx / n) * n;
-    if (j < i) continue;
+  for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+    int i, j;
+    upper_index(idx, n, i, j);
     double2 acc = make_double2(i == j ? -1.0 : 0.0, 0.0);
     for (int r = 0; r < n; ++r) fma_conj<double>(acc, V[r * n + i], V[r * n + j]);
     if (i == j) acc.y = 0.0;
@@ -400,9 +420,9 @@ __device__ double orthonormalise(double2* V, int n, double2* G, int ldg, double*
   if (threadIdx.x == 0) scal[6] = 0.0;
   __syncthreads();
   // K = X1^dagger X1 with X1 = P(E): K_ij = sum_{k <= i} conj(X1_ki) X1_kj  (i <= j)
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx - (idx / n) * n;
-    if (j < i) continue;
+  for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+    int i, j;
+    upper_index(idx, n, i, j);
     double2 acc = make_double2(0.0, 0.0);
     for (int k = 0; k <= i; ++k) {
       double2 xki = G[k * ldg + i], xkj = G[k * ldg + j];
@@ -415,9 +435,9 @@ __device__ double orthonormalise(double2* V, int n, double2* G, int ldg, double*
   }
   __syncthreads();
   // X = P(E - K) in the upper triangle; record max |E|
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx - (idx / n) * n;
-    if (j < i) continue;
+  for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+    int i, j;
+    upper_index(idx, n, i, j);
     const double2 e = G[i * ldg + j];
     const double ae = fabs(e.x) + fabs(e.y);
     if (ae > scal[6]) atomicMax(reinterpret_cast<unsigned long long*>(scal + 6), __double_as_longlong(ae));
@@ -426,9 +446,9 @@ __device__ double orthonormalise(double2* V, int n, double2* G, int ldg, double*
   }
   __syncthreads();
   // X^2 (upper triangular) into the strict lower triangle and dg
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx - (idx / n) * n;
-    if (j < i) continue;
+  for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+    int i, j;
+    upper_index(idx, n, i, j);
     double2 acc = make_double2(0.0, 0.0);
     for (int k = i; k <= j; ++k) fma_c<double>(acc, G[i * ldg + k], G[k * ldg + j]);
     if (i == j) dg[i] = acc.x;
@@ -436,9 +456,9 @@ __device__ double orthonormalise(double2* V, int n, double2* G, int ldg, double*
   }
   __syncthreads();
   // M = X^2 - X in the upper triangle
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx - (idx / n) * n;
-    if (j < i) continue;
+  for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+    int i, j;
+    upper_index(idx, n, i, j);
     if (i == j) G[i * ldg + i] = make_double2(dg[i] - G[i * ldg + i].x, 0.0);
     else G[i * ldg + j] = csub(G[j * ldg + i], G[i * ldg + j]);
   }
@@ -513,9 +533,9 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
     X[i * ldr + j] = acc;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx - (idx / n) * n;
-    if (j < i) continue;
+  for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+    int i, j;
+    upper_index(idx, n, i, j);
     double2 acc = make_double2(0.0, 0.0);
     for (int k = 0; k < n; ++k) fma_conj<double>(acc, Vm[k * n + i], X[k * ldr + j]);
     RHO[i * ldr + j] = acc;
@@ -744,9 +764,9 @@ __device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T
       H[x * D + l] = acc;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      const int x = idx / n, y = idx - (idx / n) * n;
-      if (y < x) continue;
+    for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+      int x, y;
+      upper_index(idx, n, x, y);
       V2<T> acc = mk<T>(0, 0);
       for (int l = 0; l < D; ++l) fma_c<T>(acc, H[x * D + l], F[y * D + l]);
       const int tx = x & 1, ty = y & 1;
