@@ -27,7 +27,7 @@
  *
  * Scope: graphs in which every edge has an end of degree <= 2 and every vertex
  * has degree <= 3 (true of the heavy-hex lattices of the paper, Fig. 1);
- * 1 <= D <= 32.
+ * 1 <= D <= 64 (gpeps_grad: D <= 16; gpeps_bond_update_noalloc: D <= 32).
  */
 #ifndef GPEPS_H
 #define GPEPS_H
@@ -81,7 +81,7 @@ typedef struct gpeps_handle gpeps_handle;
  * arrays are copied; *out receives the handle (free with gpeps_destroy).
  * Errors: GPEPS_EINVAL for a malformed graph, a colouring that is not a
  * matching, a vertex of degree > 3, an edge joining two degree-3 vertices,
- * D outside [1, 32] or an unknown dtype.
+ * D outside [1, 64] or an unknown dtype.
  */
 int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int32_t dtype,
                  void* stream, gpeps_handle** out);
@@ -90,14 +90,17 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
  * Bytes of the two caller-owned device buffers.  state: every Gamma_i (complex,
  * physical index outermost, legs in sorted-neighbour order, last leg fastest)
  * and every lambda_e (float64[D]).  work: kick angles, bond work lists,
- * per-bond scratch, <Z> outputs and the flag word.  Both need 256-byte
- * alignment (cudaMalloc and torch give it).
+ * per-bond scratch (for D > 34 also the 2D x 2D bond eigenproblems that do not
+ * fit in shared memory: 772 KB per bond of the largest colour class at D = 64),
+ * <Z> outputs and the flag word.  Both need 256-byte alignment (cudaMalloc and
+ * torch give it).
  */
 int gpeps_query_workspace(const gpeps_handle* h, size_t* state_bytes, size_t* work_bytes);
 
 /* Attach the two device buffers (sizes from gpeps_query_workspace) and upload
  * the work lists; enqueues copies on the stream.  Re-binding invalidates a
- * captured step graph.  Errors: GPEPS_EINVAL for NULL or misaligned pointers. */
+ * captured step graph.  Errors: GPEPS_EINVAL for NULL or misaligned pointers,
+ * or a current device with less than 227 KB of opt-in shared memory per block. */
 int gpeps_bind(gpeps_handle* h, void* d_state, void* d_work);
 
 /* Product state |0...0> of Eq. 3 on every instance: Gamma_i[0,0,...,0] = 1,

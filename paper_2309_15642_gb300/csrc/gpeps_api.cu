@@ -73,7 +73,8 @@ struct gpeps_handle {
   size_t state_bytes = 0, work_bytes = 0;
   size_t s_lam = 0, s_gamma = 0;
   size_t w_pending = 0, w_flags = 0, w_sweeps = 0, w_cycles = 0, w_queue = 0, w_z = 0, w_mean = 0, w_sites = 0, w_inst_site0 = 0,
-         w_site_inst = 0, w_site_off = 0, w_partials = 0, w_Y = 0, w_theta_a = 0;
+         w_site_inst = 0, w_site_off = 0, w_partials = 0, w_Y = 0, w_theta_a = 0, w_bond_scratch = 0;
+  size_t bond_slot = 0;  // bytes per bond-kernel CTA of global scratch (0: all in shared memory)
   char* d_state = nullptr;
   char* d_work = nullptr;
   bool bound = false;
@@ -228,7 +229,8 @@ int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr, void* vsave = 
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[1], h->stream));
   GP_CUDA(Launch<T>::bond(bonds, nbd, partials, h->gamma(), h->lam(), h->pending(), Y, theta_a, h->flags(),
                           h->sweeps(), h->cycles(), vsave, h->D, h->jp, h->stream,
-                          h->persistent ? h->at<unsigned int>(h->w_queue) : nullptr, h->n_sms));
+                          h->persistent ? h->at<unsigned int>(h->w_queue) : nullptr, h->n_sms,
+                          h->bond_slot ? h->d_work + h->w_bond_scratch : nullptr));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[2], h->stream));
   GP_CUDA(Launch<T>::update(tiles, nt, bonds, h->gamma(), h->lam(), Y, theta_a, h->D, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[3], h->stream));
@@ -425,6 +427,10 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   h->w_partials = carve((size_t)h->max_parts * 2 * D * D * h->elt);
   h->w_Y = carve((size_t)h->max_bonds * 2 * D * D * h->elt);
   h->w_theta_a = carve((size_t)h->max_bonds * sizeof(double));
+  // n x n bond matrices beyond shared memory: one slot per bond of the largest
+  // class (a CTA of either schedule indexes its slot by blockIdx.x)
+  h->bond_slot = bond_footprint(D, kBondSmemMax).slot;
+  if (h->bond_slot) h->w_bond_scratch = carve((size_t)h->max_bonds * h->bond_slot);
   h->work_bytes = w;
   *out = h;
   return GPEPS_OK;
@@ -449,6 +455,9 @@ int gpeps_bind(gpeps_handle* h, void* d_state, void* d_work) {
     int dev = 0;
     GP_CUDA(cudaGetDevice(&dev));
     GP_CUDA(cudaDeviceGetAttribute(&h->n_sms, cudaDevAttrMultiProcessorCount, dev));
+    int optin = 0;
+    GP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if ((size_t)optin < kSmemOptin) return GPEPS_EINVAL;  // not an sm_100-class device
   }
   auto up = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
     if (bytes == 0) return cudaSuccess;

@@ -10,7 +10,10 @@
 
 namespace gpeps {
 
-constexpr int kMaxD = 32;          // bond dimension limit of this build
+constexpr int kMaxD = 64;          // bond dimension limit of this build
+constexpr int kMaxLevel = 32;      // indices of one extra FP32 level (one per lane of a warp)
+constexpr size_t kSmemOptin = 232448;  // opt-in shared memory per CTA of sm_100/sm_103 (227 KB)
+constexpr size_t kBondSmemMax = kSmemOptin - 1024;  // dynamic part of a bond CTA (static variables need the rest)
 constexpr int kTileRows = 64;      // rows of a big-side tile (Gram and update launches)
 constexpr int kThreads = 256;      // threads of the streaming and readout CTAs
 constexpr int kBondThreads = 512;  // threads of the bond-eigenproblem CTA (one CTA per SM: more warps hide FP64 latency)
@@ -85,7 +88,8 @@ struct Launch {
   static cudaError_t bond(const BondDesc* bonds, int n_bonds, const void* partials, void* gamma, double* lam,
                           double* pending, void* Y, double* theta_a, int* flags,
                           unsigned long long* sweeps, unsigned long long* cycles, void* vsave, int D,
-                          JacobiParams jp, cudaStream_t st, unsigned int* queue = nullptr, int n_ctas = 0);
+                          JacobiParams jp, cudaStream_t st, unsigned int* queue = nullptr, int n_ctas = 0,
+                          void* scratch = nullptr);
   static cudaError_t update(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, void* gamma,
                             const double* lam, const void* Y, const double* theta_a, int D, cudaStream_t st);
   static cudaError_t readout(const SiteDesc* sites, int n_sites, const void* gamma, const double* lam,
@@ -109,6 +113,15 @@ struct Adjoint {
 };
 
 cudaError_t launch_mean(const double* z, const int32_t* inst_site0, int n_inst, double* mean, cudaStream_t st);
-size_t bond_smem_bytes(int D, int n);
+
+// Memory of one bond-eigenproblem CTA at bond dimension D: the dynamic shared
+// memory of its launch and, when the n x n matrices (n = 2D) do not fit the
+// device's opt-in shared memory `smem_optin`, the bytes of the global scratch
+// slot that holds them (0 otherwise; one slot per concurrently running bond).
+struct BondFootprint {
+  size_t smem;
+  size_t slot;
+};
+BondFootprint bond_footprint(int D, size_t smem_optin);
 
 }  // namespace gpeps

@@ -34,13 +34,14 @@ constexpr size_t kSweepsOff = 16;                                // u64[4]
 constexpr size_t kCyclesOff = 48;                                // u64[kCounters]
 constexpr size_t kPendingOff = 256;                              // double pending[2], theta_a[1]
 constexpr size_t kDescOff = 512;                                 // BondDesc, TileDesc[...]
-constexpr size_t kMaxTiles = (kMaxD * kMaxD + kTileRows - 1) / kTileRows;
+constexpr int kNoallocMaxD = 32;                                 // bond dimension limit of this entry point
+constexpr size_t kMaxTiles = (kNoallocMaxD * kNoallocMaxD + kTileRows - 1) / kTileRows;
 constexpr size_t kYOff = 1024;                                   // 2 D^2 complex
-constexpr size_t kPartOff = kYOff + (size_t)2 * kMaxD * kMaxD * 16;  // tiles x 2 D^2 complex
+constexpr size_t kPartOff = kYOff + (size_t)2 * kNoallocMaxD * kNoallocMaxD * 16;  // tiles x 2 D^2 complex
 
 static_assert(kCyclesOff + kCounters * sizeof(unsigned long long) <= kPendingOff, "counter area");
 static_assert(sizeof(BondDesc) + kMaxTiles * sizeof(TileDesc) <= kYOff - kDescOff, "descriptor area");
-static_assert(kPartOff + kMaxTiles * 2 * kMaxD * kMaxD * 16 <= GPEPS_NOALLOC_SCRATCH_BYTES, "scratch size");
+static_assert(kPartOff + kMaxTiles * 2 * kNoallocMaxD * kNoallocMaxD * 16 <= GPEPS_NOALLOC_SCRATCH_BYTES, "scratch size");
 
 int fail_cuda(cudaError_t) { return GPEPS_ECUDA; }
 
@@ -129,7 +130,7 @@ int run(char* scratch, int D, void* base, const BondDesc& bd, int n_tiles, doubl
 extern "C" int gpeps_bond_update_noalloc(int32_t D, int32_t dtype, void* gamma_a, int32_t deg_a, int32_t leg_a,
                                          void* gamma_b, int32_t deg_b, int32_t leg_b, double* lam,
                                          const double* theta, void* stream, int32_t* flags_out) {
-  if (D < 1 || D > kMaxD) return GPEPS_EINVAL;
+  if (D < 1 || D > kNoallocMaxD) return GPEPS_EINVAL;
   if (dtype != GPEPS_C128 && dtype != GPEPS_MIXED_C64) return GPEPS_EINVAL;
   if (!gamma_a || !gamma_b || !lam || gamma_a == gamma_b) return GPEPS_EINVAL;
   if (deg_a < 1 || deg_a > 3 || deg_b < 1 || deg_b > 3) return GPEPS_EINVAL;

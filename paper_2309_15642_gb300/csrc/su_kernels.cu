@@ -186,16 +186,20 @@ __device__ __forceinline__ V2<T> c_sub(V2<T> a, V2<T> b) {
   return mk<T>(a.x - b.x, a.y - b.y);
 }
 
-// Shared-memory layout of bond_kernel for a bond whose small end has nb rows
-// (n = 2 nb).  Three large regions of complex doubles:
+// Memory layout of bond_kernel for a bond whose small end has nb rows
+// (n = 2 nb).  Three large regions of complex doubles (the big part):
 //   R    [n][n+1]                 the bond matrix rho, later V^dagger rho V
 //   Vr   max(n*n, 2D^2 + n*D)     Gram blocks C_s and H while rho is formed, then V
 //   X    max(n*(n+1), n*D)        F; then the FP32 copies rho32 [n][n+1] and V32 [n][n];
 //                                 then the Gram/Cholesky factor of V; then rho V; then F again
-// followed by the small arrays (rotations of both precisions, eigenvalues, indices).
+// and the small arrays (rotations of both precisions, eigenvalues, indices).
+// Both parts sit in shared memory when they fit (D <= 34); beyond that the big
+// part is a slot of a global scratch buffer (held in L2 by the running CTAs)
+// and only the small arrays stay in shared memory.  Offsets of the big part
+// are relative to its base, offsets of the small arrays to theirs.
 struct BondSmem {
-  size_t off_R, off_V, off_X, off_re, off_re32, off_lamo, off_ev, off_sv, off_rc, off_rs, off_scal, off_rc32,
-      off_rs32, off_int, total;
+  size_t off_R, off_V, off_X, big, off_re, off_re32, off_lamo, off_ev, off_sv, off_rc, off_rs, off_scal, off_rc32,
+      off_rs32, off_int, small;
   __host__ __device__ BondSmem(int D, int n) {
     const int m = n / 2;
     size_t v = (size_t)n * n;
@@ -205,7 +209,8 @@ struct BondSmem {
     off_R = 0;
     off_V = off_R + (size_t)n * (n + 1) * 16;
     off_X = off_V + v * 16;
-    off_re = off_X + x * 16;
+    big = off_X + x * 16;
+    off_re = 0;
     off_re32 = off_re + (size_t)m * 16;
     off_lamo = off_re32 + (size_t)((m + 1) / 2) * 16;
     off_ev = off_lamo + (size_t)D * 8;
@@ -216,11 +221,15 @@ struct BondSmem {
     off_rc32 = off_scal + 8 * 8;
     off_rs32 = off_rc32 + (size_t)((m + 1) / 2) * 8;
     off_int = off_rs32 + (size_t)((m + 1) / 2) * 8;
-    total = off_int + (size_t)(n + 2 * m + 8) * 4;
+    small = (off_int + (size_t)(n + 2 * m + 8) * 4 + 15) & ~(size_t)15;
   }
 };
 
-size_t bond_smem_bytes(int D, int n) { return BondSmem(D, n).total; }
+BondFootprint bond_footprint(int D, size_t smem_optin) {
+  const BondSmem L(D, 2 * D);
+  if (L.big + L.small <= smem_optin) return BondFootprint{L.big + L.small, 0};
+  return BondFootprint{L.small, (L.big + 255) & ~(size_t)255};
+}
 
 // Rotation of the pair (p, q) (Golub & Van Loan, Alg. 8.4.1, sym.schur2, after
 // the diagonal phase that makes a_pq real): J = [[c, s], [-s e, c e]],
@@ -467,16 +476,23 @@ __device__ double orthonormalise(double2* V, int n, double2* G, int ldg, double*
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int r = warp; r < n; r += nw) {
     double2* v = V + r * n;
-    double2 out[kMaxD * 2 / 32];
-    int cnt = 0;
-    for (int j = lane; j < n; j += 32) {
-      double2 acc = v[j];
-      for (int i = 0; i <= j; ++i) fma_c<double>(acc, v[i], G[i * ldg + j]);
-      out[cnt++] = acc;
+    constexpr int kPer = kMaxD * 2 / 32;  // columns per lane (n <= 2 kMaxD)
+    double2 out[kPer];
+#pragma unroll
+    for (int c = 0; c < kPer; ++c) {
+      const int j = lane + 32 * c;
+      if (j < n) {
+        double2 acc = v[j];
+        for (int i = 0; i <= j; ++i) fma_c<double>(acc, v[i], G[i * ldg + j]);
+        out[c] = acc;
+      }
     }
     __syncwarp();
-    cnt = 0;
-    for (int j = lane; j < n; j += 32) v[j] = out[cnt++];
+#pragma unroll
+    for (int c = 0; c < kPer; ++c) {
+      const int j = lane + 32 * c;
+      if (j < n) v[j] = out[c];
+    }
     __syncwarp();
   }
   __syncthreads();
@@ -572,7 +588,7 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
         int ns = 0;
         for (int i = 0; i < n; ++i)
           if (dcur[i] <= hi && dcur[i] > lo) cand[ns++] = i;
-        // keep at most n/2, the largest first
+        // keep at most min(n/2, 32), the largest first
         for (int a = 0; a < ns; ++a)
           for (int b = a + 1; b < ns; ++b)
             if (dcur[cand[b]] > dcur[cand[a]]) {
@@ -581,6 +597,7 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
               cand[b] = t;
             }
         if (ns > n / 2) ns = n / 2;
+        if (ns > kMaxLevel) ns = kMaxLevel;
         ns &= ~1;  // even: drop the smallest
         iflag[1] = ns;
         scal[7] = ns > 0 ? dcur[cand[0]] : 0.0;
@@ -696,7 +713,7 @@ template <typename T>
 __device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T>* __restrict__ partials, V2<T>* gamma,
                 double* lam, double* pending, V2<T>* __restrict__ Yout, double* __restrict__ theta_a,
                 int* flags, unsigned long long* sweeps_out, unsigned long long* cycles, double2* vsave, int D,
-                JacobiParams jp) {
+                JacobiParams jp, unsigned char* big) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BondDesc bd = bonds[bi];
   const SideDesc sb = bd.b;
@@ -704,24 +721,26 @@ __device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T
   const int n = 2 * nb;
   const int D2 = D * D;
   const BondSmem L(D, n);
-  double2* RHO = reinterpret_cast<double2*>(smem_raw + L.off_R);  // [n][n+1]
-  double2* Vr = reinterpret_cast<double2*>(smem_raw + L.off_V);
-  double2* X = reinterpret_cast<double2*>(smem_raw + L.off_X);
+  unsigned char* bigp = big ? big : smem_raw;                   // R, Vr, X
+  unsigned char* smallp = big ? smem_raw : smem_raw + L.big;   // the small arrays
+  double2* RHO = reinterpret_cast<double2*>(bigp + L.off_R);  // [n][n+1]
+  double2* Vr = reinterpret_cast<double2*>(bigp + L.off_V);
+  double2* X = reinterpret_cast<double2*>(bigp + L.off_X);
   V2<T>* Cs = reinterpret_cast<V2<T>*>(Vr);  // [2][D][D], storage precision
   V2<T>* H = Cs + 2 * D2;                     // [n][D]
   double2* Vm = Vr;                           // [n][n]
   V2<T>* F = reinterpret_cast<V2<T>*>(X);     // [n][D]
-  double2* re = reinterpret_cast<double2*>(smem_raw + L.off_re);
-  float2* re32 = reinterpret_cast<float2*>(smem_raw + L.off_re32);
-  double* lamo = reinterpret_cast<double*>(smem_raw + L.off_lamo);
-  double* ev = reinterpret_cast<double*>(smem_raw + L.off_ev);
-  double* sv = reinterpret_cast<double*>(smem_raw + L.off_sv);
-  double* rc = reinterpret_cast<double*>(smem_raw + L.off_rc);
-  double* rs = reinterpret_cast<double*>(smem_raw + L.off_rs);
-  double* scal = reinterpret_cast<double*>(smem_raw + L.off_scal);  // [0] trace [1] norm [2] max lambda_o [4] tmp
-  float* rc32 = reinterpret_cast<float*>(smem_raw + L.off_rc32);
-  float* rs32 = reinterpret_cast<float*>(smem_raw + L.off_rs32);
-  int* order = reinterpret_cast<int*>(smem_raw + L.off_int);
+  double2* re = reinterpret_cast<double2*>(smallp + L.off_re);
+  float2* re32 = reinterpret_cast<float2*>(smallp + L.off_re32);
+  double* lamo = reinterpret_cast<double*>(smallp + L.off_lamo);
+  double* ev = reinterpret_cast<double*>(smallp + L.off_ev);
+  double* sv = reinterpret_cast<double*>(smallp + L.off_sv);
+  double* rc = reinterpret_cast<double*>(smallp + L.off_rc);
+  double* rs = reinterpret_cast<double*>(smallp + L.off_rs);
+  double* scal = reinterpret_cast<double*>(smallp + L.off_scal);  // [0] trace [1] norm [2] max lambda_o [4] tmp
+  float* rc32 = reinterpret_cast<float*>(smallp + L.off_rc32);
+  float* rs32 = reinterpret_cast<float*>(smallp + L.off_rs32);
+  int* order = reinterpret_cast<int*>(smallp + L.off_int);
   int* rp = order + n;
   int* rq = rp + n / 2;
   int* iflag = rq + n / 2;  // [4]
@@ -897,14 +916,16 @@ __device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T
   mark(5);
 }
 
-// One CTA per bond.
+// One CTA per bond.  `scratch` (null when everything fits in shared memory):
+// one slot of `slot` bytes per CTA for the big part of the layout.
 template <typename T>
 __global__ void __launch_bounds__(kBondThreads, 1)
     bond_kernel(const BondDesc* __restrict__ bonds, const V2<T>* __restrict__ partials, V2<T>* gamma, double* lam,
                 double* pending, V2<T>* __restrict__ Yout, double* __restrict__ theta_a, int* flags,
-                unsigned long long* sweeps_out, unsigned long long* cycles, double2* vsave, int D, JacobiParams jp) {
+                unsigned long long* sweeps_out, unsigned long long* cycles, double2* vsave, int D, JacobiParams jp,
+                unsigned char* scratch, size_t slot) {
   bond_body<T>(blockIdx.x, bonds, partials, gamma, lam, pending, Yout, theta_a, flags, sweeps_out, cycles, vsave, D,
-               jp);
+               jp, scratch ? scratch + (size_t)blockIdx.x * slot : nullptr);
 }
 
 // Persistent form: one CTA per SM takes bonds from a work queue (bonds are
@@ -916,15 +937,17 @@ __global__ void __launch_bounds__(kBondThreads, 1)
                            const V2<T>* __restrict__ partials, V2<T>* gamma, double* lam, double* pending,
                            V2<T>* __restrict__ Yout, double* __restrict__ theta_a, int* flags,
                            unsigned long long* sweeps_out, unsigned long long* cycles, double2* vsave, int D,
-                           JacobiParams jp) {
+                           JacobiParams jp, unsigned char* scratch, size_t slot) {
   __shared__ int next;
+  unsigned char* big = scratch ? scratch + (size_t)blockIdx.x * slot : nullptr;
   for (;;) {
     if (threadIdx.x == 0) next = (int)atomicAdd(queue, 1u);
     __syncthreads();
     const int bi = next;
     __syncthreads();
     if (bi >= n_bonds) break;
-    bond_body<T>(bi, bonds, partials, gamma, lam, pending, Yout, theta_a, flags, sweeps_out, cycles, vsave, D, jp);
+    bond_body<T>(bi, bonds, partials, gamma, lam, pending, Yout, theta_a, flags, sweeps_out, cycles, vsave, D, jp,
+                 big);
     __syncthreads();
   }
 }
@@ -939,15 +962,14 @@ __global__ void __launch_bounds__(kThreads)
   const TileDesc t = tiles[blockIdx.x];
   const SideDesc sa = bonds[t.bond].a;
   const int D2 = D * D;
-  V2<T>* Ys = reinterpret_cast<V2<T>*>(smem_raw);  // [2][D][D]
-  V2<T>* A = Ys + 2 * D2;                          // tile, layout chosen for the write order
+  V2<T>* Ys = reinterpret_cast<V2<T>*>(smem_raw);  // [D][D]: Y_s of the spin block being written
+  V2<T>* A = Ys + D2;                              // tile, layout chosen for the write order
   const size_t a_elems_r = (size_t)t.nrows * (2 * D + 1), a_elems_c = (size_t)(2 * D) * (t.nrows + 1);
   float* mask = reinterpret_cast<float*>(A + (a_elems_r > a_elems_c ? a_elems_r : a_elems_c));
   __shared__ double cut[2];
   const bool kfast = sa.str_k == 1;
   // kfast: A[r][(2D+1)] with (s, k) inside; else A[(s, k)][nrows+1] with r inside
   const int ldr = 2 * D + 1, ldc = t.nrows + 1;
-  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) Ys[o] = Y[(int64_t)t.bond * 2 * D2 + o];
   if (threadIdx.x < 2) {
     const int lo = threadIdx.x == 0 ? sa.lam_o1 : sa.lam_o2;
     double mx = 0.0;
@@ -988,32 +1010,34 @@ __global__ void __launch_bounds__(kThreads)
     mask[r] = ok ? 1.f : 0.f;
   }
   __syncthreads();
-  const int nout = t.nrows * 2 * D;
-  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-    int r, sidx, kk;
-    if (kfast) {  // kk fastest
-      r = o / (2 * D);
-      const int rem = o - r * 2 * D;
-      sidx = rem / D;
-      kk = rem - sidx * D;
-    } else {  // r fastest
-      const int col = o / t.nrows;
-      r = o - col * t.nrows;
-      sidx = col / D;
-      kk = col - sidx * D;
+  // one pass per spin block s: Gamma_a'[s][row][kk] = mask(row) sum_k A_s[row][k] Y_s[k][kk]
+  const int nout = t.nrows * D;
+  for (int sidx = 0; sidx < 2; ++sidx) {
+    for (int o = threadIdx.x; o < D2; o += blockDim.x) Ys[o] = Y[((int64_t)t.bond * 2 + sidx) * D2 + o];
+    __syncthreads();
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+      int r, kk;
+      if (kfast) {  // kk fastest
+        r = o / D;
+        kk = o - r * D;
+      } else {  // r fastest
+        kk = o / t.nrows;
+        r = o - kk * t.nrows;
+      }
+      V2<T> acc = mk<T>(0, 0);
+      const V2<T>* Yc = Ys + kk;
+      if (kfast) {
+        const V2<T>* Ar = A + r * ldr + sidx * D;
+        for (int k = 0; k < D; ++k) fma_c<T>(acc, Ar[k], Yc[k * D]);
+      } else {
+        const V2<T>* Ar = A + (sidx * D) * ldc + r;
+        for (int k = 0; k < D; ++k) fma_c<T>(acc, Ar[k * ldc], Yc[k * D]);
+      }
+      const T mk_ = (T)mask[r];
+      const RowPos p = row_pos(sa, t.row0 + r);
+      gamma[elem(sa, sidx, p, kk)] = mk<T>(acc.x * mk_, acc.y * mk_);
     }
-    V2<T> acc = mk<T>(0, 0);
-    const V2<T>* Yc = Ys + sidx * D2 + kk;
-    if (kfast) {
-      const V2<T>* Ar = A + r * ldr + sidx * D;
-      for (int k = 0; k < D; ++k) fma_c<T>(acc, Ar[k], Yc[k * D]);
-    } else {
-      const V2<T>* Ar = A + (sidx * D) * ldc + r;
-      for (int k = 0; k < D; ++k) fma_c<T>(acc, Ar[k * ldc], Yc[k * D]);
-    }
-    const T mk_ = (T)mask[r];
-    const RowPos p = row_pos(sa, t.row0 + r);
-    gamma[elem(sa, sidx, p, kk)] = mk<T>(acc.x * mk_, acc.y * mk_);
+    __syncthreads();
   }
 }
 
@@ -1086,7 +1110,7 @@ __global__ void mean_kernel(const double* __restrict__ z, const int32_t* __restr
 static size_t gram_smem(int D) { return (size_t)kTileRows * (2 * D + 1) * 16; }
 static size_t update_smem(int D, size_t elt) {
   const size_t r = (size_t)kTileRows * (2 * D + 1), c = (size_t)(kTileRows + 1) * 2 * D;
-  return (size_t)2 * D * D * elt + (r > c ? r : c) * elt + (size_t)kTileRows * 4 + 64;
+  return (size_t)D * D * elt + (r > c ? r : c) * elt + (size_t)kTileRows * 4 + 64;
 }
 
 // Opt in to the dynamic shared memory of the largest supported D (called once
@@ -1096,11 +1120,10 @@ cudaError_t Launch<T>::init() {
   cudaError_t e = cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)gram_smem(kMaxD));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(bond_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)bond_smem_bytes(kMaxD, 2 * kMaxD));
+  e = cudaFuncSetAttribute(bond_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBondSmemMax);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(bond_kernel_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)bond_smem_bytes(kMaxD, 2 * kMaxD));
+                           (int)kBondSmemMax);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)update_smem(kMaxD, sizeof(V2<T>)));
@@ -1142,22 +1165,24 @@ template <typename T>
 cudaError_t Launch<T>::bond(const BondDesc* bonds, int n_bonds, const void* partials, void* gamma, double* lam,
                             double* pending, void* Y, double* theta_a, int* flags, unsigned long long* sweeps,
                             unsigned long long* cycles, void* vsave, int D, JacobiParams jp, cudaStream_t st,
-                            unsigned int* queue, int n_ctas) {
+                            unsigned int* queue, int n_ctas, void* scratch) {
   if (n_bonds == 0) return cudaSuccess;
-  const size_t sm = bond_smem_bytes(D, 2 * D);
+  const BondFootprint fp = bond_footprint(D, kBondSmemMax);
+  if (fp.slot && !scratch) return cudaErrorInvalidValue;
+  unsigned char* sp = fp.slot ? static_cast<unsigned char*>(scratch) : nullptr;
   if (queue) {
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     const int grid = n_ctas < n_bonds ? n_ctas : n_bonds;
-    bond_kernel_persistent<T><<<grid, kBondThreads, sm, st>>>(
+    bond_kernel_persistent<T><<<grid, kBondThreads, fp.smem, st>>>(
         n_bonds, queue, bonds, static_cast<const V2<T>*>(partials), static_cast<V2<T>*>(gamma), lam, pending,
-        static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles, static_cast<double2*>(vsave), D, jp);
+        static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles, static_cast<double2*>(vsave), D, jp, sp, fp.slot);
     return cudaGetLastError();
   }
-  bond_kernel<T><<<n_bonds, kBondThreads, sm, st>>>(bonds, static_cast<const V2<T>*>(partials),
-                                                 static_cast<V2<T>*>(gamma), lam, pending,
-                                                 static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles,
-                                                 static_cast<double2*>(vsave), D, jp);
+  bond_kernel<T><<<n_bonds, kBondThreads, fp.smem, st>>>(bonds, static_cast<const V2<T>*>(partials),
+                                                      static_cast<V2<T>*>(gamma), lam, pending,
+                                                      static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles,
+                                                      static_cast<double2*>(vsave), D, jp, sp, fp.slot);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 
     python tests/golden/make_oracle_golden.py eagle_sweep16_d16
     python tests/golden/make_oracle_golden.py heavyhex_mix_d32
+    python tests/golden/make_oracle_golden.py eagle_d64
 
 Each run writes ``tests/golden/oracle_<workload>.json``: the mean <Z> of every
 instance after every Trotter step, the per-qubit <Z> after a few sampled steps
@@ -24,7 +25,8 @@ import numpy as np  # noqa: E402
 from oracle.su import GPEPS  # noqa: E402
 from workloads import kick_angles, workload  # noqa: E402
 
-SAMPLE_STEPS = {"eagle_sweep16_d16": [1, 4, 5, 10, 20], "heavyhex_mix_d32": [1, 5, 6, 10, 25, 50]}
+SAMPLE_STEPS = {"eagle_sweep16_d16": [1, 4, 5, 10, 20], "heavyhex_mix_d32": [1, 5, 6, 10, 25, 50],
+                "eagle_d64": [1, 5, 6, 7, 8]}
 
 
 def sampled_edges(n_edges, k=8):

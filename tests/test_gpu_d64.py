@@ -1,0 +1,161 @@
+"""Bond dimension D = 64: 128 x 128 bond eigenproblems, whose matrices the bond
+kernel keeps in a global-memory slot per CTA instead of shared memory.
+
+Pins: the exact regime (a heavy-hex tree with D = 2^n; every qubit of the
+127-qubit lattice against its light cone), the oracle on 127 qubits for 8 steps
+(truncation from step 7; committed values of ``tests/golden/make_oracle_golden.py
+eagle_d64``), and the full-size 1121-qubit lattice in the launch configuration of
+the benchmark (graph replay) checked bond by bond: after 7 steps the oracle
+updates sampled bonds of colour class 0 from the GPU's own state, and their new
+lambda and the <Z> of both ends must agree with the GPU's update.
+Tolerances as in test_gpu_parity.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import statevector as sv
+from oracle import su
+from oracle.lightcone import lightcone_z
+from workloads import CONDOR, EAGLE, heavy_hex, induced_subgraph, workload
+
+from ._gpu_util import gpu_lib, run_layers, split
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-10, "mixed": 1e-4}
+TOL_SITE_TRUNC = {"c128": 5e-9, "mixed": 1e-4}
+M127, E127 = heavy_hex(*EAGLE)
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def lam_check(gpu_lam, orc_lam, dtype, truncated=False):
+    d = np.abs(np.sort(gpu_lam)[::-1] - np.sort(orc_lam)[::-1])
+    assert d.max() < (1e-6 if dtype == "c128" else 2e-3), d.max()
+    if dtype == "c128":
+        big = np.sort(orc_lam)[::-1] > 1e-3
+        if big.any():
+            assert d[big].max() < (5e-8 if truncated else 1e-9), d[big].max()
+
+
+@pytest.mark.parametrize("dtype", ["c128", "mixed"])
+def test_d64_tree_exact(dtype):
+    """16-qubit heavy-hex tree, D = 64, 6 steps (Schmidt ranks <= 2^6): the state vector."""
+    m, e, _ = induced_subgraph(E127, range(16))
+    zg, _, g = run_layers([(m, e)], 64, dtype, [0.8], 6)
+    ref = sv.kicked_ising_z(m, e, 0.8, 6)
+    assert np.abs(zg - ref).max() < TOL[dtype]
+    assert g.status() == 0
+
+
+@pytest.mark.parametrize("dtype", ["c128", "mixed"])
+def test_d64_full_lattice_lightcone_exact(dtype):
+    """127 qubits, D = 64, 4 steps: every qubit equals its light-cone value (balls are trees)."""
+    theta = 0.8
+    zg, _, _ = run_layers([(M127, E127)], 64, dtype, [theta], 4)
+    for n in (1, 2, 3, 4):
+        ref = np.array([lightcone_z(M127, E127, theta, q, n) for q in range(M127)])
+        assert np.abs(zg[n - 1] - ref).max() < TOL[dtype], n
+
+
+@pytest.mark.parametrize("dtype", ["c128", "mixed"])
+def test_eagle_d64_matches_oracle(dtype):
+    """127 qubits, D = 64, theta = 0.8, 8 steps, graph replay: mean <Z> of every step,
+    per-qubit <Z> and sampled lambda at the committed steps."""
+    with open(os.path.join(GOLD, "oracle_eagle_d64.json")) as f:
+        gold = json.load(f)
+    inst = gold["instances"][0]
+    w = workload("eagle_d64")
+    g = gpu_lib()(w.graphs(), w.D, dtype=dtype)
+    g.reset()
+    th = torch.tensor([0.8], dtype=torch.float64, device="cuda")
+    done, means = 0, []
+    for s in sorted(int(k) for k in inst["z"]):
+        means.append(g.step(s - done, th).cpu().numpy()[:, 0])
+        done = s
+        z, _ = g.expect_z()
+        tol = TOL[dtype] if 2 ** s <= w.D else TOL_SITE_TRUNC[dtype]
+        assert np.abs(z.cpu().numpy() - np.array(inst["z"][str(s)])).max() < tol, s
+        for e, lam in inst["lambda"][str(s)].items():
+            lam_check(g.lambdas(0, int(e)), np.array(lam), dtype, truncated=2 ** s > w.D)
+    means = np.concatenate(means)
+    assert np.abs(means - np.array(inst["mean_z"][:done])).max() < TOL[dtype]
+    assert g.status() == 0
+    g.close()
+
+
+def _oracle_bond(g, graph, i, j, theta, D):
+    """The oracle's update of bond (i, j) from the GPU's current state (both ends carrying the
+    pending kick theta), on the subgraph of the edges at i and j.  Returns (lambda, <Z_i>, <Z_j>)."""
+    n, edges = graph
+    nbr = {v: [] for v in (i, j)}
+    for a, b in edges:
+        a, b = int(a), int(b)
+        if a in nbr:
+            nbr[a].append(b)
+        if b in nbr:
+            nbr[b].append(a)
+    sites = sorted({i, j} | set(nbr[i]) | set(nbr[j]))
+    relabel = {v: k for k, v in enumerate(sites)}      # monotone: leg order is kept
+    sub = sorted({(min(relabel[u], relabel[v]), max(relabel[u], relabel[v]))
+                  for u in (i, j) for v in nbr[u]})
+    peps = su.GPEPS(len(sites), np.array(sub), D)
+    full_edge = {(min(int(a), int(b)), max(int(a), int(b))): k for k, (a, b) in enumerate(edges)}
+    rx = su.rx(theta)
+    for v in (i, j):
+        t, nb = g.site_tensor(0, v)
+        assert nb == sorted(nbr[v])
+        peps.gamma[relabel[v]] = np.tensordot(rx, t.cpu().numpy().astype(np.complex128), axes=(1, 0))
+    for k, (a, b) in enumerate(sub):
+        u, v = sites[a], sites[b]
+        peps.lam[k] = g.lambda_tensor(0, full_edge[(min(u, v), max(u, v))]).cpu().numpy()
+    e_sub = sub.index((min(relabel[i], relabel[j]), max(relabel[i], relabel[j])))
+    peps.bond_update(e_sub)
+    z = peps.expect_z()
+    return peps.lam[e_sub].copy(), z[relabel[i]], z[relabel[j]]
+
+
+@pytest.mark.parametrize("dtype", ["mixed", "c128"])
+def test_condor_d64_full_size_sampled_bonds(dtype):
+    """1121 qubits, D = 64, theta = 0.8 (the large workload) by graph replay for 7 steps, then
+    kick + colour class 0 explicitly: sampled bonds of every kind against the oracle's update of
+    the same bond from the same state; every lambda stays normalised."""
+    w = workload("condor_d64")
+    graph = heavy_hex(*CONDOR)
+    n, edges = graph
+    theta = w.theta[0]
+    g = gpu_lib()([graph], w.D, dtype=dtype)
+    g.reset()
+    th = torch.tensor([theta], dtype=torch.float64, device="cuda")
+    g.step(7, th)
+    assert g.status() == 0
+    # greedy colouring of the library (same rule as the oracle's)
+    from oracle.graph import greedy_colouring
+    col = greedy_colouring(edges)
+    deg = np.bincount(edges.reshape(-1), minlength=n)
+    cls0 = [k for k in range(len(edges)) if col[k] == 0]
+    kinds = {}
+    for k in cls0:
+        a, b = (int(x) for x in edges[k])
+        kinds.setdefault(tuple(sorted((deg[a], deg[b]))), []).append(k)
+    sample = []
+    for kind, ks in sorted(kinds.items()):
+        sample += [ks[0], ks[len(ks) // 2], ks[-1]]
+    g.kick(th)
+    refs = {k: _oracle_bond(g, graph, int(edges[k][0]), int(edges[k][1]), theta, w.D) for k in sample}
+    g.zz_layer(0)
+    z, _ = g.expect_z()
+    z = z.cpu().numpy()
+    assert g.status() == 0
+    for k, (lam_o, zi, zj) in refs.items():
+        a, b = (int(x) for x in edges[k])
+        lam_check(g.lambdas(0, k), lam_o, dtype, truncated=True)
+        assert abs(z[a] - zi) < TOL[dtype], (k, z[a], zi)
+        assert abs(z[b] - zj) < TOL[dtype], (k, z[b], zj)
+    lam = np.array([g.lambda_tensor(0, k).cpu().numpy() for k in range(len(edges))])
+    assert np.abs((lam ** 2).sum(axis=1) - 1.0).max() < 1e-12
+    assert np.abs(z).max() <= 1.0 + 1e-12
+    g.close()

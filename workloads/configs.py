@@ -66,6 +66,9 @@ WORKLOADS = {
                                note="127 q, D=16, 20 steps, theta_i ~ U[0.5, 0.9] seeded 15642"),
     "condor_d64": Workload("condor_d64", (CONDOR,), 64, 100, (0.8,),
                            note="1121 q, D=64, 100 steps, theta=0.8"),
+    "eagle_d64": Workload("eagle_d64", (EAGLE,), 64, 8, (0.8,),
+                          note="127 q, D=64, 8 steps, theta=0.8: the 128 x 128 bond eigenproblems of "
+                               "condor_d64 on a lattice the oracle finishes in minutes (truncation from step 7)"),
 }
 
 
