@@ -222,13 +222,16 @@ struct BondSmem {
     off_rs32 = off_rc32 + (size_t)((m + 1) / 2) * 8;
     off_int = off_rs32 + (size_t)((m + 1) / 2) * 8;
     small = (off_int + (size_t)(n + 2 * m + 8) * 4 + 15) & ~(size_t)15;
+    // global-memory mode: the FP32 level's packed rho32 and V32 follow the small arrays
+    f32 = ((size_t)n * (n + 1) / 2 + (size_t)n * n) * 8;
   }
+  size_t f32;
 };
 
 BondFootprint bond_footprint(int D, size_t smem_optin) {
   const BondSmem L(D, 2 * D);
   if (L.big + L.small <= smem_optin) return BondFootprint{L.big + L.small, 0};
-  return BondFootprint{L.small, (L.big + 255) & ~(size_t)255};
+  return BondFootprint{L.small + L.f32, (L.big + 255) & ~(size_t)255};
 }
 
 // Rotation of the pair (p, q) (Golub & Van Loan, Alg. 8.4.1, sym.schur2, after
@@ -277,8 +280,36 @@ __device__ __forceinline__ bool rotation(double app, double aqq, double2 apq, do
   return true;
 }
 
-// Parallel cyclic Jacobi for the Hermitian n x n matrix A (row stride lda) in
-// shared memory, accumulating V (row stride ldv) <- V * product of rotations
+// Storage of the Hermitian matrix of a Jacobi solve.  HermFull: n x n with row
+// stride lda, both triangles kept.  HermPacked: the upper triangle row by row
+// (n(n+1)/2 entries, row i starting at i(2n - i + 1)/2); the lower triangle is
+// implied, so a rotated entry is written once at its upper-triangle place.
+template <typename R>
+struct HermFull {
+  V2<R>* A;
+  int lda;
+  __device__ __forceinline__ V2<R> get(int i, int j) const { return A[i * lda + j]; }
+  __device__ __forceinline__ void put(int i, int j, V2<R> v, bool mirror) const {
+    A[i * lda + j] = v;
+    if (mirror) A[j * lda + i] = c_conj<R>(v);
+  }
+};
+template <typename R>
+struct HermPacked {
+  V2<R>* P;
+  int n;
+  __device__ __forceinline__ int at(int i, int j) const { return ((i * (2 * n - i + 1)) >> 1) + j - i; }
+  __device__ __forceinline__ V2<R> get(int i, int j) const {
+    return i <= j ? P[at(i, j)] : c_conj<R>(P[at(j, i)]);
+  }
+  __device__ __forceinline__ void put(int i, int j, V2<R> v, bool) const {
+    if (i <= j) P[at(i, j)] = v;
+    else P[at(j, i)] = c_conj<R>(v);
+  }
+};
+
+// Parallel cyclic Jacobi for the Hermitian n x n matrix A (storage policy S:
+// HermFull or HermPacked), accumulating V (row stride ldv) <- V * product of rotations
 // (V is initialised by the caller).  The (n-1) rounds of a sweep use the
 // round-robin pairing, so the n/2 rotations of a round are disjoint and applied
 // together: A <- J^dagger A J on 2x2 blocks (a, b) enumerated circulantly
@@ -287,8 +318,8 @@ __device__ __forceinline__ bool rotation(double app, double aqq, double2 apq, do
 // With kExact the off-diagonal of a rotated diagonal block is set to zero (the
 // FP32 angle is exact for FP32 arithmetic); the FP64 sweeps keep the computed
 // residual instead.  Returns the sweeps run; max_sweeps + 1 = cap hit.
-template <typename R, bool kExact>
-__device__ int jacobi_hermitian(V2<R>* A, int lda, V2<R>* V, int ldv, int n, R tol, R floor_abs, int max_sweeps,
+template <typename R, bool kExact, typename S>
+__device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_abs, int max_sweeps,
                                 R* rc, R* rs, V2<R>* re, int* rp, int* rq, int* iflag,
                                 unsigned long long* rot_count) {
   const int m = n / 2;
@@ -317,7 +348,7 @@ __device__ int jacobi_hermitian(V2<R>* A, int lda, V2<R>* V, int ldv, int n, R t
         }
         R cs = 1, sn = 0;
         V2<R> e = mk<R>(1, 0);
-        if (rotation(A[p * lda + p].x, A[q * lda + q].x, A[p * lda + q], tol, floor_abs, cs, sn, e)) {
+        if (rotation(A.get(p, p).x, A.get(q, q).x, A.get(p, q), tol, floor_abs, cs, sn, e)) {
           iflag[0] = 1;
           atomicAdd(iflag + 2, 1);
         }
@@ -336,8 +367,8 @@ __device__ int jacobi_hermitian(V2<R>* A, int lda, V2<R>* V, int ldv, int n, R t
         const int pa = rp[a], qa = rq[a], pb = rp[b], qb = rq[b];
         const R ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
         const V2<R> ea = re[a], eb = re[b];
-        const V2<R> b00 = A[pa * lda + pb], b01 = A[pa * lda + qb];
-        const V2<R> b10 = A[qa * lda + pb], b11 = A[qa * lda + qb];
+        const V2<R> b00 = A.get(pa, pb), b01 = A.get(pa, qb);
+        const V2<R> b10 = A.get(qa, pb), b11 = A.get(qa, qb);
         const V2<R> b01e = c_mul<R>(b01, eb), b11e = c_mul<R>(b11, eb);
         const V2<R> t00 = c_sub<R>(c_scale<R>(b00, cb), c_scale<R>(b01e, sb));
         const V2<R> t01 = c_add<R>(c_scale<R>(b00, sb), c_scale<R>(b01e, cb));
@@ -359,16 +390,10 @@ __device__ int jacobi_hermitian(V2<R>* A, int lda, V2<R>* V, int ldv, int n, R t
           }
           n10 = c_conj<R>(n01);
         }
-        A[pa * lda + pb] = n00;
-        A[pa * lda + qb] = n01;
-        A[qa * lda + pb] = n10;
-        A[qa * lda + qb] = n11;
-        if (d != 0) {
-          A[pb * lda + pa] = c_conj<R>(n00);
-          A[qb * lda + pa] = c_conj<R>(n01);
-          A[pb * lda + qa] = c_conj<R>(n10);
-          A[qb * lda + qa] = c_conj<R>(n11);
-        }
+        A.put(pa, pb, n00, d != 0);
+        A.put(pa, qb, n01, d != 0);
+        A.put(qa, pb, n10, d != 0);
+        A.put(qa, qb, n11, d != 0);
       }
       for (int idx = threadIdx.x; idx < n * m; idx += blockDim.x) {
         const int i = idx / m, k = idx - (idx / m) * m;
@@ -510,10 +535,13 @@ __device__ double orthonormalise(double2* V, int n, double2* G, int ldg, double*
 __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, double trace, const JacobiParams& jp,
                          double2* re, float2* re32, double* ev, double* rc, double* rs, double* scal, float* rc32,
                          float* rs32, int* order, int* rp, int* rq, int* iflag, unsigned long long* sweeps_out,
-                         unsigned long long* cycles, int* flags, long long& t_prev) {
+                         unsigned long long* cycles, int* flags, long long& t_prev, float2* f32s) {
   const int ldr = n + 1;
-  float2* R32 = reinterpret_cast<float2*>(X);  // [n][n+1]
-  float2* V32 = R32 + (size_t)n * (n + 1);     // [n][n]
+  // FP32 level: rho32 [n][n+1] and V32 [n][n] in X, or (f32s given: the n x n
+  // matrices live in global memory) rho32 packed and V32 in shared memory f32s
+  const bool packed = f32s != nullptr;
+  float2* R32 = packed ? f32s : reinterpret_cast<float2*>(X);
+  float2* V32 = packed ? f32s + (size_t)n * (n + 1) / 2 : R32 + (size_t)n * (n + 1);
   auto mark = [&](int phase) {
     if (threadIdx.x == 0 && cycles) {
       const long long t = clock64();
@@ -522,16 +550,30 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
     }
   };
   // FP32 Jacobi on a rounded copy
-  for (int idx = threadIdx.x; idx < n * ldr; idx += blockDim.x) {
-    const double2 v = RHO[idx];
-    R32[idx] = make_float2((float)v.x, (float)v.y);
+  const HermPacked<float> P32{R32, n};
+  if (packed) {
+    for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+      int i, j;
+      upper_index(idx, n, i, j);
+      const double2 v = RHO[i * ldr + j];
+      R32[P32.at(i, j)] = make_float2((float)v.x, (float)v.y);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < n * ldr; idx += blockDim.x) {
+      const double2 v = RHO[idx];
+      R32[idx] = make_float2((float)v.x, (float)v.y);
+    }
   }
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x)
     V32[idx] = make_float2((idx / n) == (idx % n) ? 1.f : 0.f, 0.f);
   __syncthreads();
-  const int sw32 = jacobi_hermitian<float, true>(R32, ldr, V32, n, n, (float)jp.tol32,
-                                                 (float)(jp.floor32 * trace), jp.max_sweeps32, rc32, rs32, re32,
-                                                 rp, rq, iflag, cycles ? cycles + kPhases : nullptr);
+  unsigned long long* rc32_count = cycles ? cycles + kPhases : nullptr;
+  const int sw32 =
+      packed ? jacobi_hermitian<float, true>(P32, V32, n, n, (float)jp.tol32, (float)(jp.floor32 * trace),
+                                             jp.max_sweeps32, rc32, rs32, re32, rp, rq, iflag, rc32_count)
+             : jacobi_hermitian<float, true>(HermFull<float>{R32, ldr}, V32, n, n, (float)jp.tol32,
+                                             (float)(jp.floor32 * trace), jp.max_sweeps32, rc32, rs32, re32, rp,
+                                             rq, iflag, rc32_count);
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const float2 v = V32[idx];
     Vm[idx] = make_double2((double)v.x, (double)v.y);
@@ -572,10 +614,12 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
   {
     int* cand = order;  // [n] candidate indices of this level
     double* dcur = ev;
-    double2* W64 = X;                                 // [ns][ns]
-    double2* Gw = X + (size_t)(n / 2) * (n / 2);      // [ns][ns+1]
-    float2* B32 = reinterpret_cast<float2*>(Gw + (size_t)(n / 2) * (n / 2 + 1));  // [ns][ns+1]
-    float2* W32 = B32 + (size_t)(n / 2) * (n / 2 + 1);                            // [ns][ns]
+    // level scratch for ns <= lv indices: in X, or in the free FP32 shared memory
+    const int lv = packed ? kMaxLevel : n / 2;
+    double2* W64 = packed ? reinterpret_cast<double2*>(f32s) : X;   // [ns][ns]
+    double2* Gw = W64 + (size_t)lv * lv;                             // [ns][ns+1]
+    float2* B32 = reinterpret_cast<float2*>(Gw + (size_t)lv * (lv + 1));  // [ns][ns+1]
+    float2* W32 = B32 + (size_t)lv * (lv + 1);                            // [ns][ns]
     double prev_scale = -1.0;  // level 0 covered everything
     for (int level = 0; level < kExtraLevels; ++level) {
       for (int i = threadIdx.x; i < n; i += blockDim.x) dcur[i] = RHO[i * ldr + i].x;
@@ -619,7 +663,7 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
       }
       for (int a = 0; a < ns; ++a) btr += dcur[cand[a]] * inv;
       __syncthreads();
-      const int swl = jacobi_hermitian<float, true>(B32, ldb, W32, ns, ns, (float)jp.tol32,
+      const int swl = jacobi_hermitian<float, true>(HermFull<float>{B32, ldb}, W32, ns, ns, (float)jp.tol32,
                                                     (float)(jp.floor32 * btr), jp.max_sweeps32, rc32, rs32, re32,
                                                     rp, rq, iflag, nullptr);
       (void)swl;
@@ -657,7 +701,8 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
     }
   }
   mark(3);
-  const int sweeps = jacobi_hermitian<double, false>(RHO, ldr, Vm, n, n, jp.tol, jp.floor_rel * trace,
+  const int sweeps = jacobi_hermitian<double, false>(HermFull<double>{RHO, ldr}, Vm, n, n, jp.tol,
+                                                     jp.floor_rel * trace,
                                                      jp.max_sweeps, rc, rs, re, rp, rq, iflag,
                                                      cycles ? cycles + kPhases + kRotSweeps : nullptr);
   mark(4);
@@ -820,7 +865,7 @@ __device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T
   }
   mark(0);
   eig_mixed(RHO, Vm, X, n, D, trace, jp, re, re32, ev, rc, rs, scal, rc32, rs32, order, rp, rq, iflag, sweeps_out,
-            cycles, flags, t_prev);
+            cycles, flags, t_prev, big ? reinterpret_cast<float2*>(smallp + L.small) : nullptr);
   // eigenvalues sorted in decreasing order (ties by index)
   for (int i = threadIdx.x; i < n; i += blockDim.x) ev[i] = RHO[i * ldr + i].x;
   __syncthreads();
