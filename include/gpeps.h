@@ -150,6 +150,18 @@ int gpeps_set_jacobi(gpeps_handle* h, double tol, double floor_rel, double tol32
                      int32_t max_sweeps, int32_t max_sweeps32);
 
 /*
+ * Extra FP32 levels of the bond eigensolver: after the first FP32 solve and
+ * the FP64 re-orthonormalisation, up to `levels` (4; at most 8) further FP32
+ * solves, each on the rescaled block of the (at most 32) largest eigenvalues
+ * that lie below level_ratio (1e-5) x the scale of the last block that held
+ * them, so that small eigenvalues start the FP64 sweeps resolved to FP32
+ * accuracy relative to their own size.  Host-only; drops a captured step
+ * graph.  Errors: GPEPS_EINVAL for level_ratio outside (0, 1) or levels
+ * outside [0, 8].
+ */
+int gpeps_set_levels(gpeps_handle* h, double level_ratio, int32_t levels);
+
+/*
  * Schedule of the bond eigenproblems: persistent = 0 launches one CTA per bond
  * (default); 1 launches one CTA per SM that takes bonds from a work queue in
  * the work buffer.  Either way the bonds of a colour class run largest first.

@@ -396,6 +396,8 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   h->jp.ev_cut = 0.0;
   h->jp.max_sweeps = 40;
   h->jp.max_sweeps32 = 20;
+  h->jp.level_ratio = 1e-5;
+  h->jp.levels = 4;
   // layouts
   size_t s = 0;
   h->s_lam = s;
@@ -669,6 +671,15 @@ int gpeps_set_jacobi(gpeps_handle* h, double tol, double floor_rel, double tol32
   h->jp.max_sweeps = max_sweeps;
   h->jp.max_sweeps32 = max_sweeps32;
   drop_graph(h);  // the captured step holds the old parameters
+  return GPEPS_OK;
+}
+
+int gpeps_set_levels(gpeps_handle* h, double level_ratio, int32_t levels) {
+  if (!h) return GPEPS_EINVAL;
+  if (!(level_ratio > 0.0 && level_ratio < 1.0) || levels < 0 || levels > kMaxExtraLevels) return GPEPS_EINVAL;
+  h->jp.level_ratio = level_ratio;
+  h->jp.levels = levels;
+  drop_graph(h);
   return GPEPS_OK;
 }
 

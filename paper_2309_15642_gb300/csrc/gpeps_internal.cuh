@@ -21,8 +21,7 @@ constexpr double kLambdaCut = 1e-13;  // pseudo-inverse threshold relative to ma
 constexpr int kPhases = 6;            // phases of the bond kernel with SM-cycle counters
 constexpr int kRotSweeps = 8;         // rotation counters kept for the first sweeps of a solve
 constexpr int kCounters = kPhases + 2 * kRotSweeps;  // cycles, FP32 rotations, FP64 rotations
-constexpr int kExtraLevels = 2;       // FP32 warm-start levels after the first (small-eigenvalue blocks)
-constexpr double kLevelRatio = 1e-5;  // a level takes the diagonals below this fraction of the last scale
+constexpr int kMaxExtraLevels = 8;    // FP32 warm-start levels after the first (small-eigenvalue blocks)
 constexpr double kNoiseRel = 1e-15;   // ... and above this fraction of the trace (FP64 rounding noise)
 
 // One end of a bond seen as a matrix: row r = (r1, r2) runs over the other legs,
@@ -73,6 +72,8 @@ struct JacobiParams {
   double ev_cut;     // eigenvalues <= ev_cut * max eigenvalue are dropped (lambda = 0)
   int max_sweeps;    // FP64 cap (hitting it sets GPEPS_FLAG_NOCONV)
   int max_sweeps32;  // FP32 cap (hitting it only costs FP64 sweeps)
+  double level_ratio;  // an extra FP32 level takes the diagonals below this fraction of their block's scale
+  int levels;          // extra FP32 levels at most (0..kMaxExtraLevels)
 };
 
 // Launchers (su_kernels.cu).  T = float for GPEPS_MIXED_C64, double for GPEPS_C128.

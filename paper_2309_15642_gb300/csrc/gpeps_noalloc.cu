@@ -186,6 +186,8 @@ extern "C" int gpeps_bond_update_noalloc(int32_t D, int32_t dtype, void* gamma_a
   jp.ev_cut = 0.0;
   jp.max_sweeps = 40;
   jp.max_sweeps32 = 20;
+  jp.level_ratio = 1e-5;
+  jp.levels = 4;
   void* base = reinterpret_cast<void*>(pbig);
   st = dtype == GPEPS_C128 ? run<double>(scratch, D, base, bd, bd.n_parts, lam, jp, cs)
                            : run<float>(scratch, D, base, bd, bd.n_parts, lam, jp, cs);

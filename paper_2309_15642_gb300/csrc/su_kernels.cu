@@ -606,51 +606,57 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
   }
   __syncthreads();
   // Further FP32 levels for the eigenvalues the previous level could not
-  // resolve (FP32 rounding ~1e-7 of that level's largest entry): the indices
-  // whose diagonal lies below kLevelRatio x the previous level's scale (and
-  // above rounding noise of the whole matrix) are diagonalised again in FP32
-  // on a rescaled copy of their block, and the rotation, re-orthonormalised in
-  // FP64, is applied to V and to rho' in FP64.
+  // resolve (FP32 rounding ~1e-7 of that level's largest entry).  Every index
+  // remembers the scale of the last block that held it (the whole matrix at
+  // first); a level takes the largest indices (at most min(n/2, 32)) whose
+  // diagonal lies below jp.level_ratio x that scale and above rounding noise of
+  // the whole matrix, diagonalises their block again in FP32 on a rescaled copy,
+  // and applies the rotation, re-orthonormalised in FP64, to V and to rho' in FP64.
   {
-    int* cand = order;  // [n] candidate indices of this level
+    int* cand = order;    // [n] candidate indices of this level, largest first
     double* dcur = ev;
+    double* rscale = rc;  // [n] (rc and rs are contiguous and idle until the FP64 sweeps)
+    int* mark_c = rp;     // [n] (rp and rq likewise, idle during the selection)
+    const int cap = (n / 2 < kMaxLevel) ? n / 2 : kMaxLevel;
     // level scratch for ns <= lv indices: in X, or in the free FP32 shared memory
     const int lv = packed ? kMaxLevel : n / 2;
     double2* W64 = packed ? reinterpret_cast<double2*>(f32s) : X;   // [ns][ns]
     double2* Gw = W64 + (size_t)lv * lv;                             // [ns][ns+1]
     float2* B32 = reinterpret_cast<float2*>(Gw + (size_t)lv * (lv + 1));  // [ns][ns+1]
     float2* W32 = B32 + (size_t)lv * (lv + 1);                            // [ns][ns]
-    double prev_scale = -1.0;  // level 0 covered everything
-    for (int level = 0; level < kExtraLevels; ++level) {
+    const double lo = kNoiseRel * trace;
+    for (int level = 0; level < jp.levels; ++level) {
       for (int i = threadIdx.x; i < n; i += blockDim.x) dcur[i] = RHO[i * ldr + i].x;
       __syncthreads();
-      if (threadIdx.x == 0) {
-        double scale = 0.0;
-        for (int i = 0; i < n; ++i)
-          if (prev_scale < 0.0 || dcur[i] <= prev_scale) scale = fmax(scale, dcur[i]);
-        const double hi = kLevelRatio * scale, lo = kNoiseRel * trace;
-        int ns = 0;
-        for (int i = 0; i < n; ++i)
-          if (dcur[i] <= hi && dcur[i] > lo) cand[ns++] = i;
-        // keep at most min(n/2, 32), the largest first
-        for (int a = 0; a < ns; ++a)
-          for (int b = a + 1; b < ns; ++b)
-            if (dcur[cand[b]] > dcur[cand[a]]) {
-              const int t = cand[a];
-              cand[a] = cand[b];
-              cand[b] = t;
-            }
-        if (ns > n / 2) ns = n / 2;
-        if (ns > kMaxLevel) ns = kMaxLevel;
-        ns &= ~1;  // even: drop the smallest
-        iflag[1] = ns;
-        scal[7] = ns > 0 ? dcur[cand[0]] : 0.0;
-        scal[3] = hi;
+      if (level == 0) {
+        if (threadIdx.x == 0) {
+          double s0 = 0.0;
+          for (int i = 0; i < n; ++i) s0 = fmax(s0, dcur[i]);
+          scal[3] = s0;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) rscale[i] = scal[3];
       }
+      for (int i = threadIdx.x; i < n; i += blockDim.x)
+        mark_c[i] = (dcur[i] > lo && dcur[i] <= jp.level_ratio * rscale[i]) ? 1 : 0;
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (!mark_c[i]) continue;
+        const double di = dcur[i];
+        int rank = 0;
+        for (int j = 0; j < n; ++j) rank += mark_c[j] && (dcur[j] > di || (dcur[j] == di && j < i));
+        if (rank < cap) cand[rank] = i;
+      }
+      if (threadIdx.x == 0) {
+        int cnt = 0;
+        for (int j = 0; j < n; ++j) cnt += mark_c[j];
+        iflag[1] = (cnt < cap ? cnt : cap) & ~1;  // even: drop the smallest
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) scal[7] = iflag[1] > 0 ? dcur[cand[0]] : 0.0;
       __syncthreads();
       const int ns = iflag[1];
       const double bscale = scal[7];
-      prev_scale = scal[3];
       if (ns < 2 || !(bscale > 0.0)) break;
       const int ldb = ns + 1;
       const double inv = 1.0 / bscale;
@@ -696,6 +702,7 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
         if (lane < ns) RHO[cand[lane] * ldr + c] = out;
         __syncwarp();
       }
+      for (int a = threadIdx.x; a < ns; a += blockDim.x) rscale[cand[a]] = bscale;
       __syncthreads();
       if (threadIdx.x == 0) atomicAdd(sweeps_out + 2, 1ull);
     }

@@ -169,6 +169,10 @@ class GPEPS:
         check(self.lib.gpeps_set_jacobi(self.h, float(tol), float(floor_rel), float(tol32), float(floor32),
                                         int(max_sweeps), int(max_sweeps32)), "gpeps_set_jacobi")
 
+    def set_levels(self, level_ratio=1e-5, levels=4):
+        """Extra FP32 levels of the bond eigensolver (see gpeps_set_levels)."""
+        check(self.lib.gpeps_set_levels(self.h, float(level_ratio), int(levels)), "gpeps_set_levels")
+
     # -------------------------------------------------------------- gradient
     def grad(self, theta, n_steps, ckpt_every=5, dL_dz=None):
         """Gradient path (complex128, D <= 16): returns ``(z, dtheta)`` with z = <Z_i> after
