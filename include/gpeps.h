@@ -140,7 +140,7 @@ int gpeps_zz_layer_profiled(gpeps_handle* h, int32_t colour, float* ms);
 /*
  * Thresholds of the bond eigensolver (defaults in parentheses): FP64 sweeps
  * stop rotating a pair when |a_pq| <= max(tol sqrt(a_pp a_qq), floor_rel *
- * trace) (complex128: 1e-15, 4.4e-16; mixed: 1e-9, 1e-9); the FP32 levels use tol32
+ * trace) (complex128: 1e-15, 4.4e-16; mixed: 1e-9, 1e-8); the FP32 levels use tol32
  * (1e-6) and floor32 (2e-7); sweep caps max_sweeps (40; hitting it sets
  * GPEPS_FLAG_NOCONV) and max_sweeps32 (20).  Host-only; drops a captured step
  * graph.  Errors: GPEPS_EINVAL for non-positive thresholds or caps outside

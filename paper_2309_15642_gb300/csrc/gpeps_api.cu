@@ -386,11 +386,11 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   // Jacobi thresholds: the bond matrix carries FP64 rounding (C128) or the
   // FP32 rounding of its Gram inputs (mixed); eigenvalues below that level are noise.
   // FP64 sweeps stop at |a_pq| <= max(tol sqrt(a_pp a_qq), floor_rel * trace):
-  // at FP64 rounding for complex128 (rho carries ~eps * trace), and far below
-  // the ~1e-7 * trace rounding that the mixed path's rho inherits from its
-  // FP32 inputs (resolving that rho further changes nothing)
+  // at FP64 rounding for complex128 (rho carries ~eps * trace), and a decade
+  // below the ~1e-7 * trace rounding that the mixed path's rho inherits from
+  // its FP32 inputs (resolving that rho further only fits noise)
   h->jp.tol = dtype == GPEPS_C128 ? 1e-15 : 1e-9;
-  h->jp.floor_rel = dtype == GPEPS_C128 ? 4.4e-16 : 1e-9;
+  h->jp.floor_rel = dtype == GPEPS_C128 ? 4.4e-16 : 1e-8;
   h->jp.tol32 = 1e-6;
   h->jp.floor32 = 2e-7;
   h->jp.ev_cut = 0.0;

@@ -180,7 +180,7 @@ extern "C" int gpeps_bond_update_noalloc(int32_t D, int32_t dtype, void* gamma_a
   // Jacobi thresholds of the batched path for this dtype
   JacobiParams jp{};
   jp.tol = dtype == GPEPS_C128 ? 1e-15 : 1e-9;
-  jp.floor_rel = dtype == GPEPS_C128 ? 4.4e-16 : 1e-9;
+  jp.floor_rel = dtype == GPEPS_C128 ? 4.4e-16 : 1e-8;
   jp.tol32 = 1e-6;
   jp.floor32 = 2e-7;
   jp.ev_cut = 0.0;

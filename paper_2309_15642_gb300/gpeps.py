@@ -165,7 +165,7 @@ class GPEPS:
         if tol is None:
             tol = 1e-15 if self.dtype == "c128" else 1e-9
         if floor_rel is None:
-            floor_rel = 4.4e-16 if self.dtype == "c128" else 1e-9
+            floor_rel = 4.4e-16 if self.dtype == "c128" else 1e-8
         check(self.lib.gpeps_set_jacobi(self.h, float(tol), float(floor_rel), float(tol32), float(floor32),
                                         int(max_sweeps), int(max_sweeps32)), "gpeps_set_jacobi")
 
