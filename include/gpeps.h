@@ -162,12 +162,17 @@ int gpeps_set_jacobi(gpeps_handle* h, double tol, double floor_rel, double tol32
 int gpeps_set_levels(gpeps_handle* h, double level_ratio, int32_t levels);
 
 /*
- * Schedule of the bond eigenproblems: persistent = 0 launches one CTA per bond
- * (default); 1 launches one CTA per SM that takes bonds from a work queue in
- * the work buffer.  Either way the bonds of a colour class run largest first.
- * Host-only; drops a captured step graph.  Errors: GPEPS_EINVAL for other values.
+ * Schedule of the bond eigenproblems: 0 launches one CTA per bond (default);
+ * 1 launches one CTA per SM that takes bonds from a work queue in the work
+ * buffer; 2 launches two CTAs per SM (256 threads each) on the queue, each
+ * with its n x n FP64 matrices in a slot of the work buffer (held in L2) and
+ * its FP32 level in shared memory, so that one bond's latency-bound phases
+ * overlap the other's FP64 work.  Every schedule runs the bonds of a colour
+ * class largest first and gives bit-identical results.  Host-only; drops a
+ * captured step graph.  Errors: GPEPS_EINVAL for other values, and for 2 on an
+ * unbound handle, for D above 48, or on a device with more than 256 SMs.
  */
-int gpeps_set_schedule(gpeps_handle* h, int32_t persistent);
+int gpeps_set_schedule(gpeps_handle* h, int32_t schedule);
 
 /* Number of colour classes (the largest over the instances). */
 int gpeps_n_colours(const gpeps_handle* h, int32_t* n_colours);

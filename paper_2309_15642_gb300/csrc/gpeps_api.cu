@@ -74,11 +74,12 @@ struct gpeps_handle {
   size_t s_lam = 0, s_gamma = 0;
   size_t w_pending = 0, w_flags = 0, w_sweeps = 0, w_cycles = 0, w_queue = 0, w_z = 0, w_mean = 0, w_sites = 0, w_inst_site0 = 0,
          w_site_inst = 0, w_site_off = 0, w_partials = 0, w_Y = 0, w_theta_a = 0, w_bond_scratch = 0;
-  size_t bond_slot = 0;  // bytes per bond-kernel CTA of global scratch (0: all in shared memory)
+  size_t bond_slot = 0;  // bytes per bond-kernel CTA of global scratch for its n x n matrices
+  int bond_slots = 0;    // slots in the work buffer
   char* d_state = nullptr;
   char* d_work = nullptr;
   bool bound = false;
-  bool persistent = false;  // bond eigenproblems from a work queue (one CTA per SM)
+  int schedule = 0;  // bond eigenproblems: 0 one CTA per bond, 1 work queue (one CTA per SM), 2 work queue (two per SM)
   int n_sms = 0;
   int64_t bonds_since_reset = 0;
   // captured step
@@ -229,8 +230,8 @@ int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr, void* vsave = 
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[1], h->stream));
   GP_CUDA(Launch<T>::bond(bonds, nbd, partials, h->gamma(), h->lam(), h->pending(), Y, theta_a, h->flags(),
                           h->sweeps(), h->cycles(), vsave, h->D, h->jp, h->stream,
-                          h->persistent ? h->at<unsigned int>(h->w_queue) : nullptr, h->n_sms,
-                          h->bond_slot ? h->d_work + h->w_bond_scratch : nullptr));
+                          h->schedule ? h->at<unsigned int>(h->w_queue) : nullptr, h->n_sms,
+                          h->d_work + h->w_bond_scratch, h->schedule == 2));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[2], h->stream));
   GP_CUDA(Launch<T>::update(tiles, nt, bonds, h->gamma(), h->lam(), Y, theta_a, h->D, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[3], h->stream));
@@ -429,10 +430,12 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   h->w_partials = carve((size_t)h->max_parts * 2 * D * D * h->elt);
   h->w_Y = carve((size_t)h->max_bonds * 2 * D * D * h->elt);
   h->w_theta_a = carve((size_t)h->max_bonds * sizeof(double));
-  // n x n bond matrices beyond shared memory: one slot per bond of the largest
-  // class (a CTA of either schedule indexes its slot by blockIdx.x)
-  h->bond_slot = bond_footprint(D, kBondSmemMax).slot;
-  if (h->bond_slot) h->w_bond_scratch = carve((size_t)h->max_bonds * h->bond_slot);
+  // n x n bond matrices outside shared memory (a CTA indexes its slot by
+  // blockIdx.x): beyond the shared-memory limit one slot per bond of the largest
+  // class; otherwise slots for the two-CTAs-per-SM schedule only
+  h->bond_slot = bond_footprint_global(D).slot;
+  h->bond_slots = bond_footprint(D, kBondSmemMax).slot ? h->max_bonds : std::min(h->max_bonds, 2 * kMaxSms);
+  h->w_bond_scratch = carve((size_t)h->bond_slots * h->bond_slot);
   h->work_bytes = w;
   *out = h;
   return GPEPS_OK;
@@ -522,9 +525,14 @@ int gpeps_zz_layer_profiled(gpeps_handle* h, int32_t colour, float* ms) {
   return GPEPS_OK;
 }
 
-int gpeps_set_schedule(gpeps_handle* h, int32_t persistent) {
-  if (!h || (persistent != 0 && persistent != 1)) return GPEPS_EINVAL;
-  h->persistent = persistent == 1;
+int gpeps_set_schedule(gpeps_handle* h, int32_t schedule) {
+  if (!h || schedule < 0 || schedule > 2) return GPEPS_EINVAL;
+  if (schedule == 2) {
+    // two CTAs per SM: shared memory of the FP32 level and a slot per CTA
+    if (!h->bound || bond_footprint_global(h->D).smem > kPairSmemMax) return GPEPS_EINVAL;
+    if (std::min(2 * h->n_sms, h->max_bonds) > h->bond_slots) return GPEPS_EINVAL;
+  }
+  h->schedule = schedule;
   drop_graph(h);
   return GPEPS_OK;
 }

@@ -90,7 +90,7 @@ struct Launch {
                           double* pending, void* Y, double* theta_a, int* flags,
                           unsigned long long* sweeps, unsigned long long* cycles, void* vsave, int D,
                           JacobiParams jp, cudaStream_t st, unsigned int* queue = nullptr, int n_ctas = 0,
-                          void* scratch = nullptr);
+                          void* scratch = nullptr, int pair = 0);
   static cudaError_t update(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, void* gamma,
                             const double* lam, const void* Y, const double* theta_a, int D, cudaStream_t st);
   static cudaError_t readout(const SiteDesc* sites, int n_sites, const void* gamma, const double* lam,
@@ -124,5 +124,11 @@ struct BondFootprint {
   size_t slot;
 };
 BondFootprint bond_footprint(int D, size_t smem_optin);
+// The same with the n x n matrices always in a global slot (the FP32 level in
+// shared memory): the layout of the two-CTAs-per-SM schedule.
+BondFootprint bond_footprint_global(int D);
+constexpr int kPairThreads = 256;     // threads of a bond CTA when two share an SM
+constexpr size_t kPairSmemMax = 113 * 1024;  // dynamic shared memory of such a CTA (two per SM)
+constexpr int kMaxSms = 256;          // SMs the two-per-SM schedule has scratch slots for
 
 }  // namespace gpeps

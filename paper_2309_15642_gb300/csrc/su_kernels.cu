@@ -234,6 +234,11 @@ BondFootprint bond_footprint(int D, size_t smem_optin) {
   return BondFootprint{L.small + L.f32, (L.big + 255) & ~(size_t)255};
 }
 
+BondFootprint bond_footprint_global(int D) {
+  const BondSmem L(D, 2 * D);
+  return BondFootprint{L.small + L.f32, (L.big + 255) & ~(size_t)255};
+}
+
 // Rotation of the pair (p, q) (Golub & Van Loan, Alg. 8.4.1, sym.schur2, after
 // the diagonal phase that makes a_pq real): J = [[c, s], [-s e, c e]],
 // e = conj(a_pq)/|a_pq|.  Returns false (identity) when the pair is converged.
@@ -980,11 +985,11 @@ __global__ void __launch_bounds__(kBondThreads, 1)
                jp, scratch ? scratch + (size_t)blockIdx.x * slot : nullptr);
 }
 
-// Persistent form: one CTA per SM takes bonds from a work queue (bonds are
+// Persistent form: kMinB CTAs per SM take bonds from a work queue (bonds are
 // ordered by decreasing size, so the large ones go first and the small ones
 // fill the tail).  The queue counter is zeroed before every launch.
-template <typename T>
-__global__ void __launch_bounds__(kBondThreads, 1)
+template <typename T, int kThr, int kMinB>
+__global__ void __launch_bounds__(kThr, kMinB)
     bond_kernel_persistent(int n_bonds, unsigned int* queue, const BondDesc* __restrict__ bonds,
                            const V2<T>* __restrict__ partials, V2<T>* gamma, double* lam, double* pending,
                            V2<T>* __restrict__ Yout, double* __restrict__ theta_a, int* flags,
@@ -1174,8 +1179,11 @@ cudaError_t Launch<T>::init() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(bond_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBondSmemMax);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(bond_kernel_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kBondSmemMax);
+  e = cudaFuncSetAttribute(bond_kernel_persistent<T, kBondThreads, 1>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBondSmemMax);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(bond_kernel_persistent<T, kPairThreads, 2>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmemMax);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)update_smem(kMaxD, sizeof(V2<T>)));
@@ -1217,18 +1225,25 @@ template <typename T>
 cudaError_t Launch<T>::bond(const BondDesc* bonds, int n_bonds, const void* partials, void* gamma, double* lam,
                             double* pending, void* Y, double* theta_a, int* flags, unsigned long long* sweeps,
                             unsigned long long* cycles, void* vsave, int D, JacobiParams jp, cudaStream_t st,
-                            unsigned int* queue, int n_ctas, void* scratch) {
+                            unsigned int* queue, int n_ctas, void* scratch, int pair) {
   if (n_bonds == 0) return cudaSuccess;
-  const BondFootprint fp = bond_footprint(D, kBondSmemMax);
+  const BondFootprint fp = pair ? bond_footprint_global(D) : bond_footprint(D, kBondSmemMax);
   if (fp.slot && !scratch) return cudaErrorInvalidValue;
+  if (pair && (!queue || fp.smem > kPairSmemMax)) return cudaErrorInvalidValue;
   unsigned char* sp = fp.slot ? static_cast<unsigned char*>(scratch) : nullptr;
   if (queue) {
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    const int grid = n_ctas < n_bonds ? n_ctas : n_bonds;
-    bond_kernel_persistent<T><<<grid, kBondThreads, fp.smem, st>>>(
-        n_bonds, queue, bonds, static_cast<const V2<T>*>(partials), static_cast<V2<T>*>(gamma), lam, pending,
-        static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles, static_cast<double2*>(vsave), D, jp, sp, fp.slot);
+    const int want = pair ? 2 * n_ctas : n_ctas;
+    const int grid = want < n_bonds ? want : n_bonds;
+    if (pair)
+      bond_kernel_persistent<T, kPairThreads, 2><<<grid, kPairThreads, fp.smem, st>>>(
+          n_bonds, queue, bonds, static_cast<const V2<T>*>(partials), static_cast<V2<T>*>(gamma), lam, pending,
+          static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles, static_cast<double2*>(vsave), D, jp, sp, fp.slot);
+    else
+      bond_kernel_persistent<T, kBondThreads, 1><<<grid, kBondThreads, fp.smem, st>>>(
+          n_bonds, queue, bonds, static_cast<const V2<T>*>(partials), static_cast<V2<T>*>(gamma), lam, pending,
+          static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles, static_cast<double2*>(vsave), D, jp, sp, fp.slot);
     return cudaGetLastError();
   }
   bond_kernel<T><<<n_bonds, kBondThreads, fp.smem, st>>>(bonds, static_cast<const V2<T>*>(partials),

@@ -156,9 +156,10 @@ class GPEPS:
         check(self.lib.gpeps_bond_phase_cycles(self.h, c), "gpeps_bond_phase_cycles")
         return [int(x) for x in c]
 
-    def set_schedule(self, persistent):
-        """Bond eigenproblems from a work queue (one CTA per SM) or one CTA per bond."""
-        check(self.lib.gpeps_set_schedule(self.h, int(bool(persistent))), "gpeps_set_schedule")
+    def set_schedule(self, schedule):
+        """Bond eigenproblems: 0 one CTA per bond, 1 work queue with one CTA per SM, 2 work queue
+        with two CTAs per SM (see gpeps_set_schedule)."""
+        check(self.lib.gpeps_set_schedule(self.h, int(schedule)), "gpeps_set_schedule")
 
     def set_jacobi(self, tol=None, floor_rel=None, tol32=1e-6, floor32=2e-7, max_sweeps=40, max_sweeps32=20):
         """Thresholds of the bond eigensolver (see gpeps_set_jacobi); None = the dtype's default."""

@@ -30,7 +30,7 @@ def run_layers(graphs, D, dtype, theta, steps, per_qubit=False, colours=None):
     return np.array(zs), np.array(ms), g
 
 
-def run_step(graphs, D, dtype, theta, steps, per_qubit=False):
+def run_step(graphs, D, dtype, theta, steps, per_qubit=False, check_status=True):
     """gpeps_step (captured CUDA graph replay), the launch configuration of bench.py."""
     GPEPS = gpu_lib()
     g = GPEPS(graphs, D, dtype=dtype)
@@ -38,7 +38,8 @@ def run_step(graphs, D, dtype, theta, steps, per_qubit=False):
     th = torch.as_tensor(np.asarray(theta, dtype=np.float64), device="cuda")
     means = g.step(steps, th, per_qubit=per_qubit)
     out = means.cpu().numpy()
-    assert g.status() == 0
+    if check_status:
+        assert g.status() == 0
     return out, g
 
 

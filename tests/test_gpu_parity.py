@@ -172,7 +172,19 @@ def test_theta_sweep_16_instances(dtype):
     w = workload("eagle_sweep16_d16")
     graphs = w.graphs()
     theta = [th[0] for th in kick_angles(w)]
-    means, g = run_step(graphs, w.D, dtype, theta, w.steps)
+    means, g = run_step(graphs, w.D, dtype, theta, w.steps, check_status=False)
+    flags = g.status()
+    if flags:
+        # At theta = pi/2 every Schmidt spectrum is flat and the truncation keeps an
+        # arbitrary D-dimensional part of a degenerate eigenspace; two neighbouring
+        # bonds can keep parts whose overlap vanishes, so a later update of the bond
+        # between them finds a zero two-site state, leaves it unchanged and raises
+        # GPEPS_FLAG_NUMERIC.  Only the tie instance may do that: the other 15 angles,
+        # batched alone, raise no flag.
+        assert flags == 2, flags
+        rest = [k for k in range(len(theta)) if not _is_clifford_tie(theta[k], w.steps, w.D)]
+        _, g2 = run_step([graphs[k] for k in rest], w.D, dtype, [theta[k] for k in rest], w.steps)
+        g2.close()
     ref = np.array([inst["mean_z"] for inst in gold["instances"]]).T
     for k in range(len(theta)):
         for t in range(w.steps):
@@ -248,12 +260,13 @@ def test_checkpoint_restore_and_readout_on_gpu_state():
     assert np.abs(peps.expect_z() - zb.cpu().numpy()).max() < 1e-12
 
 
-def test_persistent_schedule_is_bit_identical():
-    """The work-queue schedule changes which SM runs a bond, not its arithmetic."""
+def test_schedules_are_bit_identical():
+    """The work-queue schedules (one or two CTAs per SM, the latter with its n x n matrices in
+    global memory) change which SM runs a bond and where its matrices live, not its arithmetic."""
     import torch
     from ._gpu_util import gpu_lib
     outs = []
-    for persistent in (0, 1):
+    for persistent in (0, 1, 2):
         g = gpu_lib()([(M127, E127), heavy_hex(*OSPREY)], 8, dtype="mixed")
         g.set_schedule(persistent)
         g.reset()
@@ -262,7 +275,8 @@ def test_persistent_schedule_is_bit_identical():
         outs.append((m.cpu().numpy(), z.cpu().numpy()))
         assert g.status() == 0
         g.close()
-    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    for o in outs[1:]:
+        assert np.array_equal(outs[0][0], o[0]) and np.array_equal(outs[0][1], o[1])
 
 
 def test_autotuned_setting_stays_within_tolerance():
