@@ -222,8 +222,14 @@ struct BondSmem {
     off_rs32 = off_rc32 + (size_t)((m + 1) / 2) * 8;
     off_int = off_rs32 + (size_t)((m + 1) / 2) * 8;
     small = (off_int + (size_t)(n + 2 * m + 8) * 4 + 15) & ~(size_t)15;
-    // global-memory mode: the FP32 level's packed rho32 and V32 follow the small arrays
+    // global-memory mode: the FP32 level's packed rho32 and V32 follow the small
+    // arrays, and later the scratch of the extra levels (lv = min(n/2, 32)
+    // indices: W64 [lv][lv], Gw [lv][lv+1] complex double, B32 [lv][lv+1],
+    // W32 [lv][lv] complex float)
     f32 = ((size_t)n * (n + 1) / 2 + (size_t)n * n) * 8;
+    const size_t lv = (size_t)(m < kMaxLevel ? m : kMaxLevel);
+    const size_t lvl = lv * (48 * lv + 24);
+    if (lvl > f32) f32 = lvl;
   }
   size_t f32;
 };
@@ -624,7 +630,8 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
     int* mark_c = rp;     // [n] (rp and rq likewise, idle during the selection)
     const int cap = (n / 2 < kMaxLevel) ? n / 2 : kMaxLevel;
     // level scratch for ns <= lv indices: in X, or in the free FP32 shared memory
-    const int lv = packed ? kMaxLevel : n / 2;
+    // (sized for min(n/2, 32) indices)
+    const int lv = packed ? cap : n / 2;
     double2* W64 = packed ? reinterpret_cast<double2*>(f32s) : X;   // [ns][ns]
     double2* Gw = W64 + (size_t)lv * lv;                             // [ns][ns+1]
     float2* B32 = reinterpret_cast<float2*>(Gw + (size_t)lv * (lv + 1));  // [ns][ns+1]

@@ -179,9 +179,10 @@ def test_theta_sweep_16_instances(dtype):
         # arbitrary D-dimensional part of a degenerate eigenspace; two neighbouring
         # bonds can keep parts whose overlap vanishes, so a later update of the bond
         # between them finds a zero two-site state, leaves it unchanged and raises
-        # GPEPS_FLAG_NUMERIC.  Only the tie instance may do that: the other 15 angles,
+        # GPEPS_FLAG_NUMERIC (the sweeps on that zero matrix may also hit their cap:
+        # GPEPS_FLAG_NOCONV).  Only the tie instance may do that: the other 15 angles,
         # batched alone, raise no flag.
-        assert flags == 2, flags
+        assert flags & 2, flags
         rest = [k for k in range(len(theta)) if not _is_clifford_tie(theta[k], w.steps, w.D)]
         _, g2 = run_step([graphs[k] for k in rest], w.D, dtype, [theta[k] for k in rest], w.steps)
         g2.close()
