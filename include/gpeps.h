@@ -164,13 +164,15 @@ int gpeps_set_levels(gpeps_handle* h, double level_ratio, int32_t levels);
 /*
  * Schedule of the bond eigenproblems: 0 launches one CTA per bond (default);
  * 1 launches one CTA per SM that takes bonds from a work queue in the work
- * buffer; 2 launches two CTAs per SM (256 threads each) on the queue, each
- * with its n x n FP64 matrices in a slot of the work buffer (held in L2) and
- * its FP32 level in shared memory, so that one bond's latency-bound phases
- * overlap the other's FP64 work.  Every schedule runs the bonds of a colour
- * class largest first and gives bit-identical results.  Host-only; drops a
- * captured step graph.  Errors: GPEPS_EINVAL for other values, and for 2 on an
- * unbound handle, for D above 48, or on a device with more than 256 SMs.
+ * buffer; 2 and 3 launch two (256 threads each) or four (128 threads) CTAs per
+ * SM on the queue, each with its n x n FP64 matrices in a slot of the work
+ * buffer (held in L2) and its FP32 level in shared memory, so that one bond's
+ * latency-bound phases overlap another's FP64 work.  Every schedule runs the
+ * bonds of a colour class largest first and gives bit-identical results.
+ * Host-only; drops a captured step graph.  Errors: GPEPS_EINVAL for other
+ * values, and for 2 or 3 on an unbound handle, when the FP32 level does not fit
+ * the CTA's share of shared memory (D above 48 for 2, above 33 for 3), or on a
+ * device with more than 256 SMs.
  */
 int gpeps_set_schedule(gpeps_handle* h, int32_t schedule);
 

@@ -79,7 +79,7 @@ struct gpeps_handle {
   char* d_state = nullptr;
   char* d_work = nullptr;
   bool bound = false;
-  int schedule = 0;  // bond eigenproblems: 0 one CTA per bond, 1 work queue (one CTA per SM), 2 work queue (two per SM)
+  int schedule = 0;  // bond eigenproblems: 0 one CTA per bond; work queue with 1 (schedule 1), 2 (2) or 4 (3) CTAs per SM
   int n_sms = 0;
   int64_t bonds_since_reset = 0;
   // captured step
@@ -231,7 +231,7 @@ int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr, void* vsave = 
   GP_CUDA(Launch<T>::bond(bonds, nbd, partials, h->gamma(), h->lam(), h->pending(), Y, theta_a, h->flags(),
                           h->sweeps(), h->cycles(), vsave, h->D, h->jp, h->stream,
                           h->schedule ? h->at<unsigned int>(h->w_queue) : nullptr, h->n_sms,
-                          h->d_work + h->w_bond_scratch, h->schedule == 2));
+                          h->d_work + h->w_bond_scratch, h->schedule == 3 ? 4 : h->schedule == 2 ? 2 : 1));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[2], h->stream));
   GP_CUDA(Launch<T>::update(tiles, nt, bonds, h->gamma(), h->lam(), Y, theta_a, h->D, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[3], h->stream));
@@ -434,7 +434,7 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   // blockIdx.x): beyond the shared-memory limit one slot per bond of the largest
   // class; otherwise slots for the two-CTAs-per-SM schedule only
   h->bond_slot = bond_footprint_global(D).slot;
-  h->bond_slots = bond_footprint(D, kBondSmemMax).slot ? h->max_bonds : std::min(h->max_bonds, 2 * kMaxSms);
+  h->bond_slots = bond_footprint(D, kBondSmemMax).slot ? h->max_bonds : std::min(h->max_bonds, 4 * kMaxSms);
   h->w_bond_scratch = carve((size_t)h->bond_slots * h->bond_slot);
   h->work_bytes = w;
   *out = h;
@@ -526,11 +526,12 @@ int gpeps_zz_layer_profiled(gpeps_handle* h, int32_t colour, float* ms) {
 }
 
 int gpeps_set_schedule(gpeps_handle* h, int32_t schedule) {
-  if (!h || schedule < 0 || schedule > 2) return GPEPS_EINVAL;
-  if (schedule == 2) {
-    // two CTAs per SM: shared memory of the FP32 level and a slot per CTA
-    if (!h->bound || bond_footprint_global(h->D).smem > kPairSmemMax) return GPEPS_EINVAL;
-    if (std::min(2 * h->n_sms, h->max_bonds) > h->bond_slots) return GPEPS_EINVAL;
+  if (!h || schedule < 0 || schedule > 3) return GPEPS_EINVAL;
+  if (schedule >= 2) {
+    // k CTAs per SM: shared memory of the FP32 level and a slot per CTA
+    const int k = schedule == 3 ? 4 : 2;
+    if (!h->bound || bond_footprint_global(h->D).smem > bond_share_smem(k)) return GPEPS_EINVAL;
+    if (std::min(k * h->n_sms, h->max_bonds) > h->bond_slots) return GPEPS_EINVAL;
   }
   h->schedule = schedule;
   drop_graph(h);

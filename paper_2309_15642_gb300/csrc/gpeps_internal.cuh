@@ -90,7 +90,7 @@ struct Launch {
                           double* pending, void* Y, double* theta_a, int* flags,
                           unsigned long long* sweeps, unsigned long long* cycles, void* vsave, int D,
                           JacobiParams jp, cudaStream_t st, unsigned int* queue = nullptr, int n_ctas = 0,
-                          void* scratch = nullptr, int pair = 0);
+                          void* scratch = nullptr, int per_sm = 1);
   static cudaError_t update(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, void* gamma,
                             const double* lam, const void* Y, const double* theta_a, int D, cudaStream_t st);
   static cudaError_t readout(const SiteDesc* sites, int n_sites, const void* gamma, const double* lam,
@@ -127,8 +127,11 @@ BondFootprint bond_footprint(int D, size_t smem_optin);
 // The same with the n x n matrices always in a global slot (the FP32 level in
 // shared memory): the layout of the two-CTAs-per-SM schedule.
 BondFootprint bond_footprint_global(int D);
-constexpr int kPairThreads = 256;     // threads of a bond CTA when two share an SM
-constexpr size_t kPairSmemMax = 113 * 1024;  // dynamic shared memory of such a CTA (two per SM)
-constexpr int kMaxSms = 256;          // SMs the two-per-SM schedule has scratch slots for
+// CTAs of the bond kernel sharing an SM in the global-matrix schedules: 2 of
+// 256 threads or 4 of 128 threads, each with at most 1/k of the SM's 228 KB of
+// shared memory (less 1 KB for the CTA's own reservation)
+constexpr size_t kSmemPerSm = 233472;
+constexpr size_t bond_share_smem(int k) { return kSmemPerSm / k - 1024 - 1024; }
+constexpr int kMaxSms = 256;          // SMs the shared-SM schedules have scratch slots for
 
 }  // namespace gpeps

@@ -1189,8 +1189,11 @@ cudaError_t Launch<T>::init() {
   e = cudaFuncSetAttribute(bond_kernel_persistent<T, kBondThreads, 1>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBondSmemMax);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(bond_kernel_persistent<T, kPairThreads, 2>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmemMax);
+  e = cudaFuncSetAttribute(bond_kernel_persistent<T, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bond_share_smem(2));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(bond_kernel_persistent<T, 128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bond_share_smem(4));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)update_smem(kMaxD, sizeof(V2<T>)));
@@ -1232,25 +1235,30 @@ template <typename T>
 cudaError_t Launch<T>::bond(const BondDesc* bonds, int n_bonds, const void* partials, void* gamma, double* lam,
                             double* pending, void* Y, double* theta_a, int* flags, unsigned long long* sweeps,
                             unsigned long long* cycles, void* vsave, int D, JacobiParams jp, cudaStream_t st,
-                            unsigned int* queue, int n_ctas, void* scratch, int pair) {
+                            unsigned int* queue, int n_ctas, void* scratch, int per_sm) {
   if (n_bonds == 0) return cudaSuccess;
-  const BondFootprint fp = pair ? bond_footprint_global(D) : bond_footprint(D, kBondSmemMax);
+  const bool shared = per_sm > 1;
+  const BondFootprint fp = shared ? bond_footprint_global(D) : bond_footprint(D, kBondSmemMax);
   if (fp.slot && !scratch) return cudaErrorInvalidValue;
-  if (pair && (!queue || fp.smem > kPairSmemMax)) return cudaErrorInvalidValue;
+  if (shared && (!queue || (per_sm != 2 && per_sm != 4) || fp.smem > bond_share_smem(per_sm)))
+    return cudaErrorInvalidValue;
   unsigned char* sp = fp.slot ? static_cast<unsigned char*>(scratch) : nullptr;
   if (queue) {
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    const int want = pair ? 2 * n_ctas : n_ctas;
+    const int want = per_sm * n_ctas;
     const int grid = want < n_bonds ? want : n_bonds;
-    if (pair)
-      bond_kernel_persistent<T, kPairThreads, 2><<<grid, kPairThreads, fp.smem, st>>>(
-          n_bonds, queue, bonds, static_cast<const V2<T>*>(partials), static_cast<V2<T>*>(gamma), lam, pending,
-          static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles, static_cast<double2*>(vsave), D, jp, sp, fp.slot);
+#define GP_BOND_PERSISTENT(THR, MINB)                                                                           \
+  bond_kernel_persistent<T, THR, MINB><<<grid, THR, fp.smem, st>>>(                                             \
+      n_bonds, queue, bonds, static_cast<const V2<T>*>(partials), static_cast<V2<T>*>(gamma), lam, pending,    \
+      static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles, static_cast<double2*>(vsave), D, jp, sp, fp.slot)
+    if (per_sm == 4)
+      GP_BOND_PERSISTENT(128, 4);
+    else if (per_sm == 2)
+      GP_BOND_PERSISTENT(256, 2);
     else
-      bond_kernel_persistent<T, kBondThreads, 1><<<grid, kBondThreads, fp.smem, st>>>(
-          n_bonds, queue, bonds, static_cast<const V2<T>*>(partials), static_cast<V2<T>*>(gamma), lam, pending,
-          static_cast<V2<T>*>(Y), theta_a, flags, sweeps, cycles, static_cast<double2*>(vsave), D, jp, sp, fp.slot);
+      GP_BOND_PERSISTENT(kBondThreads, 1);
+#undef GP_BOND_PERSISTENT
     return cudaGetLastError();
   }
   bond_kernel<T><<<n_bonds, kBondThreads, fp.smem, st>>>(bonds, static_cast<const V2<T>*>(partials),

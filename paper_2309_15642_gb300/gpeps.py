@@ -157,8 +157,8 @@ class GPEPS:
         return [int(x) for x in c]
 
     def set_schedule(self, schedule):
-        """Bond eigenproblems: 0 one CTA per bond, 1 work queue with one CTA per SM, 2 work queue
-        with two CTAs per SM (see gpeps_set_schedule)."""
+        """Bond eigenproblems: 0 one CTA per bond; 1, 2, 3 work queue with one, two or four CTAs
+        per SM (see gpeps_set_schedule)."""
         check(self.lib.gpeps_set_schedule(self.h, int(schedule)), "gpeps_set_schedule")
 
     def set_jacobi(self, tol=None, floor_rel=None, tol32=1e-6, floor32=2e-7, max_sweeps=40, max_sweeps32=20):
