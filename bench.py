@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile-steps", type=int, default=2, help="profiled steps after the timed region (>= 1)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule and thresholds")
+    ap.add_argument("--schedule", type=int, default=None,
+                    help="with --no-autotune: bond schedule (0 one CTA per bond; 1, 2, 3 work queue with 1, 2, 4 "
+                         "CTAs per SM)")
+    ap.add_argument("--floor-rel", type=float, default=None,
+                    help="with --no-autotune: FP64 Jacobi floor (fraction of the trace) of the mixed path")
     return ap.parse_args()
 
 
@@ -220,6 +225,11 @@ def run_gpeps(args, rank, world, local_rank):
     def timed(dtype, K, W, tune):
         g = GPEPS(graphs, w.D, dtype=dtype, device=str(dev))
         tuning = None
+        if not tune:
+            if args.schedule is not None:
+                g.set_schedule(args.schedule)
+            if args.floor_rel is not None and dtype == "mixed":
+                g.set_jacobi(floor_rel=args.floor_rel)
         if tune:
             from paper_2309_15642_gb300.autotune import autotune
             best, table = autotune(g, theta)
