@@ -1114,23 +1114,24 @@ __global__ void __launch_bounds__(kThreads)
   const SiteDesc sd = sites[blockIdx.x];
   int nel = 1;
   for (int q = 0; q < sd.deg; ++q) nel *= D;
+  // per element: kick and weighted |psi|^2 in the storage precision (the
+  // tensors carry no more), accumulation in FP64
   const double th = pending[blockIdx.x];
-  const double c = cos(0.5 * th), s = sin(0.5 * th);
+  const T c = (T)cos(0.5 * th), s = (T)sin(0.5 * th);
   double p0 = 0.0, p1 = 0.0;
   for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
-    double w = 1.0;
+    T w = (T)1;
     int rest = idx;
     for (int q = sd.deg - 1; q >= 0; --q) {
       const int l = rest % D;
       rest /= D;
-      const double lv = lam[sd.lam[q] + l];
+      const T lv = (T)lam[sd.lam[q] + l];
       w *= lv * lv;
     }
-    const V2<T> g0 = gamma[sd.off + idx], g1 = gamma[sd.off + nel + idx];
-    double2 a0, a1;
-    kick2<double>(c, s, make_double2(g0.x, g0.y), make_double2(g1.x, g1.y), a0, a1);
-    p0 += w * (a0.x * a0.x + a0.y * a0.y);
-    p1 += w * (a1.x * a1.x + a1.y * a1.y);
+    V2<T> a0, a1;
+    kick2<T>(c, s, gamma[sd.off + idx], gamma[sd.off + nel + idx], a0, a1);
+    p0 += (double)(w * (a0.x * a0.x + a0.y * a0.y));
+    p1 += (double)(w * (a1.x * a1.x + a1.y * a1.y));
   }
   __shared__ double red[2][kThreads / 32];
   for (int off = 16; off > 0; off >>= 1) {
