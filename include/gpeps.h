@@ -50,6 +50,7 @@ extern "C" {
 /* device flag bits returned by gpeps_status */
 #define GPEPS_FLAG_NOCONV 1
 #define GPEPS_FLAG_NUMERIC 2
+#define GPEPS_FLAG_TIMEOUT 4  /* a wait of the fused step kernel gave up (schedule 4) */
 
 /* storage / arithmetic of the evolution */
 #define GPEPS_C128 0       /* complex128 tensors; every product and the eigensolver in FP64 */
@@ -162,6 +163,16 @@ int gpeps_set_jacobi(gpeps_handle* h, double tol, double floor_rel, double tol32
 int gpeps_set_levels(gpeps_handle* h, double level_ratio, int32_t levels);
 
 /*
+ * Wait limit of the fused step (schedule 4), in SM clock cycles (default
+ * 2e10, about 10 s): a bond that waits longer for an earlier bond on one of its
+ * sites gives up, raises GPEPS_FLAG_TIMEOUT and runs on what it finds, so a
+ * launch always ends.  0 gives up at once whenever a dependency is still
+ * running (failure-detection tests use it).  Host-only; drops a captured step
+ * graph.  Errors: GPEPS_EINVAL for a negative value.
+ */
+int gpeps_set_wait_limit(gpeps_handle* h, int64_t cycles);
+
+/*
  * Schedule of the bond eigenproblems: 0 launches one CTA per bond (default);
  * 1 launches one CTA per SM that takes bonds from a work queue in the work
  * buffer; 2 and 3 launch two (256 threads each) or four (128 threads) CTAs per
@@ -169,10 +180,18 @@ int gpeps_set_levels(gpeps_handle* h, double level_ratio, int32_t levels);
  * buffer (held in L2) and its FP32 level in shared memory, so that one bond's
  * latency-bound phases overlap another's FP64 work.  Every schedule runs the
  * bonds of a colour class largest first and gives bit-identical results.
+ * 4 makes gpeps_step run every bond update of a Trotter step in one persistent
+ * launch (two CTAs per SM where they fit, else one): the Gram pass of the
+ * larger end, the bond eigenproblem and the update of the larger end run in the
+ * CTA that takes the bond, bonds are taken colour class by colour class, and a
+ * bond waits only until the earlier bonds on its two sites are done, so the
+ * classes need no barrier between them (same results; a wait that gives up
+ * after ~10 s raises GPEPS_FLAG_TIMEOUT instead of hanging); gpeps_zz_layer
+ * then uses schedule 2 (or 1 where 2 does not fit).
  * Host-only; drops a captured step graph.  Errors: GPEPS_EINVAL for other
- * values, and for 2 or 3 on an unbound handle, when the FP32 level does not fit
- * the CTA's share of shared memory (D above 48 for 2, above 33 for 3), or on a
- * device with more than 256 SMs.
+ * values, and for 2, 3 or 4 on an unbound handle, when the FP32 level does not
+ * fit the CTA's share of shared memory (D above 48 for 2, above 33 for 3), or
+ * on a device with more than 256 SMs.
  */
 int gpeps_set_schedule(gpeps_handle* h, int32_t schedule);
 

@@ -8,7 +8,8 @@ max_i |<Z_i> - <Z_i>_ref| <= ``budget``.  The fastest accepted candidate is
 applied to the handle and returned with the timings.
 
 Candidates (mixed path): schedule (one CTA per bond | work queue with one, two or
-four CTAs per SM; a schedule the handle rejects is skipped) x
+four CTAs per SM | one fused launch per step; a schedule the handle rejects is
+skipped) x
 FP32-level thresholds (tol32, floor32) x FP64 stopping thresholds (tol,
 floor_rel = 1e-8 or 3e-8 of the trace: below the ~1e-7 relative rounding that
 the bond matrix inherits from its FP32 Gram inputs); complex128 keeps its
@@ -23,7 +24,7 @@ import torch
 STRICT_MIXED = dict(tol=1e-9, floor_rel=1e-11, tol32=1e-6, floor32=2e-7)
 FP32_LEVELS = [(1e-6, 2e-7), (3e-6, 1e-6)]
 FP64_STOPS = [(1e-9, 1e-8), (1e-9, 3e-8)]
-SCHEDULES = (0, 1, 2, 3)
+SCHEDULES = (0, 1, 2, 3, 4)
 
 
 def candidates(dtype):

@@ -79,7 +79,10 @@ struct gpeps_handle {
   char* d_state = nullptr;
   char* d_work = nullptr;
   bool bound = false;
-  int schedule = 0;  // bond eigenproblems: 0 one CTA per bond; work queue with 1 (schedule 1), 2 (2) or 4 (3) CTAs per SM
+  int schedule = 0;  // bond eigenproblems: 0 one CTA per bond; work queue with 1 (schedule 1), 2 (2) or 4 (3)
+                     // CTAs per SM; 4 fused step (gpeps_step: one persistent launch over every colour class)
+  std::vector<StepTask> tasks;  // fused step: every bond of a step, colour by colour, with its dependencies
+  size_t w_tasks = 0, w_done = 0;
   int n_sms = 0;
   int64_t bonds_since_reset = 0;
   // captured step
@@ -215,6 +218,32 @@ struct PhaseEvents {
   cudaEvent_t ev[4];
 };
 
+// CTAs per SM of the layered bond launch (schedule 4 runs its layers, outside
+// gpeps_step, on the work queue with two CTAs per SM where they fit)
+int layered_per_sm(const gpeps_handle* h) {
+  switch (h->schedule) {
+    case 2: return 2;
+    case 3: return 4;
+    case 4: return bond_footprint_global(h->D).smem <= bond_share_smem(2) ? 2 : 1;
+    default: return 1;
+  }
+}
+
+// CTAs per SM of the fused step launch
+int step_per_sm(const gpeps_handle* h) {
+  return step_footprint(h->D, h->elt).smem <= bond_share_smem(2) ? 2 : 1;
+}
+
+template <typename T>
+int fused_step_impl(gpeps_handle* h) {
+  GP_CUDA(Launch<T>::step(h->at<StepTask>(h->w_tasks), (int)h->tasks.size(), h->at<unsigned int>(h->w_queue),
+                          h->at<int>(h->w_done), h->gamma(), h->lam(), h->pending(), h->flags(), h->sweeps(),
+                          h->cycles(), h->D, h->jp, h->stream, h->n_sms, h->d_work + h->w_bond_scratch,
+                          h->bond_slot, step_per_sm(h)));
+  h->bonds_since_reset += (int64_t)h->tasks.size();
+  return GPEPS_OK;
+}
+
 template <typename T>
 int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr, void* vsave = nullptr) {
   ColourPlan& cp = h->colours[c];
@@ -231,7 +260,7 @@ int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr, void* vsave = 
   GP_CUDA(Launch<T>::bond(bonds, nbd, partials, h->gamma(), h->lam(), h->pending(), Y, theta_a, h->flags(),
                           h->sweeps(), h->cycles(), vsave, h->D, h->jp, h->stream,
                           h->schedule ? h->at<unsigned int>(h->w_queue) : nullptr, h->n_sms,
-                          h->d_work + h->w_bond_scratch, h->schedule == 3 ? 4 : h->schedule == 2 ? 2 : 1));
+                          h->d_work + h->w_bond_scratch, layered_per_sm(h)));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[2], h->stream));
   GP_CUDA(Launch<T>::update(tiles, nt, bonds, h->gamma(), h->lam(), Y, theta_a, h->D, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[3], h->stream));
@@ -271,9 +300,14 @@ int readout_impl(gpeps_handle* h) {
 int one_step(gpeps_handle* h, const double* theta, int per_qubit) {
   int st = kick_impl(h, theta, per_qubit);
   if (st) return st;
-  for (int c = 0; c < (int)h->colours.size(); ++c) {
-    st = layer(h, c);
+  if (h->schedule == 4) {
+    st = h->dtype == GPEPS_C128 ? fused_step_impl<double>(h) : fused_step_impl<float>(h);
     if (st) return st;
+  } else {
+    for (int c = 0; c < (int)h->colours.size(); ++c) {
+      st = layer(h, c);
+      if (st) return st;
+    }
   }
   return readout_impl(h);
 }
@@ -384,6 +418,32 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
     h->max_parts = std::max(h->max_parts, cp.n_parts);
     h->max_bonds = std::max(h->max_bonds, (int)cp.bonds.size());
   }
+  // fused step: every bond of a step, colour by colour; a task waits for the
+  // last earlier task on each of its sites.  Class 0 keeps its cost order; a
+  // later class is ordered by its latest dependency (then cost), so that the
+  // tasks taken first are those whose sites were freed first.
+  {
+    std::vector<int> last((size_t)h->total_sites, -1);
+    for (auto& cp : h->colours) {
+      std::vector<int> idx(cp.bonds.size());
+      for (int i = 0; i < (int)idx.size(); ++i) idx[i] = i;
+      auto dep = [&](int i) { return std::max(last[cp.bonds[i].a.site], last[cp.bonds[i].b.site]); };
+      std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return dep(x) < dep(y); });
+      const int c = (int)(&cp - h->colours.data());
+      std::vector<std::pair<int, int>> touched;
+      for (int i : idx) {
+        StepTask t{};
+        t.bd = cp.bonds[i];
+        t.dep_a = last[t.bd.a.site];
+        t.dep_b = last[t.bd.b.site];
+        t.colour = c;
+        touched.emplace_back(t.bd.a.site, (int)h->tasks.size());
+        touched.emplace_back(t.bd.b.site, (int)h->tasks.size());
+        h->tasks.push_back(t);
+      }
+      for (auto& pr : touched) last[pr.first] = pr.second;
+    }
+  }
   // Jacobi thresholds: the bond matrix carries FP64 rounding (C128) or the
   // FP32 rounding of its Gram inputs (mixed); eigenvalues below that level are noise.
   // FP64 sweeps stop at |a_pq| <= max(tol sqrt(a_pp a_qq), floor_rel * trace):
@@ -399,6 +459,7 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   h->jp.max_sweeps32 = 20;
   h->jp.level_ratio = 1e-5;
   h->jp.levels = 4;
+  h->jp.wait_cycles = kWaitCycles;
   // layouts
   size_t s = 0;
   h->s_lam = s;
@@ -433,9 +494,13 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   // n x n bond matrices outside shared memory (a CTA indexes its slot by
   // blockIdx.x): beyond the shared-memory limit one slot per bond of the largest
   // class; otherwise slots for the two-CTAs-per-SM schedule only
-  h->bond_slot = bond_footprint_global(D).slot;
+  // (slots of the fused step are larger: they also hold the Gram sums and Y)
+  h->bond_slot = std::max(bond_footprint_global(D).slot, step_footprint(D, h->elt).slot);
   h->bond_slots = bond_footprint(D, kBondSmemMax).slot ? h->max_bonds : std::min(h->max_bonds, 4 * kMaxSms);
+  h->bond_slots = std::max(h->bond_slots, std::min((int)h->tasks.size(), 2 * kMaxSms));
   h->w_bond_scratch = carve((size_t)h->bond_slots * h->bond_slot);
+  h->w_tasks = carve(h->tasks.size() * sizeof(StepTask));
+  h->w_done = carve(h->tasks.size() * sizeof(int));
   h->work_bytes = w;
   *out = h;
   return GPEPS_OK;
@@ -476,6 +541,7 @@ int gpeps_bind(gpeps_handle* h, void* d_state, void* d_work) {
     GP_CUDA(up(cp.w_bonds, cp.bonds.data(), cp.bonds.size() * sizeof(BondDesc)));
     GP_CUDA(up(cp.w_tiles, cp.tiles.data(), cp.tiles.size() * sizeof(TileDesc)));
   }
+  GP_CUDA(up(h->w_tasks, h->tasks.data(), h->tasks.size() * sizeof(StepTask)));
   GP_CUDA(cudaMemsetAsync(h->d_work + h->w_flags, 0, sizeof(int) * 4, h->stream));
   GP_CUDA(cudaMemsetAsync(h->d_work + h->w_sweeps, 0, sizeof(unsigned long long), h->stream));
   GP_CUDA(cudaMemsetAsync(h->d_work + h->w_pending, 0, h->total_sites * sizeof(double), h->stream));
@@ -526,7 +592,15 @@ int gpeps_zz_layer_profiled(gpeps_handle* h, int32_t colour, float* ms) {
 }
 
 int gpeps_set_schedule(gpeps_handle* h, int32_t schedule) {
-  if (!h || schedule < 0 || schedule > 3) return GPEPS_EINVAL;
+  if (!h || schedule < 0 || schedule > 4) return GPEPS_EINVAL;
+  if (schedule == 4) {
+    // fused step: shared memory of one CTA (alone or two per SM) and a slot per CTA
+    if (!h->bound) return GPEPS_EINVAL;
+    const BondFootprint fp = step_footprint(h->D, h->elt);
+    if (fp.smem > kBondSmemMax || fp.slot > h->bond_slot) return GPEPS_EINVAL;
+    if (std::min(step_per_sm(h) * h->n_sms, (int)h->tasks.size()) > h->bond_slots) return GPEPS_EINVAL;
+    if (layered_per_sm(h) == 2 && std::min(2 * h->n_sms, h->max_bonds) > h->bond_slots) return GPEPS_EINVAL;
+  }
   if (schedule >= 2) {
     // k CTAs per SM: shared memory of the FP32 level and a slot per CTA
     const int k = schedule == 3 ? 4 : 2;
@@ -680,6 +754,13 @@ int gpeps_set_jacobi(gpeps_handle* h, double tol, double floor_rel, double tol32
   h->jp.max_sweeps = max_sweeps;
   h->jp.max_sweeps32 = max_sweeps32;
   drop_graph(h);  // the captured step holds the old parameters
+  return GPEPS_OK;
+}
+
+int gpeps_set_wait_limit(gpeps_handle* h, int64_t cycles) {
+  if (!h || cycles < 0) return GPEPS_EINVAL;
+  h->jp.wait_cycles = cycles;
+  drop_graph(h);
   return GPEPS_OK;
 }
 

@@ -58,6 +58,16 @@ struct TileDesc {
   int32_t part;     // Gram-partial slot written by this tile
 };
 
+// One bond update of the fused step: the bond, and the earlier tasks of the
+// same step on its two sites (-1: none) that must be complete before it starts.
+struct StepTask {
+  BondDesc bd;
+  int32_t dep_a;
+  int32_t dep_b;
+  int32_t colour;
+  int32_t pad;
+};
+
 struct SiteDesc {
   int64_t off;      // element offset of Gamma
   int32_t deg;
@@ -74,6 +84,7 @@ struct JacobiParams {
   int max_sweeps32;  // FP32 cap (hitting it only costs FP64 sweeps)
   double level_ratio;  // an extra FP32 level takes the diagonals below this fraction of their block's scale
   int levels;          // extra FP32 levels at most (0..kMaxExtraLevels)
+  long long wait_cycles;  // fused step: a wait for an earlier task gives up after this many SM cycles
 };
 
 // Launchers (su_kernels.cu).  T = float for GPEPS_MIXED_C64, double for GPEPS_C128.
@@ -95,7 +106,14 @@ struct Launch {
                             const double* lam, const void* Y, const double* theta_a, int D, cudaStream_t st);
   static cudaError_t readout(const SiteDesc* sites, int n_sites, const void* gamma, const double* lam,
                              const double* pending, double* z, int D, cudaStream_t st);
+  // Every bond update of one Trotter step in one persistent launch (per_sm CTAs
+  // per SM over the ordered task list; `done` holds one flag per task).
+  static cudaError_t step(const StepTask* tasks, int n_tasks, unsigned int* queue, int* done, void* gamma,
+                          double* lam, double* pending, int* flags, unsigned long long* sweeps,
+                          unsigned long long* cycles, int D, JacobiParams jp, cudaStream_t st, int n_ctas,
+                          void* scratch, size_t slot, int per_sm);
 };
+
 
 constexpr int kMaxGradD = 16;  // bond dimension limit of the reverse mode (shared memory of its bond kernel)
 
@@ -133,5 +151,11 @@ BondFootprint bond_footprint_global(int D);
 constexpr size_t kSmemPerSm = 233472;
 constexpr size_t bond_share_smem(int k) { return kSmemPerSm / k - 1024 - 1024; }
 constexpr int kMaxSms = 256;          // SMs the shared-SM schedules have scratch slots for
+
+// Memory of a fused-step CTA: dynamic shared memory, and the bytes of its
+// global slot (n x n matrices of the bond eigenproblem, FP64 Gram sums, Y and
+// the kick angle of end a).
+BondFootprint step_footprint(int D, size_t elt);
+constexpr long long kWaitCycles = 20000000000LL;  // default wait limit of the fused step (~10 s of SM cycles)
 
 }  // namespace gpeps

@@ -91,10 +91,19 @@ __device__ __forceinline__ int64_t elem(const SideDesc& sd, int s, RowPos p, int
   return sd.off + (int64_t)s * sd.str_s + (int64_t)p.r1 * sd.str_o1 + (int64_t)p.r2 * sd.str_o2 +
          (int64_t)k * sd.str_k;
 }
+// Loads of state that another CTA of the same launch may have written (the
+// fused step kernel) go around L1, which is not coherent between SMs; the
+// layered kernels read state written by earlier launches only.
+template <bool kCG, typename X>
+__device__ __forceinline__ X ldst(const X* p) {
+  if constexpr (kCG) return __ldcg(p);
+  else return *p;
+}
+template <bool kCG = false>
 __device__ __forceinline__ double row_weight(const SideDesc& sd, const double* lam, RowPos p) {
   double w = 1.0;
-  if (sd.lam_o1 >= 0) w *= lam[sd.lam_o1 + p.r1];
-  if (sd.lam_o2 >= 0) w *= lam[sd.lam_o2 + p.r2];
+  if (sd.lam_o1 >= 0) w *= ldst<kCG>(lam + sd.lam_o1 + p.r1);
+  if (sd.lam_o2 >= 0) w *= ldst<kCG>(lam + sd.lam_o2 + p.r2);
   return w;
 }
 
@@ -736,24 +745,23 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
 // A bond whose spectrum is not usable (NaN/Inf or zero norm) is left as it
 // was: Y = identity so that the update launch only applies the pending kick
 // to end a, lambda and end b untouched; the flag word reports it.
-template <typename T>
-__device__ void bond_fail(int bi, const BondDesc& bd, V2<T>* Yout, double* theta_a, double* pending, int* flags,
-                          int D) {
+template <typename T, bool kCG>
+__device__ void bond_fail(const BondDesc& bd, V2<T>* Y, double* theta_a, double* pending, int* flags, int D) {
   const int D2 = D * D;
   for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
     const int kl = o % D2;
-    Yout[(int64_t)bi * 2 * D2 + o] = mk<T>((T)((kl / D) == (kl % D) ? 1 : 0), (T)0);
+    Y[o] = mk<T>((T)((kl / D) == (kl % D) ? 1 : 0), (T)0);
   }
   if (threadIdx.x == 0) {
     atomicOr(flags, 2);
-    theta_a[bi] = pending[bd.a.site];
+    *theta_a = ldst<kCG>(pending + bd.a.site);
     pending[bd.a.site] = 0.0;
   }
 }
 
 // F[(row, t)][k]: kicked Gamma_b with the lambda of its other legs, in the
 // storage precision T.
-template <typename T>
+template <typename T, bool kCG>
 __device__ void load_F(const SideDesc& sb, const V2<T>* gamma, const double* lam, double th, V2<T>* F, int D) {
   const T c = (T)cos(0.5 * th), s = (T)sin(0.5 * th);
   for (int idx = threadIdx.x; idx < sb.rows * D; idx += blockDim.x) {
@@ -761,8 +769,8 @@ __device__ void load_F(const SideDesc& sb, const V2<T>* gamma, const double* lam
     const RowPos p = row_pos(sb, rj);
     const int64_t e = elem(sb, 0, p, k);
     V2<T> a0, a1;
-    kick2<T>(c, s, gamma[e], gamma[e + sb.str_s], a0, a1);
-    const T w = (T)row_weight(sb, lam, p);
+    kick2<T>(c, s, ldst<kCG>(gamma + e), ldst<kCG>(gamma + e + sb.str_s), a0, a1);
+    const T w = (T)row_weight<kCG>(sb, lam, p);
     F[(rj * 2 + 0) * D + k] = c_scale<T>(a0, w);
     F[(rj * 2 + 1) * D + k] = c_scale<T>(a1, w);
   }
@@ -773,13 +781,17 @@ __device__ void load_F(const SideDesc& sb, const V2<T>* gamma, const double* lam
 // FP32 eigenvectors, rho' = V^dagger rho V and FP64 Jacobi sweeps on rho' until
 // every off-diagonal is at FP64 rounding level (mixed-precision Jacobi: a
 // low-precision eigenbasis as preconditioner of the high-precision sweeps).
-template <typename T>
-__device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T>* __restrict__ partials, V2<T>* gamma,
-                double* lam, double* pending, V2<T>* __restrict__ Yout, double* __restrict__ theta_a,
-                int* flags, unsigned long long* sweeps_out, unsigned long long* cycles, double2* vsave, int D,
-                JacobiParams jp, unsigned char* big) {
+// The Gram blocks of end a come either as bd.n_parts storage-precision
+// partials (partials: this bond's first) summed here in FP64, or already summed
+// (gsum, FP64).  Outputs: Y (2 D^2, this bond's), *theta_a (the kick of end a,
+// consumed), vs (sorted eigenpairs for the reverse mode, or null), the new
+// Gamma_b and lambda of the bond.
+template <typename T, bool kCG>
+__device__ void bond_body(const BondDesc bd, const V2<T>* __restrict__ partials, const double2* gsum, V2<T>* gamma,
+                          double* lam, double* pending, V2<T>* __restrict__ Y, double* __restrict__ theta_a,
+                          int* flags, unsigned long long* sweeps_out, unsigned long long* cycles, double2* vs, int D,
+                          JacobiParams jp, unsigned char* big) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const BondDesc bd = bonds[bi];
   const SideDesc sb = bd.b;
   const int nb = sb.rows;
   const int n = 2 * nb;
@@ -809,7 +821,7 @@ __device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T
   int* rq = rp + n / 2;
   int* iflag = rq + n / 2;  // [4]
   const int ldr = n + 1;
-  const double th_b = pending[sb.site];
+  const double th_b = ldst<kCG>(pending + sb.site);
   long long t_prev = clock64();
   auto mark = [&](int phase) {
     if (threadIdx.x == 0) {
@@ -819,21 +831,25 @@ __device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T
     }
   };
 
-  for (int k = threadIdx.x; k < D; k += blockDim.x) lamo[k] = lam[bd.lam_e + k];
+  for (int k = threadIdx.x; k < D; k += blockDim.x) lamo[k] = ldst<kCG>(lam + bd.lam_e + k);
   __syncthreads();
   for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
     double2 acc = make_double2(0.0, 0.0);
-    for (int p = 0; p < bd.n_parts; ++p) {
-      const V2<T> v = partials[(int64_t)(bd.part0 + p) * 2 * D2 + o];
-      acc.x += (double)v.x;
-      acc.y += (double)v.y;
+    if (gsum) {
+      acc = gsum[o];
+    } else {
+      for (int p = 0; p < bd.n_parts; ++p) {
+        const V2<T> v = partials[(int64_t)p * 2 * D2 + o];
+        acc.x += (double)v.x;
+        acc.y += (double)v.y;
+      }
     }
     const int kl = o % D2;
     const int k = kl / D, l = kl - (kl / D) * D;
     const double2 v = cscale(acc, lamo[k] * lamo[l]);
     Cs[o] = mk<T>((T)v.x, (T)v.y);
   }
-  load_F<T>(sb, gamma, lam, th_b, F, D);
+  load_F<T, kCG>(sb, gamma, lam, th_b, F, D);
   for (int idx = threadIdx.x; idx < n * ldr; idx += blockDim.x) RHO[idx] = make_double2(0.0, 0.0);
   __syncthreads();
   // rho = sum_s phase(s) o (conj(F) C_s F^T), upper triangle, then mirrored;
@@ -879,7 +895,7 @@ __device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T
   __syncthreads();
   const double trace = scal[0];
   if (!(trace > 0.0) || !isfinite(trace)) {
-    bond_fail<T>(bi, bd, Yout, theta_a, pending, flags, D);
+    bond_fail<T, kCG>(bd, Y, theta_a, pending, flags, D);
     return;
   }
   mark(0);
@@ -895,9 +911,7 @@ __device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T
     order[rank] = i;
   }
   __syncthreads();
-  if (vsave) {  // sorted eigenvectors and eigenvalues for the reverse mode (slot of 2D x 2D + 2D)
-    const int nm = 2 * D;
-    double2* vs = vsave + (int64_t)bi * (nm * nm + nm);
+  if (vs) {  // sorted eigenvectors and eigenvalues for the reverse mode (slot of 2D x 2D + 2D)
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
       const int x = idx / n, j = idx - (idx / n) * n;
       vs[x * n + j] = Vm[x * n + order[j]];
@@ -921,14 +935,14 @@ __device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T
     double mx = 0.0;
     const int lo = sb.lam_o1 >= 0 ? sb.lam_o1 : sb.lam_o2;
     if (lo >= 0)
-      for (int k = 0; k < D; ++k) mx = fmax(mx, lam[lo + k]);
+      for (int k = 0; k < D; ++k) mx = fmax(mx, ldst<kCG>(lam + lo + k));
     scal[2] = mx;
   }
-  load_F<T>(sb, gamma, lam, th_b, F, D);
+  load_F<T, kCG>(sb, gamma, lam, th_b, F, D);
   __syncthreads();
   const double nrm = scal[1];
   if (!(nrm > 0.0) || !isfinite(nrm)) {
-    bond_fail<T>(bi, bd, Yout, theta_a, pending, flags, D);
+    bond_fail<T, kCG>(bd, Y, theta_a, pending, flags, D);
     return;
   }
   // Y_s[k][kk] = lam_k sum_x F[x][k] g(s, t_x) V[x][order[kk]] / sv[kk], in the
@@ -949,7 +963,7 @@ __device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T
       }
       acc = c_scale<T>(acc, (T)(lamo[k] / sv[kk]));
     }
-    Yout[(int64_t)bi * 2 * D2 + o] = acc;
+    Y[o] = acc;
   }
   // Gamma_b'[t][row][kk] = conj(V[(row, t)][order[kk]]) / lambda_other(row)
   {
@@ -961,7 +975,7 @@ __device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T
       double winv = 1.0;
       const int lo = sb.lam_o1 >= 0 ? sb.lam_o1 : sb.lam_o2;
       if (lo >= 0) {
-        const double lv = lam[lo + (sb.lam_o1 >= 0 ? p.r1 : p.r2)];
+        const double lv = ldst<kCG>(lam + lo + (sb.lam_o1 >= 0 ? p.r1 : p.r2));
         winv = lv > kLambdaCut * mx ? 1.0 / lv : 0.0;
       }
       double2 v = make_double2(0.0, 0.0);
@@ -973,11 +987,25 @@ __device__ void bond_body(int bi, const BondDesc* __restrict__ bonds, const V2<T
   // new lambda of the bond; kick angles consumed
   for (int kk = threadIdx.x; kk < D; kk += blockDim.x) lam[bd.lam_e + kk] = sv[kk] / nrm;
   if (threadIdx.x == 0) {
-    theta_a[bi] = pending[bd.a.site];
+    *theta_a = ldst<kCG>(pending + bd.a.site);
     pending[bd.a.site] = 0.0;
     pending[sb.site] = 0.0;
   }
   mark(5);
+}
+
+template <typename T>
+__device__ __forceinline__ void bond_body_layered(int bi, const BondDesc* __restrict__ bonds,
+                                                  const V2<T>* __restrict__ partials, V2<T>* gamma, double* lam,
+                                                  double* pending, V2<T>* __restrict__ Yout,
+                                                  double* __restrict__ theta_a, int* flags,
+                                                  unsigned long long* sweeps_out, unsigned long long* cycles,
+                                                  double2* vsave, int D, JacobiParams jp, unsigned char* big) {
+  const BondDesc bd = bonds[bi];
+  const int D2 = D * D, nm = 2 * D;
+  bond_body<T, false>(bd, partials + (int64_t)bd.part0 * 2 * D2, nullptr, gamma, lam, pending,
+                      Yout + (int64_t)bi * 2 * D2, theta_a + bi, flags, sweeps_out, cycles,
+                      vsave ? vsave + (int64_t)bi * (nm * nm + nm) : nullptr, D, jp, big);
 }
 
 // One CTA per bond.  `scratch` (null when everything fits in shared memory):
@@ -988,8 +1016,8 @@ __global__ void __launch_bounds__(kBondThreads, 1)
                 double* pending, V2<T>* __restrict__ Yout, double* __restrict__ theta_a, int* flags,
                 unsigned long long* sweeps_out, unsigned long long* cycles, double2* vsave, int D, JacobiParams jp,
                 unsigned char* scratch, size_t slot) {
-  bond_body<T>(blockIdx.x, bonds, partials, gamma, lam, pending, Yout, theta_a, flags, sweeps_out, cycles, vsave, D,
-               jp, scratch ? scratch + (size_t)blockIdx.x * slot : nullptr);
+  bond_body_layered<T>(blockIdx.x, bonds, partials, gamma, lam, pending, Yout, theta_a, flags, sweeps_out, cycles,
+                       vsave, D, jp, scratch ? scratch + (size_t)blockIdx.x * slot : nullptr);
 }
 
 // Persistent form: kMinB CTAs per SM take bonds from a work queue (bonds are
@@ -1010,9 +1038,237 @@ __global__ void __launch_bounds__(kThr, kMinB)
     const int bi = next;
     __syncthreads();
     if (bi >= n_bonds) break;
-    bond_body<T>(bi, bonds, partials, gamma, lam, pending, Yout, theta_a, flags, sweeps_out, cycles, vsave, D, jp,
-                 big);
+    bond_body_layered<T>(bi, bonds, partials, gamma, lam, pending, Yout, theta_a, flags, sweeps_out, cycles, vsave,
+                         D, jp, big);
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- fused step
+// Every bond update of one Trotter step in one persistent launch.  The tasks
+// are ordered colour by colour; a CTA takes the next one from the queue and
+// waits until the earlier tasks on both of its sites are done (they were taken
+// before it by running CTAs, so the wait ends), then runs, for end a, the Gram
+// pass of the gram launch (same per-tile arithmetic, summed in FP64 in tile
+// order as the bond launch sums the partials), the bond eigenproblem, and the
+// update pass of the update launch.  So the results equal those of the layered
+// launches bit for bit, and a colour class needs no barrier: its tail overlaps
+// the next class.
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0: wait (bounded) until task d is done; a wait that gives up raises
+// GPEPS_FLAG_TIMEOUT and lets the task run on what it finds.
+__device__ void wait_done(const int* done, int d, int* flags, long long limit) {
+  if (d < 0) return;
+  const long long t0 = clock64();
+  while (ld_acquire(done + d) == 0) {
+    if (clock64() - t0 >= limit) {
+      atomicOr(flags, 4);
+      return;
+    }
+    __nanosleep(256);
+  }
+}
+
+template <typename T>
+__device__ void fused_gram(const SideDesc& sa, const V2<T>* gamma, const double* lam, double th, double2* gsum, int D,
+                           unsigned char* sm) {
+  V2<T>* A = reinterpret_cast<V2<T>*>(sm);  // [nrows][2D+1]
+  const int ld = 2 * D + 1;
+  const int D2 = D * D, nout = 2 * D2;
+  const T c = (T)cos(0.5 * th), s = (T)sin(0.5 * th);
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) gsum[o] = make_double2(0.0, 0.0);
+  const int ntiles = (sa.rows + kTileRows - 1) / kTileRows;
+  for (int tp = 0; tp < ntiles; ++tp) {
+    const int row0 = tp * kTileRows;
+    const int nrows = sa.rows - row0 < kTileRows ? sa.rows - row0 : kTileRows;
+    const int nel = nrows * D;
+    for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+      int r, k;
+      if (sa.str_k == 1) {
+        r = idx / D;
+        k = idx - r * D;
+      } else {
+        k = idx / nrows;
+        r = idx - k * nrows;
+      }
+      const RowPos p = row_pos(sa, row0 + r);
+      const int64_t e = elem(sa, 0, p, k);
+      const T w = (T)row_weight<true>(sa, lam, p);
+      V2<T> a0, a1;
+      kick2<T>(c, s, __ldcg(gamma + e), __ldcg(gamma + e + sa.str_s), a0, a1);
+      A[r * ld + k] = mk<T>(a0.x * w, a0.y * w);
+      A[r * ld + D + k] = mk<T>(a1.x * w, a1.y * w);
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+      const int sidx = o / D2;
+      const int kl = o - sidx * D2;
+      const int k = kl / D;
+      const int l = kl - k * D;
+      const V2<T>* ck = A + sidx * D + k;
+      const V2<T>* cl = A + sidx * D + l;
+      V2<T> acc = mk<T>(0, 0);
+      for (int r = 0; r < nrows; ++r) fma_conj<T>(acc, ck[r * ld], cl[r * ld]);
+      double2 g = gsum[o];
+      g.x += (double)acc.x;
+      g.y += (double)acc.y;
+      gsum[o] = g;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__device__ void fused_update(const SideDesc& sa, V2<T>* gamma, const double* lam, const V2<T>* Y, double th, int D,
+                             unsigned char* sm) {
+  __shared__ double cut[2];
+  const int D2 = D * D;
+  V2<T>* Ys = reinterpret_cast<V2<T>*>(sm);  // [D][D]
+  V2<T>* A = Ys + D2;
+  const size_t a_elems_r = (size_t)kTileRows * (2 * D + 1), a_elems_c = (size_t)(2 * D) * (kTileRows + 1);
+  float* mask = reinterpret_cast<float*>(A + (a_elems_r > a_elems_c ? a_elems_r : a_elems_c));
+  const bool kfast = sa.str_k == 1;
+  if (threadIdx.x < 2) {
+    const int lo = threadIdx.x == 0 ? sa.lam_o1 : sa.lam_o2;
+    double mx = 0.0;
+    if (lo >= 0)
+      for (int k = 0; k < D; ++k) mx = fmax(mx, __ldcg(lam + lo + k));
+    cut[threadIdx.x] = kLambdaCut * mx;
+  }
+  const T c = (T)cos(0.5 * th), s = (T)sin(0.5 * th);
+  const int ntiles = (sa.rows + kTileRows - 1) / kTileRows;
+  for (int tp = 0; tp < ntiles; ++tp) {
+    const int row0 = tp * kTileRows;
+    const int nrows = sa.rows - row0 < kTileRows ? sa.rows - row0 : kTileRows;
+    const int ldr = 2 * D + 1, ldc = nrows + 1;
+    const int nel = nrows * D;
+    for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+      int r, k;
+      if (kfast) {
+        r = idx / D;
+        k = idx - r * D;
+      } else {
+        k = idx / nrows;
+        r = idx - k * nrows;
+      }
+      const RowPos p = row_pos(sa, row0 + r);
+      const int64_t e = elem(sa, 0, p, k);
+      V2<T> a0, a1;
+      kick2<T>(c, s, __ldcg(gamma + e), __ldcg(gamma + e + sa.str_s), a0, a1);
+      if (kfast) {
+        A[r * ldr + k] = a0;
+        A[r * ldr + D + k] = a1;
+      } else {
+        A[k * ldc + r] = a0;
+        A[(D + k) * ldc + r] = a1;
+      }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+      const RowPos p = row_pos(sa, row0 + r);
+      bool ok = true;
+      if (sa.lam_o1 >= 0) ok = ok && __ldcg(lam + sa.lam_o1 + p.r1) > cut[0];
+      if (sa.lam_o2 >= 0) ok = ok && __ldcg(lam + sa.lam_o2 + p.r2) > cut[1];
+      mask[r] = ok ? 1.f : 0.f;
+    }
+    const int nout = nrows * D;
+    for (int sidx = 0; sidx < 2; ++sidx) {
+      for (int o = threadIdx.x; o < D2; o += blockDim.x) Ys[o] = Y[sidx * D2 + o];
+      __syncthreads();
+      for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        int r, kk;
+        if (kfast) {
+          r = o / D;
+          kk = o - r * D;
+        } else {
+          kk = o / nrows;
+          r = o - kk * nrows;
+        }
+        V2<T> acc = mk<T>(0, 0);
+        const V2<T>* Yc = Ys + kk;
+        if (kfast) {
+          const V2<T>* Ar = A + r * ldr + sidx * D;
+          for (int k = 0; k < D; ++k) fma_c<T>(acc, Ar[k], Yc[k * D]);
+        } else {
+          const V2<T>* Ar = A + (sidx * D) * ldc + r;
+          for (int k = 0; k < D; ++k) fma_c<T>(acc, Ar[k * ldc], Yc[k * D]);
+        }
+        const T mk_ = (T)mask[r];
+        const RowPos p = row_pos(sa, row0 + r);
+        gamma[elem(sa, sidx, p, kk)] = mk<T>(acc.x * mk_, acc.y * mk_);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Layout of a fused-step CTA's global slot: the big part of the bond layout at
+// n = 2D, then the FP64 Gram sums [2][D][D], Y [2][D][D] and the kick angle of end a.
+struct StepSlot {
+  size_t off_gsum, off_Y, off_th, total;
+  __host__ __device__ StepSlot(int D, size_t elt) {
+    const BondSmem L(D, 2 * D);
+    off_gsum = (L.big + 255) & ~(size_t)255;
+    off_Y = off_gsum + (size_t)2 * D * D * 16;
+    off_th = off_Y + (size_t)2 * D * D * elt;
+    total = (off_th + 16 + 255) & ~(size_t)255;
+  }
+};
+
+BondFootprint step_footprint(int D, size_t elt) {
+  const BondSmem L(D, 2 * D);
+  size_t sm = L.small + L.f32;
+  const size_t gram = (size_t)kTileRows * (2 * D + 1) * elt;
+  const size_t r = (size_t)kTileRows * (2 * D + 1), c = (size_t)(2 * D) * (kTileRows + 1);
+  const size_t upd = (size_t)D * D * elt + (r > c ? r : c) * elt + (size_t)kTileRows * 4;
+  if (gram > sm) sm = gram;
+  if (upd > sm) sm = upd;
+  return BondFootprint{(sm + 15) & ~(size_t)15, StepSlot(D, elt).total};
+}
+
+template <typename T, int kThr, int kMinB>
+__global__ void __launch_bounds__(kThr, kMinB)
+    step_kernel(const StepTask* __restrict__ tasks, int n_tasks, unsigned int* queue, int* done, V2<T>* gamma,
+                double* lam, double* pending, int* flags, unsigned long long* sweeps_out, unsigned long long* cycles,
+                int D, JacobiParams jp, unsigned char* scratch, size_t slot) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int next;
+  unsigned char* mine = scratch + (size_t)blockIdx.x * slot;
+  const StepSlot SL(D, sizeof(V2<T>));
+  double2* gsum = reinterpret_cast<double2*>(mine + SL.off_gsum);
+  V2<T>* Y = reinterpret_cast<V2<T>*>(mine + SL.off_Y);
+  double* th_a = reinterpret_cast<double*>(mine + SL.off_th);
+  for (;;) {
+    if (threadIdx.x == 0) next = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int ti = next;
+    __syncthreads();
+    if (ti >= n_tasks) break;
+    const BondDesc bd = tasks[ti].bd;
+    if (threadIdx.x == 0) {
+      wait_done(done, tasks[ti].dep_a, flags, jp.wait_cycles);
+      wait_done(done, tasks[ti].dep_b, flags, jp.wait_cycles);
+    }
+    __syncthreads();
+    fused_gram<T>(bd.a, gamma, lam, __ldcg(pending + bd.a.site), gsum, D, smem_raw);
+    bond_body<T, true>(bd, nullptr, gsum, gamma, lam, pending, Y, th_a, flags, sweeps_out, cycles, nullptr, D, jp,
+                       mine);
+    __syncthreads();
+    fused_update<T>(bd.a, gamma, lam, Y, *th_a, D, smem_raw);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(done + ti, 1);
+    }
   }
 }
 
@@ -1196,6 +1452,12 @@ cudaError_t Launch<T>::init() {
   e = cudaFuncSetAttribute(bond_kernel_persistent<T, 128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bond_share_smem(4));
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(step_kernel<T, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bond_share_smem(2));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(step_kernel<T, kBondThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kBondSmemMax);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)update_smem(kMaxD, sizeof(V2<T>)));
 }
@@ -1290,6 +1552,32 @@ cudaError_t Launch<T>::readout(const SiteDesc* sites, int n_sites, const void* g
 cudaError_t launch_mean(const double* z, const int32_t* inst_site0, int n_inst, double* mean, cudaStream_t st) {
   if (n_inst == 0) return cudaSuccess;
   mean_kernel<<<n_inst, kThreads, 0, st>>>(z, inst_site0, mean);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::step(const StepTask* tasks, int n_tasks, unsigned int* queue, int* done, void* gamma,
+                            double* lam, double* pending, int* flags, unsigned long long* sweeps,
+                            unsigned long long* cycles, int D, JacobiParams jp, cudaStream_t st, int n_ctas,
+                            void* scratch, size_t slot, int per_sm) {
+  if (n_tasks == 0) return cudaSuccess;
+  const BondFootprint fp = step_footprint(D, sizeof(V2<T>));
+  if (!scratch || slot < fp.slot || (per_sm != 1 && per_sm != 2)) return cudaErrorInvalidValue;
+  if (fp.smem > (per_sm == 2 ? bond_share_smem(2) : kBondSmemMax)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(done, 0, (size_t)n_tasks * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const int want = per_sm * n_ctas;
+  const int grid = want < n_tasks ? want : n_tasks;
+  unsigned char* sp = static_cast<unsigned char*>(scratch);
+  if (per_sm == 2)
+    step_kernel<T, 256, 2><<<grid, 256, fp.smem, st>>>(tasks, n_tasks, queue, done, static_cast<V2<T>*>(gamma), lam,
+                                                       pending, flags, sweeps, cycles, D, jp, sp, slot);
+  else
+    step_kernel<T, kBondThreads, 1><<<grid, kBondThreads, fp.smem, st>>>(
+        tasks, n_tasks, queue, done, static_cast<V2<T>*>(gamma), lam, pending, flags, sweeps, cycles, D, jp, sp,
+        slot);
   return cudaGetLastError();
 }
 
@@ -1486,7 +1774,7 @@ __global__ void __launch_bounds__(kThreads)
     Cs[o] = cscale(g, lamo[k] * lamo[l]);
     Yb[o] = y;
   }
-  load_F<double>(sb, gamma, lam, 0.0, F, D);
+  load_F<double, false>(sb, gamma, lam, 0.0, F, D);
   // the forward's eigenvectors (sorted by decreasing eigenvalue) and eigenvalues: the
   // output adjoints are expressed in the forward's gauge, so the same V must be used
   {

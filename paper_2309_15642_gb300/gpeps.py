@@ -57,7 +57,7 @@ class GPEPS:
         sb, wb = ctypes.c_size_t(), ctypes.c_size_t()
         check(self.lib.gpeps_query_workspace(self.h, ctypes.byref(sb), ctypes.byref(wb)), "gpeps_query_workspace")
         self.state_bytes, self.work_bytes = sb.value, wb.value
-        self.state = torch.empty(self.state_bytes, dtype=torch.uint8, device=self.device)
+        self.state = torch.zeros(self.state_bytes, dtype=torch.uint8, device=self.device)  # padding defined
         self.work = torch.empty(self.work_bytes, dtype=torch.uint8, device=self.device)
         check(self.lib.gpeps_bind(self.h, ctypes.c_void_p(self.state.data_ptr()),
                                   ctypes.c_void_p(self.work.data_ptr())), "gpeps_bind")
@@ -158,7 +158,8 @@ class GPEPS:
 
     def set_schedule(self, schedule):
         """Bond eigenproblems: 0 one CTA per bond; 1, 2, 3 work queue with one, two or four CTAs
-        per SM (see gpeps_set_schedule)."""
+        per SM; 4 one fused persistent launch per Trotter step in :meth:`step` (see
+        gpeps_set_schedule)."""
         check(self.lib.gpeps_set_schedule(self.h, int(schedule)), "gpeps_set_schedule")
 
     def set_jacobi(self, tol=None, floor_rel=None, tol32=1e-6, floor32=2e-7, max_sweeps=40, max_sweeps32=20):
@@ -169,6 +170,10 @@ class GPEPS:
             floor_rel = 4.4e-16 if self.dtype == "c128" else 1e-8
         check(self.lib.gpeps_set_jacobi(self.h, float(tol), float(floor_rel), float(tol32), float(floor32),
                                         int(max_sweeps), int(max_sweeps32)), "gpeps_set_jacobi")
+
+    def set_wait_limit(self, cycles=20000000000):
+        """Wait limit of the fused step in SM cycles (see gpeps_set_wait_limit)."""
+        check(self.lib.gpeps_set_wait_limit(self.h, int(cycles)), "gpeps_set_wait_limit")
 
     def set_levels(self, level_ratio=1e-5, levels=4):
         """Extra FP32 levels of the bond eigensolver (see gpeps_set_levels)."""

@@ -263,12 +263,13 @@ def test_checkpoint_restore_and_readout_on_gpu_state():
 
 def test_schedules_are_bit_identical():
     """The work-queue schedules (one, two or four CTAs per SM, the latter two with their n x n
-    matrices in global memory) change which SM runs a bond and where its matrices live, not its
-    arithmetic."""
+    matrices in global memory) and the fused step (one persistent launch per Trotter step with
+    per-site dependencies between colour classes) change which SM runs a bond, where its matrices
+    live and when it starts, not its arithmetic."""
     import torch
     from ._gpu_util import gpu_lib
     outs = []
-    for persistent in (0, 1, 2, 3):
+    for persistent in (0, 1, 2, 3, 4):
         g = gpu_lib()([(M127, E127), heavy_hex(*OSPREY)], 8, dtype="mixed")
         g.set_schedule(persistent)
         g.reset()
