@@ -164,7 +164,7 @@ int gpeps_set_levels(gpeps_handle* h, double level_ratio, int32_t levels);
 
 /*
  * Wait limit of the fused step (schedule 4), in SM clock cycles (default
- * 2e10, about 10 s): a bond that waits longer for an earlier bond on one of its
+ * 4e9, about 2 s; a bond update takes at most ~0.2 s at D = 64): a bond that waits longer for an earlier bond on one of its
  * sites gives up, raises GPEPS_FLAG_TIMEOUT and runs on what it finds, so a
  * launch always ends.  0 gives up at once whenever a dependency is still
  * running (failure-detection tests use it).  Host-only; drops a captured step
@@ -186,7 +186,7 @@ int gpeps_set_wait_limit(gpeps_handle* h, int64_t cycles);
  * CTA that takes the bond, bonds are taken colour class by colour class, and a
  * bond waits only until the earlier bonds on its two sites are done, so the
  * classes need no barrier between them (same results; a wait that gives up
- * after ~10 s raises GPEPS_FLAG_TIMEOUT instead of hanging); gpeps_zz_layer
+ * after ~2 s raises GPEPS_FLAG_TIMEOUT instead of hanging); gpeps_zz_layer
  * then uses schedule 2 (or 1 where 2 does not fit).
  * Host-only; drops a captured step graph.  Errors: GPEPS_EINVAL for other
  * values, and for 2, 3 or 4 on an unbound handle, when the FP32 level does not

@@ -156,6 +156,6 @@ constexpr int kMaxSms = 256;          // SMs the shared-SM schedules have scratc
 // global slot (n x n matrices of the bond eigenproblem, FP64 Gram sums, Y and
 // the kick angle of end a).
 BondFootprint step_footprint(int D, size_t elt);
-constexpr long long kWaitCycles = 20000000000LL;  // default wait limit of the fused step (~10 s of SM cycles)
+constexpr long long kWaitCycles = 4000000000LL;  // default wait limit of the fused step (~2 s of SM cycles)
 
 }  // namespace gpeps

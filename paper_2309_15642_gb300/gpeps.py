@@ -171,7 +171,7 @@ class GPEPS:
         check(self.lib.gpeps_set_jacobi(self.h, float(tol), float(floor_rel), float(tol32), float(floor32),
                                         int(max_sweeps), int(max_sweeps32)), "gpeps_set_jacobi")
 
-    def set_wait_limit(self, cycles=20000000000):
+    def set_wait_limit(self, cycles=4000000000):
         """Wait limit of the fused step in SM cycles (see gpeps_set_wait_limit)."""
         check(self.lib.gpeps_set_wait_limit(self.h, int(cycles)), "gpeps_set_wait_limit")
 
