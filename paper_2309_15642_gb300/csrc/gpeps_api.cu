@@ -599,9 +599,11 @@ int gpeps_set_schedule(gpeps_handle* h, int32_t schedule) {
     const BondFootprint fp = step_footprint(h->D, h->elt);
     if (fp.smem > kBondSmemMax || fp.slot > h->bond_slot) return GPEPS_EINVAL;
     if (std::min(step_per_sm(h) * h->n_sms, (int)h->tasks.size()) > h->bond_slots) return GPEPS_EINVAL;
-    if (layered_per_sm(h) == 2 && std::min(2 * h->n_sms, h->max_bonds) > h->bond_slots) return GPEPS_EINVAL;
+    // its layers (gpeps_zz_layer) run two CTAs per SM where they fit
+    const bool pair = bond_footprint_global(h->D).smem <= bond_share_smem(2);
+    if (pair && std::min(2 * h->n_sms, h->max_bonds) > h->bond_slots) return GPEPS_EINVAL;
   }
-  if (schedule >= 2) {
+  if (schedule == 2 || schedule == 3) {
     // k CTAs per SM: shared memory of the FP32 level and a slot per CTA
     const int k = schedule == 3 ? 4 : 2;
     if (!h->bound || bond_footprint_global(h->D).smem > bond_share_smem(k)) return GPEPS_EINVAL;
