@@ -133,6 +133,19 @@ def bond_kernel_flops(w, sweeps64, sweeps32):
     return form + orth + rot + ymat + sweeps64 * sweep, sweeps32 * sweep
 
 
+def big_end_flops(graphs, D):
+    """FP32 flops of the Gram and update passes over the larger ends of one Trotter step: per
+    bond 4 D^2 R complex MACs (8 flops each), R = D^(deg - 1) rows of the larger end."""
+    import numpy as np
+    tot = 0
+    for n, edges in graphs:
+        deg = np.bincount(np.asarray(edges).ravel(), minlength=n)
+        for a, b in edges:
+            rows = D ** (int(max(deg[a], deg[b])) - 1)
+            tot += 4 * D * D * rows * 8
+    return float(tot)
+
+
 def step_bytes(graphs, D, elt):
     """Algorithmic HBM bytes of one Trotter step: every bond reads and writes both site
     tensors once (its larger end twice: Gram and update pass), the readout reads every
@@ -265,11 +278,18 @@ def run_gpeps(args, rank, world, local_rank):
     value = world * bonds_step * K / (ms * 1e-3)
     mean_last = out[K - 1].cpu().numpy().tolist() if K else []
 
-    # per-kernel durations of profiled steps right after the timed region
-    prof = {"gram": [], "bond": [], "update": []}
+    # per-kernel durations of profiled steps right after the timed region, under the schedule
+    # of the timed region (fused: one launch per step; layered: three per colour class)
+    sched = (tuning["chosen"].get("persistent", 0) if tuning else (args.schedule or 0))
+    fused = sched == 4
+    prof = {"gram": [], "bond": [], "update": []} if not fused else {"kick": [], "bond_updates": [], "readout": []}
     s0, q0, b0 = g.sweeps()
     c0 = g.bond_phase_cycles()
     for _ in range(args.profile_steps):
+        if fused:
+            for k, v in zip(("kick", "bond_updates", "readout"), g.step_profiled(th)):
+                prof[k].append(v)
+            continue
         g.kick(th)
         for c in range(g.n_colours):
             t3 = g.zz_layer_profiled(c)
@@ -284,19 +304,28 @@ def run_gpeps(args, rank, world, local_rank):
     sweeps_per_bond = (s1 - s0) / max(b1 - b0, 1)
     sweeps32_per_bond = (q1 - q0) / max(b1 - b0, 1)
     layer_ms = {k: sum(v) / max(args.profile_steps, 1) for k, v in prof.items()}   # per step, all colours
-    bond_launch_ms = sum(prof["bond"]) / max(len(prof["bond"]), 1)
-    bonds_per_launch = bonds_step / g.n_colours
     f64, f32 = bond_kernel_flops(w, sweeps_per_bond, sweeps32_per_bond)
+    if fused:
+        launch_ms = sum(prof["bond_updates"]) / max(len(prof["bond_updates"]), 1)
+        bonds_per_launch = bonds_step
+        f32_big = big_end_flops(graphs, w.D)          # Gram and update passes inside the launch
+        kernel = ("step_kernel (fused step: Gram pass, 2D x 2D bond eigenproblem with FP64 Jacobi and update "
+                  "of every bond of a Trotter step, one launch)")
+    else:
+        launch_ms = sum(prof["bond"]) / max(len(prof["bond"]), 1)
+        bonds_per_launch = bonds_step / g.n_colours
+        f32_big = 0.0
+        kernel = "bond_kernel (2D x 2D bond eigenproblem, FP64 Jacobi)"
     flops_launch = f64 * bonds_per_launch
-    achieved = flops_launch / (bond_launch_ms * 1e-3) / 1e9
-    roofline = {"kernel": "bond_kernel (2D x 2D bond eigenproblem, FP64 Jacobi)", "bound": "alu",
+    achieved = flops_launch / (launch_ms * 1e-3) / 1e9
+    roofline = {"kernel": kernel, "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
                 "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
                 "peak_source": "nominal FP64 1.25 TFLOP/s of the GB300 (no FP64 figure in MEASURED_PEAKS.json)",
                 "fp64_sweeps_per_bond": sweeps_per_bond, "fp32_sweeps_per_bond": sweeps32_per_bond,
-                "fp32_gflops": f32 * bonds_per_launch / (bond_launch_ms * 1e-3) / 1e9,
-                "launch_ms": bond_launch_ms, "cycles_per_bond_by_phase": phase_cycles,
-                "per_step_ms": layer_ms}
+                "fp32_gflops": (f32 * bonds_per_launch + f32_big * (1 if fused else 0)) / (launch_ms * 1e-3) / 1e9,
+                "launch_ms": launch_ms, "units_per_launch": bonds_per_launch, "schedule": sched,
+                "cycles_per_bond_by_phase": phase_cycles, "per_step_ms": layer_ms}
     elt = 8 if args.dtype == "mixed" else 16
     sb = step_bytes(graphs, w.D, elt)
     hbm = {"algorithmic_bytes_per_step": sb, "achieved_gbs_whole_step": sb / (ms / K * 1e-3) / 1e9}
@@ -329,7 +358,11 @@ def run_gpeps(args, rank, world, local_rank):
                  "parity": golden_parity(w, outp.cpu().numpy(), Wp, Kp)}
         gp.close()
     parity = golden_parity(w, out.cpu().numpy(), W, K)
+    # kernels of ours per timed step: kick, the bond updates (one fused launch, or Gram + bond +
+    # update per colour class), readout, mean
+    launches_per_step = 1 + (1 if fused else 3 * g.n_colours) + 2
     return dict(value=value, ms=ms, bonds_step=bonds_step, clocks=clocks, flags=flags, roofline=roofline,
+                launches_per_step=launches_per_step,
                 e2e=e2e, plain=plain, hbm=hbm, mean_last=mean_last, w=w, tuning=tuning, parity=parity)
 
 
@@ -396,7 +429,7 @@ def main():
             "roofline": r["roofline"], "hbm": r["hbm"], "clocks": r["clocks"], "e2e": r["e2e"],
             "plain_c128": r["plain"], "cpu_baseline": cpu, "parity": r["parity"],
             "tuning": (r["tuning"] or {}).get("chosen"),
-            "gpu_launches": (1 + 3 * 3 + 2) * args.steps, "device_flags": r["flags"],
+            "gpu_launches": r["launches_per_step"] * args.steps, "device_flags": r["flags"],
             "mean_z_last_step": r["mean_last"],
         }
         print(json.dumps(line))

@@ -139,6 +139,16 @@ int gpeps_zz_layer(gpeps_handle* h, int32_t colour);
 int gpeps_zz_layer_profiled(gpeps_handle* h, int32_t colour, float* ms);
 
 /*
+ * One Trotter step as gpeps_step runs it under the current schedule, launched
+ * directly (no graph) with CUDA events around its parts: ms (host float[3])
+ * receives [0] the kick, [1] the bond updates of every colour class (the fused
+ * launch of schedule 4, or the Gram, bond and update launches of each class),
+ * [2] the readout and mean.  Synchronises the stream.  Errors: GPEPS_EINVAL for
+ * a NULL pointer or an unbound handle.
+ */
+int gpeps_step_profiled(gpeps_handle* h, const double* theta, int32_t per_qubit, float* ms);
+
+/*
  * Thresholds of the bond eigensolver (defaults in parentheses): FP64 sweeps
  * stop rotating a pair when |a_pq| <= max(tol sqrt(a_pp a_qq), floor_rel *
  * trace) (complex128: 1e-15, 4.4e-16; mixed: 1e-9, 1e-8); the FP32 levels use tol32

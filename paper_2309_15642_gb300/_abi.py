@@ -20,6 +20,7 @@ SIGNATURES = {
     "gpeps_kick": (c_int, [c_void_p, c_void_p, c_int32]),
     "gpeps_zz_layer": (c_int, [c_void_p, c_int32]),
     "gpeps_zz_layer_profiled": (c_int, [c_void_p, c_int32, POINTER(ctypes.c_float)]),
+    "gpeps_step_profiled": (c_int, [c_void_p, c_void_p, c_int32, POINTER(ctypes.c_float)]),
     "gpeps_set_jacobi": (c_int, [c_void_p, c_double, c_double, c_double, c_double, c_int32, c_int32]),
     "gpeps_set_levels": (c_int, [c_void_p, c_double, c_int32]),
     "gpeps_set_wait_limit": (c_int, [c_void_p, c_int64]),

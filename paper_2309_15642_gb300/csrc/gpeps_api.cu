@@ -591,6 +591,34 @@ int gpeps_zz_layer_profiled(gpeps_handle* h, int32_t colour, float* ms) {
   return GPEPS_OK;
 }
 
+int gpeps_step_profiled(gpeps_handle* h, const double* theta, int32_t per_qubit, float* ms) {
+  if (!h || !h->bound || !theta || !ms) return GPEPS_EINVAL;
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) GP_CUDA(cudaEventCreate(&ev[i]));
+  auto body = [&]() -> int {
+    GP_CUDA(cudaEventRecord(ev[0], h->stream));
+    int st = kick_impl(h, theta, per_qubit ? 1 : 0);
+    if (st) return st;
+    GP_CUDA(cudaEventRecord(ev[1], h->stream));
+    if (h->schedule == 4) {
+      st = h->dtype == GPEPS_C128 ? fused_step_impl<double>(h) : fused_step_impl<float>(h);
+    } else {
+      for (int c = 0; c < (int)h->colours.size() && !st; ++c) st = layer(h, c);
+    }
+    if (st) return st;
+    GP_CUDA(cudaEventRecord(ev[2], h->stream));
+    st = readout_impl(h);
+    if (st) return st;
+    GP_CUDA(cudaEventRecord(ev[3], h->stream));
+    GP_CUDA(cudaEventSynchronize(ev[3]));
+    for (int i = 0; i < 3; ++i) GP_CUDA(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
+    return GPEPS_OK;
+  };
+  const int st = body();
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  return st;
+}
+
 int gpeps_set_schedule(gpeps_handle* h, int32_t schedule) {
   if (!h || schedule < 0 || schedule > 4) return GPEPS_EINVAL;
   if (schedule == 4) {

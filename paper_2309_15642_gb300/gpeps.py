@@ -107,6 +107,16 @@ class GPEPS:
         check(self.lib.gpeps_zz_layer_profiled(self.h, int(colour), ms), "gpeps_zz_layer_profiled")
         return [float(x) for x in ms]
 
+    def step_profiled(self, theta, per_qubit=False):
+        """One Trotter step under the current schedule, launched directly with events around its
+        parts; returns ms[3] (kick, bond updates of every colour class, readout and mean)."""
+        t = self._theta(theta, per_qubit)
+        self._after_torch()
+        ms = (ctypes.c_float * 3)()
+        check(self.lib.gpeps_step_profiled(self.h, ctypes.c_void_p(t.data_ptr()), int(bool(per_qubit)), ms),
+              "gpeps_step_profiled")
+        return [float(x) for x in ms]
+
     def expect_z(self):
         """Return ``(z[total_qubits], mean[n_instances])`` as float64 CUDA tensors."""
         z = torch.empty(self.total_qubits, dtype=torch.float64, device=self.device)
