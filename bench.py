@@ -113,6 +113,11 @@ class Clocks:
                 "power_w_max": max(power) if power else None}
 
 
+# DRAM bytes per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by workload, dtype and schedule; reported as the roofline's
+# `traffic` only for that configuration (profiles/step_kernel_heavyhex_mix_d32.md)
+NCU_TRAFFIC = {("heavyhex_mix_d32", "mixed", 4): 2.038412e9 + 1.615236e9}
+
 # ------------------------------------------------------------------ algorithmic counts
 def bond_kernel_flops(w, sweeps64, sweeps32):
     """(FP64, FP32) flops of the bond-eigenproblem launch per bond, n = 2D (8 flops per
@@ -320,7 +325,8 @@ def run_gpeps(args, rank, world, local_rank):
     achieved = flops_launch / (launch_ms * 1e-3) / 1e9
     roofline = {"kernel": kernel, "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
-                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_GFLOPS,
+                "traffic": NCU_TRAFFIC.get((w.name, args.dtype, sched)),
                 "peak_source": "nominal FP64 1.25 TFLOP/s of the GB300 (no FP64 figure in MEASURED_PEAKS.json)",
                 "fp64_sweeps_per_bond": sweeps_per_bond, "fp32_sweeps_per_bond": sweeps32_per_bond,
                 "fp32_gflops": (f32 * bonds_per_launch + f32_big * (1 if fused else 0)) / (launch_ms * 1e-3) / 1e9,
