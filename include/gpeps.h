@@ -217,6 +217,21 @@ int gpeps_n_colours(const gpeps_handle* h, int32_t* n_colours);
 int gpeps_expect_z(gpeps_handle* h, double* d_z, double* d_mean);
 
 /*
+ * n_steps inverse Trotter steps U^dagger(theta)^n (App. B): since
+ * U(theta) = ZZ K(theta) (Eq. 2), one inverse step applies every colour class
+ * with the conjugate gate exp(-i pi/4 Z Z), in the reverse order of a forward
+ * step, and then the kick exp(+i theta X / 2) (pending, like gpeps_kick).
+ * With theta = pi/2 after n forward steps this gives the state
+ * |omega(theta_h, n)> = U^dagger(pi/2)^n |psi(theta_h, n)> whose single-site
+ * <Z_P> (gpeps_expect_z) is the Weight-N observable <U^n(pi/2) Z_P
+ * U^dagger(pi/2)^n> of App. B (e.g. P = 13 gives Weight 10 on the 127-qubit
+ * lattice).  theta: device, as in gpeps_kick.  Launched directly on the stream
+ * (no graph).  Errors: GPEPS_EINVAL for a NULL pointer, an unbound handle or
+ * n_steps < 0.
+ */
+int gpeps_inverse_steps(gpeps_handle* h, int32_t n_steps, const double* theta, int32_t per_qubit);
+
+/*
  * n_steps Trotter steps U(theta) of Eq. 2: kick with theta (device, as in
  * gpeps_kick), then every colour class in increasing order, then the mean
  * <Z> of every instance into d_mean_per_step[t * n_instances + k] (device

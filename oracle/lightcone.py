@@ -12,7 +12,7 @@ import numpy as np
 
 from workloads.heavyhex import graph_ball, induced_subgraph
 
-from .statevector import kicked_ising_states
+from .statevector import back_evolved_z_cancelled, kicked_ising_states
 
 
 def lightcone_z(n_qubits, edges, theta, q, n):
@@ -29,3 +29,19 @@ def lightcone_z(n_qubits, edges, theta, q, n):
     p = np.abs(psi) ** 2
     pq = np.ascontiguousarray(np.moveaxis(p, k, 0)).reshape(2, -1).sum(axis=1)
     return float((pq[0] - pq[1]) / (pq[0] + pq[1]))
+
+
+def lightcone_weight_z(n_qubits, edges, theta, q, n):
+    """Exact <Z_q> of |omega(theta, n)> = U^dagger(pi/2)^n |psi(theta, n)> (App. B).
+
+    The last forward and the first inverse ZZ layer cancel, leaving 2n - 2 ZZ
+    layers and a kick last, so U-conjugation of Z_q reaches the ball of radius
+    2n - 2 around q and no further; the circuit on that ball with its induced
+    edges gives the value exactly."""
+    if n == 0:
+        return 1.0
+    ball = graph_ball(n_qubits, edges, q, max(2 * n - 2, 0))
+    m, sub, verts = induced_subgraph(edges, ball)
+    th = np.broadcast_to(np.asarray(theta, dtype=np.float64), (n_qubits,))[verts]
+    z = back_evolved_z_cancelled(m, sub, th, n)
+    return float(z[verts.index(int(q))])

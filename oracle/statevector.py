@@ -79,6 +79,46 @@ def dense_unitary(m, edges, theta, zz_sign=+1.0):
     return np.diag(np.exp(zz_sign * 1j * math.pi / 4.0 * diag)) @ K
 
 
+def _kick_all(psi, theta):
+    m = psi.ndim
+    th = np.broadcast_to(np.asarray(theta, dtype=np.float64), (m,))
+    for q in range(m):
+        psi = np.moveaxis(np.tensordot(_rx(th[q]), psi, axes=(1, q)), 0, q)
+    return psi
+
+
+def back_evolved_z(m, edges, theta_h, n):
+    """<Z_q> of |omega> = U^dagger(pi/2)^n U(theta_h)^n |0> (App. B), built literally: n forward
+    steps, then n inverse steps (the ZZ layer with the opposite phase, then the kick by -pi/2)."""
+    psi = None
+    for psi in kicked_ising_states(m, edges, theta_h, n):
+        pass
+    if psi is None:
+        psi = np.zeros((2,) * m, dtype=np.complex128)
+        psi[(0,) * m] = 1.0
+    inv_phase = _zz_diagonal(m, edges, -1.0)
+    for _ in range(n):
+        psi = _kick_all(psi * inv_phase, -math.pi / 2)
+    return z_expectations(psi)
+
+
+def back_evolved_z_cancelled(m, edges, theta_h, n):
+    """The same state built from U^dagger(pi/2) U(theta_h) = K(theta_h - pi/2) (the ZZ layers of
+    the last forward and first inverse step cancel): U^dagger(pi/2)^(n-1) K(theta_h - pi/2)
+    U(theta_h)^(n-1) |0>.  ``theta_h`` scalar or per qubit."""
+    psi = np.zeros((2,) * m, dtype=np.complex128)
+    psi[(0,) * m] = 1.0
+    if n >= 2:
+        for psi in kicked_ising_states(m, edges, theta_h, n - 1):
+            pass
+    th = np.broadcast_to(np.asarray(theta_h, dtype=np.float64), (m,))
+    psi = _kick_all(psi, th - math.pi / 2)
+    inv_phase = _zz_diagonal(m, edges, -1.0)
+    for _ in range(n - 1):
+        psi = _kick_all(psi * inv_phase, -math.pi / 2)
+    return z_expectations(psi)
+
+
 def schmidt_values(psi, part_a):
     """Schmidt coefficients of the state tensor across (part_a | rest), sorted descending."""
     m = psi.ndim

@@ -272,13 +272,13 @@ int layer(gpeps_handle* h, int c, PhaseEvents* pe = nullptr, void* vsave = nullp
   return h->dtype == GPEPS_C128 ? layer_impl<double>(h, c, pe, vsave) : layer_impl<float>(h, c, pe, vsave);
 }
 
-int kick_impl(gpeps_handle* h, const double* theta, int per_qubit) {
+int kick_impl(gpeps_handle* h, const double* theta, int per_qubit, double scale = 1.0) {
   const int n = (int)h->total_sites;
   cudaError_t e = h->dtype == GPEPS_C128
                       ? Launch<double>::kick(h->pending(), theta, h->at<int32_t>(h->w_site_inst), n, per_qubit,
-                                             h->stream)
+                                             h->stream, scale)
                       : Launch<float>::kick(h->pending(), theta, h->at<int32_t>(h->w_site_inst), n, per_qubit,
-                                            h->stream);
+                                            h->stream, scale);
   if (e != cudaSuccess) return cuda_fail(e, "kick");
   return GPEPS_OK;
 }
@@ -460,6 +460,7 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   h->jp.level_ratio = 1e-5;
   h->jp.levels = 4;
   h->jp.wait_cycles = kWaitCycles;
+  h->jp.gate_sign = 1;
   // layouts
   size_t s = 0;
   h->s_lam = s;
@@ -657,6 +658,22 @@ int gpeps_expect_z(gpeps_handle* h, double* d_z, double* d_mean) {
   if (d_mean)
     GP_CUDA(cudaMemcpyAsync(d_mean, h->mean(), h->n_inst * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   return GPEPS_OK;
+}
+
+int gpeps_inverse_steps(gpeps_handle* h, int32_t n_steps, const double* theta, int32_t per_qubit) {
+  if (!h || !h->bound || !theta || n_steps < 0) return GPEPS_EINVAL;
+  // U(theta) = ZZ K(theta), so U^dagger(theta) = K(-theta) ZZ^dagger: the colour
+  // classes with the conjugate gate, in the reverse order of a forward step,
+  // then the kick by -theta (pending, fused into the next bond or the readout)
+  const int saved = h->jp.gate_sign;
+  h->jp.gate_sign = -1;
+  int st = GPEPS_OK;
+  for (int t = 0; t < n_steps && !st; ++t) {
+    for (int c = (int)h->colours.size() - 1; c >= 0 && !st; --c) st = layer(h, c);
+    if (!st) st = kick_impl(h, theta, per_qubit ? 1 : 0, -1.0);
+  }
+  h->jp.gate_sign = saved;
+  return st;
 }
 
 int gpeps_step(gpeps_handle* h, int32_t n_steps, const double* theta, int32_t per_qubit,

@@ -85,6 +85,7 @@ struct JacobiParams {
   double level_ratio;  // an extra FP32 level takes the diagonals below this fraction of their block's scale
   int levels;          // extra FP32 levels at most (0..kMaxExtraLevels)
   long long wait_cycles;  // fused step: a wait for an earlier task gives up after this many SM cycles
+  int gate_sign;          // +1: the paper's exp(+i pi/4 Z Z); -1: its inverse exp(-i pi/4 Z Z)
 };
 
 // Launchers (su_kernels.cu).  T = float for GPEPS_MIXED_C64, double for GPEPS_C128.
@@ -93,8 +94,9 @@ struct Launch {
   static cudaError_t init();
   static cudaError_t reset(void* gamma, double* lam, int64_t n_gamma, int64_t n_lam_edges, int D,
                            const int64_t* d_site_off, int n_sites, double* pending, cudaStream_t st);
+  // pending[i] += scale * theta (scale = -1: the inverse kick exp(+i theta X / 2))
   static cudaError_t kick(double* pending, const double* theta, const int32_t* site_inst, int n_sites,
-                          int per_qubit, cudaStream_t st);
+                          int per_qubit, cudaStream_t st, double scale = 1.0);
   static cudaError_t gram(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, const void* gamma,
                           const double* lam, const double* pending, void* partials, int D, cudaStream_t st);
   static cudaError_t bond(const BondDesc* bonds, int n_bonds, const void* partials, void* gamma, double* lam,

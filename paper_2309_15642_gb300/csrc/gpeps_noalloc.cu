@@ -189,6 +189,7 @@ extern "C" int gpeps_bond_update_noalloc(int32_t D, int32_t dtype, void* gamma_a
   jp.level_ratio = 1e-5;
   jp.levels = 4;
   jp.wait_cycles = kWaitCycles;
+  jp.gate_sign = 1;
   void* base = reinterpret_cast<void*>(pbig);
   st = dtype == GPEPS_C128 ? run<double>(scratch, D, base, bd, bd.n_parts, lam, jp, cs)
                            : run<float>(scratch, D, base, bd, bd.n_parts, lam, jp, cs);

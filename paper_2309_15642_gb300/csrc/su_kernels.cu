@@ -120,9 +120,9 @@ __global__ void reset_kernel(V2<T>* gamma, double* lam, const int64_t* site_off,
 }
 
 __global__ void kick_kernel(double* pending, const double* theta, const int32_t* site_inst, int n_sites,
-                            int per_qubit) {
+                            int per_qubit, double scale) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n_sites) pending[i] += per_qubit ? theta[i] : theta[site_inst[i]];
+  if (i < n_sites) pending[i] += scale * (per_qubit ? theta[i] : theta[site_inst[i]]);
 }
 
 // ---------------------------------------------------------------- Gram partials
@@ -872,7 +872,7 @@ __device__ void bond_body(const BondDesc bd, const V2<T>* __restrict__ partials,
       double2 v;
       if (tx == ty) {
         v = make_double2((double)acc.x, (double)acc.y);
-      } else if (sidx == ty) {  // +i
+      } else if ((sidx == ty) == (jp.gate_sign > 0)) {  // +i (the conjugate gate swaps +i and -i)
         v = make_double2(-(double)acc.y, (double)acc.x);
       } else {  // -i
         v = make_double2((double)acc.y, -(double)acc.x);
@@ -957,7 +957,7 @@ __device__ void bond_body(const BondDesc bd, const V2<T>* __restrict__ partials,
       const int col = order[kk];
       for (int x = 0; x < n; ++x) {
         const V2<T> fv = F[x * D + k];
-        const V2<T> g = mk<T>(r2, (sidx == (x & 1)) ? r2 : -r2);
+        const V2<T> g = mk<T>(r2, ((sidx == (x & 1)) == (jp.gate_sign > 0)) ? r2 : -r2);
         const double2 vd = Vm[x * n + col];
         fma_c<T>(acc, c_mul<T>(fv, g), mk<T>((T)vd.x, (T)vd.y));
       }
@@ -1478,9 +1478,9 @@ cudaError_t Launch<T>::reset(void* gamma, double* lam, int64_t n_gamma, int64_t 
 
 template <typename T>
 cudaError_t Launch<T>::kick(double* pending, const double* theta, const int32_t* site_inst, int n_sites,
-                            int per_qubit, cudaStream_t st) {
+                            int per_qubit, cudaStream_t st, double scale) {
   if (n_sites == 0) return cudaSuccess;
-  kick_kernel<<<(n_sites + 255) / 256, 256, 0, st>>>(pending, theta, site_inst, n_sites, per_qubit);
+  kick_kernel<<<(n_sites + 255) / 256, 256, 0, st>>>(pending, theta, site_inst, n_sites, per_qubit, scale);
   return cudaGetLastError();
 }
 

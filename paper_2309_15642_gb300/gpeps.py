@@ -7,6 +7,7 @@ orders the library's stream against torch's current stream.
 from __future__ import annotations
 
 import ctypes
+import math
 
 import numpy as np
 import torch
@@ -138,6 +139,27 @@ class GPEPS:
         self._before_torch()
         self._last_theta = t  # the captured graph reads this buffer
         return out
+
+    def inverse_steps(self, n_steps, theta, per_qubit=False):
+        """Apply U^dagger(theta)^n_steps (App. B: colour classes in reverse order with the conjugate
+        gate, then the kick by -theta); see gpeps_inverse_steps."""
+        t = self._theta(theta, per_qubit)
+        self._after_torch()
+        check(self.lib.gpeps_inverse_steps(self.h, int(n_steps), ctypes.c_void_p(t.data_ptr()),
+                                           int(bool(per_qubit))), "gpeps_inverse_steps")
+        t.record_stream(self.stream)
+
+    def weight_z(self, theta_h, n_steps, per_qubit=False):
+        """Weight-N observables by Clifford back-evolution (App. B): from |0...0>, n_steps Trotter
+        steps at theta_h, then n_steps inverse steps at pi/2; returns <Z_i> of that state for every
+        qubit (float64 tensor), i.e. <U^n(pi/2) Z_i U^dagger(pi/2)^n> in |psi(theta_h, n)>.  Qubit
+        P = 13 of the 127-qubit lattice gives the Weight-10 operator of App. B."""
+        self.reset()
+        self.step(n_steps, theta_h, per_qubit=per_qubit)
+        half_pi = torch.full_like(self._theta(theta_h, per_qubit), math.pi / 2)
+        self.inverse_steps(n_steps, half_pi, per_qubit=per_qubit)
+        z, _ = self.expect_z()
+        return z
 
     def status(self):
         f = ctypes.c_int32()
