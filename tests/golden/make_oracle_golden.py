@@ -3,12 +3,13 @@
     python tests/golden/make_oracle_golden.py eagle_sweep16_d16
     python tests/golden/make_oracle_golden.py heavyhex_mix_d32
     python tests/golden/make_oracle_golden.py eagle_d64
+    python tests/golden/make_oracle_golden.py infinite_sweep16_d32
 
 Each run writes ``tests/golden/oracle_<workload>.json``: the mean <Z> of every
 instance after every Trotter step, the per-qubit <Z> after a few sampled steps
 and the sorted lambda spectra of a few sampled edges.  The oracle is the plain
-FP64 simple update of ``oracle/su.py`` (greedy colouring, same inputs as the
-GPU tests from ``workloads``).
+FP64 simple update of ``oracle/su.py`` (the workload's colouring: greedy, or the
+unit cell's periodic one; same inputs as the GPU tests from ``workloads``).
 """
 from __future__ import annotations
 
@@ -26,7 +27,7 @@ from oracle.su import GPEPS  # noqa: E402
 from workloads import kick_angles, workload  # noqa: E402
 
 SAMPLE_STEPS = {"eagle_sweep16_d16": [1, 4, 5, 10, 20], "heavyhex_mix_d32": [1, 5, 6, 10, 25, 50],
-                "eagle_d64": [1, 5, 6, 7, 8]}
+                "eagle_d64": [1, 5, 6, 7, 8], "infinite_sweep16_d32": [1, 3, 5]}
 
 
 def sampled_edges(n_edges, k=8):
@@ -40,8 +41,8 @@ def run(name, steps=None):
     sample = [s for s in SAMPLE_STEPS.get(name, [steps]) if s <= steps]
     out = {"workload": name, "D": w.D, "steps": steps, "instances": []}
     t0 = time.time()
-    for k, ((n, edges), th) in enumerate(zip(w.graphs(), thetas)):
-        peps = GPEPS(n, edges, w.D)
+    for k, ((n, edges), th, col) in enumerate(zip(w.graphs(), thetas, w.colours())):
+        peps = GPEPS(n, edges, w.D, colour=col)
         inst = {"n_qubits": int(n), "theta": float(th[0]) if w.per_qubit_seed is None else None,
                 "mean_z": [], "z": {}, "lambda": {}}
         ed = sampled_edges(len(edges))

@@ -12,7 +12,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .heavyhex import CONDOR, EAGLE, OSPREY, heavy_hex
+from .heavyhex import CELL, CONDOR, EAGLE, OSPREY, heavy_hex, heavy_hex_cell, heavy_hex_cell_colour
 
 
 @dataclass(frozen=True)
@@ -31,9 +31,14 @@ class Workload:
         out = []
         for lat in self.lattices:
             if lat not in cache:
-                cache[lat] = heavy_hex(*lat)
+                cache[lat] = heavy_hex_cell() if lat == CELL else heavy_hex(*lat)
             out.append(cache[lat])
         return out
+
+    def colours(self):
+        """Per instance: the edge colour classes to use (the unit cell's periodic colouring), or
+        None for the greedy colouring of the library and the oracle."""
+        return [heavy_hex_cell_colour() if lat == CELL else None for lat in self.lattices]
 
     @property
     def n_instances(self):
@@ -66,6 +71,11 @@ WORKLOADS = {
                                note="127 q, D=16, 20 steps, theta_i ~ U[0.5, 0.9] seeded 15642"),
     "condor_d64": Workload("condor_d64", (CONDOR,), 64, 100, (0.8,),
                            note="1121 q, D=64, 100 steps, theta=0.8"),
+    "infinite_sweep16_d32": Workload(
+        "infinite_sweep16_d32", (CELL,) * 16, 32, 5,
+        tuple(float(t) for t in np.linspace(0.0, math.pi / 2, 16)),
+        note="infinite heavy-hex lattice (10-site unit cell, periodic couplers) x 16 instances, "
+             "theta evenly spaced in [0, pi/2], D=32, 5 steps"),
     "eagle_d64": Workload("eagle_d64", (EAGLE,), 64, 8, (0.8,),
                           note="127 q, D=64, 8 steps, theta=0.8: the 128 x 128 bond eigenproblems of "
                                "condor_d64 on a lattice the oracle finishes in minutes (truncation from step 7)"),

@@ -30,6 +30,7 @@ import numpy as np
 EAGLE = (7, 15)
 OSPREY = (13, 27)
 CONDOR = (21, 43)
+CELL = "cell"      # the infinite lattice as its 10-site unit cell (heavy_hex_cell)
 LATTICES = {127: EAGLE, 433: OSPREY, 1121: CONDOR}
 
 
@@ -72,6 +73,69 @@ def heavy_hex(rows: int, width: int):
             edges.append((b, row_label[r + 1][c]))
     e = np.array(sorted((min(a, b), max(a, b)) for a, b in edges), dtype=np.int32)
     return label, e
+
+
+def heavy_hex_coords(rows: int, width: int):
+    """Per label of ``heavy_hex(rows, width)``: ``("row", r, c)`` for the qubit of row r in column
+    c, ``("bridge", r, c)`` for the bridge of layer r (between rows r and r+1) in column c."""
+    out = []
+    for r in range(rows):
+        lo = 1 if r == rows - 1 else 0
+        hi = width - 2 if r == 0 else width - 1
+        out += [("row", r, c) for c in range(lo, hi + 1)]
+        if r < rows - 1:
+            out += [("bridge", r, c) for c in range(0 if r % 2 == 0 else 2, width, 4)]
+    return out
+
+
+# The infinite lattice of the same rule repeats every 4 columns and every 2 rows (the
+# bridge offsets alternate 0, 2 between successive row pairs): a unit cell of 8 row qubits
+# and 2 bridges, the 10-site cell of the paper's infinite-lattice simulations ("Method").
+CELL_COORDS = ([("row", 0, c) for c in range(4)] + [("bridge", 0, 0)]
+               + [("row", 1, c) for c in range(4)] + [("bridge", 1, 2)])
+
+
+def heavy_hex_cell():
+    """The infinite heavy-hex lattice as its translation-invariant 10-site unit cell with
+    periodic couplers (a 10-vertex, 12-edge graph on a torus).
+
+    Labels left to right, top to bottom (``CELL_COORDS``): row 0 = 0..3, the bridge of layer 0
+    (column 0, between rows 0 and 1) = 4, row 1 = 5..8, the bridge of layer 1 (column 2, between
+    row 1 and row 0 of the next cell down) = 9.  Rows close on themselves after 4 columns.  The
+    simple update of a translation-invariant state on the infinite lattice updates each coupler
+    class of this cell once per colour, so it is the simple update of this graph.
+    Returns ``(10, edges)`` like :func:`heavy_hex`."""
+    e = [(0, 1), (1, 2), (2, 3), (3, 0), (5, 6), (6, 7), (7, 8), (8, 5),
+         (0, 4), (4, 5), (7, 9), (9, 2)]
+    return 10, np.array(sorted((min(a, b), max(a, b)) for a, b in e), dtype=np.int32)
+
+
+# Colour class of each coupler of heavy_hex_cell() (in its sorted edge order): the pattern that
+# the greedy colouring of the finite lattices (edges sorted by label, first fit) takes in their
+# interior, which repeats with the cell's period, so the infinite lattice is updated in the same
+# order as the bulk of the finite ones.  The greedy rule applied to the 12 cell edges themselves
+# would need a fourth colour.
+CELL_COLOUR = {(0, 1): 1, (0, 3): 0, (0, 4): 2, (1, 2): 2, (2, 3): 1, (2, 9): 0,
+               (4, 5): 0, (5, 6): 1, (5, 8): 2, (6, 7): 0, (7, 8): 1, (7, 9): 2}
+
+
+def heavy_hex_cell_colour():
+    """int array of the colour class of every edge of heavy_hex_cell(), in its edge order."""
+    _, e = heavy_hex_cell()
+    return np.array([CELL_COLOUR[(int(a), int(b))] for a, b in e], dtype=np.int64)
+
+
+def equivalent_site(rows: int, width: int, cell_site: int, row_near: int, col_near: int):
+    """A label of ``heavy_hex(rows, width)`` occupying the place of cell site ``cell_site`` (same
+    kind, row parity and column modulo 4), near (row_near, col_near)."""
+    kind, r0, c0 = CELL_COORDS[cell_site]
+    best = None
+    for lab, (k, r, c) in enumerate(heavy_hex_coords(rows, width)):
+        if k == kind and r % 2 == r0 % 2 and c % 4 == c0:
+            d = abs(r - row_near) + abs(c - col_near)
+            if best is None or d < best[0]:
+                best = (d, lab)
+    return best[1]
 
 
 def induced_subgraph(edges, vertices):
