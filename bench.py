@@ -119,23 +119,30 @@ class Clocks:
 NCU_TRAFFIC = {("heavyhex_mix_d32", "mixed", 4): 2.038412e9 + 1.615236e9}
 
 # ------------------------------------------------------------------ algorithmic counts
-def bond_kernel_flops(w, sweeps64, sweeps32):
-    """(FP64, FP32) flops of the bond-eigenproblem launch per bond, n = 2D (8 flops per
-    complex MAC): rho formation 2 (n D^2 + n(n+1)/2 D) MACs; Cholesky-QR of the FP32
-    eigenvectors n^3/2 + n^3/6 + n^3/2 MACs; rho' = V^dagger rho V 3 n^3/2 MACs; Y matrices
-    2 D^2 n MACs; a Jacobi sweep is (n-1) rounds of n/2 (n/2+1)/2 two-sided 2x2 block
-    rotations (72 flops) and n^2/2 eigenvector rotations (18 flops), counted for every
-    pair (an upper bound: converged pairs are skipped)."""
-    D = w.D
-    n = 2 * D
-    m = n // 2
-    mac = 8
-    form = 2 * (n * D * D + n * (n + 1) // 2 * D) * mac
-    orth = (n ** 3 // 2 + n ** 3 // 6 + n ** 3 // 2) * mac
-    rot = (3 * n ** 3 // 2) * mac
-    ymat = 2 * D * D * n * mac
-    sweep = (n - 1) * (m * (m + 1) // 2 * 72 + n * m * 18)
-    return form + orth + rot + ymat + sweeps64 * sweep, sweeps32 * sweep
+def bond_fixed_flops(graphs, D, dtype):
+    """(FP64, FP32) flops of one Trotter step's bond eigenproblems that do not depend on how the
+    Jacobi sweeps converge, per bond with its own n = 2 D^(deg - 1) (deg of the smaller end;
+    8 flops per complex MAC): re-orthonormalisation of the FP32 eigenvectors 4 n^3 / 3 MACs and
+    rho' = V^dagger rho V 3 n^3 / 2 MACs in FP64; the rho formation 2 (n D^2 + n(n+1)/2 D) MACs
+    and the Y matrices 2 D^2 n MACs in the storage precision (FP64 for complex128, FP32 for the
+    mixed path).  The extra FP32 levels' FP64 row and column updates are not counted."""
+    import numpy as np
+    f64 = f32 = 0.0
+    for n_q, edges in graphs:
+        deg = np.bincount(np.asarray(edges).ravel(), minlength=n_q)
+        for a, b in edges:
+            n = 2 * D ** (int(min(deg[a], deg[b])) - 1)
+            f64 += (4.0 * n ** 3 / 3.0 + 1.5 * n ** 3) * 8
+            prod = (2 * (n * D * D + n * (n + 1) / 2 * D) + 2 * D * D * n) * 8
+            if dtype == "c128":
+                f64 += prod
+            else:
+                f32 += prod
+    return f64, f32
+
+
+# flops of one executed Jacobi 2x2 block update (both sides) and one eigenvector pair update
+JACOBI_BLOCK_FLOPS, JACOBI_VEC_FLOPS = 72, 18
 
 
 def big_end_flops(graphs, D):
@@ -290,6 +297,7 @@ def run_gpeps(args, rank, world, local_rank):
     prof = {"gram": [], "bond": [], "update": []} if not fused else {"kick": [], "bond_updates": [], "readout": []}
     s0, q0, b0 = g.sweeps()
     c0 = g.bond_phase_cycles()
+    w0 = g.jacobi_work()
     for _ in range(args.profile_steps):
         if fused:
             for k, v in zip(("kick", "bond_updates", "readout"), g.step_profiled(th)):
@@ -303,25 +311,33 @@ def run_gpeps(args, rank, world, local_rank):
         g.expect_z()
     s1, q1, b1 = g.sweeps()
     c1 = g.bond_phase_cycles()
+    w1 = g.jacobi_work()
+    work_step = [(b - a) / max(args.profile_steps, 1) for a, b in zip(w0, w1)]
     phase_names = ["rho", "fp32_jacobi", "fp64_orthonormalise", "rotate_and_fp32_levels", "fp64_jacobi",
                    "epilogue"]
     phase_cycles = {k: (b - a) / max(b1 - b0, 1) for k, a, b in zip(phase_names, c0, c1)}
     sweeps_per_bond = (s1 - s0) / max(b1 - b0, 1)
     sweeps32_per_bond = (q1 - q0) / max(b1 - b0, 1)
     layer_ms = {k: sum(v) / max(args.profile_steps, 1) for k, v in prof.items()}   # per step, all colours
-    f64, f32 = bond_kernel_flops(w, sweeps_per_bond, sweeps32_per_bond)
+    # flops of one step's bond eigenproblems: the fixed dense phases plus the Jacobi work the
+    # kernel executed (counted in the kernel; converged pairs are skipped and not counted)
+    fix64, fix32 = bond_fixed_flops(graphs, w.D, args.dtype)
+    f64_step = fix64 + work_step[0] * JACOBI_BLOCK_FLOPS + work_step[1] * JACOBI_VEC_FLOPS
+    f32_step = fix32 + work_step[2] * JACOBI_BLOCK_FLOPS + work_step[3] * JACOBI_VEC_FLOPS
     if fused:
         launch_ms = sum(prof["bond_updates"]) / max(len(prof["bond_updates"]), 1)
         bonds_per_launch = bonds_step
+        launches_step = 1
         f32_big = big_end_flops(graphs, w.D)          # Gram and update passes inside the launch
         kernel = ("step_kernel (fused step: Gram pass, 2D x 2D bond eigenproblem with FP64 Jacobi and update "
                   "of every bond of a Trotter step, one launch)")
     else:
         launch_ms = sum(prof["bond"]) / max(len(prof["bond"]), 1)
         bonds_per_launch = bonds_step / g.n_colours
+        launches_step = g.n_colours
         f32_big = 0.0
         kernel = "bond_kernel (2D x 2D bond eigenproblem, FP64 Jacobi)"
-    flops_launch = f64 * bonds_per_launch
+    flops_launch = f64_step / launches_step
     achieved = flops_launch / (launch_ms * 1e-3) / 1e9
     roofline = {"kernel": kernel, "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
@@ -329,7 +345,10 @@ def run_gpeps(args, rank, world, local_rank):
                 "traffic": NCU_TRAFFIC.get((w.name, args.dtype, sched)),
                 "peak_source": "nominal FP64 1.25 TFLOP/s of the GB300 (no FP64 figure in MEASURED_PEAKS.json)",
                 "fp64_sweeps_per_bond": sweeps_per_bond, "fp32_sweeps_per_bond": sweeps32_per_bond,
-                "fp32_gflops": (f32 * bonds_per_launch + f32_big * (1 if fused else 0)) / (launch_ms * 1e-3) / 1e9,
+                "fp32_gflops": (f32_step / launches_step + f32_big) / (launch_ms * 1e-3) / 1e9,
+                "fp64_flops_per_launch": flops_launch,
+                "jacobi_work_per_step": dict(zip(("fp64_blocks", "fp64_vector_pairs", "fp32_blocks",
+                                                  "fp32_vector_pairs"), work_step)),
                 "launch_ms": launch_ms, "units_per_launch": bonds_per_launch, "schedule": sched,
                 "cycles_per_bond_by_phase": phase_cycles, "per_step_ms": layer_ms}
     elt = 8 if args.dtype == "mixed" else 16

@@ -299,6 +299,16 @@ int gpeps_sizes(const gpeps_handle* h, int64_t* total_qubits, int64_t* total_edg
  * (any may be NULL); synchronises. */
 int gpeps_sweeps(gpeps_handle* h, int64_t* sweeps64, int64_t* sweeps32, int64_t* total_bonds);
 
+/*
+ * Jacobi work executed since gpeps_reset, summed over every bond eigenproblem:
+ * work (host int64[4]) = FP64 2x2 block updates (each rotates a 2x2 block of
+ * the matrix from both sides, 72 flops), FP64 eigenvector pair updates (one row
+ * of V, 18 flops), and the same two counts of the FP32 levels.  Converged pairs
+ * are skipped and not counted.  Synchronises the stream.  Errors: GPEPS_EINVAL
+ * for NULL pointers or an unbound handle.
+ */
+int gpeps_jacobi_work(gpeps_handle* h, int64_t* work);
+
 /* Counters of the bond-eigenproblem kernel since the last gpeps_reset, summed
  * over bonds, host int64[22].  [0..5] SM cycles (clock64 of one thread per
  * CTA) of its phases: [0] reduced density matrix, [1] first FP32 Jacobi level,

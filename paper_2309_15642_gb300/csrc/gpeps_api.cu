@@ -476,7 +476,7 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   };
   h->w_pending = carve(h->total_sites * sizeof(double));
   h->w_flags = carve(sizeof(int) * 4);
-  h->w_sweeps = carve(4 * sizeof(unsigned long long));
+  h->w_sweeps = carve(kWorkCounters * sizeof(unsigned long long));
   h->w_cycles = carve(kCounters * sizeof(unsigned long long));
   h->w_queue = carve(sizeof(unsigned int));
   h->w_z = carve(h->total_sites * sizeof(double));
@@ -544,7 +544,7 @@ int gpeps_bind(gpeps_handle* h, void* d_state, void* d_work) {
   }
   GP_CUDA(up(h->w_tasks, h->tasks.data(), h->tasks.size() * sizeof(StepTask)));
   GP_CUDA(cudaMemsetAsync(h->d_work + h->w_flags, 0, sizeof(int) * 4, h->stream));
-  GP_CUDA(cudaMemsetAsync(h->d_work + h->w_sweeps, 0, sizeof(unsigned long long), h->stream));
+  GP_CUDA(cudaMemsetAsync(h->d_work + h->w_sweeps, 0, kWorkCounters * sizeof(unsigned long long), h->stream));
   GP_CUDA(cudaMemsetAsync(h->d_work + h->w_pending, 0, h->total_sites * sizeof(double), h->stream));
   // host vectors are pageable: the copies above have been staged when they return
   h->bound = true;
@@ -561,7 +561,7 @@ int gpeps_reset(gpeps_handle* h) {
                                              (int)h->total_sites, h->pending(), h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "reset");
   GP_CUDA(cudaMemsetAsync(h->d_work + h->w_flags, 0, sizeof(int) * 4, h->stream));
-  GP_CUDA(cudaMemsetAsync(h->d_work + h->w_sweeps, 0, 4 * sizeof(unsigned long long), h->stream));
+  GP_CUDA(cudaMemsetAsync(h->d_work + h->w_sweeps, 0, kWorkCounters * sizeof(unsigned long long), h->stream));
   GP_CUDA(cudaMemsetAsync(h->d_work + h->w_cycles, 0, kCounters * sizeof(unsigned long long), h->stream));
   h->bonds_since_reset = 0;
   return GPEPS_OK;
@@ -777,6 +777,15 @@ int gpeps_sweeps(gpeps_handle* h, int64_t* sweeps64, int64_t* sweeps32, int64_t*
   if (sweeps64) *sweeps64 = (int64_t)s[0];
   if (sweeps32) *sweeps32 = (int64_t)s[1];
   if (total_bonds) *total_bonds = h->bonds_since_reset;
+  return GPEPS_OK;
+}
+
+int gpeps_jacobi_work(gpeps_handle* h, int64_t* work) {
+  if (!h || !h->bound || !work) return GPEPS_EINVAL;
+  GP_CUDA(cudaStreamSynchronize(h->stream));
+  unsigned long long w[kWorkCounters];
+  GP_CUDA(cudaMemcpy(w, h->sweeps(), sizeof(w), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 4; ++i) work[i] = (int64_t)w[4 + i];
   return GPEPS_OK;
 }
 

@@ -30,8 +30,8 @@ void* g_scratch[kMaxDevices] = {};
 
 // Layout of the scratch (bytes).
 constexpr size_t kFlagsOff = 0;                                  // int flags[4]
-constexpr size_t kSweepsOff = 16;                                // u64[4]
-constexpr size_t kCyclesOff = 48;                                // u64[kCounters]
+constexpr size_t kSweepsOff = 16;                                // u64[kWorkCounters]
+constexpr size_t kCyclesOff = 80;                                // u64[kCounters]
 constexpr size_t kPendingOff = 256;                              // double pending[2], theta_a[1]
 constexpr size_t kDescOff = 512;                                 // BondDesc, TileDesc[...]
 constexpr int kNoallocMaxD = 32;                                 // bond dimension limit of this entry point
@@ -39,6 +39,7 @@ constexpr size_t kMaxTiles = (kNoallocMaxD * kNoallocMaxD + kTileRows - 1) / kTi
 constexpr size_t kYOff = 1024;                                   // 2 D^2 complex
 constexpr size_t kPartOff = kYOff + (size_t)2 * kNoallocMaxD * kNoallocMaxD * 16;  // tiles x 2 D^2 complex
 
+static_assert(kSweepsOff + kWorkCounters * sizeof(unsigned long long) <= kCyclesOff, "work counters");
 static_assert(kCyclesOff + kCounters * sizeof(unsigned long long) <= kPendingOff, "counter area");
 static_assert(sizeof(BondDesc) + kMaxTiles * sizeof(TileDesc) <= kYOff - kDescOff, "descriptor area");
 static_assert(kPartOff + kMaxTiles * 2 * kNoallocMaxD * kNoallocMaxD * 16 <= GPEPS_NOALLOC_SCRATCH_BYTES, "scratch size");

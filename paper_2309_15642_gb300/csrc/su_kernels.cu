@@ -338,13 +338,16 @@ struct HermPacked {
 // With kExact the off-diagonal of a rotated diagonal block is set to zero (the
 // FP32 angle is exact for FP32 arithmetic); the FP64 sweeps keep the computed
 // residual instead.  Returns the sweeps run; max_sweeps + 1 = cap hit.
+// work (or null): adds the 2x2 block updates and the eigenvector pair updates
+// executed (converged pairs are skipped), work[0] and work[1].
 template <typename R, bool kExact, typename S>
 __device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_abs, int max_sweeps,
                                 R* rc, R* rs, V2<R>* re, int* rp, int* rq, int* iflag,
-                                unsigned long long* rot_count) {
+                                unsigned long long* rot_count, unsigned long long* work = nullptr) {
   const int m = n / 2;
   const int nd = m / 2 + 1;  // circulant offsets d = 0..m/2
-  int sweep = 0;
+  unsigned long long n_blk = 0, n_vec = 0;
+  int sweep = 0, result = max_sweeps + 1;
   for (; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) {
       iflag[0] = 0;
@@ -384,6 +387,7 @@ __device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_ab
         if (2 * d == m && a >= d) continue;  // offset m/2 pairs each block twice
         const int b = a + d < m ? a + d : a + d - m;
         if (rs[a] == R(0) && rs[b] == R(0)) continue;
+        ++n_blk;
         const int pa = rp[a], qa = rq[a], pb = rp[b], qb = rq[b];
         const R ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
         const V2<R> ea = re[a], eb = re[b];
@@ -419,6 +423,7 @@ __device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_ab
         const int i = idx / m, k = idx - (idx / m) * m;
         const R sn = rs[k];
         if (sn == R(0)) continue;
+        ++n_vec;
         const R cs = rc[k];
         const int p = rp[k], q = rq[k];
         const V2<R> vp = V[i * ldv + p];
@@ -432,9 +437,22 @@ __device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_ab
     if (rot_count && threadIdx.x == 0 && sweep < kRotSweeps)
       atomicAdd(rot_count + sweep, (unsigned long long)iflag[2]);
     __syncthreads();
-    if (done) return sweep + 1;
+    if (done) {
+      result = sweep + 1;
+      break;
+    }
   }
-  return max_sweeps + 1;
+  if (work) {
+    for (int off = 16; off > 0; off >>= 1) {
+      n_blk += __shfl_down_sync(0xffffffffu, n_blk, off);
+      n_vec += __shfl_down_sync(0xffffffffu, n_vec, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(work, n_blk);
+      atomicAdd(work + 1, n_vec);
+    }
+  }
+  return result;
 }
 
 // Bijection from [0, n(n+1)/2) onto the upper triangle i <= j of an n x n
@@ -590,10 +608,11 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
   unsigned long long* rc32_count = cycles ? cycles + kPhases : nullptr;
   const int sw32 =
       packed ? jacobi_hermitian<float, true>(P32, V32, n, n, (float)jp.tol32, (float)(jp.floor32 * trace),
-                                             jp.max_sweeps32, rc32, rs32, re32, rp, rq, iflag, rc32_count)
+                                             jp.max_sweeps32, rc32, rs32, re32, rp, rq, iflag, rc32_count,
+                                             sweeps_out + 6)
              : jacobi_hermitian<float, true>(HermFull<float>{R32, ldr}, V32, n, n, (float)jp.tol32,
                                              (float)(jp.floor32 * trace), jp.max_sweeps32, rc32, rs32, re32, rp,
-                                             rq, iflag, rc32_count);
+                                             rq, iflag, rc32_count, sweeps_out + 6);
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const float2 v = V32[idx];
     Vm[idx] = make_double2((double)v.x, (double)v.y);
@@ -692,7 +711,7 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
       __syncthreads();
       const int swl = jacobi_hermitian<float, true>(HermFull<float>{B32, ldb}, W32, ns, ns, (float)jp.tol32,
                                                     (float)(jp.floor32 * btr), jp.max_sweeps32, rc32, rs32, re32,
-                                                    rp, rq, iflag, nullptr);
+                                                    rp, rq, iflag, nullptr, sweeps_out + 6);
       (void)swl;
       for (int idx = threadIdx.x; idx < ns * ns; idx += blockDim.x) {
         const float2 v = W32[idx];
@@ -732,7 +751,8 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
   const int sweeps = jacobi_hermitian<double, false>(HermFull<double>{RHO, ldr}, Vm, n, n, jp.tol,
                                                      jp.floor_rel * trace,
                                                      jp.max_sweeps, rc, rs, re, rp, rq, iflag,
-                                                     cycles ? cycles + kPhases + kRotSweeps : nullptr);
+                                                     cycles ? cycles + kPhases + kRotSweeps : nullptr,
+                                                     sweeps_out + 4);
   mark(4);
   if (threadIdx.x == 0) {
     if (sweeps > jp.max_sweeps) atomicOr(flags, 1);

@@ -181,6 +181,13 @@ class GPEPS:
         """SM cycles per phase of the bond kernel since the last reset (summed over bonds)."""
         return self.bond_counters()[:6]
 
+    def jacobi_work(self):
+        """(FP64 block updates, FP64 eigenvector pair updates, FP32 block updates, FP32 pair
+        updates) executed since the last reset (see gpeps_jacobi_work)."""
+        w = (ctypes.c_int64 * 4)()
+        check(self.lib.gpeps_jacobi_work(self.h, w), "gpeps_jacobi_work")
+        return [int(x) for x in w]
+
     def bond_counters(self):
         """All counters of the bond kernel: 6 phase cycle sums, rotations per FP32 sweep (8),
         rotations per FP64 sweep (8)."""
