@@ -125,7 +125,7 @@ def bond_fixed_flops(graphs, D, dtype):
     8 flops per complex MAC): re-orthonormalisation of the FP32 eigenvectors 4 n^3 / 3 MACs and
     rho' = V^dagger rho V 3 n^3 / 2 MACs in FP64; the rho formation 2 (n D^2 + n(n+1)/2 D) MACs
     and the Y matrices 2 D^2 n MACs in the storage precision (FP64 for complex128, FP32 for the
-    mixed path).  The extra FP32 levels' FP64 row and column updates are not counted."""
+    mixed path).  The extra FP32 levels' FP64 work is counted in the kernel."""
     import numpy as np
     f64 = f32 = 0.0
     for n_q, edges in graphs:
@@ -322,7 +322,7 @@ def run_gpeps(args, rank, world, local_rank):
     # flops of one step's bond eigenproblems: the fixed dense phases plus the Jacobi work the
     # kernel executed (counted in the kernel; converged pairs are skipped and not counted)
     fix64, fix32 = bond_fixed_flops(graphs, w.D, args.dtype)
-    f64_step = fix64 + work_step[0] * JACOBI_BLOCK_FLOPS + work_step[1] * JACOBI_VEC_FLOPS
+    f64_step = fix64 + work_step[0] * JACOBI_BLOCK_FLOPS + work_step[1] * JACOBI_VEC_FLOPS + work_step[4] * 8
     f32_step = fix32 + work_step[2] * JACOBI_BLOCK_FLOPS + work_step[3] * JACOBI_VEC_FLOPS
     if fused:
         launch_ms = sum(prof["bond_updates"]) / max(len(prof["bond_updates"]), 1)
@@ -348,7 +348,7 @@ def run_gpeps(args, rank, world, local_rank):
                 "fp32_gflops": (f32_step / launches_step + f32_big) / (launch_ms * 1e-3) / 1e9,
                 "fp64_flops_per_launch": flops_launch,
                 "jacobi_work_per_step": dict(zip(("fp64_blocks", "fp64_vector_pairs", "fp32_blocks",
-                                                  "fp32_vector_pairs"), work_step)),
+                                                  "fp32_vector_pairs", "fp64_level_macs"), work_step)),
                 "launch_ms": launch_ms, "units_per_launch": bonds_per_launch, "schedule": sched,
                 "cycles_per_bond_by_phase": phase_cycles, "per_step_ms": layer_ms}
     elt = 8 if args.dtype == "mixed" else 16

@@ -301,10 +301,11 @@ int gpeps_sweeps(gpeps_handle* h, int64_t* sweeps64, int64_t* sweeps32, int64_t*
 
 /*
  * Jacobi work executed since gpeps_reset, summed over every bond eigenproblem:
- * work (host int64[4]) = FP64 2x2 block updates (each rotates a 2x2 block of
+ * work (host int64[5]) = FP64 2x2 block updates (each rotates a 2x2 block of
  * the matrix from both sides, 72 flops), FP64 eigenvector pair updates (one row
- * of V, 18 flops), and the same two counts of the FP32 levels.  Converged pairs
- * are skipped and not counted.  Synchronises the stream.  Errors: GPEPS_EINVAL
+ * of V, 18 flops), the same two counts of the FP32 levels, and the FP64 complex
+ * multiply-adds with which the extra FP32 levels' rotations are applied to V
+ * and rho' (8 flops each).  Converged pairs are skipped and not counted.  Synchronises the stream.  Errors: GPEPS_EINVAL
  * for NULL pointers or an unbound handle.
  */
 int gpeps_jacobi_work(gpeps_handle* h, int64_t* work);

@@ -786,6 +786,7 @@ int gpeps_jacobi_work(gpeps_handle* h, int64_t* work) {
   unsigned long long w[kWorkCounters];
   GP_CUDA(cudaMemcpy(w, h->sweeps(), sizeof(w), cudaMemcpyDeviceToHost));
   for (int i = 0; i < 4; ++i) work[i] = (int64_t)w[4 + i];
+  work[4] = (int64_t)w[3];
   return GPEPS_OK;
 }
 

@@ -22,7 +22,8 @@ constexpr int kPhases = 6;            // phases of the bond kernel with SM-cycle
 constexpr int kRotSweeps = 8;         // rotation counters kept for the first sweeps of a solve
 constexpr int kCounters = kPhases + 2 * kRotSweeps;  // cycles, FP32 rotations, FP64 rotations
 // Work counters of the bond kernels (u64 each): [0] FP64 sweeps, [1] FP32 sweeps of the first
-// level, [2] extra FP32 levels, [3] unused, [4] FP64 2x2 block updates, [5] FP64 eigenvector
+// level, [2] extra FP32 levels, [3] FP64 complex MACs of the extra levels, [4] FP64 2x2 block
+// updates, [5] FP64 eigenvector
 // pair updates, [6] FP32 2x2 block updates, [7] FP32 eigenvector pair updates (all levels)
 constexpr int kWorkCounters = 8;
 constexpr int kMaxExtraLevels = 8;    // FP32 warm-start levels after the first (small-eigenvalue blocks)

@@ -744,7 +744,13 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
       }
       for (int a = threadIdx.x; a < ns; a += blockDim.x) rscale[cand[a]] = bscale;
       __syncthreads();
-      if (threadIdx.x == 0) atomicAdd(sweeps_out + 2, 1ull);
+      if (threadIdx.x == 0) {
+        atomicAdd(sweeps_out + 2, 1ull);
+        // FP64 complex MACs of this level: rows of V and rho' (2n x ns x ns), columns of
+        // rho' (n x ns x ns), re-orthonormalisation of W (about 4 ns^3 / 3)
+        const unsigned long long nsl = (unsigned long long)ns;
+        atomicAdd(sweeps_out + 3, 3ull * n * nsl * nsl + 4ull * nsl * nsl * nsl / 3ull);
+      }
     }
   }
   mark(3);
@@ -966,7 +972,21 @@ __device__ void bond_body(const BondDesc bd, const V2<T>* __restrict__ partials,
     return;
   }
   // Y_s[k][kk] = lam_k sum_x F[x][k] g(s, t_x) V[x][order[kk]] / sv[kk], in the
-  // storage precision (Y feeds the storage-precision update of end a)
+  // storage precision (Y feeds the storage-precision update of end a).  In FP32
+  // the kept eigenvectors are rounded once into Vk [n][D], after F in X.
+  V2<T>* Vk = F + (size_t)n * D;
+  if constexpr (sizeof(T) == 4) {
+    for (int idx = threadIdx.x; idx < n * D; idx += blockDim.x) {
+      const int x = idx / D, kk = idx - (idx / D) * D;
+      V2<T> v = mk<T>(0, 0);
+      if (sv[kk] > 0.0) {
+        const double2 vd = Vm[x * n + order[kk]];
+        v = mk<T>((T)vd.x, (T)vd.y);
+      }
+      Vk[idx] = v;
+    }
+    __syncthreads();
+  }
   const T r2 = (T)0.70710678118654752440;
   for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
     const int sidx = o / D2;
@@ -978,8 +998,14 @@ __device__ void bond_body(const BondDesc bd, const V2<T>* __restrict__ partials,
       for (int x = 0; x < n; ++x) {
         const V2<T> fv = F[x * D + k];
         const V2<T> g = mk<T>(r2, ((sidx == (x & 1)) == (jp.gate_sign > 0)) ? r2 : -r2);
-        const double2 vd = Vm[x * n + col];
-        fma_c<T>(acc, c_mul<T>(fv, g), mk<T>((T)vd.x, (T)vd.y));
+        V2<T> vv;
+        if constexpr (sizeof(T) == 4) {
+          vv = Vk[x * D + kk];
+        } else {
+          const double2 vd = Vm[x * n + col];
+          vv = mk<T>((T)vd.x, (T)vd.y);
+        }
+        fma_c<T>(acc, c_mul<T>(fv, g), vv);
       }
       acc = c_scale<T>(acc, (T)(lamo[k] / sv[kk]));
     }

@@ -183,8 +183,9 @@ class GPEPS:
 
     def jacobi_work(self):
         """(FP64 block updates, FP64 eigenvector pair updates, FP32 block updates, FP32 pair
-        updates) executed since the last reset (see gpeps_jacobi_work)."""
-        w = (ctypes.c_int64 * 4)()
+        updates, FP64 complex MACs of the extra FP32 levels) executed since the last reset (see
+        gpeps_jacobi_work)."""
+        w = (ctypes.c_int64 * 5)()
         check(self.lib.gpeps_jacobi_work(self.h, w), "gpeps_jacobi_work")
         return [int(x) for x in w]
 
