@@ -230,7 +230,7 @@ struct BondSmem {
     off_rc32 = off_scal + 8 * 8;
     off_rs32 = off_rc32 + (size_t)((m + 1) / 2) * 8;
     off_int = off_rs32 + (size_t)((m + 1) / 2) * 8;
-    small = (off_int + (size_t)(n + 2 * m + 8) * 4 + 15) & ~(size_t)15;
+    small = (off_int + (size_t)(n + 2 * m + 8 + 68) * 4 + 15) & ~(size_t)15;  // order, rp, rq, iflag, Jacobi lists
     // global-memory mode: the FP32 level's packed rho32 and V32 follow the small
     // arrays, and later the scratch of the extra levels (lv = min(n/2, 32)
     // indices: W64 [lv][lv], Gw [lv][lv+1] complex double, B32 [lv][lv+1],
@@ -331,66 +331,87 @@ struct HermPacked {
 // Parallel cyclic Jacobi for the Hermitian n x n matrix A (storage policy S:
 // HermFull or HermPacked), accumulating V (row stride ldv) <- V * product of rotations
 // (V is initialised by the caller).  The (n-1) rounds of a sweep use the
-// round-robin pairing, so the n/2 rotations of a round are disjoint and applied
-// together: A <- J^dagger A J on 2x2 blocks (a, b) enumerated circulantly
-// (b = a + d mod m, each unordered pair once; block (b, a) is the mirror),
-// V <- V J.  A pair is skipped when |a_pq| <= max(tol sqrt(a_pp a_qq), floor_abs).
+// round-robin pairing, so the n/2 <= 64 rotations of a round are disjoint and
+// applied together: A <- J^dagger A J on 2x2 blocks, V <- V J.  A pair is
+// skipped when |a_pq| <= max(tol sqrt(a_pp a_qq), floor_abs).  The active pairs
+// of a round are compacted (a warp ballot per 32 pairs) and the work runs over
+// them densely: the blocks {a, b} with a active (each unordered pair once, the
+// diagonal block a = b included), and the rows of V times the active pairs; a
+// round without active pairs does no work.  So late sweeps, where few pairs
+// still rotate, do not occupy whole warps with skipped lanes.
 // With kExact the off-diagonal of a rotated diagonal block is set to zero (the
 // FP32 angle is exact for FP32 arithmetic); the FP64 sweeps keep the computed
 // residual instead.  Returns the sweeps run; max_sweeps + 1 = cap hit.
 // work (or null): adds the 2x2 block updates and the eigenvector pair updates
-// executed (converged pairs are skipped), work[0] and work[1].
+// executed, work[0] and work[1].  iflag: 8 ints, followed by 68 ints of scratch
+// (active lists of the two warps [2][32], their counts, double-buffered [2][2]).
 template <typename R, bool kExact, typename S>
 __device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_abs, int max_sweeps,
                                 R* rc, R* rs, V2<R>* re, int* rp, int* rq, int* iflag,
                                 unsigned long long* rot_count, unsigned long long* work = nullptr) {
   const int m = n / 2;
-  const int nd = m / 2 + 1;  // circulant offsets d = 0..m/2
+  int* act = iflag + 8;    // [2][32]
+  int* wcnt = iflag + 72;  // [2 buffers][2 warps]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long n_blk = 0, n_vec = 0;
   int sweep = 0, result = max_sweeps + 1;
   for (; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) {
-      iflag[0] = 0;
-      iflag[2] = 0;
-    }
-    __syncthreads();
+    int rot_sweep = 0;  // thread 0: rotations of this sweep
     for (int r = 0; r < n - 1; ++r) {
-      for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        int p, q;
-        if (k == 0) {
-          p = r;
-          q = n - 1;
-        } else {
-          p = (r + k) % (n - 1);
-          q = (r - k + (n - 1)) % (n - 1);
+      int* cnt = wcnt + 2 * (r & 1);
+      if (warp < 2) {
+        const int k = threadIdx.x;
+        bool on = false;
+        if (k < m) {
+          int p, q;
+          if (k == 0) {
+            p = r;
+            q = n - 1;
+          } else {
+            p = r + k;
+            if (p >= n - 1) p -= n - 1;
+            q = r - k;
+            if (q < 0) q += n - 1;
+          }
+          if (p > q) {
+            const int tmp = p;
+            p = q;
+            q = tmp;
+          }
+          R cs = 1, sn = 0;
+          V2<R> e = mk<R>(1, 0);
+          on = rotation(A.get(p, p).x, A.get(q, q).x, A.get(p, q), tol, floor_abs, cs, sn, e) && sn != R(0);
+          rp[k] = p;
+          rq[k] = q;
+          rc[k] = cs;
+          rs[k] = on ? sn : R(0);
+          re[k] = e;
         }
-        if (p > q) {
-          const int tmp = p;
-          p = q;
-          q = tmp;
-        }
-        R cs = 1, sn = 0;
-        V2<R> e = mk<R>(1, 0);
-        if (rotation(A.get(p, p).x, A.get(q, q).x, A.get(p, q), tol, floor_abs, cs, sn, e)) {
-          iflag[0] = 1;
-          atomicAdd(iflag + 2, 1);
-        }
-        rp[k] = p;
-        rq[k] = q;
-        rc[k] = cs;
-        rs[k] = sn;
-        re[k] = e;
+        const unsigned bal = __ballot_sync(0xffffffffu, on);
+        if (on) act[warp * 32 + __popc(bal & ((1u << lane) - 1u))] = k;
+        if (lane == 0) cnt[warp] = __popc(bal);
       }
       __syncthreads();
-      for (int idx = threadIdx.x; idx < nd * m; idx += blockDim.x) {
-        const int d = idx / m, a = idx - (idx / m) * m;
-        if (2 * d == m && a >= d) continue;  // offset m/2 pairs each block twice
-        const int b = a + d < m ? a + d : a + d - m;
-        if (rs[a] == R(0) && rs[b] == R(0)) continue;
+      const int c0 = cnt[0], na = c0 + cnt[1];
+      if (threadIdx.x == 0) rot_sweep += na;
+      if (na == 0) continue;  // nothing read below: the next round may overwrite at once
+      auto active = [&](int i) { return i < c0 ? act[i] : act[32 + i - c0]; };
+      // blocks {a, b}, a = i-th active pair, b any pair; a pair of two active pairs is
+      // done once, by the one of lower rank
+      for (int t = threadIdx.x; t < na * m; t += blockDim.x) {
+        const int ia = t / m, b = t - ia * m;
+        const int a = active(ia);
+        if (rs[b] != R(0) && b != a) {
+          // b active: skip unless b's rank is above a's
+          int rb = -1;
+          for (int j = ia + 1; j < na; ++j)
+            if (active(j) == b) rb = j;
+          if (rb < 0) continue;
+        }
         ++n_blk;
         const int pa = rp[a], qa = rq[a], pb = rp[b], qb = rq[b];
         const R ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
-        const V2<R> ea = re[a], eb = re[b];
+        const V2<R> ea = re[a], eb = rs[b] != R(0) ? re[b] : mk<R>(1, 0);
         const V2<R> b00 = A.get(pa, pb), b01 = A.get(pa, qb);
         const V2<R> b10 = A.get(qa, pb), b11 = A.get(qa, qb);
         const V2<R> b01e = c_mul<R>(b01, eb), b11e = c_mul<R>(b11, eb);
@@ -404,7 +425,8 @@ __device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_ab
         V2<R> n01 = c_sub<R>(c_scale<R>(t01, ca), c_scale<R>(u11, sa));
         V2<R> n10 = c_add<R>(c_scale<R>(t00, sa), c_scale<R>(u10, ca));
         V2<R> n11 = c_add<R>(c_scale<R>(t01, sa), c_scale<R>(u11, ca));
-        if (d == 0) {
+        const bool diag = b == a;
+        if (diag) {
           n00.y = R(0);
           n11.y = R(0);
           if (kExact) {
@@ -414,17 +436,15 @@ __device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_ab
           }
           n10 = c_conj<R>(n01);
         }
-        A.put(pa, pb, n00, d != 0);
-        A.put(pa, qb, n01, d != 0);
-        A.put(qa, pb, n10, d != 0);
-        A.put(qa, qb, n11, d != 0);
+        A.put(pa, pb, n00, !diag);
+        A.put(pa, qb, n01, !diag);
+        A.put(qa, pb, n10, !diag);
+        A.put(qa, qb, n11, !diag);
       }
-      for (int idx = threadIdx.x; idx < n * m; idx += blockDim.x) {
-        const int i = idx / m, k = idx - (idx / m) * m;
-        const R sn = rs[k];
-        if (sn == R(0)) continue;
+      for (int t = threadIdx.x; t < n * na; t += blockDim.x) {
+        const int i = t / na, k = active(t - i * na);
         ++n_vec;
-        const R cs = rc[k];
+        const R cs = rc[k], sn = rs[k];
         const int p = rp[k], q = rq[k];
         const V2<R> vp = V[i * ldv + p];
         const V2<R> vqe = c_mul<R>(V[i * ldv + q], re[k]);
@@ -433,9 +453,12 @@ __device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_ab
       }
       __syncthreads();
     }
-    const int done = (iflag[0] == 0);
-    if (rot_count && threadIdx.x == 0 && sweep < kRotSweeps)
-      atomicAdd(rot_count + sweep, (unsigned long long)iflag[2]);
+    if (threadIdx.x == 0) {
+      iflag[3] = rot_sweep;
+      if (rot_count && sweep < kRotSweeps) atomicAdd(rot_count + sweep, (unsigned long long)rot_sweep);
+    }
+    __syncthreads();
+    const int done = iflag[3] == 0;
     __syncthreads();
     if (done) {
       result = sweep + 1;
@@ -447,7 +470,7 @@ __device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_ab
       n_blk += __shfl_down_sync(0xffffffffu, n_blk, off);
       n_vec += __shfl_down_sync(0xffffffffu, n_vec, off);
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
       atomicAdd(work, n_blk);
       atomicAdd(work + 1, n_vec);
     }
