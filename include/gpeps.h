@@ -200,7 +200,7 @@ int gpeps_set_wait_limit(gpeps_handle* h, int64_t cycles);
  * then uses schedule 2 (or 1 where 2 does not fit).
  * Host-only; drops a captured step graph.  Errors: GPEPS_EINVAL for other
  * values, and for 2, 3 or 4 on an unbound handle, when the FP32 level does not
- * fit the CTA's share of shared memory (D above 47 for 2, above 33 for 3), or
+ * fit the CTA's share of shared memory (D above 47 for 2, above 32 for 3), or
  * on a device with more than 256 SMs.
  */
 int gpeps_set_schedule(gpeps_handle* h, int32_t schedule);

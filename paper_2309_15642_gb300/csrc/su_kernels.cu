@@ -230,7 +230,7 @@ struct BondSmem {
     off_rc32 = off_scal + 8 * 8;
     off_rs32 = off_rc32 + (size_t)((m + 1) / 2) * 8;
     off_int = off_rs32 + (size_t)((m + 1) / 2) * 8;
-    small = (off_int + (size_t)(n + 2 * m + 8 + 68) * 4 + 15) & ~(size_t)15;  // order, rp, rq, iflag, Jacobi lists
+    small = (off_int + (size_t)(n + 2 * m + 8 + 144) * 4 + 15) & ~(size_t)15;  // order, rp, rq, iflag, Jacobi lists
     // global-memory mode: the FP32 level's packed rho32 and V32 follow the small
     // arrays, and later the scratch of the extra levels (lv = min(n/2, 32)
     // indices: W64 [lv][lv], Gw [lv][lv+1] complex double, B32 [lv][lv+1],
@@ -343,22 +343,24 @@ struct HermPacked {
 // FP32 angle is exact for FP32 arithmetic); the FP64 sweeps keep the computed
 // residual instead.  Returns the sweeps run; max_sweeps + 1 = cap hit.
 // work (or null): adds the 2x2 block updates and the eigenvector pair updates
-// executed, work[0] and work[1].  iflag: 8 ints, followed by 68 ints of scratch
-// (active lists of the two warps [2][32], their counts, double-buffered [2][2]).
+// executed, work[0] and work[1].  iflag: 8 ints, followed by 136 ints of scratch:
+// the active and the idle pairs of the round, per warp ([2][32] each), and their
+// counts, double-buffered by round parity ([2][4]).
 template <typename R, bool kExact, typename S>
 __device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_abs, int max_sweeps,
                                 R* rc, R* rs, V2<R>* re, int* rp, int* rq, int* iflag,
                                 unsigned long long* rot_count, unsigned long long* work = nullptr) {
   const int m = n / 2;
-  int* act = iflag + 8;    // [2][32]
-  int* wcnt = iflag + 72;  // [2 buffers][2 warps]
+  int* act = iflag + 8;     // [2 warps][32] active pairs
+  int* idle = iflag + 72;   // [2 warps][32] idle pairs
+  int* wcnt = iflag + 136;  // [2 buffers][active w0, active w1, idle w0, idle w1]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long n_blk = 0, n_vec = 0;
   int sweep = 0, result = max_sweeps + 1;
   for (; sweep < max_sweeps; ++sweep) {
     int rot_sweep = 0;  // thread 0: rotations of this sweep
     for (int r = 0; r < n - 1; ++r) {
-      int* cnt = wcnt + 2 * (r & 1);
+      int* cnt = wcnt + 4 * (r & 1);
       if (warp < 2) {
         const int k = threadIdx.x;
         bool on = false;
@@ -388,25 +390,37 @@ __device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_ab
           re[k] = e;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, on);
-        if (on) act[warp * 32 + __popc(bal & ((1u << lane) - 1u))] = k;
-        if (lane == 0) cnt[warp] = __popc(bal);
+        const unsigned bid = __ballot_sync(0xffffffffu, k < m && !on);
+        const unsigned below = (1u << lane) - 1u;
+        if (on) act[warp * 32 + __popc(bal & below)] = k;
+        if (k < m && !on) idle[warp * 32 + __popc(bid & below)] = k;
+        if (lane == 0) {
+          cnt[warp] = __popc(bal);
+          cnt[2 + warp] = __popc(bid);
+        }
       }
       __syncthreads();
-      const int c0 = cnt[0], na = c0 + cnt[1];
+      const int c0 = cnt[0], na = c0 + cnt[1], i0 = cnt[2], ni = i0 + cnt[3];
       if (threadIdx.x == 0) rot_sweep += na;
       if (na == 0) continue;  // nothing read below: the next round may overwrite at once
       auto active = [&](int i) { return i < c0 ? act[i] : act[32 + i - c0]; };
-      // blocks {a, b}, a = i-th active pair, b any pair; a pair of two active pairs is
-      // done once, by the one of lower rank
-      for (int t = threadIdx.x; t < na * m; t += blockDim.x) {
-        const int ia = t / m, b = t - ia * m;
-        const int a = active(ia);
-        if (rs[b] != R(0) && b != a) {
-          // b active: skip unless b's rank is above a's
-          int rb = -1;
-          for (int j = ia + 1; j < na; ++j)
-            if (active(j) == b) rb = j;
-          if (rb < 0) continue;
+      auto idle_at = [&](int j) { return j < i0 ? idle[j] : idle[32 + j - i0]; };
+      // blocks {a, b} touching an active pair, each once: a active and b idle
+      // (na x ni), then both active with rank(a) <= rank(b) (triangle, diagonal included)
+      const int n_ai = na * ni, n_blocks = n_ai + na * (na + 1) / 2;
+      for (int t = threadIdx.x; t < n_blocks; t += blockDim.x) {
+        int a, b;
+        if (t < n_ai) {
+          const int ia = t / ni;
+          a = active(ia);
+          b = idle_at(t - ia * ni);
+        } else {
+          const int u = t - n_ai;
+          int row = (int)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
+          while (row * (row + 1) / 2 > u) --row;
+          while ((row + 1) * (row + 2) / 2 <= u) ++row;
+          a = active(u - row * (row + 1) / 2);
+          b = active(row);
         }
         ++n_blk;
         const int pa = rp[a], qa = rq[a], pb = rp[b], qb = rq[b];
