@@ -197,13 +197,14 @@ int gpeps_set_wait_limit(gpeps_handle* h, int64_t cycles);
  * bond waits only until the earlier bonds on its two sites are done, so the
  * classes need no barrier between them (same results; a wait that gives up
  * after ~2 s raises GPEPS_FLAG_TIMEOUT instead of hanging); gpeps_zz_layer
- * then uses schedule 2 (or 1 where 2 does not fit).
+ * then uses schedule 2 (or 1 where 2 does not fit).  5 is the fused step with
+ * three 192-thread CTAs per SM (where their shared memory fits, D <= 32).
  * Host-only; drops a captured step graph.  Errors: GPEPS_EINVAL for other
  * values, and for 2, 3 or 4 on an unbound handle, when the FP32 level does not
  * fit the CTA's share of shared memory (D above 47 for 2, above 32 for 3), or
  * on a device with more than 256 SMs.
  */
-int gpeps_set_schedule(gpeps_handle* h, int32_t schedule);
+int gpeps_set_schedule(gpeps_handle* h, int32_t schedule);  /* 0..5 */
 
 /* Number of colour classes (the largest over the instances). */
 int gpeps_n_colours(const gpeps_handle* h, int32_t* n_colours);

@@ -24,7 +24,7 @@ import torch
 STRICT_MIXED = dict(tol=1e-9, floor_rel=1e-11, tol32=1e-6, floor32=2e-7)
 FP32_LEVELS = [(1e-6, 2e-7), (3e-6, 1e-6)]
 FP64_STOPS = [(1e-9, 1e-8), (1e-9, 3e-8)]
-SCHEDULES = (0, 1, 2, 3, 4)
+SCHEDULES = (0, 1, 2, 3, 4, 5)
 
 
 def candidates(dtype):

@@ -224,14 +224,17 @@ int layered_per_sm(const gpeps_handle* h) {
   switch (h->schedule) {
     case 2: return 2;
     case 3: return 4;
-    case 4: return bond_footprint_global(h->D).smem <= bond_share_smem(2) ? 2 : 1;
+    case 4:
+    case 5: return bond_footprint_global(h->D).smem <= bond_share_smem(2) ? 2 : 1;
     default: return 1;
   }
 }
 
 // CTAs per SM of the fused step launch
 int step_per_sm(const gpeps_handle* h) {
-  return step_footprint(h->D, h->elt).smem <= bond_share_smem(2) ? 2 : 1;
+  const size_t sm = step_footprint(h->D, h->elt).smem;
+  if (h->schedule == 5 && sm <= bond_share_smem(3)) return 3;
+  return sm <= bond_share_smem(2) ? 2 : 1;
 }
 
 template <typename T>
@@ -300,7 +303,7 @@ int readout_impl(gpeps_handle* h) {
 int one_step(gpeps_handle* h, const double* theta, int per_qubit) {
   int st = kick_impl(h, theta, per_qubit);
   if (st) return st;
-  if (h->schedule == 4) {
+  if (h->schedule >= 4) {
     st = h->dtype == GPEPS_C128 ? fused_step_impl<double>(h) : fused_step_impl<float>(h);
     if (st) return st;
   } else {
@@ -601,7 +604,7 @@ int gpeps_step_profiled(gpeps_handle* h, const double* theta, int32_t per_qubit,
     int st = kick_impl(h, theta, per_qubit ? 1 : 0);
     if (st) return st;
     GP_CUDA(cudaEventRecord(ev[1], h->stream));
-    if (h->schedule == 4) {
+    if (h->schedule >= 4) {
       st = h->dtype == GPEPS_C128 ? fused_step_impl<double>(h) : fused_step_impl<float>(h);
     } else {
       for (int c = 0; c < (int)h->colours.size() && !st; ++c) st = layer(h, c);
@@ -621,13 +624,16 @@ int gpeps_step_profiled(gpeps_handle* h, const double* theta, int32_t per_qubit,
 }
 
 int gpeps_set_schedule(gpeps_handle* h, int32_t schedule) {
-  if (!h || schedule < 0 || schedule > 4) return GPEPS_EINVAL;
-  if (schedule == 4) {
+  if (!h || schedule < 0 || schedule > 5) return GPEPS_EINVAL;
+  if (schedule == 5 && (!h->bound || step_footprint(h->D, h->elt).smem > bond_share_smem(3) ||
+                        std::min(3 * h->n_sms, (int)h->tasks.size()) > h->bond_slots))
+    return GPEPS_EINVAL;
+  if (schedule >= 4) {
     // fused step: shared memory of one CTA (alone or two per SM) and a slot per CTA
     if (!h->bound) return GPEPS_EINVAL;
     const BondFootprint fp = step_footprint(h->D, h->elt);
     if (fp.smem > kBondSmemMax || fp.slot > h->bond_slot) return GPEPS_EINVAL;
-    if (std::min(step_per_sm(h) * h->n_sms, (int)h->tasks.size()) > h->bond_slots) return GPEPS_EINVAL;
+    if (std::min(2 * h->n_sms, (int)h->tasks.size()) > h->bond_slots) return GPEPS_EINVAL;
     // its layers (gpeps_zz_layer) run two CTAs per SM where they fit
     const bool pair = bond_footprint_global(h->D).smem <= bond_share_smem(2);
     if (pair && std::min(2 * h->n_sms, h->max_bonds) > h->bond_slots) return GPEPS_EINVAL;

@@ -1538,6 +1538,9 @@ cudaError_t Launch<T>::init() {
   e = cudaFuncSetAttribute(step_kernel<T, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bond_share_smem(2));
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(step_kernel<T, 192, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bond_share_smem(3));
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(step_kernel<T, kBondThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kBondSmemMax);
   if (e != cudaSuccess) return e;
@@ -1645,8 +1648,8 @@ cudaError_t Launch<T>::step(const StepTask* tasks, int n_tasks, unsigned int* qu
                             void* scratch, size_t slot, int per_sm) {
   if (n_tasks == 0) return cudaSuccess;
   const BondFootprint fp = step_footprint(D, sizeof(V2<T>));
-  if (!scratch || slot < fp.slot || (per_sm != 1 && per_sm != 2)) return cudaErrorInvalidValue;
-  if (fp.smem > (per_sm == 2 ? bond_share_smem(2) : kBondSmemMax)) return cudaErrorInvalidValue;
+  if (!scratch || slot < fp.slot || per_sm < 1 || per_sm > 3) return cudaErrorInvalidValue;
+  if (fp.smem > (per_sm > 1 ? bond_share_smem(per_sm) : kBondSmemMax)) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(done, 0, (size_t)n_tasks * sizeof(int), st);
@@ -1654,7 +1657,10 @@ cudaError_t Launch<T>::step(const StepTask* tasks, int n_tasks, unsigned int* qu
   const int want = per_sm * n_ctas;
   const int grid = want < n_tasks ? want : n_tasks;
   unsigned char* sp = static_cast<unsigned char*>(scratch);
-  if (per_sm == 2)
+  if (per_sm == 3)
+    step_kernel<T, 192, 3><<<grid, 192, fp.smem, st>>>(tasks, n_tasks, queue, done, static_cast<V2<T>*>(gamma), lam,
+                                                       pending, flags, sweeps, cycles, D, jp, sp, slot);
+  else if (per_sm == 2)
     step_kernel<T, 256, 2><<<grid, 256, fp.smem, st>>>(tasks, n_tasks, queue, done, static_cast<V2<T>*>(gamma), lam,
                                                        pending, flags, sweeps, cycles, D, jp, sp, slot);
   else

@@ -269,7 +269,7 @@ def test_schedules_are_bit_identical():
     import torch
     from ._gpu_util import gpu_lib
     outs = []
-    for persistent in (0, 1, 2, 3, 4):
+    for persistent in (0, 1, 2, 3, 4, 5):
         g = gpu_lib()([(M127, E127), heavy_hex(*OSPREY)], 8, dtype="mixed")
         g.set_schedule(persistent)
         g.reset()
