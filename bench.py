@@ -34,7 +34,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "bond updates/s at D=32 (mixed vs FP64 plain, |d<Z>|<=1e-4); % of roofline"
-FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 (vector) rate; measured 1197 by an FMA loop
+# FP64 vector peak from the unit counts and the maximum SM clock: 152 SMs x 2 FP64 FMA per clock
+# x 2 flops x 2.07 GHz (an FP64 FMA loop on this part measured 1197 GFLOP/s)
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 
 
 def parse():
@@ -343,7 +345,8 @@ def run_gpeps(args, rank, world, local_rank):
                 "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
                 "frac": achieved / FP64_PEAK_GFLOPS,
                 "traffic": NCU_TRAFFIC.get((w.name, args.dtype, sched)),
-                "peak_source": "nominal FP64 1.25 TFLOP/s of the GB300 (no FP64 figure in MEASURED_PEAKS.json)",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x 2.07 GHz (MEASURED_PEAKS.json has "
+                               "no FP64 figure; an FP64 FMA loop measured 1197 GFLOP/s)",
                 "fp64_sweeps_per_bond": sweeps_per_bond, "fp32_sweeps_per_bond": sweeps32_per_bond,
                 "fp32_gflops": (f32_step / launches_step + f32_big) / (launch_ms * 1e-3) / 1e9,
                 "fp64_flops_per_launch": flops_launch,
