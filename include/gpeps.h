@@ -292,6 +292,44 @@ int gpeps_query_grad_workspace(const gpeps_handle* h, int32_t n_steps, int32_t c
 int gpeps_grad(gpeps_handle* h, const double* theta, int32_t n_steps, int32_t ckpt_every, const double* dL_dz,
                double* z_out, double* dtheta, void* d_grad_work, size_t grad_work_bytes);
 
+/*
+ * Belief-propagation (BP) regauging of the state (paper, section "Method":
+ * the PEPS re-gauged with BP after each Trotter step, for comparison;
+ * "Results", "Benchmarking").  Messages of the norm network, one D x D
+ * Hermitian matrix per leg of every site:
+ *   m_{i->e}[a][a'] = sum Gamma_i[.., a, ..] conj(Gamma_i[.., a', ..]) prod_f E_f
+ * over s and every other leg f of i, with E_f = diag(lambda_f) m_{k->f}
+ * diag(lambda_f) built from the message of the neighbour k across f.  They
+ * start at identity / D; an iteration recomputes all of them from the previous
+ * iteration's, keeps them Hermitian, restricts them to the support of their
+ * bond's lambda (entries k with lambda[k] <= cut * max zero; cut = 1e-13 for
+ * GPEPS_C128, 1e-7 for GPEPS_MIXED_C64, below which a rank-deficient bond holds
+ * only rounding residue) and normalises them to unit trace, until the largest
+ * elementwise change is <= tol or after max_iter iterations.  Then
+ * every edge e = (i, j) is gauged with the converged messages: with
+ * R = conj(m)^{1/2} at both ends (pseudo-inverse below 1e-13 of the largest
+ * eigenvalue), C = R_i diag(lambda_e) R_j^T = U S V^H, lambda_e' = S / ||S||,
+ * Gamma_i <- Gamma_i (R_i^+ U) and Gamma_j <- Gamma_j (R_j^+ conj(V)) on leg e
+ * (columns with S <= 1e-13 S_max zeroed).  The state is unchanged; the
+ * mean-field readout afterwards uses the new gauge.  Messages, gauge and lambda
+ * are FP64; the message contractions run in the storage precision (FP32 for
+ * GPEPS_MIXED_C64).  A pending kick commutes with the regauge and stays pending.
+ *   d_bp_work:  device, 256-byte aligned, >= gpeps_query_bp_workspace(max_iter)
+ *               bytes (the messages of two iterations, the gauge matrices, the
+ *               work lists and one global scratch slot per CTA)
+ *   iterations: host, or NULL: BP iterations run
+ *   residual:   host, or NULL: the largest elementwise change of the last one
+ * Synchronises the stream once per iteration (the convergence test), so it
+ * cannot be captured into a CUDA graph.  Device flags: GPEPS_FLAG_NOCONV (a
+ * gauge eigenproblem hit its sweep cap), GPEPS_FLAG_NUMERIC (a message with
+ * non-positive or non-finite trace, or a vanishing gauged bond: that edge keeps
+ * its gauge).  Errors: GPEPS_EINVAL for an unbound handle, max_iter < 1,
+ * negative or NaN tol, a NULL, misaligned or too small workspace.
+ */
+int gpeps_query_bp_workspace(gpeps_handle* h, int32_t max_iter, size_t* bytes);
+int gpeps_bp_regauge(gpeps_handle* h, int32_t max_iter, double tol, void* d_bp_work, size_t bp_work_bytes,
+                     int32_t* iterations, double* residual);
+
 /* Totals of the batch: qubits, edges, bond updates per Trotter step. */
 int gpeps_sizes(const gpeps_handle* h, int64_t* total_qubits, int64_t* total_edges);
 

@@ -16,9 +16,18 @@ D x D Hermitian matrix over the (ket a, bra a') index pair of that leg:
 
 where E_f = diag(lambda_f) m_{k->f} diag(lambda_f) is the environment of i's
 other leg f, built from the message that the neighbour k across f sends along
-f.  All messages start at identity / D; an iteration recomputes every message
-from the previous iteration's (parallel schedule), keeps its Hermitian part
-(m + m^H) / 2 and normalises it to unit trace; iterations stop when the largest
+f.  A message lives on the support of its own bond's lambda_e: the rows and
+columns k with lambda_e[k] <= LAMBDA_CUT * max(lambda_e) are zero (the
+pseudo-inverse convention of ``oracle.su``, which already treats those
+directions as absent; ``support_cut`` sets the threshold).  A low-precision
+simple update leaves rounding residue in the empty directions of a
+rank-deficient bond: lambda far below its resolution, with Gamma columns that
+are rounding noise.  Kept in the messages, that residue sends BP to another
+fixed point (a wrong mean-field readout after the gauge), so a path that
+stores Gamma in FP32 restricts the messages at its own resolution (1e-7).  All messages start at identity / D; an iteration
+recomputes every message from the previous iteration's (parallel schedule),
+keeps its Hermitian part (m + m^H) / 2, restricts it to the support and
+normalises it to unit trace; iterations stop when the largest
 elementwise change is <= tol, or after max_iter.  The exact message is
 Hermitian; its rounding noise is not, and an anti-Hermitian multiple of a
 message is not removed by the trace normalisation: it spreads along the loops
@@ -44,8 +53,8 @@ edge uses the messages of the same converged iteration.  After the gauge, BP
 messages are proportional to the identity (the Vidal gauge on a tree).
 
 Readings where the paper is silent (also in the design notes): messages start
-at identity / D, are made Hermitian and normalised to unit trace; parallel
-update schedule;
+at identity / D, are made Hermitian, restricted to the support of their
+bond's lambda and normalised to unit trace; parallel update schedule;
 convergence test on the largest elementwise change; the gauge uses the
 converged messages of every edge at once; GRAM_CUT = 1e-13 relative.
 
@@ -73,8 +82,9 @@ def identity_messages(peps):
             for i in range(peps.n) for p in range(len(peps.nb[i]))}
 
 
-def message(peps, i, p, msgs):
-    """m_{i->e} for leg p of site i from the messages ``msgs`` of i's other legs (unit trace)."""
+def message(peps, i, p, msgs, support_cut=LAMBDA_CUT):
+    """m_{i->e} for leg p of site i from the messages ``msgs`` of i's other legs (unit trace),
+    restricted to the support of lambda_e (entries k with lambda_e[k] <= support_cut * max zero)."""
     G = peps.gamma[i]
     X = G.conj()
     for q, k in enumerate(peps.nb[i]):
@@ -86,18 +96,21 @@ def message(peps, i, p, msgs):
     axes = [ax for ax in range(G.ndim) if ax != p + 1]
     m = np.tensordot(G, X, axes=(axes, axes))
     m = 0.5 * (m + m.conj().T)
+    lam_e = peps.lam[peps.edge_of[(i, peps.nb[i][p])]]
+    keep = lam_e > support_cut * float(lam_e.max())
+    m = m * np.outer(keep, keep)
     tr = float(np.trace(m).real)
     if not np.isfinite(tr) or tr <= 0.0:
         raise FloatingPointError(f"message of site {i}, leg {p}: trace {tr}")
     return m / tr
 
 
-def messages(peps, max_iter=50, tol=1e-12, start=None):
+def messages(peps, max_iter=50, tol=1e-12, start=None, support_cut=LAMBDA_CUT):
     """Iterate BP to a fixed point.  Returns (messages, iterations run, last residual)."""
     msgs = identity_messages(peps) if start is None else start
     it, res = 0, float("inf")
     for it in range(1, max_iter + 1):
-        new = {key: message(peps, key[0], key[1], msgs) for key in msgs}
+        new = {key: message(peps, key[0], key[1], msgs, support_cut) for key in msgs}
         res = max((float(np.abs(new[k] - msgs[k]).max()) for k in msgs), default=0.0)
         msgs = new
         if res <= tol:
@@ -144,9 +157,9 @@ def gauge(peps, msgs):
     peps.lam = lam_new
 
 
-def regauge(peps, max_iter=50, tol=1e-12):
+def regauge(peps, max_iter=50, tol=1e-12, support_cut=LAMBDA_CUT):
     """BP messages to convergence, then the gauge.  Returns (iterations, residual)."""
-    msgs, it, res = messages(peps, max_iter, tol)
+    msgs, it, res = messages(peps, max_iter, tol, support_cut=support_cut)
     gauge(peps, msgs)
     return it, res
 

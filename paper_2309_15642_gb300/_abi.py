@@ -38,6 +38,9 @@ SIGNATURES = {
     "gpeps_query_grad_workspace": (c_int, [c_void_p, c_int32, c_int32, POINTER(c_size_t)]),
     "gpeps_grad": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                            c_size_t]),
+    "gpeps_query_bp_workspace": (c_int, [c_void_p, c_int32, POINTER(c_size_t)]),
+    "gpeps_bp_regauge": (c_int, [c_void_p, c_int32, c_double, c_void_p, c_size_t, POINTER(c_int32),
+                                 POINTER(c_double)]),
     "gpeps_sizes": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
     "gpeps_sweeps": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
     "gpeps_bond_phase_cycles": (c_int, [c_void_p, POINTER(c_int64)]),

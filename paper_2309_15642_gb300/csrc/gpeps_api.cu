@@ -82,6 +82,12 @@ struct gpeps_handle {
   int schedule = 0;  // bond eigenproblems: 0 one CTA per bond; work queue with 1 (schedule 1), 2 (2) or 4 (3)
                      // CTAs per SM; 4 fused step (gpeps_step: one persistent launch over every colour class)
   std::vector<StepTask> tasks;  // fused step: every bond of a step, colour by colour, with its dependencies
+  // BP regauging: half-edges (one per leg of every site), work lists built on first use
+  int64_t n_half = 0;
+  std::vector<int32_t> he0;  // half-edge index of leg 0 of every site
+  std::vector<BpMsgTask> bp_msgs;
+  std::vector<BpEdgeTask> bp_edges;
+  std::vector<BpSiteTask> bp_sites;
   size_t w_tasks = 0, w_done = 0;
   int n_sms = 0;
   int64_t bonds_since_reset = 0;
@@ -979,6 +985,176 @@ int gpeps_grad(gpeps_handle* h, const double* theta, int32_t n_steps, int32_t ck
       GP_CUDA(Adjoint::kick(sites, n_sites, post.first, ad.first, theta, dtheta, h->D, s));
     }
   }
+  return GPEPS_OK;
+}
+
+namespace {
+
+// ---------------------------------------------------------------- BP regauging
+void bp_plan(gpeps_handle* h) {
+  if (!h->he0.empty()) return;
+  const int D = h->D;
+  h->he0.assign(h->total_sites + 1, 0);
+  for (int64_t gs = 0; gs < h->total_sites; ++gs) h->he0[gs + 1] = h->he0[gs] + h->sites[gs].deg;
+  h->n_half = h->he0[h->total_sites];
+  for (int want = 3; want >= 1; --want) {  // the costly messages and sites first
+    for (int k = 0; k < h->n_inst; ++k) {
+      const InstGraph& ig = h->g[k];
+      for (int v = 0; v < ig.n; ++v) {
+        const int gs = h->inst_site0[k] + v;
+        const SiteDesc& sd = h->sites[gs];
+        if (sd.deg != want) continue;
+        for (int p = 0; p < sd.deg; ++p) {
+          BpMsgTask t{};
+          t.off = sd.off;
+          t.deg = sd.deg;
+          t.leg = p;
+          t.out = h->he0[gs] + p;
+          for (int q = 0; q < 3; ++q) {
+            t.in[q] = -1;
+            t.lam[q] = q < sd.deg ? sd.lam[q] : 0;
+            if (q < sd.deg) {
+              const int nbr = ig.nb[v][q];
+              const int back = (int)(std::find(ig.nb[nbr].begin(), ig.nb[nbr].end(), v) - ig.nb[nbr].begin());
+              t.in[q] = h->he0[h->inst_site0[k] + nbr] + back;
+            }
+          }
+          h->bp_msgs.push_back(t);
+        }
+        BpSiteTask st{};
+        st.off = sd.off;
+        st.deg = sd.deg;
+        st.h0 = h->he0[gs];
+        h->bp_sites.push_back(st);
+      }
+    }
+  }
+  for (int k = 0; k < h->n_inst; ++k) {
+    const InstGraph& ig = h->g[k];
+    for (int e = 0; e < (int)ig.edges.size(); ++e) {
+      const int u = ig.edges[e].first, v = ig.edges[e].second;
+      const int pu = (int)(std::find(ig.nb[u].begin(), ig.nb[u].end(), v) - ig.nb[u].begin());
+      const int pv = (int)(std::find(ig.nb[v].begin(), ig.nb[v].end(), u) - ig.nb[v].begin());
+      BpEdgeTask t{};
+      t.hi = h->he0[h->inst_site0[k] + u] + pu;
+      t.hj = h->he0[h->inst_site0[k] + v] + pv;
+      t.lam = (h->inst_edge0[k] + e) * D;
+      h->bp_edges.push_back(t);
+    }
+  }
+}
+
+struct BpLayout {
+  size_t msg_a, msg_b, P, tasks, edges, sites, residual, scratch, total;
+  int64_t slot_elems;  // complex elements (of the storage type for messages, FP64 for the gauge) per CTA slot
+  int n_ctas;
+};
+
+int bp_ctas(const gpeps_handle* h) {
+  int per_sm = 1;
+  const size_t smem = h->dtype == GPEPS_C128 ? BpLaunch<double>::message_smem(h->D)
+                                              : BpLaunch<float>::message_smem(h->D);
+  per_sm = (int)(kSmemPerSm / (smem + 1024));
+  per_sm = std::max(1, std::min(per_sm, 4));
+  return std::max(1, h->n_sms) * per_sm;
+}
+
+BpLayout bp_layout(const gpeps_handle* h, int max_iter) {
+  BpLayout L{};
+  const int D = h->D;
+  const size_t msg = align256((size_t)h->n_half * D * D * sizeof(double2));
+  int maxdeg = 0;
+  for (const SiteDesc& sd : h->sites) maxdeg = std::max(maxdeg, (int)sd.deg);
+  const int n = D + (D & 1);
+  const int64_t site_elems = 2 * ipow(D, std::max(maxdeg, 1));
+  const size_t slot = std::max((size_t)site_elems * h->elt, (size_t)7 * n * n * sizeof(double2));
+  L.slot_elems = (int64_t)(align256(slot) / 16);  // in units of 16 bytes
+  L.n_ctas = bp_ctas(h);
+  size_t o = 0;
+  L.msg_a = o;
+  o += msg;
+  L.msg_b = o;
+  o += msg;
+  L.P = o;
+  o += msg;
+  L.tasks = o;
+  o += align256(h->bp_msgs.size() * sizeof(BpMsgTask));
+  L.edges = o;
+  o += align256(h->bp_edges.size() * sizeof(BpEdgeTask));
+  L.sites = o;
+  o += align256(h->bp_sites.size() * sizeof(BpSiteTask));
+  L.residual = o;
+  o += align256((size_t)max_iter * sizeof(unsigned long long));
+  L.scratch = o;
+  o += (size_t)L.n_ctas * (size_t)L.slot_elems * 16;
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+int gpeps_query_bp_workspace(gpeps_handle* h, int32_t max_iter, size_t* bytes) {
+  if (!h || !h->bound || !bytes || max_iter < 1) return GPEPS_EINVAL;
+  bp_plan(h);
+  *bytes = bp_layout(h, max_iter).total;
+  return GPEPS_OK;
+}
+
+int gpeps_bp_regauge(gpeps_handle* h, int32_t max_iter, double tol, void* d_bp_work, size_t bp_work_bytes,
+                     int32_t* iterations, double* residual) {
+  if (!h || !h->bound || max_iter < 1 || !(tol >= 0.0) || !d_bp_work) return GPEPS_EINVAL;
+  if (reinterpret_cast<uintptr_t>(d_bp_work) & 255) return GPEPS_EINVAL;
+  bp_plan(h);
+  const BpLayout L = bp_layout(h, max_iter);
+  if (bp_work_bytes < L.total) return GPEPS_EINVAL;
+  char* w = static_cast<char*>(d_bp_work);
+  cudaStream_t s = h->stream;
+  const int D = h->D;
+  const bool c128 = h->dtype == GPEPS_C128;
+  GP_CUDA(c128 ? BpLaunch<double>::init() : BpLaunch<float>::init());
+  auto up = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(w + off, src, bytes, cudaMemcpyHostToDevice, s);
+  };
+  GP_CUDA(up(L.tasks, h->bp_msgs.data(), h->bp_msgs.size() * sizeof(BpMsgTask)));
+  GP_CUDA(up(L.edges, h->bp_edges.data(), h->bp_edges.size() * sizeof(BpEdgeTask)));
+  GP_CUDA(up(L.sites, h->bp_sites.data(), h->bp_sites.size() * sizeof(BpSiteTask)));
+  GP_CUDA(cudaMemsetAsync(w + L.residual, 0, (size_t)max_iter * sizeof(unsigned long long), s));
+  double2* cur = reinterpret_cast<double2*>(w + L.msg_a);
+  double2* nxt = reinterpret_cast<double2*>(w + L.msg_b);
+  GP_CUDA(c128 ? BpLaunch<double>::identity(cur, (int)h->n_half, D, s)
+               : BpLaunch<float>::identity(cur, (int)h->n_half, D, s));
+  const BpMsgTask* tasks = reinterpret_cast<const BpMsgTask*>(w + L.tasks);
+  unsigned long long* res = reinterpret_cast<unsigned long long*>(w + L.residual);
+  void* scratch = w + L.scratch;
+  const int64_t slot_t = L.slot_elems * 16 / (int64_t)h->elt;  // the slot in storage-type complex elements
+  int it = 0;
+  double r = 0.0;
+  while (it < max_iter) {
+    cudaError_t e = c128 ? BpLaunch<double>::message(tasks, (int)h->bp_msgs.size(), h->gamma(), h->lam(), cur, nxt,
+                                                    scratch, slot_t, D, res + it, h->flags(), L.n_ctas, s)
+                         : BpLaunch<float>::message(tasks, (int)h->bp_msgs.size(), h->gamma(), h->lam(), cur, nxt,
+                                                   scratch, slot_t, D, res + it, h->flags(), L.n_ctas, s);
+    GP_CUDA(e);
+    unsigned long long bits = 0;
+    GP_CUDA(cudaMemcpyAsync(&bits, res + it, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    double2* t = cur;
+    cur = nxt;
+    nxt = t;
+    ++it;
+    std::memcpy(&r, &bits, sizeof(r));
+    if (h->bp_msgs.empty() || r <= tol) break;
+  }
+  double2* P = reinterpret_cast<double2*>(w + L.P);
+  GP_CUDA(bp_gauge(reinterpret_cast<const BpEdgeTask*>(w + L.edges), (int)h->bp_edges.size(), cur, h->lam(), P,
+                   reinterpret_cast<double2*>(scratch), L.slot_elems, D, h->flags(), L.n_ctas, s));
+  GP_CUDA(c128 ? BpLaunch<double>::apply(reinterpret_cast<const BpSiteTask*>(w + L.sites), (int)h->bp_sites.size(),
+                                          h->gamma(), P, D, s)
+               : BpLaunch<float>::apply(reinterpret_cast<const BpSiteTask*>(w + L.sites), (int)h->bp_sites.size(),
+                                         h->gamma(), P, D, s));
+  if (iterations) *iterations = it;
+  if (residual) *residual = r;
   return GPEPS_OK;
 }
 

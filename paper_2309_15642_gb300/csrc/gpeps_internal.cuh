@@ -165,4 +165,47 @@ constexpr int kMaxSms = 256;          // SMs the shared-SM schedules have scratc
 BondFootprint step_footprint(int D, size_t elt);
 constexpr long long kWaitCycles = 4000000000LL;  // default wait limit of the fused step (~2 s of SM cycles)
 
+// ---------------------------------------------------------------- BP regauging
+// Messages live per half-edge h (a leg of a site), D x D complex FP64 each at
+// msgs + h * D * D; the gauge matrices of the half-edges likewise.
+struct BpMsgTask {
+  int64_t off;     // element offset of Gamma_i
+  int32_t deg;     // legs of site i
+  int32_t leg;     // the leg p the message is sent along
+  int32_t out;     // half-edge index of (i, p)
+  int32_t in[3];   // per leg q != p: half-edge index of the neighbour's message towards i
+  int32_t lam[3];  // per leg: lambda offset (float64 elements) of its edge
+  int32_t pad;
+};
+struct BpEdgeTask {
+  int32_t hi, hj;  // half-edge indices of the edge at its two ends
+  int32_t lam;     // lambda offset of the edge
+  int32_t pad;
+};
+struct BpSiteTask {
+  int64_t off;     // element offset of Gamma_i
+  int32_t deg;
+  int32_t h0;      // half-edge index of leg 0 (legs are h0 .. h0 + deg - 1)
+};
+constexpr int kBpThreads = 256;      // threads of every BP CTA
+constexpr double kBpGramCut = 1e-13; // eigenvalues of G below this fraction of the largest: pseudo-inverse 0
+constexpr double kBpSupportCutF32 = 1e-7;  // complex64 storage: message support lambda_k > cut * max(lambda)
+
+// Launchers (bp_kernels.cu).  T is the storage type of Gamma; messages, gauge
+// and lambda are FP64.
+template <typename T>
+struct BpLaunch {
+  static cudaError_t init();
+  static size_t message_smem(int D);
+  static cudaError_t identity(double2* msgs, int n_half, int D, cudaStream_t st);
+  static cudaError_t message(const BpMsgTask* tasks, int n_tasks, const void* gamma, const double* lam,
+                             const double2* msg_in, double2* msg_out, void* scratch, int64_t slot_elems, int D,
+                             unsigned long long* residual, int* flags, int n_ctas, cudaStream_t st);
+  static cudaError_t apply(const BpSiteTask* sites, int n_sites, void* gamma, const double2* P, int D,
+                           cudaStream_t st);
+};
+// FP64 gauge of every edge (bp_kernels.cu); scratch: 7 n x n complex per CTA, n = D rounded up to even.
+cudaError_t bp_gauge(const BpEdgeTask* edges, int n_edges, const double2* msgs, double* lam, double2* P,
+                     double2* scratch, int64_t slot_elems, int D, int* flags, int n_ctas, cudaStream_t st);
+
 }  // namespace gpeps

@@ -69,6 +69,7 @@ class GPEPS:
         check(self.lib.gpeps_n_colours(self.h, ctypes.byref(nc)), "gpeps_n_colours")
         self.n_colours = nc.value
         self.bonds_per_step = self.total_edges
+        self._bp_work, self._bp_iter = None, 0
 
     # -------------------------------------------------------------- stream order
     def _after_torch(self):
@@ -243,6 +244,27 @@ class GPEPS:
         self._before_torch()
         self.stream.synchronize()
         return z, dth
+
+    def bp_regauge(self, max_iter=100, tol=None):
+        """Belief-propagation regauging of the state (see ``gpeps_bp_regauge``).  ``tol``
+        defaults to 1e-12 (complex128) or 1e-6 (mixed: FP32 message contractions).  Returns
+        ``(iterations, residual)``."""
+        if tol is None:
+            tol = 1e-12 if self.dtype == "c128" else 1e-6
+        if self._bp_work is None or self._bp_iter < max_iter:
+            nbytes = ctypes.c_size_t()
+            check(self.lib.gpeps_query_bp_workspace(self.h, int(max_iter), ctypes.byref(nbytes)),
+                  "gpeps_query_bp_workspace")
+            self._bp_work = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=self.device)
+            self._bp_iter = int(max_iter)
+        it = ctypes.c_int32()
+        res = ctypes.c_double()
+        self._after_torch()
+        check(self.lib.gpeps_bp_regauge(self.h, int(max_iter), float(tol), ctypes.c_void_p(self._bp_work.data_ptr()),
+                                        self._bp_work.numel(), ctypes.byref(it), ctypes.byref(res)),
+              "gpeps_bp_regauge")
+        self._before_torch()
+        return it.value, res.value
 
     # -------------------------------------------------------------- state access
     def site_tensor(self, instance, site):

@@ -169,11 +169,11 @@ def test_exact_regime_needs_no_work():
 
 # ------------------------------------------------------------------ planted mistakes
 def test_planted_mistake_environment_without_lambda(monkeypatch):
-    def bad(peps, i, p, msgs):
+    def bad(peps, i, p, msgs, support_cut=su.LAMBDA_CUT):
         saved = peps.lam
         peps.lam = np.ones_like(saved)
         try:
-            return _ORIG_MESSAGE(peps, i, p, msgs)
+            return _ORIG_MESSAGE(peps, i, p, msgs, support_cut)
         finally:
             peps.lam = saved
     monkeypatch.setattr(bp, "message", bad)
@@ -182,8 +182,8 @@ def test_planted_mistake_environment_without_lambda(monkeypatch):
 
 
 def test_planted_mistake_environment_conjugated(monkeypatch):
-    def bad(peps, i, p, msgs):
-        return _ORIG_MESSAGE(peps, i, p, {k: v.conj() for k, v in msgs.items()})
+    def bad(peps, i, p, msgs, support_cut=su.LAMBDA_CUT):
+        return _ORIG_MESSAGE(peps, i, p, {k: v.conj() for k, v in msgs.items()}, support_cut)
     monkeypatch.setattr(bp, "message", bad)
     z_err, lam_err = tree_errors()
     assert max(z_err, lam_err) > 1e-6
@@ -204,7 +204,7 @@ def test_planted_mistake_same_unitary_on_both_ends(monkeypatch):
 
 
 def test_planted_mistake_no_hermitian_projection(monkeypatch):
-    def bad(peps, i, p, msgs):
+    def bad(peps, i, p, msgs, support_cut=su.LAMBDA_CUT):
         G = peps.gamma[i]
         X = G.conj()
         for q, k in enumerate(peps.nb[i]):
@@ -224,3 +224,52 @@ def test_planted_mistake_no_hermitian_projection(monkeypatch):
         res = np.inf
     assert res > 1e-6
 
+
+
+
+
+class _Residue(su.GPEPS):
+    """Simple update that leaves rounding residue in the empty directions of a rank-deficient
+    bond, as an FP32 eigensolver does: lambda ~ 1e-16 .. 1e-8 there, with random Gamma columns
+    at one end (the state changes by less than 1e-8)."""
+
+    def __init__(self, *a, **k):
+        self.rng = np.random.default_rng(5)
+        super().__init__(*a, **k)
+
+    def bond_update(self, e):
+        super().bond_update(e)
+        lam = self.lam[e]
+        empty = lam <= 1e-10 * lam.max()
+        if not empty.any():
+            return
+        lam[empty] = 10.0 ** self.rng.uniform(-16, -8, int(empty.sum()))
+        i, j = int(self.edges[e][0]), int(self.edges[e][1])
+        p = self.leg(i, j)
+        T = np.moveaxis(self.gamma[i], p + 1, -1).copy()
+        idx = np.nonzero(empty)[0]
+        shape = T[..., idx].shape
+        T[..., idx] = self.rng.normal(size=shape) + 1j * self.rng.normal(size=shape)
+        self.gamma[i] = np.moveaxis(T, -1, p + 1)
+
+
+def _residue_error(support_cut):
+    clean = su.GPEPS(M127, E127, 16)
+    dirty = _Residue(M127, E127, 16)
+    for _ in range(2):                                  # Schmidt rank <= 4 < D
+        clean.step(0.6)
+        dirty.step(0.6)
+    assert np.abs(dirty.expect_z() - clean.expect_z()).max() < 1e-6
+    bp.regauge(clean, 100, 1e-13)
+    bp.regauge(dirty, 100, 1e-13, support_cut=support_cut)
+    return float(np.abs(dirty.expect_z() - clean.expect_z()).max())
+
+
+def test_messages_live_on_the_lambda_support():
+    """Rank-deficient bonds with rounding residue below the support cut in their empty
+    directions: the regauge does not see the residue (the FP32 resolution 1e-7)."""
+    assert _residue_error(1e-7) < 1e-8
+
+
+def test_planted_mistake_no_support_restriction():
+    assert _residue_error(0.0) > 1e-3
