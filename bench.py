@@ -15,6 +15,10 @@ times of the dominant kernel against the FP64 ALU roofline, an end-to-end
 number through the public API with host buffers, and the FP64 CPU oracle
 timed on a bounded sample.  ``--impl reference`` times the oracle alone.
 
+``--bp`` times Trotter steps with a belief-propagation regauge after each (the
+paper's BP comparison): value = Trotter steps/s of the batch, with the BP
+iterations, the per-phase device times and the message kernel's roofline.
+
 Multi-GPU (torchrun): replicas only.  Every rank evolves its own copy of the
 batch; there is no collective on the data path; value = all ranks' bond
 updates / max-over-ranks time.
@@ -54,6 +58,10 @@ def parse():
     ap.add_argument("--schedule", type=int, default=None,
                     help="with --no-autotune: bond schedule (0 one CTA per bond; 1, 2, 3 work queue with 1, 2, 4 "
                          "CTAs per SM)")
+    ap.add_argument("--bp", action="store_true",
+                    help="time Trotter steps with a belief-propagation regauge after each (the paper's BP "
+                         "comparison) instead of the plain step")
+    ap.add_argument("--bp-max-iter", type=int, default=200)
     ap.add_argument("--floor-rel", type=float, default=None,
                     help="with --no-autotune: FP64 Jacobi floor (fraction of the trace) of the mixed path")
     return ap.parse_args()
@@ -145,6 +153,130 @@ def bond_fixed_flops(graphs, D, dtype):
 
 # flops of one executed Jacobi 2x2 block update (both sides) and one eigenvector pair update
 JACOBI_BLOCK_FLOPS, JACOBI_VEC_FLOPS = 72, 18
+
+
+# FP32 vector peak from the unit counts and the maximum SM clock: 152 SMs x 128 FP32 FMA per
+# clock x 2 flops x 2.07 GHz
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
+
+
+def bp_message_flops(graphs, D):
+    """Real flops of one BP iteration (every message of the batch): per message of a site of
+    degree z, (z - 1) leg products of 2 D^(z+1) complex MACs and the upper triangle of the Gram,
+    D (D + 1) / 2 entries of 2 D^(z-1) complex MACs; 8 real flops per complex MAC."""
+    import numpy as np
+    total = 0
+    for n, edges in graphs:
+        deg = np.bincount(np.asarray(edges).reshape(-1), minlength=n)
+        for z in deg:
+            z = int(z)
+            if z == 0:
+                continue
+            cmac = (z - 1) * 2 * D ** (z + 1) + D * (D + 1) // 2 * 2 * D ** (z - 1)
+            total += z * 8 * cmac
+    return float(total)
+
+
+def cpu_oracle_bp(w, seconds_cap=10.0):
+    """The FP64 oracle's BP messages on a bounded sample: the first lattice of the batch after
+    two Trotter steps, message updates (the half-edges in turn, degree-3 sites first, from
+    identity messages) until ``seconds_cap`` seconds have passed.  Returns BP message updates/s."""
+    import numpy as np
+    from oracle import bp
+    from oracle.su import GPEPS as OraclePEPS
+    from workloads import kick_angles
+    (n, edges) = w.graphs()[0]
+    th = kick_angles(w)[0]
+    peps = OraclePEPS(n, edges, w.D)
+    for _ in range(2):
+        peps.step(th)
+    msgs = bp.identity_messages(peps)
+    keys = sorted(msgs, key=lambda k: -len(peps.nb[k[0]]))
+    t0 = time.perf_counter()
+    done = 0
+    while time.perf_counter() - t0 < seconds_cap:
+        i, p = keys[done % len(keys)]
+        bp.message(peps, i, p, msgs)
+        done += 1
+    dt = time.perf_counter() - t0
+    deg = np.array([len(peps.nb[keys[k % len(keys)][0]]) for k in range(done)])
+    return {"value": done / dt, "unit": "BP message updates/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} message updates ({int((deg == 3).sum())} of degree-3 sites) of the {n}-qubit "
+                      f"lattice at D={w.D} after 2 steps, numpy FP64, {dt:.1f} s"}
+
+
+def run_bp(args, local_rank):
+    """Trotter steps with a BP regauge after each: W untimed, then K timed (CUDA events on the
+    library's stream around step + regauge, the regauge's per-iteration convergence test
+    included)."""
+    import torch
+    from paper_2309_15642_gb300 import _build
+    _build.build()
+    from paper_2309_15642_gb300 import GPEPS
+    from workloads import kick_angles, workload
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = workload(args.workload)
+    graphs = w.graphs()
+    theta = [float(t[0]) for t in kick_angles(w)]
+    K, W = args.steps, args.warmup
+    g = GPEPS(graphs, w.D, dtype=args.dtype, device=str(dev))
+    tuning = None
+    if not args.no_autotune:
+        from paper_2309_15642_gb300.autotune import autotune
+        best, _ = autotune(g, theta)
+        tuning = best
+    g.reset()
+    th = torch.tensor(theta, dtype=torch.float64, device=dev)
+    out = torch.empty((1, g.n_instances), dtype=torch.float64, device=dev)
+    for _ in range(W):
+        g.step(1, th, out=out)
+        g.bp_regauge(args.bp_max_iter)
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(local_rank)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters, phases, su_ms = [], [0.0, 0.0, 0.0], 0.0
+    means = []
+    e0.record(g.stream)
+    for _ in range(K):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(g.stream)
+        g.step(1, th, out=out)
+        b.record(g.stream)
+        it, res, ms3 = g.bp_regauge(args.bp_max_iter, profile=True)
+        b.synchronize()
+        su_ms += a.elapsed_time(b)
+        iters.append(it)
+        phases = [x + y for x, y in zip(phases, ms3)]
+        z, m = g.expect_z()
+        means.append(m.cpu().numpy().tolist())
+    e1.record(g.stream)
+    e1.synchronize()
+    torch.cuda.synchronize(dev)
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    flags = g.status()
+    n_msg = sum(2 * len(e) for _, e in graphs)
+    flops_iter = bp_message_flops(graphs, w.D)
+    msg_launch_ms = phases[0] / max(sum(iters), 1)
+    achieved = flops_iter / (msg_launch_ms * 1e-3) / 1e9
+    peak = FP64_PEAK_GFLOPS if args.dtype == "c128" else FP32_PEAK_GFLOPS
+    roofline = {"kernel": "bp_message_kernel (every BP message of the batch: leg products with the neighbours' "
+                          "environments and the Hermitian Gram, one launch per iteration)",
+                "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "GFLOP/s (FP64)" if args.dtype == "c128" else "GFLOP/s (FP32)",
+                "frac": achieved / peak,
+                "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x 2.07 GHz" if args.dtype == "c128"
+                                else "derived: 152 SMs x 128 FP32 FMA/clock x 2 flops x 2.07 GHz"),
+                "traffic": None, "flops_per_launch": flops_iter, "launch_ms": msg_launch_ms,
+                "units_per_launch": n_msg}
+    e2e_unit = "Trotter steps/s with BP regauging"
+    g.close()
+    return dict(value=K / (ms * 1e-3), ms=ms, clocks=ck, flags=flags, roofline=roofline, iters=iters,
+                phases_ms=[x / K for x in phases], su_ms=su_ms / K, n_msg=n_msg, means=means, w=w,
+                tuning=tuning, e2e_unit=e2e_unit)
 
 
 def big_end_flops(graphs, D):
@@ -432,6 +564,36 @@ def main():
             "cpu_baseline": {"value": v, "unit": "bond updates/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "bond updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    if args.bp:
+        if rank != 0:
+            return
+        r = run_bp(args, local_rank)
+        cpu = None if args.no_cpu else cpu_oracle_bp(r["w"])
+        K = args.steps
+        it_mean = sum(r["iters"]) / max(len(r["iters"]), 1)
+        msg_rate = r["n_msg"] * sum(r["iters"]) / max(r["phases_ms"][0] * K * 1e-3, 1e-12)
+        print(json.dumps({
+            "metric": "Trotter steps/s with a BP regauge after each step (the paper's BP comparison)",
+            "value": r["value"], "unit": "Trotter steps/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
+            "ms_per_step": r["ms"] / max(K, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64+f64" if args.dtype == "mixed" else "c128", "data": "synthetic",
+            "config": {"workload": r["w"].name, "lattices": [list(l) for l in r["w"].lattices], "D": r["w"].D,
+                       "theta": list(r["w"].theta), "messages_per_iteration": r["n_msg"],
+                       "timed_steps": f"{args.warmup + 1}..{args.warmup + K} from |0...0>",
+                       "l2": "state larger than L2 (no flush)"},
+            "bp": {"iterations_per_step": r["iters"], "mean_iterations": it_mean,
+                   "ms_per_step": {"trotter_step": r["su_ms"], "messages": r["phases_ms"][0],
+                                   "gauge": r["phases_ms"][1], "apply": r["phases_ms"][2]},
+                   "message_updates_per_s": msg_rate},
+            "roofline": r["roofline"], "clocks": r["clocks"], "cpu_baseline": cpu,
+            "e2e": {"value": r["value"], "unit": r["e2e_unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step":
+                    8 * len(r["w"].lattices)},
+            # per step: the fused Trotter step (kick, step kernel, readout, mean), the regauge
+            # (identity messages, one message launch per iteration, gauge, apply), expect_z (2)
+            "gpu_launches": sum(r["iters"]) + 9 * K, "device_flags": r["flags"],
+            "tuning": r["tuning"], "mean_z_last_step": r["means"][-1] if r["means"] else None}))
         return
 
     if world > 1:

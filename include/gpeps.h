@@ -319,6 +319,8 @@ int gpeps_grad(gpeps_handle* h, const double* theta, int32_t n_steps, int32_t ck
  *               work lists and one global scratch slot per CTA)
  *   iterations: host, or NULL: BP iterations run
  *   residual:   host, or NULL: the largest elementwise change of the last one
+ *   phase_ms:   host float[3], or NULL: device milliseconds (CUDA events) of the
+ *               message launches (summed over iterations), the gauge and the apply
  * Synchronises the stream once per iteration (the convergence test), so it
  * cannot be captured into a CUDA graph.  Device flags: GPEPS_FLAG_NOCONV (a
  * gauge eigenproblem hit its sweep cap), GPEPS_FLAG_NUMERIC (a message with
@@ -328,7 +330,7 @@ int gpeps_grad(gpeps_handle* h, const double* theta, int32_t n_steps, int32_t ck
  */
 int gpeps_query_bp_workspace(gpeps_handle* h, int32_t max_iter, size_t* bytes);
 int gpeps_bp_regauge(gpeps_handle* h, int32_t max_iter, double tol, void* d_bp_work, size_t bp_work_bytes,
-                     int32_t* iterations, double* residual);
+                     int32_t* iterations, double* residual, float* phase_ms);
 
 /* Totals of the batch: qubits, edges, bond updates per Trotter step. */
 int gpeps_sizes(const gpeps_handle* h, int64_t* total_qubits, int64_t* total_edges);

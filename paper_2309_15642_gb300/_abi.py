@@ -40,7 +40,7 @@ SIGNATURES = {
                            c_size_t]),
     "gpeps_query_bp_workspace": (c_int, [c_void_p, c_int32, POINTER(c_size_t)]),
     "gpeps_bp_regauge": (c_int, [c_void_p, c_int32, c_double, c_void_p, c_size_t, POINTER(c_int32),
-                                 POINTER(c_double)]),
+                                 POINTER(c_double), c_void_p]),
     "gpeps_sizes": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
     "gpeps_sweeps": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
     "gpeps_bond_phase_cycles": (c_int, [c_void_p, POINTER(c_int64)]),

@@ -1101,7 +1101,7 @@ int gpeps_query_bp_workspace(gpeps_handle* h, int32_t max_iter, size_t* bytes) {
 }
 
 int gpeps_bp_regauge(gpeps_handle* h, int32_t max_iter, double tol, void* d_bp_work, size_t bp_work_bytes,
-                     int32_t* iterations, double* residual) {
+                     int32_t* iterations, double* residual, float* phase_ms) {
   if (!h || !h->bound || max_iter < 1 || !(tol >= 0.0) || !d_bp_work) return GPEPS_EINVAL;
   if (reinterpret_cast<uintptr_t>(d_bp_work) & 255) return GPEPS_EINVAL;
   bp_plan(h);
@@ -1130,15 +1130,34 @@ int gpeps_bp_regauge(gpeps_handle* h, int32_t max_iter, double tol, void* d_bp_w
   const int64_t slot_t = L.slot_elems * 16 / (int64_t)h->elt;  // the slot in storage-type complex elements
   int it = 0;
   double r = 0.0;
+  // optional device times of the phases (CUDA events on the stream): messages, gauge, apply
+  struct Events {
+    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+    ~Events() {
+      for (auto& x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } evs;
+  cudaEvent_t* ev = evs.e;
+  float msg_ms = 0.f;
+  if (phase_ms)
+    for (int k = 0; k < 4; ++k) GP_CUDA(cudaEventCreate(&ev[k]));
   while (it < max_iter) {
+    if (phase_ms) GP_CUDA(cudaEventRecord(ev[0], s));
     cudaError_t e = c128 ? BpLaunch<double>::message(tasks, (int)h->bp_msgs.size(), h->gamma(), h->lam(), cur, nxt,
                                                     scratch, slot_t, D, res + it, h->flags(), L.n_ctas, s)
                          : BpLaunch<float>::message(tasks, (int)h->bp_msgs.size(), h->gamma(), h->lam(), cur, nxt,
                                                    scratch, slot_t, D, res + it, h->flags(), L.n_ctas, s);
     GP_CUDA(e);
+    if (phase_ms) GP_CUDA(cudaEventRecord(ev[1], s));
     unsigned long long bits = 0;
     GP_CUDA(cudaMemcpyAsync(&bits, res + it, sizeof(bits), cudaMemcpyDeviceToHost, s));
     GP_CUDA(cudaStreamSynchronize(s));
+    if (phase_ms) {
+      float t = 0.f;
+      GP_CUDA(cudaEventElapsedTime(&t, ev[0], ev[1]));
+      msg_ms += t;
+    }
     double2* t = cur;
     cur = nxt;
     nxt = t;
@@ -1147,12 +1166,24 @@ int gpeps_bp_regauge(gpeps_handle* h, int32_t max_iter, double tol, void* d_bp_w
     if (h->bp_msgs.empty() || r <= tol) break;
   }
   double2* P = reinterpret_cast<double2*>(w + L.P);
+  if (phase_ms) GP_CUDA(cudaEventRecord(ev[1], s));
   GP_CUDA(bp_gauge(reinterpret_cast<const BpEdgeTask*>(w + L.edges), (int)h->bp_edges.size(), cur, h->lam(), P,
                    reinterpret_cast<double2*>(scratch), L.slot_elems, D, h->flags(), L.n_ctas, s));
+  if (phase_ms) GP_CUDA(cudaEventRecord(ev[2], s));
   GP_CUDA(c128 ? BpLaunch<double>::apply(reinterpret_cast<const BpSiteTask*>(w + L.sites), (int)h->bp_sites.size(),
                                           h->gamma(), P, D, s)
                : BpLaunch<float>::apply(reinterpret_cast<const BpSiteTask*>(w + L.sites), (int)h->bp_sites.size(),
                                          h->gamma(), P, D, s));
+  if (phase_ms) {
+    GP_CUDA(cudaEventRecord(ev[3], s));
+    GP_CUDA(cudaEventSynchronize(ev[3]));
+    float tg = 0.f, ta = 0.f;
+    GP_CUDA(cudaEventElapsedTime(&tg, ev[1], ev[2]));
+    GP_CUDA(cudaEventElapsedTime(&ta, ev[2], ev[3]));
+    phase_ms[0] = msg_ms;
+    phase_ms[1] = tg;
+    phase_ms[2] = ta;
+  }
   if (iterations) *iterations = it;
   if (residual) *residual = r;
   return GPEPS_OK;

@@ -245,10 +245,11 @@ class GPEPS:
         self.stream.synchronize()
         return z, dth
 
-    def bp_regauge(self, max_iter=100, tol=None):
+    def bp_regauge(self, max_iter=100, tol=None, profile=False):
         """Belief-propagation regauging of the state (see ``gpeps_bp_regauge``).  ``tol``
         defaults to 1e-12 (complex128) or 1e-6 (mixed: FP32 message contractions).  Returns
-        ``(iterations, residual)``."""
+        ``(iterations, residual)``, and with ``profile`` also the device milliseconds of the
+        message launches, the gauge and the apply."""
         if tol is None:
             tol = 1e-12 if self.dtype == "c128" else 1e-6
         if self._bp_work is None or self._bp_iter < max_iter:
@@ -259,11 +260,15 @@ class GPEPS:
             self._bp_iter = int(max_iter)
         it = ctypes.c_int32()
         res = ctypes.c_double()
+        ms = (ctypes.c_float * 3)()
         self._after_torch()
         check(self.lib.gpeps_bp_regauge(self.h, int(max_iter), float(tol), ctypes.c_void_p(self._bp_work.data_ptr()),
-                                        self._bp_work.numel(), ctypes.byref(it), ctypes.byref(res)),
+                                        self._bp_work.numel(), ctypes.byref(it), ctypes.byref(res),
+                                        ctypes.cast(ms, ctypes.c_void_p) if profile else None),
               "gpeps_bp_regauge")
         self._before_torch()
+        if profile:
+            return it.value, res.value, tuple(float(x) for x in ms)
         return it.value, res.value
 
     # -------------------------------------------------------------- state access

@@ -183,7 +183,7 @@ def test_workspace_errors():
     small = torch.empty(256, dtype=torch.uint8, device="cuda")
     it, res = ctypes.c_int32(), ctypes.c_double()
     assert g.lib.gpeps_bp_regauge(g.h, 10, 1e-12, ctypes.c_void_p(small.data_ptr()), 256, ctypes.byref(it),
-                                  ctypes.byref(res)) == 1
+                                  ctypes.byref(res), None) == 1
     assert g.lib.gpeps_bp_regauge(g.h, 10, -1.0, ctypes.c_void_p(small.data_ptr()), nbytes.value,
-                                  ctypes.byref(it), ctypes.byref(res)) == 1
+                                  ctypes.byref(it), ctypes.byref(res), None) == 1
     g.close()
