@@ -19,7 +19,8 @@
 //            keeps it exactly so (its rounding noise would otherwise grow along
 //            the loops of the lattice).  Normalised to unit trace in FP64; the
 //            largest elementwise change is reduced into the iteration's residual.
-//   gauge    one CTA per edge, FP64: the Hermitian square root R and pseudo-
+//   gauge    one CTA per edge (the square roots of G in FP32 for complex64
+//            storage, everything else FP64): the Hermitian square root R and pseudo-
 //            inverse R^+ of G = conj(m) at both ends (Jacobi eigenproblems),
 //            C = R_i diag(lambda) R_j^T, its left singular vectors U from the
 //            eigenproblem of C C^H, and Y = C^T conj(U), whose column norms are the
@@ -46,7 +47,12 @@ namespace gpeps {
 
 namespace {
 
-constexpr int kGramPer = (kMaxD * (kMaxD + 1) / 2 + kBpThreads - 1) / kBpThreads;  // upper-triangle pairs per thread
+// Upper-triangle pairs per thread of the message Gram: D <= 32 and D <= 64.
+constexpr int kGramPerSmall = (32 * 33 / 2 + kBpThreads - 1) / kBpThreads;
+constexpr int kGramPerLarge = (kMaxD * (kMaxD + 1) / 2 + kBpThreads - 1) / kBpThreads;
+// The apply runs in FP32 for complex64 storage when every entry of a site's
+// gauge matrices is at most this large (well-conditioned gauge), else in FP64.
+constexpr double kApplyF32Max = 64.0;
 
 __device__ __forceinline__ int64_t leg_addr(int c, int b, int I, int D) {
   const int o = c / I;
@@ -65,25 +71,53 @@ __device__ __forceinline__ void tile_pos(int idx, int I, int D, int& j, int& b) 
   }
 }
 
-// dst(c, b) = sum_b' M[b][b'] src(c, b') over the ncols columns of the leg with
-// stride I (conj(src) when kConj), in the arithmetic of TC (src and dst hold TS).
-// M: shared [D][D + 1]; tile: shared [32][D + 1], both TC.  dst may be src: a
-// tile is read completely before any of it is written.
-template <typename TS, typename TC, bool kConj>
-__device__ void leg_product(V2<TS>* dst, const V2<TS>* src, int ncols, int I, int D, const V2<TC>* M,
-                            V2<TC>* tile) {
+// dst(c, b) = sum_b' M[b][b'] src(c, b') over the columns c in [c_begin, c_end)
+// of the leg with stride I (conj(src) when kConj), in the arithmetic of TC
+// (src and dst hold TS).  Element (c, b) sits at leg_addr(c, b) - src_off in
+// src and at leg_addr(c, b) - dst_off in dst.  M: shared [D][D + 1]; tile:
+// shared [32][D + 1], both TC.  The next tile is loaded into registers (kL per
+// thread, 32 D <= kL blockDim) while the current one is multiplied.  dst may be
+// src: the columns of a tile are read completely before any of them is written,
+// and the prefetched columns are not the ones being written.
+template <typename TS, typename TC, bool kConj, int kL>
+__device__ void leg_product(V2<TS>* dst, int64_t dst_off, const V2<TS>* src, int64_t src_off, int c_begin,
+                            int c_end, int I, int D, const V2<TC>* M, V2<TC>* tile) {
   const int ld = D + 1;
-  for (int c0 = 0; c0 < ncols; c0 += 32) {
-    const int nc = min(32, ncols - c0);
-    for (int idx = threadIdx.x; idx < 32 * D; idx += blockDim.x) {
+  constexpr int kB = kL > 0 ? kL : 1;
+  V2<TS> buf[kB];
+  auto fetch = [&](int c0) {
+    const int nc = min(32, c_end - c0);
+#pragma unroll
+    for (int k = 0; k < kL; ++k) {
+      const int idx = threadIdx.x + k * blockDim.x;
       int j, b;
       tile_pos(idx, I, D, j, b);
-      if (j < nc) {
-        const V2<TS> v = src[leg_addr(c0 + j, b, I, D)];
-        tile[j * ld + b] = mk<TC>((TC)v.x, kConj ? -(TC)v.y : (TC)v.y);
+      buf[k] = (idx < 32 * D && j < nc) ? src[leg_addr(c0 + j, b, I, D) - src_off] : mk<TS>(0, 0);
+    }
+  };
+  if (kL > 0 && c_begin < c_end) fetch(c_begin);
+  for (int c0 = c_begin; c0 < c_end; c0 += 32) {
+    const int nc = min(32, c_end - c0);
+    if constexpr (kL > 0) {
+#pragma unroll
+      for (int k = 0; k < kL; ++k) {
+        const int idx = threadIdx.x + k * blockDim.x;
+        int j, b;
+        tile_pos(idx, I, D, j, b);
+        if (idx < 32 * D) tile[j * ld + b] = mk<TC>((TC)buf[k].x, kConj ? -(TC)buf[k].y : (TC)buf[k].y);
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < 32 * D; idx += blockDim.x) {
+        int j, b;
+        tile_pos(idx, I, D, j, b);
+        if (j < nc) {
+          const V2<TS> v = src[leg_addr(c0 + j, b, I, D) - src_off];
+          tile[j * ld + b] = mk<TC>((TC)v.x, kConj ? -(TC)v.y : (TC)v.y);
+        }
       }
     }
     __syncthreads();
+    if (kL > 0 && c0 + 32 < c_end) fetch(c0 + 32);
     for (int idx = threadIdx.x; idx < 32 * D; idx += blockDim.x) {
       const int b = idx >> 5, j = idx & 31;
       if (j < nc) {
@@ -91,76 +125,123 @@ __device__ void leg_product(V2<TS>* dst, const V2<TS>* src, int ncols, int I, in
         const V2<TC>* mr = M + b * ld;
         const V2<TC>* tr = tile + j * ld;
         for (int k = 0; k < D; ++k) fma_c<TC>(acc, mr[k], tr[k]);
-        dst[leg_addr(c0 + j, b, I, D)] = mk<TS>((TS)acc.x, (TS)acc.y);
+        dst[leg_addr(c0 + j, b, I, D) - dst_off] = mk<TS>((TS)acc.x, (TS)acc.y);
       }
     }
     __syncthreads();
   }
 }
 
-// Mo[a][a'] = sum_c A(c, a) B(c, a') (B = conj(A) when kConjB) for a <= a', the
-// lower triangle its conjugate mirror; FP64 result in shared Mo [D][D].
-template <typename T, bool kConjB>
-__device__ void leg_gram(const V2<T>* A, const V2<T>* B, int ncols, int I, int D, V2<T>* tA, V2<T>* tB,
-                         double2* Mo) {
-  const int ld = D + 1;
-  const int npairs = D * (D + 1) / 2;
-  int pa[kGramPer], pb[kGramPer];
-  V2<T> acc[kGramPer];
+// The upper triangle of m[a][a'] = sum_c A(c, a) B(c, a') over the columns of
+// a leg (B = conj(A) when kConjB), accumulated in registers over column ranges
+// (K pairs a <= a' per thread), then stored with its conjugate mirror.
+template <typename T, int K>
+struct GramAcc {
+  int pa[K], pb[K];
+  V2<T> acc[K];
+
+  __device__ void init(int D) {
+    const int npairs = D * (D + 1) / 2;
 #pragma unroll
-  for (int k = 0; k < kGramPer; ++k) {
-    const int u = threadIdx.x + k * blockDim.x;
-    int r = 0, c = 0;
-    if (u < npairs) {
-      r = (int)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
-      while (r * (r + 1) / 2 > u) --r;
-      while ((r + 1) * (r + 2) / 2 <= u) ++r;
-      c = u - r * (r + 1) / 2;
-    }
-    pa[k] = c;  // a <= a'
-    pb[k] = r;
-    acc[k] = mk<T>(0, 0);
-  }
-  for (int c0 = 0; c0 < ncols; c0 += 32) {
-    const int nc = min(32, ncols - c0);
-    for (int idx = threadIdx.x; idx < 32 * D; idx += blockDim.x) {
-      int j, b;
-      tile_pos(idx, I, D, j, b);
-      V2<T> va = mk<T>(0, 0), vb = mk<T>(0, 0);
-      if (j < nc) {
-        const int64_t ad = leg_addr(c0 + j, b, I, D);
-        va = A[ad];
-        vb = B[ad];
-        if (kConjB) vb.y = -vb.y;
+    for (int k = 0; k < K; ++k) {
+      const int u = threadIdx.x + k * blockDim.x;
+      int r = 0, c = 0;
+      if (u < npairs) {
+        r = (int)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
+        while (r * (r + 1) / 2 > u) --r;
+        while ((r + 1) * (r + 2) / 2 <= u) ++r;
+        c = u - r * (r + 1) / 2;
       }
-      tA[j * ld + b] = va;
-      tB[j * ld + b] = vb;
+      pa[k] = c;
+      pb[k] = r;
+      acc[k] = mk<T>(0, 0);
     }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kGramPer; ++k) {
-      if (threadIdx.x + k * blockDim.x < npairs) {
-        const V2<T>* ta = tA + pa[k];
-        const V2<T>* tb = tB + pb[k];
-        for (int j = 0; j < 32; ++j) fma_c<T>(acc[k], ta[j * ld], tb[j * ld]);
-      }
-    }
-    __syncthreads();
   }
+
+  // A(c, b) at A[leg_addr(c, b)], B(c, b) at B[leg_addr(c, b) - b_off], c in [c_begin, c_end);
+  // the next tile is loaded into registers (kL per thread) while the current one is summed
+  template <bool kConjB, int kL>
+  __device__ void add(const V2<T>* A, const V2<T>* B, int64_t b_off, int c_begin, int c_end, int I, int D,
+                      V2<T>* tA, V2<T>* tB) {
+    const int ld = D + 1;
+    const int npairs = D * (D + 1) / 2;
+    constexpr int kB = kL > 0 ? kL : 1;
+    V2<T> ba[kB], bb[kB];
+    auto fetch = [&](int c0) {
+      const int nc = min(32, c_end - c0);
 #pragma unroll
-  for (int k = 0; k < kGramPer; ++k) {
-    if (threadIdx.x + k * blockDim.x < npairs) {
-      const int a = pa[k], b = pb[k];
-      if (a == b) {
-        Mo[a * D + a] = make_double2((double)acc[k].x, 0.0);
+      for (int k = 0; k < kL; ++k) {
+        const int idx = threadIdx.x + k * blockDim.x;
+        int j, b;
+        tile_pos(idx, I, D, j, b);
+        ba[k] = mk<T>(0, 0);
+        bb[k] = mk<T>(0, 0);
+        if (idx < 32 * D && j < nc) {
+          const int64_t ad = leg_addr(c0 + j, b, I, D);
+          ba[k] = A[ad];
+          bb[k] = B[ad - b_off];
+        }
+      }
+    };
+    if (kL > 0 && c_begin < c_end) fetch(c_begin);
+    for (int c0 = c_begin; c0 < c_end; c0 += 32) {
+      if constexpr (kL > 0) {
+#pragma unroll
+        for (int k = 0; k < kL; ++k) {
+          const int idx = threadIdx.x + k * blockDim.x;
+          int j, b;
+          tile_pos(idx, I, D, j, b);
+          if (idx < 32 * D) {
+            tA[j * ld + b] = ba[k];
+            tB[j * ld + b] = kConjB ? mk<T>(bb[k].x, -bb[k].y) : bb[k];
+          }
+        }
       } else {
-        Mo[a * D + b] = make_double2((double)acc[k].x, (double)acc[k].y);
-        Mo[b * D + a] = make_double2((double)acc[k].x, -(double)acc[k].y);
+        const int nc = min(32, c_end - c0);
+        for (int idx = threadIdx.x; idx < 32 * D; idx += blockDim.x) {
+          int j, b;
+          tile_pos(idx, I, D, j, b);
+          V2<T> va = mk<T>(0, 0), vb = mk<T>(0, 0);
+          if (j < nc) {
+            const int64_t ad = leg_addr(c0 + j, b, I, D);
+            va = A[ad];
+            vb = B[ad - b_off];
+            if (kConjB) vb.y = -vb.y;
+          }
+          tA[j * ld + b] = va;
+          tB[j * ld + b] = vb;
+        }
+      }
+      __syncthreads();
+      if (kL > 0 && c0 + 32 < c_end) fetch(c0 + 32);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (threadIdx.x + k * blockDim.x < npairs) {
+          const V2<T>* ta = tA + pa[k];
+          const V2<T>* tb = tB + pb[k];
+          for (int j = 0; j < 32; ++j) fma_c<T>(acc[k], ta[j * ld], tb[j * ld]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  __device__ void store(double2* Mo, int D) const {
+    const int npairs = D * (D + 1) / 2;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (threadIdx.x + k * blockDim.x < npairs) {
+        const int a = pa[k], b = pb[k];
+        if (a == b) {
+          Mo[a * D + a] = make_double2((double)acc[k].x, 0.0);
+        } else {
+          Mo[a * D + b] = make_double2((double)acc[k].x, (double)acc[k].y);
+          Mo[b * D + a] = make_double2((double)acc[k].x, -(double)acc[k].y);
+        }
       }
     }
   }
-  __syncthreads();
-}
+};
 
 __device__ __forceinline__ double block_max(double v, double* red) {
   for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
@@ -183,7 +264,10 @@ __global__ void bp_identity_kernel(double2* msgs, int64_t n, int D) {
   msgs[i] = make_double2(a == b ? 1.0 / D : 0.0, 0.0);
 }
 
-template <typename T>
+// One BP iteration.  A message is computed one physical component s at a time
+// (the products never mix s), so the scratch tensor X of a CTA holds D^deg
+// elements and the launch's scratch stays in L2.
+template <typename T, int K>
 __global__ void __launch_bounds__(kBpThreads) bp_message_kernel(const BpMsgTask* __restrict__ tasks, int n_tasks,
                                                                 const V2<T>* __restrict__ gamma,
                                                                 const double* __restrict__ lam,
@@ -195,41 +279,56 @@ __global__ void __launch_bounds__(kBpThreads) bp_message_kernel(const BpMsgTask*
   __shared__ double red[32];
   __shared__ double s_trace, s_cut;
   const int ld = D + 1;
-  V2<T>* M = reinterpret_cast<V2<T>*>(smem);  // [D][D + 1]
+  V2<T>* M = reinterpret_cast<V2<T>*>(smem);  // [D][D + 1]: the environment of one other leg
   V2<T>* tA = M + D * ld;                      // [32][D + 1]
   V2<T>* tB = tA + 32 * ld;                    // [32][D + 1]
   double2* Mo = reinterpret_cast<double2*>(tB + 32 * ld);  // [D][D]
   V2<T>* X = scratch + (int64_t)blockIdx.x * slot_elems;
+  // tiles are loaded straight into shared memory: a register prefetch of the next
+  // tile, or a 2 x D/16 register tile per thread, cost more in occupancy than
+  // they saved (measured: 5.26 and 5.51 ms against 4.76 ms per launch at D = 32)
+  constexpr int kL = 0;
   double my_res = 0.0;
   bool bad = false;
   for (int t = blockIdx.x; t < n_tasks; t += gridDim.x) {
     const BpMsgTask tk = tasks[t];
     const V2<T>* G = gamma + tk.off;
     const int z = tk.deg, p = tk.leg;
-    int ncols = 2;
-    for (int k = 1; k < z; ++k) ncols *= D;
-    bool first = true;
-    for (int q = 0; q < z; ++q) {
-      if (q == p) continue;
-      const double* lq = lam + tk.lam[q];
-      const double2* mi = msg_in + (int64_t)tk.in[q] * D * D;
-      for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
-        const int b = idx / D, bb = idx - b * D;
-        const double2 v = mi[idx];
-        const double w = lq[b] * lq[bb];
-        M[b * ld + bb] = mk<T>((T)(v.x * w), (T)(v.y * w));
-      }
-      __syncthreads();
-      int I = 1;
-      for (int k = q + 1; k < z; ++k) I *= D;
-      if (first) leg_product<T, T, true>(X, G, ncols, I, D, M, tA);
-      else leg_product<T, T, false>(X, X, ncols, I, D, M, tA);
-      first = false;
-    }
+    int half = 1;  // columns (and elements) per physical component: D^(deg-1) and D^deg
+    for (int k = 1; k < z; ++k) half *= D;
+    const int64_t sz = (int64_t)half * D;
+    int legs[2] = {-1, -1}, nl = 0;
+    for (int q = 0; q < z; ++q)
+      if (q != p) legs[nl++] = q;
     int Ip = 1;
     for (int k = p + 1; k < z; ++k) Ip *= D;
-    if (first) leg_gram<T, true>(G, G, ncols, Ip, D, tA, tB, Mo);
-    else leg_gram<T, false>(G, X, ncols, Ip, D, tA, tB, Mo);
+    GramAcc<T, K> gram;
+    gram.init(D);
+    for (int s = 0; s < 2; ++s) {
+      const int c0 = s * half, c1 = c0 + half;
+      const int64_t off = s * sz;
+      for (int l = 0; l < nl; ++l) {
+        // E_q = diag(lambda_q) m_q diag(lambda_q); the product's first barrier
+        // (after its first tile load) orders these writes before any read of M,
+        // and the previous product's last barrier orders them after its reads
+        const double* lq = lam + tk.lam[legs[l]];
+        const double2* mi = msg_in + (int64_t)tk.in[legs[l]] * D * D;
+        for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
+          const int b = idx / D, bb = idx - b * D;
+          const double2 v = mi[idx];
+          const double w = lq[b] * lq[bb];
+          M[b * ld + bb] = mk<T>((T)(v.x * w), (T)(v.y * w));
+        }
+        int I = 1;
+        for (int k = legs[l] + 1; k < z; ++k) I *= D;
+        if (l == 0) leg_product<T, T, true, kL>(X, off, G, 0, c0, c1, I, D, M, tA);
+        else leg_product<T, T, false, kL>(X, off, X, off, c0, c1, I, D, M, tA);
+      }
+      if (nl == 0) gram.template add<true, kL>(G, G, 0, c0, c1, Ip, D, tA, tB);
+      else gram.template add<false, kL>(G, X, off, c0, c1, Ip, D, tA, tB);
+    }
+    gram.store(Mo, D);
+    __syncthreads();
     // the support of lambda_e: entries k with lambda_e[k] <= support_cut * max are zero
     const double* le = lam + tk.lam[p];
     if (threadIdx.x == 0) {
@@ -285,129 +384,241 @@ template <typename T>
 __global__ void __launch_bounds__(kBpThreads) bp_apply_kernel(const BpSiteTask* __restrict__ sites, int n_sites,
                                                               V2<T>* gamma, const double2* __restrict__ P, int D) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32];
   const int ld = D + 1;
-  // FP64 arithmetic whatever the storage: the gauge matrices of nearly null
-  // directions are large, and rounding them to FP32 would spoil the cancellation
-  double2* M = reinterpret_cast<double2*>(smem);  // [D][D + 1]
-  double2* tile = M + D * ld;                      // [32][D + 1]
+  // Storage-precision arithmetic when the site's gauge matrices are well
+  // conditioned; FP64 otherwise (a gauge matrix with large entries, rounded to
+  // FP32, would spoil the cancellation of the product)
+  double2* M64 = reinterpret_cast<double2*>(smem);  // [D][D + 1]
+  double2* tile64 = M64 + D * ld;                    // [32][D + 1]
+  V2<T>* M32 = reinterpret_cast<V2<T>*>(smem);
+  V2<T>* tile32 = M32 + D * ld;
   for (int t = blockIdx.x; t < n_sites; t += gridDim.x) {
     const BpSiteTask st = sites[t];
     V2<T>* G = gamma + st.off;
     int ncols = 2;
     for (int k = 1; k < st.deg; ++k) ncols *= D;
+    bool low = false;
+    if constexpr (sizeof(T) == 4) {
+      double mx = 0.0;
+      const double2* P0 = P + (int64_t)st.h0 * D * D;
+      for (int idx = threadIdx.x; idx < st.deg * D * D; idx += blockDim.x)
+        mx = fmax(mx, fmax(fabs(P0[idx].x), fabs(P0[idx].y)));
+      low = block_max(mx, red) <= kApplyF32Max;  // thread 0 holds the maximum
+      if (threadIdx.x == 0) red[0] = low ? 1.0 : 0.0;
+      __syncthreads();
+      low = red[0] != 0.0;
+      __syncthreads();
+    }
     for (int p = 0; p < st.deg; ++p) {
       // (G x_p P)[.., k, ..] = sum_a G[.., a, ..] P[a][k]: M[k][a] = P[a][k]
       const double2* Pp = P + (int64_t)(st.h0 + p) * D * D;
       for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
         const int a = idx / D, k = idx - a * D;
-        M[k * ld + a] = Pp[idx];
+        if (low) M32[k * ld + a] = mk<T>((T)Pp[idx].x, (T)Pp[idx].y);
+        else M64[k * ld + a] = Pp[idx];
       }
       __syncthreads();
       int I = 1;
       for (int k = p + 1; k < st.deg; ++k) I *= D;
-      leg_product<T, double, false>(G, G, ncols, I, D, M, tile);
+      if (low) leg_product<T, T, false, 32 * kMaxD / kBpThreads>(G, 0, G, 0, 0, ncols, I, D, M32, tile32);
+      else leg_product<T, double, false, 0>(G, 0, G, 0, 0, ncols, I, D, M64, tile64);
     }
   }
 }
 
-// ---------------------------------------------------------------- gauge (FP64)
+// ---------------------------------------------------------------- gauge
+// The square roots of G run in the arithmetic R: FP64 for complex128, FP32 for
+// complex64 storage (whose messages are FP32-accurate; the gauge preserves the
+// state whatever the accuracy of the roots, which only sets how close the new
+// gauge is to the BP fixed point).  Messages in, gauge matrices and lambda out
+// are FP64.
+template <typename R>
 struct GaugeSmall {
-  double rc[64], rs[64];
-  double2 re[64];
+  R rc[64], rs[64];
+  V2<R> re[64];
   int rp[64], rq[64];
   int iflag[160];
-  double w[64], S[64], lamv[64];
+  double w[64], winv[64];
+  double S[64], lamv[64];
   int order[64];
   double scal[4];
 };
 
-constexpr double kGaugeTol = 1e-15;      // Jacobi: |a_pq| <= tol sqrt(a_pp a_qq) ...
-constexpr double kGaugeFloor = 4.4e-16;  // ... or <= floor * trace
+template <typename R> struct GaugeTol;
+template <> struct GaugeTol<double> {
+  static constexpr double tol = 1e-15, floor = 4.4e-16;  // |a_pq| <= tol sqrt(a_pp a_qq) or <= floor * trace
+};
+template <> struct GaugeTol<float> {  // warm start only (FP64 sweeps finish)
+  static constexpr double tol = 1e-6, floor = 2e-7;
+};
 constexpr int kGaugeSweeps = 40;
 
 // Jacobi eigenproblem of the n x n Hermitian matrix in Am (destroyed), eigenvectors in W.
-__device__ void gauge_eig(double2* Am, double2* W, int n, GaugeSmall& sm, int* flags) {
+template <typename R>
+__device__ void gauge_eig(V2<R>* Am, V2<R>* W, int n, GaugeSmall<R>& sm, int* flags) {
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int a = idx / n;
-    W[idx] = make_double2(a * n + a == idx ? 1.0 : 0.0, 0.0);
+    W[idx] = mk<R>(a * n + a == idx ? R(1) : R(0), R(0));
   }
   for (int i = threadIdx.x; i < 160; i += blockDim.x) sm.iflag[i] = 0;
   __syncthreads();
   if (threadIdx.x == 0) {
     double tr = 0.0;
-    for (int a = 0; a < n; ++a) tr += Am[a * n + a].x;
+    for (int a = 0; a < n; ++a) tr += (double)Am[a * n + a].x;
     sm.scal[0] = tr;
   }
   __syncthreads();
-  const double floor_abs = kGaugeFloor * fmax(sm.scal[0], 0.0);
-  const int sw = jacobi_hermitian<double, false>(HermFull<double>{Am, n}, W, n, n, kGaugeTol, floor_abs,
-                                                 kGaugeSweeps, sm.rc, sm.rs, sm.re, sm.rp, sm.rq, sm.iflag,
-                                                 nullptr, nullptr);
+  const R floor_abs = (R)(GaugeTol<R>::floor * fmax(sm.scal[0], 0.0));
+  const int sw = jacobi_hermitian<R, sizeof(R) == 4>(HermFull<R>{Am, n}, W, n, n, (R)GaugeTol<R>::tol, floor_abs,
+                                                     kGaugeSweeps, sm.rc, sm.rs, sm.re, sm.rp, sm.rq, sm.iflag,
+                                                     nullptr, nullptr);
   if (threadIdx.x == 0 && sw > kGaugeSweeps) atomicOr(flags, GPEPS_FLAG_NOCONV);
   __syncthreads();
 }
 
-// R = G^{1/2} and Rinv = (G^{1/2})^+ of G = conj(m) (m: D x D message; n >= D, padded with zeros).
-__device__ void gauge_root(const double2* m, int D, int n, double2* Am, double2* W, double2* R, double2* Rinv,
-                           GaugeSmall& sm, int* flags) {
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+// Rt = G^{1/2} and Rinv = (G^{1/2})^+ of G = conj(m) (m: D x D FP64 message; n >= D,
+// padded with zeros), both FP64.  region: 2 n x n FP64 complex of work space.  With
+// R = float the eigenproblem is warm-started in FP32: its eigenvectors W are made
+// orthonormal in FP64 (one Newton-Schulz step, W <- W (3 - W^H W) / 2), G is rotated
+// into that basis in FP64 (W^H G W, nearly diagonal) and FP64 Jacobi sweeps finish it,
+// accumulating into W; as for R = double, W is then orthonormal and the eigenpairs
+// accurate to FP64, so Rinv Rt is the projector whatever the conditioning of G and the
+// gauge keeps the state exactly.
+template <typename R>
+__device__ void gauge_root(const double2* m, int D, int n, double2* region, double2* Rt, double2* Rinv,
+                           GaugeSmall<R>& sm, GaugeSmall<double>& sm64, int* flags) {
+  const int nn = n * n;
+  V2<R>* Am = reinterpret_cast<V2<R>*>(region);  // FP32: [0, 8 nn) bytes; FP64: [0, 16 nn)
+  V2<R>* W = Am + nn;
+  double2* A64 = region;                          // FP64 matrix: [0, 16 nn) bytes
+  double2* W64 = region + nn;                     // FP64 eigenvectors: [16 nn, 32 nn) bytes
+  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
     const int a = idx / n, b = idx - a * n;
-    double2 v = make_double2(0.0, 0.0);
+    V2<R> v = mk<R>(0, 0);
     if (a < D && b < D) {
       const double2 x = m[a * D + b];
-      v = make_double2(x.x, -x.y);
+      v = mk<R>((R)x.x, (R)(-x.y));
     }
     Am[idx] = v;
   }
   __syncthreads();
-  gauge_eig(Am, W, n, sm, flags);
+  gauge_eig<R>(Am, W, n, sm, flags);
+  if constexpr (sizeof(R) == 4) {
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x)
+      W64[idx] = make_double2((double)W[idx].x, (double)W[idx].y);
+    __syncthreads();
+    // orthonormalise: S = W^H W (in A64), then W <- 1.5 W - 0.5 W S (W S in Rt)
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+      const int a = idx / n, b = idx - a * n;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = 0; k < n; ++k) fma_conj<double>(acc, W64[k * n + a], W64[k * n + b]);
+      A64[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+      const int a = idx / n, b = idx - a * n;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = 0; k < n; ++k) fma_c<double>(acc, W64[a * n + k], A64[k * n + b]);
+      Rt[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+      const double2 w = W64[idx], t = Rt[idx];
+      W64[idx] = make_double2(1.5 * w.x - 0.5 * t.x, 1.5 * w.y - 0.5 * t.y);
+    }
+    __syncthreads();
+    // G W (in Rt), then A = W^H G W (in A64)
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+      const int a = idx / n, l = idx - a * n;
+      double2 acc = make_double2(0.0, 0.0);
+      if (a < D)
+        for (int b = 0; b < D; ++b) {
+          const double2 x = m[a * D + b];
+          fma_c<double>(acc, make_double2(x.x, -x.y), W64[b * n + l]);
+        }
+      Rt[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+      const int k = idx / n, l = idx - k * n;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int a = 0; a < n; ++a) fma_conj<double>(acc, W64[a * n + k], Rt[a * n + l]);
+      A64[idx] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 160; i += blockDim.x) sm64.iflag[i] = 0;
+    if (threadIdx.x == 0) {
+      double tr = 0.0;
+      for (int k = 0; k < n; ++k) tr += A64[k * n + k].x;
+      sm64.scal[0] = tr;
+    }
+    __syncthreads();
+    const int sw = jacobi_hermitian<double, false>(HermFull<double>{A64, n}, W64, n, n, GaugeTol<double>::tol,
+                                                   GaugeTol<double>::floor * fmax(sm64.scal[0], 0.0),
+                                                   kGaugeSweeps, sm64.rc, sm64.rs, sm64.re, sm64.rp, sm64.rq,
+                                                   sm64.iflag, nullptr, nullptr);
+    if (threadIdx.x == 0 && sw > kGaugeSweeps) atomicOr(flags, GPEPS_FLAG_NOCONV);
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
     double wmax = 0.0;
-    for (int k = 0; k < n; ++k) wmax = fmax(wmax, Am[k * n + k].x);
+    for (int k = 0; k < n; ++k) wmax = fmax(wmax, A64[k * n + k].x);
     for (int k = 0; k < n; ++k) {
-      const double wk = Am[k * n + k].x;
+      const double wk = A64[k * n + k].x;
       const bool keep = wk > kBpGramCut * wmax && wk > 0.0;
-      sm.w[k] = keep ? sqrt(wk) : 0.0;
-      sm.S[k] = keep ? 1.0 / sqrt(wk) : 0.0;
+      sm64.w[k] = keep ? sqrt(wk) : 0.0;
+      sm64.winv[k] = keep ? 1.0 / sqrt(wk) : 0.0;
     }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
     const int a = idx / n, b = idx - a * n;
     double2 r = make_double2(0.0, 0.0), ri = make_double2(0.0, 0.0);
     for (int k = 0; k < n; ++k) {
-      const double2 u = W[a * n + k], v = W[b * n + k];
+      const double2 u = W64[a * n + k], v = W64[b * n + k];
       const double2 uv = make_double2(u.x * v.x + u.y * v.y, u.y * v.x - u.x * v.y);  // u conj(v)
-      r.x = fma(sm.w[k], uv.x, r.x);
-      r.y = fma(sm.w[k], uv.y, r.y);
-      ri.x = fma(sm.S[k], uv.x, ri.x);
-      ri.y = fma(sm.S[k], uv.y, ri.y);
+      r.x = fma(sm64.w[k], uv.x, r.x);
+      r.y = fma(sm64.w[k], uv.y, r.y);
+      ri.x = fma(sm64.winv[k], uv.x, ri.x);
+      ri.y = fma(sm64.winv[k], uv.y, ri.y);
     }
-    R[idx] = r;
+    Rt[idx] = r;
     Rinv[idx] = ri;
   }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBpThreads) bp_gauge_kernel(const BpEdgeTask* __restrict__ edges, int n_edges,
-                                                              const double2* __restrict__ msgs, double* lam,
-                                                              double2* P, double2* scratch, int64_t slot_elems,
-                                                              int D, int* flags) {
-  __shared__ GaugeSmall sm;
+// 128-thread CTAs, four per SM.  The eigenproblems of G are warm-started in the
+// arithmetic R (FP32 for complex64 storage) and finished in FP64; the roots, C, its
+// eigenproblem C C^H (which sets
+// lambda' and resolves the smallest Schmidt directions) and the gauge matrices
+// are FP64.  Slot layout (n x n FP64 complex each): Ri, Ri^+, Rj, Rj^+, C; the
+// Jacobi work space (2 n x n) in dynamic shared memory when it fits (in_smem),
+// else after C in the slot.
+template <typename R>
+__global__ void __launch_bounds__(kGaugeThreads, 4) bp_gauge_kernel(const BpEdgeTask* __restrict__ edges,
+                                                                   int n_edges, const double2* __restrict__ msgs,
+                                                                   double* lam, double2* P, double2* scratch,
+                                                                   int64_t slot_elems, int D, int in_smem,
+                                                                   int* flags) {
+  extern __shared__ __align__(16) unsigned char gsmem[];
+  __shared__ GaugeSmall<R> sm;
+  __shared__ GaugeSmall<double> sm64;
   const int n = D + (D & 1);
   const int nn = n * n;
-  double2* Am = scratch + (int64_t)blockIdx.x * slot_elems;
-  double2* W = Am + nn;
-  double2* Ri = W + nn;
+  double2* Ri = scratch + (int64_t)blockIdx.x * slot_elems;
   double2* Rii = Ri + nn;
   double2* Rj = Rii + nn;
   double2* Rji = Rj + nn;
   double2* C = Rji + nn;
+  double2* Am = in_smem ? reinterpret_cast<double2*>(gsmem) : C + nn;
+  double2* W = Am + nn;
   for (int e = blockIdx.x; e < n_edges; e += gridDim.x) {
     const BpEdgeTask tk = edges[e];
-    gauge_root(msgs + (int64_t)tk.hi * D * D, D, n, Am, W, Ri, Rii, sm, flags);
-    gauge_root(msgs + (int64_t)tk.hj * D * D, D, n, Am, W, Rj, Rji, sm, flags);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) sm.lamv[k] = k < D ? lam[tk.lam + k] : 0.0;
+    gauge_root<R>(msgs + (int64_t)tk.hi * D * D, D, n, Am, Ri, Rii, sm, sm64, flags);
+    gauge_root<R>(msgs + (int64_t)tk.hj * D * D, D, n, Am, Rj, Rji, sm, sm64, flags);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) sm64.lamv[k] = k < D ? lam[tk.lam + k] : 0.0;
     __syncthreads();
     // C = Ri diag(lambda) Rj^T
     for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
@@ -415,7 +626,7 @@ __global__ void __launch_bounds__(kBpThreads) bp_gauge_kernel(const BpEdgeTask* 
       double2 acc = make_double2(0.0, 0.0);
       for (int c = 0; c < n; ++c) {
         const double2 x = Ri[a * n + c], y = Rj[b * n + c];
-        const double l = sm.lamv[c];
+        const double l = sm64.lamv[c];
         acc.x = fma(l, x.x * y.x - x.y * y.y, acc.x);
         acc.y = fma(l, x.x * y.y + x.y * y.x, acc.y);
       }
@@ -430,47 +641,48 @@ __global__ void __launch_bounds__(kBpThreads) bp_gauge_kernel(const BpEdgeTask* 
       Am[idx] = acc;
     }
     __syncthreads();
-    gauge_eig(Am, W, n, sm, flags);
-    // Y = C^T conj(U) (in Ri), S_k = ||Y[:, k]||
+    gauge_eig<double>(Am, W, n, sm64, flags);
+    // Y = C^T conj(U) (in Am, whose eigenvalues are not used), S_k = ||Y[:, k]||
     for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
       const int a = idx / n, k = idx - a * n;
       double2 acc = make_double2(0.0, 0.0);
       for (int b = 0; b < n; ++b) fma_conj<double>(acc, W[b * n + k], C[b * n + a]);
-      Ri[idx] = acc;
+      Am[idx] = acc;
     }
     __syncthreads();
+    double2* Y = Am;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       double s2 = 0.0;
       for (int a = 0; a < n; ++a) {
-        const double2 y = Ri[a * n + k];
+        const double2 y = Y[a * n + k];
         s2 += y.x * y.x + y.y * y.y;
       }
-      sm.S[k] = sqrt(s2);
+      sm64.S[k] = sqrt(s2);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       int rank = 0;
-      const double sk = sm.S[k];
-      for (int j = 0; j < n; ++j) rank += (sm.S[j] > sk) || (sm.S[j] == sk && j < k);
-      sm.order[rank] = k;
+      const double sk = sm64.S[k];
+      for (int j = 0; j < n; ++j) rank += (sm64.S[j] > sk) || (sm64.S[j] == sk && j < k);
+      sm64.order[rank] = k;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       double nrm2 = 0.0;
-      for (int kk = 0; kk < D; ++kk) nrm2 += sm.S[sm.order[kk]] * sm.S[sm.order[kk]];
-      sm.scal[1] = sqrt(nrm2);
-      sm.scal[2] = sm.S[sm.order[0]];
+      for (int kk = 0; kk < D; ++kk) nrm2 += sm64.S[sm64.order[kk]] * sm64.S[sm64.order[kk]];
+      sm64.scal[1] = sqrt(nrm2);
+      sm64.scal[2] = sm64.S[sm64.order[0]];
     }
     __syncthreads();
-    const double nrm = sm.scal[1], smax = sm.scal[2];
+    const double nrm = sm64.scal[1], smax = sm64.scal[2];
     const bool ok = nrm > 0.0 && isfinite(nrm);
     if (threadIdx.x == 0 && !ok) atomicOr(flags, GPEPS_FLAG_NUMERIC);
     double2* Pi = P + (int64_t)tk.hi * D * D;
     double2* Pj = P + (int64_t)tk.hj * D * D;
     for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
       const int a = idx / D, kk = idx - a * D;
-      const int k = sm.order[kk];
-      const double sk = sm.S[k];
+      const int k = sm64.order[kk];
+      const double sk = sm64.S[k];
       double2 pi = make_double2(0.0, 0.0), pj = make_double2(0.0, 0.0);
       if (!ok) {  // leave the state as it is
         pi = make_double2(a == kk ? 1.0 : 0.0, 0.0);
@@ -478,7 +690,7 @@ __global__ void __launch_bounds__(kBpThreads) bp_gauge_kernel(const BpEdgeTask* 
       } else if (sk > kLambdaCut * smax) {
         for (int b = 0; b < n; ++b) {
           fma_c<double>(pi, Rii[a * n + b], W[b * n + k]);
-          fma_c<double>(pj, Rji[a * n + b], Ri[b * n + k]);
+          fma_c<double>(pj, Rji[a * n + b], Y[b * n + k]);
         }
         pj.x /= sk;
         pj.y /= sk;
@@ -487,7 +699,7 @@ __global__ void __launch_bounds__(kBpThreads) bp_gauge_kernel(const BpEdgeTask* 
       Pj[idx] = pj;
     }
     if (ok)
-      for (int kk = threadIdx.x; kk < D; kk += blockDim.x) lam[tk.lam + kk] = sm.S[sm.order[kk]] / nrm;
+      for (int kk = threadIdx.x; kk < D; kk += blockDim.x) lam[tk.lam + kk] = sm64.S[sm64.order[kk]] / nrm;
     __syncthreads();
   }
 }
@@ -499,13 +711,36 @@ size_t BpLaunch<T>::message_smem(int D) {
   return (size_t)(D + 64) * (D + 1) * sizeof(V2<T>) + (size_t)D * D * sizeof(double2);
 }
 
+static size_t apply_smem(int D) { return (size_t)(D + 32) * (D + 1) * sizeof(double2); }
+static size_t gauge_smem(int D) {
+  const int n = D + (D & 1);
+  const size_t b = (size_t)2 * n * n * sizeof(double2);
+  return b <= kGaugeSmemMax ? b : 0;
+}
+
 template <typename T>
 cudaError_t BpLaunch<T>::init() {
-  cudaError_t e = cudaFuncSetAttribute(bp_message_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)message_smem(kMaxD));
+  cudaError_t e = cudaFuncSetAttribute(bp_message_kernel<T, kGramPerSmall>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)message_smem(32));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(bp_message_kernel<T, kGramPerLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)message_smem(kMaxD));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(bp_gauge_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGaugeSmemMax);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(bp_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)((kMaxD + 32) * (kMaxD + 1) * sizeof(double2)));
+                              (int)apply_smem(kMaxD));
+}
+
+template <typename T>
+int BpLaunch<T>::resident(int D) {
+  int n = 0;
+  const cudaError_t e =
+      D <= 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bp_message_kernel<T, kGramPerSmall>, kBpThreads,
+                                                              message_smem(D))
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bp_message_kernel<T, kGramPerLarge>, kBpThreads,
+                                                              message_smem(D));
+  return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
 template <typename T>
@@ -522,9 +757,15 @@ cudaError_t BpLaunch<T>::message(const BpMsgTask* tasks, int n_tasks, const void
                                  unsigned long long* residual, int* flags, int n_ctas, cudaStream_t st) {
   if (n_tasks == 0) return cudaSuccess;
   const int grid = n_tasks < n_ctas ? n_tasks : n_ctas;
-  bp_message_kernel<T><<<grid, kBpThreads, message_smem(D), st>>>(
-      tasks, n_tasks, static_cast<const V2<T>*>(gamma), lam, msg_in, msg_out, static_cast<V2<T>*>(scratch),
-      slot_elems, D, sizeof(T) == 4 ? kBpSupportCutF32 : kLambdaCut, residual, flags);
+  const double cut = sizeof(T) == 4 ? kBpSupportCutF32 : kLambdaCut;
+  if (D <= 32)
+    bp_message_kernel<T, kGramPerSmall><<<grid, kBpThreads, message_smem(D), st>>>(
+        tasks, n_tasks, static_cast<const V2<T>*>(gamma), lam, msg_in, msg_out, static_cast<V2<T>*>(scratch),
+        slot_elems, D, cut, residual, flags);
+  else
+    bp_message_kernel<T, kGramPerLarge><<<grid, kBpThreads, message_smem(D), st>>>(
+        tasks, n_tasks, static_cast<const V2<T>*>(gamma), lam, msg_in, msg_out, static_cast<V2<T>*>(scratch),
+        slot_elems, D, cut, residual, flags);
   return cudaGetLastError();
 }
 
@@ -532,16 +773,18 @@ template <typename T>
 cudaError_t BpLaunch<T>::apply(const BpSiteTask* sites, int n_sites, void* gamma, const double2* P, int D,
                                cudaStream_t st) {
   if (n_sites == 0) return cudaSuccess;
-  const size_t smem = (size_t)(D + 32) * (D + 1) * sizeof(double2);
-  bp_apply_kernel<T><<<n_sites, kBpThreads, smem, st>>>(sites, n_sites, static_cast<V2<T>*>(gamma), P, D);
+  bp_apply_kernel<T><<<n_sites, kBpThreads, apply_smem(D), st>>>(sites, n_sites, static_cast<V2<T>*>(gamma), P, D);
   return cudaGetLastError();
 }
 
-cudaError_t bp_gauge(const BpEdgeTask* edges, int n_edges, const double2* msgs, double* lam, double2* P,
-                     double2* scratch, int64_t slot_elems, int D, int* flags, int n_ctas, cudaStream_t st) {
+template <typename T>
+cudaError_t BpLaunch<T>::gauge(const BpEdgeTask* edges, int n_edges, const double2* msgs, double* lam, double2* P,
+                               double2* scratch, int64_t slot_elems, int D, int* flags, int n_ctas, cudaStream_t st) {
   if (n_edges == 0) return cudaSuccess;
+  const size_t smem = gauge_smem(D);
   const int grid = n_edges < n_ctas ? n_edges : n_ctas;
-  bp_gauge_kernel<<<grid, kBpThreads, 0, st>>>(edges, n_edges, msgs, lam, P, scratch, slot_elems, D, flags);
+  bp_gauge_kernel<T><<<grid, kGaugeThreads, smem, st>>>(edges, n_edges, msgs, lam, P, scratch, slot_elems, D,
+                                                        smem > 0 ? 1 : 0, flags);
   return cudaGetLastError();
 }
 

@@ -1050,13 +1050,14 @@ struct BpLayout {
   int n_ctas;
 };
 
+// One message CTA per resident slot (occupancy of the message kernel at this D),
+// so that the CTAs' scratch tensors stay in L2.  The launchers' shared-memory
+// limits are raised first: the occupancy depends on them.
 int bp_ctas(const gpeps_handle* h) {
-  int per_sm = 1;
-  const size_t smem = h->dtype == GPEPS_C128 ? BpLaunch<double>::message_smem(h->D)
-                                              : BpLaunch<float>::message_smem(h->D);
-  per_sm = (int)(kSmemPerSm / (smem + 1024));
-  per_sm = std::max(1, std::min(per_sm, 4));
-  return std::max(1, h->n_sms) * per_sm;
+  if (h->dtype == GPEPS_C128) BpLaunch<double>::init();
+  else BpLaunch<float>::init();
+  const int per_sm = h->dtype == GPEPS_C128 ? BpLaunch<double>::resident(h->D) : BpLaunch<float>::resident(h->D);
+  return std::max(1, h->n_sms) * std::max(1, per_sm);
 }
 
 BpLayout bp_layout(const gpeps_handle* h, int max_iter) {
@@ -1066,7 +1067,7 @@ BpLayout bp_layout(const gpeps_handle* h, int max_iter) {
   int maxdeg = 0;
   for (const SiteDesc& sd : h->sites) maxdeg = std::max(maxdeg, (int)sd.deg);
   const int n = D + (D & 1);
-  const int64_t site_elems = 2 * ipow(D, std::max(maxdeg, 1));
+  const int64_t site_elems = ipow(D, std::max(maxdeg, 1));  // one physical component of the largest site
   const size_t slot = std::max((size_t)site_elems * h->elt, (size_t)7 * n * n * sizeof(double2));
   L.slot_elems = (int64_t)(align256(slot) / 16);  // in units of 16 bytes
   L.n_ctas = bp_ctas(h);
@@ -1167,8 +1168,13 @@ int gpeps_bp_regauge(gpeps_handle* h, int32_t max_iter, double tol, void* d_bp_w
   }
   double2* P = reinterpret_cast<double2*>(w + L.P);
   if (phase_ms) GP_CUDA(cudaEventRecord(ev[1], s));
-  GP_CUDA(bp_gauge(reinterpret_cast<const BpEdgeTask*>(w + L.edges), (int)h->bp_edges.size(), cur, h->lam(), P,
-                   reinterpret_cast<double2*>(scratch), L.slot_elems, D, h->flags(), L.n_ctas, s));
+  {
+    const BpEdgeTask* et = reinterpret_cast<const BpEdgeTask*>(w + L.edges);
+    const int ne = (int)h->bp_edges.size();
+    double2* sc = reinterpret_cast<double2*>(scratch);
+    GP_CUDA(c128 ? BpLaunch<double>::gauge(et, ne, cur, h->lam(), P, sc, L.slot_elems, D, h->flags(), L.n_ctas, s)
+                 : BpLaunch<float>::gauge(et, ne, cur, h->lam(), P, sc, L.slot_elems, D, h->flags(), L.n_ctas, s));
+  }
   if (phase_ms) GP_CUDA(cudaEventRecord(ev[2], s));
   GP_CUDA(c128 ? BpLaunch<double>::apply(reinterpret_cast<const BpSiteTask*>(w + L.sites), (int)h->bp_sites.size(),
                                           h->gamma(), P, D, s)

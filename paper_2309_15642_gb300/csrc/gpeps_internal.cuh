@@ -190,6 +190,8 @@ struct BpSiteTask {
 constexpr int kBpThreads = 256;      // threads of every BP CTA
 constexpr double kBpGramCut = 1e-13; // eigenvalues of G below this fraction of the largest: pseudo-inverse 0
 constexpr double kBpSupportCutF32 = 1e-7;  // complex64 storage: message support lambda_k > cut * max(lambda)
+constexpr size_t kGaugeSmemMax = 2 * 32 * 32 * 16;  // the gauge CTA's Jacobi pair in shared memory up to D = 32
+constexpr int kGaugeThreads = 128;                  // threads of a gauge CTA (four per SM)
 
 // Launchers (bp_kernels.cu).  T is the storage type of Gamma; messages, gauge
 // and lambda are FP64.
@@ -197,15 +199,17 @@ template <typename T>
 struct BpLaunch {
   static cudaError_t init();
   static size_t message_smem(int D);
+  static int resident(int D);  // message CTAs per SM (occupancy at D)
   static cudaError_t identity(double2* msgs, int n_half, int D, cudaStream_t st);
   static cudaError_t message(const BpMsgTask* tasks, int n_tasks, const void* gamma, const double* lam,
                              const double2* msg_in, double2* msg_out, void* scratch, int64_t slot_elems, int D,
                              unsigned long long* residual, int* flags, int n_ctas, cudaStream_t st);
   static cudaError_t apply(const BpSiteTask* sites, int n_sites, void* gamma, const double2* P, int D,
                            cudaStream_t st);
+  // gauge of every edge in the arithmetic of T; scratch: 7 n x n complex of T per CTA, n = D
+  // rounded up to even (up to D = 32 two of them sit in shared memory instead)
+  static cudaError_t gauge(const BpEdgeTask* edges, int n_edges, const double2* msgs, double* lam, double2* P,
+                           double2* scratch, int64_t slot_elems, int D, int* flags, int n_ctas, cudaStream_t st);
 };
-// FP64 gauge of every edge (bp_kernels.cu); scratch: 7 n x n complex per CTA, n = D rounded up to even.
-cudaError_t bp_gauge(const BpEdgeTask* edges, int n_edges, const double2* msgs, double* lam, double2* P,
-                     double2* scratch, int64_t slot_elems, int D, int* flags, int n_ctas, cudaStream_t st);
 
 }  // namespace gpeps
