@@ -48,8 +48,8 @@ namespace gpeps {
 namespace {
 
 // Upper-triangle pairs per thread of the message Gram: D <= 32 and D <= 64.
-constexpr int kGramPerSmall = (32 * 33 / 2 + kBpThreads - 1) / kBpThreads;
-constexpr int kGramPerLarge = (kMaxD * (kMaxD + 1) / 2 + kBpThreads - 1) / kBpThreads;
+constexpr int kGramPerSmall = (32 * 33 / 2 + kBpMsgThreads - 1) / kBpMsgThreads;
+constexpr int kGramPerLarge = (kMaxD * (kMaxD + 1) / 2 + kBpMsgThreads - 1) / kBpMsgThreads;
 // The apply runs in FP32 for complex64 storage when every entry of a site's
 // gauge matrices is at most this large (well-conditioned gauge), else in FP64.
 constexpr double kApplyF32Max = 64.0;
@@ -268,7 +268,7 @@ __global__ void bp_identity_kernel(double2* msgs, int64_t n, int D) {
 // (the products never mix s), so the scratch tensor X of a CTA holds D^deg
 // elements and the launch's scratch stays in L2.
 template <typename T, int K>
-__global__ void __launch_bounds__(kBpThreads) bp_message_kernel(const BpMsgTask* __restrict__ tasks, int n_tasks,
+__global__ void __launch_bounds__(kBpMsgThreads) bp_message_kernel(const BpMsgTask* __restrict__ tasks, int n_tasks,
                                                                 const V2<T>* __restrict__ gamma,
                                                                 const double* __restrict__ lam,
                                                                 const double2* __restrict__ msg_in,
@@ -736,9 +736,9 @@ template <typename T>
 int BpLaunch<T>::resident(int D) {
   int n = 0;
   const cudaError_t e =
-      D <= 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bp_message_kernel<T, kGramPerSmall>, kBpThreads,
+      D <= 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bp_message_kernel<T, kGramPerSmall>, kBpMsgThreads,
                                                               message_smem(D))
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bp_message_kernel<T, kGramPerLarge>, kBpThreads,
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bp_message_kernel<T, kGramPerLarge>, kBpMsgThreads,
                                                               message_smem(D));
   return (e == cudaSuccess && n > 0) ? n : 1;
 }
@@ -759,11 +759,11 @@ cudaError_t BpLaunch<T>::message(const BpMsgTask* tasks, int n_tasks, const void
   const int grid = n_tasks < n_ctas ? n_tasks : n_ctas;
   const double cut = sizeof(T) == 4 ? kBpSupportCutF32 : kLambdaCut;
   if (D <= 32)
-    bp_message_kernel<T, kGramPerSmall><<<grid, kBpThreads, message_smem(D), st>>>(
+    bp_message_kernel<T, kGramPerSmall><<<grid, kBpMsgThreads, message_smem(D), st>>>(
         tasks, n_tasks, static_cast<const V2<T>*>(gamma), lam, msg_in, msg_out, static_cast<V2<T>*>(scratch),
         slot_elems, D, cut, residual, flags);
   else
-    bp_message_kernel<T, kGramPerLarge><<<grid, kBpThreads, message_smem(D), st>>>(
+    bp_message_kernel<T, kGramPerLarge><<<grid, kBpMsgThreads, message_smem(D), st>>>(
         tasks, n_tasks, static_cast<const V2<T>*>(gamma), lam, msg_in, msg_out, static_cast<V2<T>*>(scratch),
         slot_elems, D, cut, residual, flags);
   return cudaGetLastError();

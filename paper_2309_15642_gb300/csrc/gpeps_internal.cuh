@@ -187,7 +187,10 @@ struct BpSiteTask {
   int32_t deg;
   int32_t h0;      // half-edge index of leg 0 (legs are h0 .. h0 + deg - 1)
 };
-constexpr int kBpThreads = 256;      // threads of every BP CTA
+constexpr int kBpThreads = 256;      // threads of the BP apply CTA
+constexpr int kBpMsgThreads = 256;   // threads of a BP message CTA (288, two upper-triangle entries per
+                                     // thread at D = 32 instead of up to three, measured slower: 4.95
+                                     // against 4.76 ms, one CTA per SM fewer)
 constexpr double kBpGramCut = 1e-13; // eigenvalues of G below this fraction of the largest: pseudo-inverse 0
 constexpr double kBpSupportCutF32 = 1e-7;  // complex64 storage: message support lambda_k > cut * max(lambda)
 constexpr size_t kGaugeSmemMax = 2 * 32 * 32 * 16;  // the gauge CTA's Jacobi pair in shared memory up to D = 32
