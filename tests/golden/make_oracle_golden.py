@@ -4,12 +4,15 @@
     python tests/golden/make_oracle_golden.py heavyhex_mix_d32
     python tests/golden/make_oracle_golden.py eagle_d64
     python tests/golden/make_oracle_golden.py infinite_sweep16_d32
+    python tests/golden/make_oracle_golden.py eagle_bp_d32
 
 Each run writes ``tests/golden/oracle_<workload>.json``: the mean <Z> of every
 instance after every Trotter step, the per-qubit <Z> after a few sampled steps
 and the sorted lambda spectra of a few sampled edges.  The oracle is the plain
 FP64 simple update of ``oracle/su.py`` (the workload's colouring: greedy, or the
-unit cell's periodic one; same inputs as the GPU tests from ``workloads``).
+unit cell's periodic one; same inputs as the GPU tests from ``workloads``); for a
+workload with ``bp`` set, followed after every step by the BP regauge of
+``oracle/bp.py`` (to a residual of 1e-13), whose iteration counts are recorded.
 """
 from __future__ import annotations
 
@@ -23,11 +26,12 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 import numpy as np  # noqa: E402
 
+from oracle import bp  # noqa: E402
 from oracle.su import GPEPS  # noqa: E402
 from workloads import kick_angles, workload  # noqa: E402
 
 SAMPLE_STEPS = {"eagle_sweep16_d16": [1, 4, 5, 10, 20], "heavyhex_mix_d32": [1, 5, 6, 10, 25, 50],
-                "eagle_d64": [1, 5, 6, 7, 8], "infinite_sweep16_d32": [1, 3, 5]}
+                "eagle_d64": [1, 5, 6, 7, 8], "infinite_sweep16_d32": [1, 3, 5], "eagle_bp_d32": [1, 5, 6, 7, 8]}
 
 
 def sampled_edges(n_edges, k=8):
@@ -45,9 +49,16 @@ def run(name, steps=None):
         peps = GPEPS(n, edges, w.D, colour=col)
         inst = {"n_qubits": int(n), "theta": float(th[0]) if w.per_qubit_seed is None else None,
                 "mean_z": [], "z": {}, "lambda": {}}
+        if w.bp:
+            inst["bp_iterations"] = []
         ed = sampled_edges(len(edges))
         for t in range(1, steps + 1):
             peps.step(th)
+            if w.bp:
+                it, res = bp.regauge(peps, 500, 1e-13)
+                if res > 1e-13:
+                    raise RuntimeError(f"BP did not converge at step {t}: residual {res}")
+                inst["bp_iterations"].append(it)
             z = peps.expect_z()
             inst["mean_z"].append(float(z.mean()))
             if t in sample:

@@ -187,3 +187,31 @@ def test_workspace_errors():
     assert g.lib.gpeps_bp_regauge(g.h, 10, -1.0, ctypes.c_void_p(small.data_ptr()), nbytes.value,
                                   ctypes.byref(it), ctypes.byref(res), None) == 1
     g.close()
+
+
+@pytest.mark.parametrize("dtype", ["c128", "mixed"])
+def test_eagle_bp_d32_matches_oracle_golden(dtype):
+    """127 qubits at the benchmark's D = 32, theta = 0.7, 8 steps with a regauge after each
+    (truncation from step 6): mean <Z> of every step, every qubit and sampled lambda at the
+    committed steps of ``tests/golden/make_oracle_golden.py eagle_bp_d32``."""
+    import json
+    import os
+    from workloads import workload
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_eagle_bp_d32.json")) as f:
+        inst = json.load(f)["instances"][0]
+    w = workload("eagle_bp_d32")
+    g = gpu_lib()(w.graphs(), w.D, dtype=dtype)
+    g.reset()
+    th = torch.tensor([w.theta[0]], dtype=torch.float64, device="cuda")
+    for s in range(1, w.steps + 1):
+        g.step(1, th)
+        it, res = g.bp_regauge(300)
+        assert it < 300, (s, it, res)
+        z, mean = g.expect_z()
+        assert abs(float(mean.cpu().numpy()[0]) - inst["mean_z"][s - 1]) < TOL[dtype], s
+        if str(s) in inst["z"]:
+            assert np.abs(z.cpu().numpy() - np.array(inst["z"][str(s)])).max() < TOL[dtype], s
+            for e, lam in inst["lambda"][str(s)].items():
+                assert np.abs(sorted_lam(g.lambdas(0, int(e))) - np.array(lam)).max() < TOL_LAM[dtype], (s, e)
+    assert g.status() == 0
+    g.close()

@@ -24,6 +24,7 @@ class Workload:
     theta: tuple             # one kick angle per instance (ignored when per_qubit_seed is set)
     per_qubit_seed: int | None = None
     note: str = ""
+    bp: bool = False         # a BP regauge after every Trotter step
 
     def graphs(self):
         """List of ``(n_qubits, edges)``, one per instance."""
@@ -79,6 +80,9 @@ WORKLOADS = {
     "eagle_d64": Workload("eagle_d64", (EAGLE,), 64, 8, (0.8,),
                           note="127 q, D=64, 8 steps, theta=0.8: the 128 x 128 bond eigenproblems of "
                                "condor_d64 on a lattice the oracle finishes in minutes (truncation from step 7)"),
+    "eagle_bp_d32": Workload("eagle_bp_d32", (EAGLE,), 32, 8, (0.7,), bp=True,
+                             note="127 q, D=32, 8 steps, theta=0.7, a BP regauge after every step (the paper's "
+                                  "BP comparison at the benchmark's bond dimension; truncation from step 6)"),
 }
 
 
