@@ -48,6 +48,17 @@ def sorted_lam(x):
     return -np.sort(-np.asarray(x), axis=-1)
 
 
+def lam_close(gpu, ref, dtype, truncated=False):
+    """Sorted spectra: complex128 to 1e-6 everywhere and 1e-9 (5e-8 once truncated) where
+    lambda > 1e-3 (Schmidt values come from eigenvalues of the squared bond matrix, so the
+    small ones are resolved to ~sqrt(eps) of the largest); mixed to 2e-3."""
+    d = np.abs(sorted_lam(gpu) - np.asarray(ref))
+    if dtype != "c128":
+        return d.max() < TOL_LAM["mixed"]
+    big = np.asarray(ref) > 1e-3
+    return d.max() < 1e-6 and (not big.any() or d[big].max() < (5e-8 if truncated else 1e-9))
+
+
 @pytest.mark.parametrize("dtype", ["c128", "mixed"])
 def test_tree_random_gauge_recovers_schmidt_values(dtype):
     m, e, _ = induced_subgraph(E127, range(16))
@@ -212,6 +223,6 @@ def test_eagle_bp_d32_matches_oracle_golden(dtype):
         if str(s) in inst["z"]:
             assert np.abs(z.cpu().numpy() - np.array(inst["z"][str(s)])).max() < TOL[dtype], s
             for e, lam in inst["lambda"][str(s)].items():
-                assert np.abs(sorted_lam(g.lambdas(0, int(e))) - np.array(lam)).max() < TOL_LAM[dtype], (s, e)
+                assert lam_close(g.lambdas(0, int(e)), lam, dtype, truncated=2 ** s > w.D), (s, e)
     assert g.status() == 0
     g.close()
