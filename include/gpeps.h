@@ -311,9 +311,12 @@ int gpeps_grad(gpeps_handle* h, const double* theta, int32_t n_steps, int32_t ck
  * eigenvalue), C = R_i diag(lambda_e) R_j^T = U S V^H, lambda_e' = S / ||S||,
  * Gamma_i <- Gamma_i (R_i^+ U) and Gamma_j <- Gamma_j (R_j^+ conj(V)) on leg e
  * (columns with S <= 1e-13 S_max zeroed).  The state is unchanged; the
- * mean-field readout afterwards uses the new gauge.  Messages, gauge and lambda
- * are FP64; the message contractions run in the storage precision (FP32 for
- * GPEPS_MIXED_C64).  A pending kick commutes with the regauge and stays pending.
+ * mean-field readout afterwards uses the new gauge.  Messages, gauge matrices
+ * and lambda are FP64; the message contractions run in the storage precision
+ * (FP32 for GPEPS_MIXED_C64, where the eigenproblems of the gauge are also
+ * warm-started in FP32 before FP64 sweeps, and the gauge is applied in FP32
+ * when its matrices are well conditioned).  A pending kick commutes with the
+ * regauge and stays pending.
  *   d_bp_work:  device, 256-byte aligned, >= gpeps_query_bp_workspace(max_iter)
  *               bytes (the messages of two iterations, the gauge matrices, the
  *               work lists and one global scratch slot per CTA)

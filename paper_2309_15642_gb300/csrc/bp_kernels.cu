@@ -19,16 +19,17 @@
 //            keeps it exactly so (its rounding noise would otherwise grow along
 //            the loops of the lattice).  Normalised to unit trace in FP64; the
 //            largest elementwise change is reduced into the iteration's residual.
-//   gauge    one CTA per edge (the square roots of G in FP32 for complex64
-//            storage, everything else FP64): the Hermitian square root R and pseudo-
-//            inverse R^+ of G = conj(m) at both ends (Jacobi eigenproblems),
+//   gauge    one 128-thread CTA per edge, FP64 (for complex64 storage the
+//            eigenproblems of G are warm-started in FP32): the Hermitian square
+//            root R and pseudo-inverse R^+ of G = conj(m) at both ends (Jacobi),
 //            C = R_i diag(lambda) R_j^T, its left singular vectors U from the
 //            eigenproblem of C C^H, and Y = C^T conj(U), whose column norms are the
 //            singular values S (C = U Y^T holds exactly whatever the accuracy of
 //            the smallest eigenvalues).  lambda' = S / ||S||, and the gauge
 //            matrices R_i^+ U and R_j^+ Y / S of the two half-edges.
-//   apply    one CTA per site: Gamma_i <- Gamma_i x_p P_p on every leg p, in place,
-//            in FP64 arithmetic rounded once to the storage type.
+//   apply    one CTA per site: Gamma_i <- Gamma_i x_p P_p on every leg p, in place
+//            (FP32 for complex64 storage when the gauge matrices are well
+//            conditioned, else FP64 rounded once to the storage type).
 //
 // Leg products and the message Gram view a site tensor [s][leg0][leg1][leg2]
 // (last leg fastest) along leg p as columns c (s and the other legs) times the

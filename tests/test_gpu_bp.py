@@ -226,3 +226,17 @@ def test_eagle_bp_d32_matches_oracle_golden(dtype):
                 assert lam_close(g.lambdas(0, int(e)), lam, dtype, truncated=2 ** s > w.D), (s, e)
     assert g.status() == 0
     g.close()
+
+
+@pytest.mark.parametrize("D", [1, 2])
+def test_small_bond_dimensions(D):
+    """D = 1 (a product state: every message and gauge is 1 x 1, padded to 2 x 2 in the gauge)
+    and D = 2, on a 24-qubit fragment with a regauge after each of 3 steps."""
+    m, e, _ = induced_subgraph(E127, range(24))
+    _evolve_and_compare(m, e, D, 0.7, 3, "c128")
+
+
+def test_isolated_qubit_and_single_edge():
+    """A qubit without couplers (no messages, no gauge) next to one edge and a path."""
+    edges = np.array([[0, 1], [2, 3], [3, 4]], dtype=np.int32)
+    _evolve_and_compare(6, edges, 2, 0.9, 3, "c128")
