@@ -80,7 +80,7 @@ __device__ __forceinline__ void tile_pos(int idx, int I, int D, int& j, int& b) 
 // thread, 32 D <= kL blockDim) while the current one is multiplied.  dst may be
 // src: the columns of a tile are read completely before any of them is written,
 // and the prefetched columns are not the ones being written.
-template <typename TS, typename TC, bool kConj, int kL>
+template <typename TS, typename TC, bool kConj, int kL, bool kD32 = false>
 __device__ void leg_product(V2<TS>* dst, int64_t dst_off, const V2<TS>* src, int64_t src_off, int c_begin,
                             int c_end, int I, int D, const V2<TC>* M, V2<TC>* tile) {
   const int ld = D + 1;
@@ -119,14 +119,43 @@ __device__ void leg_product(V2<TS>* dst, int64_t dst_off, const V2<TS>* src, int
     }
     __syncthreads();
     if (kL > 0 && c0 + 32 < c_end) fetch(c0 + 32);
-    for (int idx = threadIdx.x; idx < 32 * D; idx += blockDim.x) {
-      const int b = idx >> 5, j = idx & 31;
-      if (j < nc) {
-        V2<TC> acc = mk<TC>(0, 0);
-        const V2<TC>* mr = M + b * ld;
-        const V2<TC>* tr = tile + j * ld;
-        for (int k = 0; k < D; ++k) fma_c<TC>(acc, mr[k], tr[k]);
-        dst[leg_addr(c0 + j, b, I, D) - dst_off] = mk<TS>((TS)acc.x, (TS)acc.y);
+    if (kD32 && blockDim.x == 256) {
+      // D = 32: a 2 x 2 register tile per thread, columns {jb, jb + 16} x leg entries
+      // {bb, bb + 16}: a half-warp reads 16 tile rows (distinct banks with the row
+      // stride 33) and shares two M values, so a complex FMA costs one shared-memory
+      // wavefront instead of three
+      const int jb = threadIdx.x & 15, bb = threadIdx.x >> 4;
+      V2<TC> a00 = mk<TC>(0, 0), a01 = a00, a10 = a00, a11 = a00;
+      const V2<TC>* t0 = tile + jb * 33;
+      const V2<TC>* t1 = t0 + 16 * 33;
+      const V2<TC>* m0 = M + bb * 33;
+      const V2<TC>* m1 = m0 + 16 * 33;
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) {
+        const V2<TC> x0 = t0[k], x1 = t1[k], y0 = m0[k], y1 = m1[k];
+        fma_c<TC>(a00, y0, x0);
+        fma_c<TC>(a01, y1, x0);
+        fma_c<TC>(a10, y0, x1);
+        fma_c<TC>(a11, y1, x1);
+      }
+      if (jb < nc) {
+        dst[leg_addr(c0 + jb, bb, I, 32) - dst_off] = mk<TS>((TS)a00.x, (TS)a00.y);
+        dst[leg_addr(c0 + jb, bb + 16, I, 32) - dst_off] = mk<TS>((TS)a01.x, (TS)a01.y);
+      }
+      if (jb + 16 < nc) {
+        dst[leg_addr(c0 + jb + 16, bb, I, 32) - dst_off] = mk<TS>((TS)a10.x, (TS)a10.y);
+        dst[leg_addr(c0 + jb + 16, bb + 16, I, 32) - dst_off] = mk<TS>((TS)a11.x, (TS)a11.y);
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < 32 * D; idx += blockDim.x) {
+        const int b = idx >> 5, j = idx & 31;
+        if (j < nc) {
+          V2<TC> acc = mk<TC>(0, 0);
+          const V2<TC>* mr = M + b * ld;
+          const V2<TC>* tr = tile + j * ld;
+          for (int k = 0; k < D; ++k) fma_c<TC>(acc, mr[k], tr[k]);
+          dst[leg_addr(c0 + j, b, I, D) - dst_off] = mk<TS>((TS)acc.x, (TS)acc.y);
+        }
       }
     }
     __syncthreads();
@@ -269,7 +298,7 @@ __global__ void bp_identity_kernel(double2* msgs, int64_t n, int D) {
 // (the products never mix s), so the scratch tensor X of a CTA holds D^deg
 // elements and the launch's scratch stays in L2.
 template <typename T, int K>
-__global__ void __launch_bounds__(kBpMsgThreads) bp_message_kernel(const BpMsgTask* __restrict__ tasks, int n_tasks,
+__global__ void __launch_bounds__(kBpMsgThreads, sizeof(T) == 4 && K == kGramPerSmall ? 5 : 1) bp_message_kernel(const BpMsgTask* __restrict__ tasks, int n_tasks,
                                                                 const V2<T>* __restrict__ gamma,
                                                                 const double* __restrict__ lam,
                                                                 const double2* __restrict__ msg_in,
@@ -322,8 +351,14 @@ __global__ void __launch_bounds__(kBpMsgThreads) bp_message_kernel(const BpMsgTa
         }
         int I = 1;
         for (int k = legs[l] + 1; k < z; ++k) I *= D;
-        if (l == 0) leg_product<T, T, true, kL>(X, off, G, 0, c0, c1, I, D, M, tA);
-        else leg_product<T, T, false, kL>(X, off, X, off, c0, c1, I, D, M, tA);
+        if (sizeof(T) == 4 && D == 32) {  // the 2 x 2 register tile (kD32); the FP64 build is
+                                          // bound by the FP64 pipe and would only lose registers
+          if (l == 0) leg_product<T, T, true, kL, true>(X, off, G, 0, c0, c1, I, D, M, tA);
+          else leg_product<T, T, false, kL, true>(X, off, X, off, c0, c1, I, D, M, tA);
+        } else {
+          if (l == 0) leg_product<T, T, true, kL>(X, off, G, 0, c0, c1, I, D, M, tA);
+          else leg_product<T, T, false, kL>(X, off, X, off, c0, c1, I, D, M, tA);
+        }
       }
       if (nl == 0) gram.template add<true, kL>(G, G, 0, c0, c1, Ip, D, tA, tB);
       else gram.template add<false, kL>(G, X, off, c0, c1, Ip, D, tA, tB);
