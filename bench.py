@@ -126,7 +126,9 @@ class Clocks:
 # DRAM bytes per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by workload, dtype and schedule; reported as the roofline's
 # `traffic` only for that configuration (profiles/step_kernel_heavyhex_mix_d32.md)
-NCU_TRAFFIC = {("heavyhex_mix_d32", "mixed", 4): 2.048679e9 + 1.742843e9}
+NCU_TRAFFIC = {("heavyhex_mix_d32", "mixed", 4): 2.048679e9 + 1.742843e9,
+               # schedule 5 (three CTAs per SM): dram__bytes.sum.per_second 122.32 GB/s x 35.60 ms
+               ("heavyhex_mix_d32", "mixed", 5): 122.321021e9 * 35.601440e-3}
 
 # ------------------------------------------------------------------ algorithmic counts
 def bond_fixed_flops(graphs, D, dtype):
