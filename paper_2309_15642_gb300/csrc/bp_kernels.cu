@@ -513,38 +513,36 @@ __device__ void gauge_eig(V2<R>* Am, V2<R>* W, int n, GaugeSmall<R>& sm, int* fl
   __syncthreads();
 }
 
-// Rt = G^{1/2} and Rinv = (G^{1/2})^+ of G = conj(m) (m: D x D FP64 message; n >= D,
-// padded with zeros), both FP64.  region: 2 n x n FP64 complex of work space.  With
-// R = float the eigenproblem is warm-started in FP32: its eigenvectors W are made
-// orthonormal in FP64 (one Newton-Schulz step, W <- W (3 - W^H W) / 2), G is rotated
-// into that basis in FP64 (W^H G W, nearly diagonal) and FP64 Jacobi sweeps finish it,
-// accumulating into W; as for R = double, W is then orthonormal and the eigenpairs
-// accurate to FP64, so Rinv Rt is the projector whatever the conditioning of G and the
-// gauge keeps the state exactly.
+// Eigenproblem of the FP64 Hermitian n x n matrix Hm (row stride n, left intact):
+// on return region[0, nn) holds W^H Hm W, diagonal to the Jacobi thresholds (the
+// eigenvalues on its diagonal), and region[nn, 2nn) the eigenvectors W, FP64 and
+// orthonormal.  region: 2 n x n FP64 complex; tmp: n x n FP64 complex of scratch.
+// R = double: FP64 Jacobi on a copy.  R = float: warm start by FP32 Jacobi on a
+// rounded copy, its eigenvectors made orthonormal in FP64 by one Newton-Schulz step
+// (W <- W (3 - W^H W) / 2), Hm rotated into that basis in FP64 (nearly diagonal)
+// and FP64 sweeps to finish, accumulated into W.  Either way W is orthonormal to
+// FP64 accuracy, so the gauge built from it keeps the state exactly whatever the
+// conditioning of Hm (FP32 eigenvectors alone are orthonormal only to ~1e-7).
 template <typename R>
-__device__ void gauge_root(const double2* m, int D, int n, double2* region, double2* Rt, double2* Rinv,
-                           GaugeSmall<R>& sm, GaugeSmall<double>& sm64, int* flags) {
+__device__ void eig_warm(const double2* Hm, int n, double2* region, double2* tmp, GaugeSmall<R>& sm,
+                         GaugeSmall<double>& sm64, int* flags) {
   const int nn = n * n;
-  V2<R>* Am = reinterpret_cast<V2<R>*>(region);  // FP32: [0, 8 nn) bytes; FP64: [0, 16 nn)
-  V2<R>* W = Am + nn;
-  double2* A64 = region;                          // FP64 matrix: [0, 16 nn) bytes
-  double2* W64 = region + nn;                     // FP64 eigenvectors: [16 nn, 32 nn) bytes
-  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
-    const int a = idx / n, b = idx - a * n;
-    V2<R> v = mk<R>(0, 0);
-    if (a < D && b < D) {
-      const double2 x = m[a * D + b];
-      v = mk<R>((R)x.x, (R)(-x.y));
-    }
-    Am[idx] = v;
-  }
-  __syncthreads();
-  gauge_eig<R>(Am, W, n, sm, flags);
-  if constexpr (sizeof(R) == 4) {
+  double2* A64 = region;      // FP64 matrix: [0, 16 nn) bytes
+  double2* W64 = region + nn;  // FP64 eigenvectors: [16 nn, 32 nn) bytes
+  if constexpr (sizeof(R) == 8) {
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) A64[idx] = Hm[idx];
+    __syncthreads();
+    gauge_eig<double>(A64, W64, n, sm64, flags);
+  } else {
+    V2<R>* Am = reinterpret_cast<V2<R>*>(region);  // FP32 pair: [0, 8 nn) and [8 nn, 16 nn) bytes
+    V2<R>* W = Am + nn;
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) Am[idx] = mk<R>((R)Hm[idx].x, (R)Hm[idx].y);
+    __syncthreads();
+    gauge_eig<R>(Am, W, n, sm, flags);
     for (int idx = threadIdx.x; idx < nn; idx += blockDim.x)
       W64[idx] = make_double2((double)W[idx].x, (double)W[idx].y);
     __syncthreads();
-    // orthonormalise: S = W^H W (in A64), then W <- 1.5 W - 0.5 W S (W S in Rt)
+    // orthonormalise: S = W^H W (in A64), then W <- 1.5 W - 0.5 W S (W S in tmp)
     for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
       const int a = idx / n, b = idx - a * n;
       double2 acc = make_double2(0.0, 0.0);
@@ -556,30 +554,26 @@ __device__ void gauge_root(const double2* m, int D, int n, double2* region, doub
       const int a = idx / n, b = idx - a * n;
       double2 acc = make_double2(0.0, 0.0);
       for (int k = 0; k < n; ++k) fma_c<double>(acc, W64[a * n + k], A64[k * n + b]);
-      Rt[idx] = acc;
+      tmp[idx] = acc;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
-      const double2 w = W64[idx], t = Rt[idx];
+      const double2 w = W64[idx], t = tmp[idx];
       W64[idx] = make_double2(1.5 * w.x - 0.5 * t.x, 1.5 * w.y - 0.5 * t.y);
     }
     __syncthreads();
-    // G W (in Rt), then A = W^H G W (in A64)
+    // Hm W (in tmp), then A = W^H Hm W (in A64)
     for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
       const int a = idx / n, l = idx - a * n;
       double2 acc = make_double2(0.0, 0.0);
-      if (a < D)
-        for (int b = 0; b < D; ++b) {
-          const double2 x = m[a * D + b];
-          fma_c<double>(acc, make_double2(x.x, -x.y), W64[b * n + l]);
-        }
-      Rt[idx] = acc;
+      for (int b = 0; b < n; ++b) fma_c<double>(acc, Hm[a * n + b], W64[b * n + l]);
+      tmp[idx] = acc;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
       const int k = idx / n, l = idx - k * n;
       double2 acc = make_double2(0.0, 0.0);
-      for (int a = 0; a < n; ++a) fma_conj<double>(acc, W64[a * n + k], Rt[a * n + l]);
+      for (int a = 0; a < n; ++a) fma_conj<double>(acc, W64[a * n + k], tmp[a * n + l]);
       A64[idx] = acc;
     }
     __syncthreads();
@@ -597,6 +591,28 @@ __device__ void gauge_root(const double2* m, int D, int n, double2* region, doub
     if (threadIdx.x == 0 && sw > kGaugeSweeps) atomicOr(flags, GPEPS_FLAG_NOCONV);
     __syncthreads();
   }
+}
+
+// Rt = G^{1/2} and Rinv = (G^{1/2})^+ of G = conj(m) (m: D x D FP64 message; n >= D,
+// padded with zeros), both FP64, through eig_warm (G is staged in Rt, Rinv is its
+// scratch until both are overwritten at the end).
+template <typename R>
+__device__ void gauge_root(const double2* m, int D, int n, double2* region, double2* Rt, double2* Rinv,
+                           GaugeSmall<R>& sm, GaugeSmall<double>& sm64, int* flags) {
+  const int nn = n * n;
+  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    const int a = idx / n, b = idx - a * n;
+    double2 v = make_double2(0.0, 0.0);
+    if (a < D && b < D) {
+      const double2 x = m[a * D + b];
+      v = make_double2(x.x, -x.y);
+    }
+    Rt[idx] = v;
+  }
+  __syncthreads();
+  eig_warm<R>(Rt, n, region, Rinv, sm, sm64, flags);
+  const double2* A64 = region;
+  const double2* W64 = region + nn;
   if (threadIdx.x == 0) {
     double wmax = 0.0;
     for (int k = 0; k < n; ++k) wmax = fmax(wmax, A64[k * n + k].x);
@@ -625,9 +641,9 @@ __device__ void gauge_root(const double2* m, int D, int n, double2* region, doub
   __syncthreads();
 }
 
-// 128-thread CTAs, four per SM.  The eigenproblems of G are warm-started in the
-// arithmetic R (FP32 for complex64 storage) and finished in FP64; the roots, C, its
-// eigenproblem C C^H (which sets
+// 128-thread CTAs, four per SM.  The three eigenproblems (both G and C C^H) are
+// warm-started in the arithmetic R (FP32 for complex64 storage) and finished in
+// FP64 (eig_warm); the roots, C, the eigenproblem of C C^H (which sets
 // lambda' and resolves the smallest Schmidt directions) and the gauge matrices
 // are FP64.  Slot layout (n x n FP64 complex each): Ri, Ri^+, Rj, Rj^+, C; the
 // Jacobi work space (2 n x n) in dynamic shared memory when it fits (in_smem),
@@ -669,15 +685,15 @@ __global__ void __launch_bounds__(kGaugeThreads, 4) bp_gauge_kernel(const BpEdge
       C[idx] = acc;
     }
     __syncthreads();
-    // H = C C^H, its eigenvectors U (in W)
+    // H = C C^H (in Ri, free now), its eigenvectors U (in W), warm-started like the roots
     for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
       const int a = idx / n, b = idx - a * n;
       double2 acc = make_double2(0.0, 0.0);
       for (int c = 0; c < n; ++c) fma_conj<double>(acc, C[b * n + c], C[a * n + c]);
-      Am[idx] = acc;
+      Ri[idx] = acc;
     }
     __syncthreads();
-    gauge_eig<double>(Am, W, n, sm64, flags);
+    eig_warm<R>(Ri, n, Am, Rj, sm, sm64, flags);
     // Y = C^T conj(U) (in Am, whose eigenvalues are not used), S_k = ||Y[:, k]||
     for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
       const int a = idx / n, k = idx - a * n;
