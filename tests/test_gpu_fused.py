@@ -42,6 +42,17 @@ def test_fused_step_bit_identical_benchmark_batch(dtype):
     assert torch.equal(a[2], b[2])
 
 
+def test_three_ctas_per_sm_fused_step_bit_identical_benchmark_batch():
+    """The benchmark batch at D = 32 (mixed) with three 192-thread fused-step CTAs per SM
+    (schedule 5, the autotuner's choice): the same state as the layered launches after 7 steps."""
+    w = workload("heavyhex_mix_d32")
+    a = _run(w.graphs(), 32, "mixed", [0.7] * 3, 7, 2)
+    b = _run(w.graphs(), 32, "mixed", [0.7] * 3, 7, 5)
+    assert a[3] == 0 and b[3] == 0
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert torch.equal(a[2], b[2])
+
+
 @pytest.mark.parametrize("dtype", ["mixed", "c128"])
 def test_fused_step_bit_identical_d64(dtype):
     """127 qubits, D = 64 (128 x 128 eigenproblems, one CTA per SM), 7 steps."""
