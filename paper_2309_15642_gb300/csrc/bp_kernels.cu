@@ -273,6 +273,70 @@ struct GramAcc {
   }
 };
 
+// The Gram at D = 32 in FP32 as a 2 x 2 register tile per thread (256 threads):
+// entries {ab, ab + 16} x {ap, ap + 16} of m, so a half-warp reads 16 consecutive
+// entries of a tA row and shares two of tB (one shared-memory wavefront per complex
+// FMA instead of about three).  The whole matrix is summed, in the same order as
+// GramAcc, and only the upper triangle is stored (mirrored), as there.
+struct GramAcc32 {
+  float2 a00, a01, a10, a11;
+
+  __device__ void init() { a00 = a01 = a10 = a11 = make_float2(0.f, 0.f); }
+
+  template <bool kConjB>
+  __device__ void add(const float2* A, const float2* B, int64_t b_off, int c_begin, int c_end, int I,
+                      float2* tA, float2* tB) {
+    constexpr int D = 32, ld = 33;
+    const int ab = threadIdx.x & 15, ap = threadIdx.x >> 4;
+    for (int c0 = c_begin; c0 < c_end; c0 += 32) {
+      const int nc = min(32, c_end - c0);
+      for (int idx = threadIdx.x; idx < 32 * D; idx += blockDim.x) {
+        int j, b;
+        tile_pos(idx, I, D, j, b);
+        float2 va = make_float2(0.f, 0.f), vb = va;
+        if (j < nc) {
+          const int64_t ad = leg_addr(c0 + j, b, I, D);
+          va = A[ad];
+          vb = B[ad - b_off];
+          if (kConjB) vb.y = -vb.y;
+        }
+        tA[j * ld + b] = va;
+        tB[j * ld + b] = vb;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) {
+        const float2 x0 = tA[j * ld + ab], x1 = tA[j * ld + ab + 16];
+        const float2 y0 = tB[j * ld + ap], y1 = tB[j * ld + ap + 16];
+        fma_c<float>(a00, x0, y0);
+        fma_c<float>(a01, x0, y1);
+        fma_c<float>(a10, x1, y0);
+        fma_c<float>(a11, x1, y1);
+      }
+      __syncthreads();
+    }
+  }
+
+  __device__ void store(double2* Mo) const {
+    constexpr int D = 32;
+    const int ab = threadIdx.x & 15, ap = threadIdx.x >> 4;
+    const int as[2] = {ab, ab + 16}, bs[2] = {ap, ap + 16};
+    const float2 v[2][2] = {{a00, a01}, {a10, a11}};
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        const int a = as[u], b = bs[w];
+        if (a == b) {
+          Mo[a * D + a] = make_double2((double)v[u][w].x, 0.0);
+        } else if (a < b) {
+          Mo[a * D + b] = make_double2((double)v[u][w].x, (double)v[u][w].y);
+          Mo[b * D + a] = make_double2((double)v[u][w].x, -(double)v[u][w].y);
+        }
+      }
+  }
+};
+
 __device__ __forceinline__ double block_max(double v, double* red) {
   for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -333,7 +397,10 @@ __global__ void __launch_bounds__(kBpMsgThreads, sizeof(T) == 4 && K == kGramPer
     int Ip = 1;
     for (int k = p + 1; k < z; ++k) Ip *= D;
     GramAcc<T, K> gram;
-    gram.init(D);
+    GramAcc32 gram32;
+    const bool tile32 = sizeof(T) == 4 && D == 32 && blockDim.x == 256;
+    if (tile32) gram32.init();
+    else gram.init(D);
     for (int s = 0; s < 2; ++s) {
       const int c0 = s * half, c1 = c0 + half;
       const int64_t off = s * sz;
@@ -360,10 +427,18 @@ __global__ void __launch_bounds__(kBpMsgThreads, sizeof(T) == 4 && K == kGramPer
           else leg_product<T, T, false, kL>(X, off, X, off, c0, c1, I, D, M, tA);
         }
       }
-      if (nl == 0) gram.template add<true, kL>(G, G, 0, c0, c1, Ip, D, tA, tB);
-      else gram.template add<false, kL>(G, X, off, c0, c1, Ip, D, tA, tB);
+      if (tile32) {
+        if constexpr (sizeof(T) == 4) {
+          if (nl == 0) gram32.add<true>(G, G, 0, c0, c1, Ip, tA, tB);
+          else gram32.add<false>(G, X, off, c0, c1, Ip, tA, tB);
+        }
+      } else {
+        if (nl == 0) gram.template add<true, kL>(G, G, 0, c0, c1, Ip, D, tA, tB);
+        else gram.template add<false, kL>(G, X, off, c0, c1, Ip, D, tA, tB);
+      }
     }
-    gram.store(Mo, D);
+    if (tile32) gram32.store(Mo);
+    else gram.store(Mo, D);
     __syncthreads();
     // the support of lambda_e: entries k with lambda_e[k] <= support_cut * max are zero
     const double* le = lam + tk.lam[p];
