@@ -11,8 +11,8 @@ Candidates (mixed path): schedule (one CTA per bond | work queue with one, two o
 four CTAs per SM | one fused launch per step; a schedule the handle rejects is
 skipped) x
 FP32-level thresholds (tol32, floor32) x FP64 stopping thresholds (tol,
-floor_rel = 1e-8 or 3e-8 of the trace: below the ~1e-7 relative rounding that
-the bond matrix inherits from its FP32 Gram inputs); complex128 keeps its
+floor_rel = 1e-8, 3e-8 or 1e-7 of the trace: up to the ~1e-7 relative rounding
+that the bond matrix inherits from its FP32 Gram inputs); complex128 keeps its
 rounding-level thresholds and tunes the schedule only.
 """
 from __future__ import annotations
@@ -23,7 +23,7 @@ import torch
 
 STRICT_MIXED = dict(tol=1e-9, floor_rel=1e-11, tol32=1e-6, floor32=2e-7)
 FP32_LEVELS = [(1e-6, 2e-7), (3e-6, 1e-6)]
-FP64_STOPS = [(1e-9, 1e-8), (1e-9, 3e-8)]
+FP64_STOPS = [(1e-9, 1e-8), (1e-9, 3e-8), (1e-9, 1e-7)]
 SCHEDULES = (0, 1, 2, 3, 4, 5)
 
 
