@@ -440,7 +440,7 @@ def run_gpeps(args, rank, world, local_rank):
     # per-kernel durations of profiled steps right after the timed region, under the schedule
     # of the timed region (fused: one launch per step; layered: three per colour class)
     sched = (tuning["chosen"].get("persistent", 0) if tuning else (args.schedule or 0))
-    fused = sched == 4
+    fused = sched >= 4          # schedules 4 and 5: the fused step (two or three CTAs per SM)
     prof = {"gram": [], "bond": [], "update": []} if not fused else {"kick": [], "bond_updates": [], "readout": []}
     s0, q0, b0 = g.sweeps()
     c0 = g.bond_phase_cycles()
@@ -477,7 +477,7 @@ def run_gpeps(args, rank, world, local_rank):
         launches_step = 1
         f32_big = big_end_flops(graphs, w.D)          # Gram and update passes inside the launch
         kernel = ("step_kernel (fused step: Gram pass, 2D x 2D bond eigenproblem with FP64 Jacobi and update "
-                  "of every bond of a Trotter step, one launch)")
+                  f"of every bond of a Trotter step, one launch, {3 if sched == 5 else 2} CTAs per SM where they fit)")
     else:
         launch_ms = sum(prof["bond"]) / max(len(prof["bond"]), 1)
         bonds_per_launch = bonds_step / g.n_colours
