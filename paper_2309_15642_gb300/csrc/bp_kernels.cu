@@ -188,62 +188,28 @@ struct GramAcc {
     }
   }
 
-  // A(c, b) at A[leg_addr(c, b)], B(c, b) at B[leg_addr(c, b) - b_off], c in [c_begin, c_end);
-  // the next tile is loaded into registers (kL per thread) while the current one is summed
-  template <bool kConjB, int kL>
+  // A(c, b) at A[leg_addr(c, b)], B(c, b) at B[leg_addr(c, b) - b_off], c in [c_begin, c_end)
+  template <bool kConjB>
   __device__ void add(const V2<T>* A, const V2<T>* B, int64_t b_off, int c_begin, int c_end, int I, int D,
                       V2<T>* tA, V2<T>* tB) {
     const int ld = D + 1;
     const int npairs = D * (D + 1) / 2;
-    constexpr int kB = kL > 0 ? kL : 1;
-    V2<T> ba[kB], bb[kB];
-    auto fetch = [&](int c0) {
+    for (int c0 = c_begin; c0 < c_end; c0 += 32) {
       const int nc = min(32, c_end - c0);
-#pragma unroll
-      for (int k = 0; k < kL; ++k) {
-        const int idx = threadIdx.x + k * blockDim.x;
+      for (int idx = threadIdx.x; idx < 32 * D; idx += blockDim.x) {
         int j, b;
         tile_pos(idx, I, D, j, b);
-        ba[k] = mk<T>(0, 0);
-        bb[k] = mk<T>(0, 0);
-        if (idx < 32 * D && j < nc) {
+        V2<T> va = mk<T>(0, 0), vb = mk<T>(0, 0);
+        if (j < nc) {
           const int64_t ad = leg_addr(c0 + j, b, I, D);
-          ba[k] = A[ad];
-          bb[k] = B[ad - b_off];
+          va = A[ad];
+          vb = B[ad - b_off];
+          if (kConjB) vb.y = -vb.y;
         }
-      }
-    };
-    if (kL > 0 && c_begin < c_end) fetch(c_begin);
-    for (int c0 = c_begin; c0 < c_end; c0 += 32) {
-      if constexpr (kL > 0) {
-#pragma unroll
-        for (int k = 0; k < kL; ++k) {
-          const int idx = threadIdx.x + k * blockDim.x;
-          int j, b;
-          tile_pos(idx, I, D, j, b);
-          if (idx < 32 * D) {
-            tA[j * ld + b] = ba[k];
-            tB[j * ld + b] = kConjB ? mk<T>(bb[k].x, -bb[k].y) : bb[k];
-          }
-        }
-      } else {
-        const int nc = min(32, c_end - c0);
-        for (int idx = threadIdx.x; idx < 32 * D; idx += blockDim.x) {
-          int j, b;
-          tile_pos(idx, I, D, j, b);
-          V2<T> va = mk<T>(0, 0), vb = mk<T>(0, 0);
-          if (j < nc) {
-            const int64_t ad = leg_addr(c0 + j, b, I, D);
-            va = A[ad];
-            vb = B[ad - b_off];
-            if (kConjB) vb.y = -vb.y;
-          }
-          tA[j * ld + b] = va;
-          tB[j * ld + b] = vb;
-        }
+        tA[j * ld + b] = va;
+        tB[j * ld + b] = vb;
       }
       __syncthreads();
-      if (kL > 0 && c0 + 32 < c_end) fetch(c0 + 32);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if (threadIdx.x + k * blockDim.x < npairs) {
@@ -433,8 +399,8 @@ __global__ void __launch_bounds__(kBpMsgThreads, sizeof(T) == 4 && K == kGramPer
           else gram32.add<false>(G, X, off, c0, c1, Ip, tA, tB);
         }
       } else {
-        if (nl == 0) gram.template add<true, kL>(G, G, 0, c0, c1, Ip, D, tA, tB);
-        else gram.template add<false, kL>(G, X, off, c0, c1, Ip, D, tA, tB);
+        if (nl == 0) gram.template add<true>(G, G, 0, c0, c1, Ip, D, tA, tB);
+        else gram.template add<false>(G, X, off, c0, c1, Ip, D, tA, tB);
       }
     }
     if (tile32) gram32.store(Mo);
