@@ -67,6 +67,25 @@ def parse():
     return ap.parse_args()
 
 
+# ------------------------------------------------------------------ replicas (N > 1)
+def max_over_ranks(ms, device=None):
+    """The largest of every rank's time (all-reduce MAX); the time itself without a process
+    group.  ``device``: where the reduction tensor lives (the rank's GPU under NCCL, the CPU
+    under gloo)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()):
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ms_max, world):
+    """Units of every replica over the slowest rank's time: the whole job's rate."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 # ------------------------------------------------------------------ clocks
 class Clocks:
     """nvidia-smi sampler (200 ms) running while the timed region runs."""
@@ -424,17 +443,13 @@ def run_gpeps(args, rank, world, local_rank):
         e1.synchronize()
         torch.cuda.synchronize(dev)
         ck = clocks.stop() if clocks else None
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), device=dev)
         flags = g.status()
         return g, th, out, ms, ck, flags, tuning
 
     g, th, out, ms, clocks, flags, tuning = timed(args.dtype, K, W, not args.no_autotune)
     bonds_step = g.bonds_per_step
-    value = world * bonds_step * K / (ms * 1e-3)
+    value = whole_job_rate(bonds_step * K, ms, world)
     mean_last = out[K - 1].cpu().numpy().tolist() if K else []
 
     # per-kernel durations of profiled steps right after the timed region, under the schedule
