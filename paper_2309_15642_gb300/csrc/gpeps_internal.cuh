@@ -10,7 +10,7 @@
 
 namespace gpeps {
 
-constexpr int kMaxD = 64;          // bond dimension limit of this build
+constexpr int kMaxD = 64;          // bond dimension limit of the library
 constexpr int kMaxLevel = 32;      // indices of one extra FP32 level (one per lane of a warp)
 constexpr size_t kSmemOptin = 232448;  // opt-in shared memory per CTA of sm_100/sm_103 (227 KB)
 constexpr size_t kBondSmemMax = kSmemOptin - 1024;  // dynamic part of a bond CTA (static variables need the rest)
