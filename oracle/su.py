@@ -32,7 +32,10 @@ is its neighbours sorted by label; ties at the truncation cut follow LAPACK's
 order.
 
 Parity pins: ``tests/test_oracle_su.py`` (state vectors on trees, light cones on
-the full lattices, the theta_h = 0, pi/2, pi invariants).
+the full lattices, the theta_h = 0, pi/2, pi invariants, and the truncation
+branch by Eckart-Young: the first truncated update on a tree in canonical form
+keeps the D largest Schmidt values of the state vector, renormalised, and the
+<Z> of both ends equals that of the state vector projected onto them).
 """
 from __future__ import annotations
 
@@ -149,13 +152,8 @@ class GPEPS:
         theta = np.einsum("ask,k,btk->asbt", Ri, lam, Rj) * self.g[None, :, None, :]   # gate
         theta = theta.reshape(2 * ri, 2 * rj)
         U, S, Vh = np.linalg.svd(theta, full_matrices=False)           # SVD
-        keep = min(D, S.size)                                           # truncate
-        U, S, Vh = U[:, :keep], S[:keep], Vh[:keep, :]
-        nrm = float(np.linalg.norm(S))
-        if not np.isfinite(nrm) or nrm == 0.0:
-            raise FloatingPointError(f"bond {e}: singular values vanish or are not finite")
-        lam_new = np.zeros(D)
-        lam_new[:keep] = S / nrm                                        # renormalise
+        U, Vh, lam_new = self._truncate(e, U, S, Vh)                    # truncate + renormalise
+        keep = U.shape[1]
         Gi = np.zeros((Qi.shape[0], 2, D), dtype=np.complex128)
         Gi[:, :, :keep] = np.einsum("ma,ask->msk", Qi, U.reshape(ri, 2, keep))
         Gj = np.zeros((Qj.shape[0], 2, D), dtype=np.complex128)
@@ -165,6 +163,21 @@ class GPEPS:
             T = np.moveaxis(G.reshape(oth + (2, D)), [nd - 2, nd - 1], [0, p + 1])
             self.gamma[site] = self._strip(T, site, p)                  # strip lambda^-1
         self.lam[e] = lam_new
+
+    def _truncate(self, e, U, S, Vh):
+        """Keep the D largest singular values (LAPACK returns them in decreasing
+        order) and their vectors; the new lambda is the kept values divided by their
+        own 2-norm, zero-padded to D ("Method": chi is the truncation parameter).
+        Returns (U[:, :keep], Vh[:keep], lambda')."""
+        D = self.D
+        keep = min(D, S.size)                                           # truncate
+        U, S, Vh = U[:, :keep], S[:keep], Vh[:keep, :]
+        nrm = float(np.linalg.norm(S))
+        if not np.isfinite(nrm) or nrm == 0.0:
+            raise FloatingPointError(f"bond {e}: singular values vanish or are not finite")
+        lam_new = np.zeros(D)
+        lam_new[:keep] = S / nrm                                        # renormalise
+        return U, Vh, lam_new
 
     def zz_layer(self, c):
         """Simple update of every edge of colour class c (a matching)."""

@@ -208,3 +208,109 @@ def test_parameter_shift_single_qubit_closed_form():
     th = 0.41
     g = parameter_shift_gradient(1, np.zeros((0, 2), int), [th], 3, np.ones(1))
     assert abs(g[0] + 3 * math.sin(3 * th)) < 1e-13
+
+
+# ------------------------------------------------------------------ truncation (Eckart-Young)
+# Trees where exactly one edge can exceed the bond dimension D: every other edge
+# has a side of at most log2(D) qubits, so its Schmidt rank never exceeds D and
+# its updates are exact.  The first update of the chosen edge whose Schmidt rank
+# exceeds D is therefore the first truncation of the run, applied to a tree in
+# exact Vidal canonical form, where the bond's SVD is the Schmidt decomposition
+# of the whole state across that edge.  By Eckart-Young the truncated update must
+# keep the D largest Schmidt values of the state-vector state after that gate,
+# renormalised to unit 2-norm, and the mean-field <Z> of both ends must be the
+# <Z> of the state vector projected onto those D Schmidt components.
+EY_CASES = [
+    ([1, 2, 3, 4, 5, 6, 15], (3, 4), 4, 0.7),        # degree-3 end (site 4) and degree-2 end
+    ([0, 1, 2, 3, 4, 5], (2, 3), 4, 0.9),            # chain: two degree-2 ends
+    ([0, 1, 2, 3, 4, 5, 6, 7, 15], (3, 4), 8, 0.8),  # D = 8, rank 16 before the cut
+]
+
+
+def _eckart_young(cls, verts, edge, D, theta):
+    """Run ``cls`` gate by gate next to the state vector until the first update of
+    ``edge`` whose Schmidt rank exceeds D.  Returns (max |lambda - top-D Schmidt
+    values renormalised|, max |<Z>| error at the two ends against the projected
+    state, the same ends' |<Z>| change caused by the projection)."""
+    m, e, labels = fragment(verts)
+    loc = {int(g): k for k, g in enumerate(labels)}
+    a, b = loc[edge[0]], loc[edge[1]]
+    peps = cls(m, e, D)
+    k_e = next(k for k, (x, y) in enumerate(e) if {int(x), int(y)} == {a, b})
+    g = nx.Graph([tuple(map(int, x)) for x in e])
+    for k, (x, y) in enumerate(e):
+        if k != k_e:   # every other edge has a side of <= log2(D) qubits
+            h = g.copy(); h.remove_edge(int(x), int(y))
+            assert 2 ** min(len(c) for c in nx.connected_components(h)) <= D
+    h = g.copy(); h.remove_edge(a, b)
+    side = sorted(nx.node_connected_component(h, a))
+    rest = [q for q in range(m) if q not in side]
+    psi = np.zeros((2,) * m, dtype=np.complex128)
+    psi[(0,) * m] = 1.0
+    for _ in range(8):
+        peps.kick(theta)
+        psi = sv._kick_all(psi, theta)
+        for c in range(peps.n_colours):
+            order = [int(k) for k in np.nonzero(peps.colour == c)[0] if k != k_e]
+            if peps.colour[k_e] == c:
+                order.append(k_e)            # a colour class is a matching: any order
+            for k in order:
+                peps.bond_update(k)
+                psi = psi * sv._zz_diagonal(m, e[k:k + 1], 1.0)
+                if k != k_e:
+                    continue
+                mat = np.transpose(psi, side + rest).reshape(2 ** len(side), -1)
+                U, S, Vh = np.linalg.svd(mat, full_matrices=False)
+                if int((S > 1e-12).sum()) <= D:
+                    continue
+                lam = S[:D] / np.linalg.norm(S[:D])
+                lam_err = float(np.abs(peps.lambdas()[k_e] - lam).max())
+                proj = (U[:, :D] * S[:D]) @ Vh[:D]
+                proj = np.transpose((proj / np.linalg.norm(proj)).reshape((2,) * m), np.argsort(side + rest))
+                z_proj, z_full, z = sv.z_expectations(proj), sv.z_expectations(psi), peps.expect_z()
+                z_err = max(abs(z[a] - z_proj[a]), abs(z[b] - z_proj[b]))
+                moved = min(abs(z_full[a] - z_proj[a]), abs(z_full[b] - z_proj[b]))
+                return lam_err, z_err, moved
+    raise AssertionError("the edge never exceeded D")
+
+
+@pytest.mark.parametrize("verts,edge,D,theta", EY_CASES)
+def test_truncation_keeps_the_largest_schmidt_values(verts, edge, D, theta):
+    lam_err, z_err, moved = _eckart_young(su.GPEPS, verts, edge, D, theta)
+    assert lam_err < 1e-13
+    assert z_err < 1e-13
+    assert moved > 1e-5        # the truncation is visible in <Z>: the pin is not vacuous
+
+
+class _KeepSmallest(su.GPEPS):
+    def _truncate(self, e, U, S, Vh):
+        keep = min(self.D, S.size)
+        lam = np.zeros(self.D)
+        lam[:keep] = S[-keep:] / np.linalg.norm(S[-keep:])
+        return U[:, -keep:], Vh[-keep:], lam
+
+
+class _NormaliseBeforeCut(su.GPEPS):
+    def _truncate(self, e, U, S, Vh):
+        keep = min(self.D, S.size)
+        lam = np.zeros(self.D)
+        lam[:keep] = (S / np.linalg.norm(S))[:keep]
+        return U[:, :keep], Vh[:keep], lam
+
+
+class _NoRenormalisation(su.GPEPS):
+    def _truncate(self, e, U, S, Vh):
+        keep = min(self.D, S.size)
+        lam = np.zeros(self.D)
+        lam[:keep] = S[:keep]
+        return U[:, :keep], Vh[:keep], lam
+
+
+@pytest.mark.parametrize("bad", [_KeepSmallest, _NormaliseBeforeCut, _NoRenormalisation])
+@pytest.mark.parametrize("verts,edge,D,theta", EY_CASES[:2])
+def test_planted_truncation_mistakes_fail_eckart_young(bad, verts, edge, D, theta):
+    try:
+        lam_err, z_err, _ = _eckart_young(bad, verts, edge, D, theta)
+    except (np.linalg.LinAlgError, FloatingPointError):
+        return   # keeping the smallest values keeps zeros before the first cut: the run breaks down
+    assert lam_err > 1e-5 or z_err > 1e-5
