@@ -149,13 +149,16 @@ int gpeps_zz_layer_profiled(gpeps_handle* h, int32_t colour, float* ms);
 int gpeps_step_profiled(gpeps_handle* h, const double* theta, int32_t per_qubit, float* ms);
 
 /*
- * Thresholds of the bond eigensolver (defaults in parentheses): FP64 sweeps
- * stop rotating a pair when |a_pq| <= max(tol sqrt(a_pp a_qq), floor_rel *
- * trace) (complex128: 1e-15, 4.4e-16; mixed: 1e-9, 1e-8); the FP32 levels use tol32
- * (1e-6) and floor32 (2e-7); sweep caps max_sweeps (40; hitting it sets
- * GPEPS_FLAG_NOCONV) and max_sweeps32 (20).  Host-only; drops a captured step
- * graph.  Errors: GPEPS_EINVAL for non-positive thresholds or caps outside
- * [1, 200] (FP64) / [0, 200] (FP32).
+ * Thresholds of the bond eigensolver (defaults in parentheses).  Mixed path: its
+ * FP64 sweeps on the squared bond matrix stop rotating a pair when |a_pq| <=
+ * max(tol sqrt(a_pp a_qq), floor_rel * trace) (1e-9, 1e-8).  Complex128 path: its
+ * FP64 one-sided sweeps on the bond core B stop rotating a column pair when
+ * |b_p^H b_q| <= max(tol |b_p| |b_q|, floor_rel ||B||_F^2) (1e-14, 1e-20).  The
+ * FP32 stages use tol32 (1e-6; complex128: relative to the two columns) and
+ * floor32 (2e-7; mixed only); sweep caps
+ * max_sweeps (40; hitting it sets GPEPS_FLAG_NOCONV) and max_sweeps32 (20).
+ * Host-only; drops a captured step graph.  Errors: GPEPS_EINVAL for
+ * non-positive thresholds or caps outside [1, 200] (FP64) / [0, 200] (FP32).
  */
 int gpeps_set_jacobi(gpeps_handle* h, double tol, double floor_rel, double tol32, double floor32,
                      int32_t max_sweeps, int32_t max_sweeps32);
@@ -356,12 +359,15 @@ int gpeps_jacobi_work(gpeps_handle* h, int64_t* work);
 
 /* Counters of the bond-eigenproblem kernel since the last gpeps_reset, summed
  * over bonds, host int64[22].  [0..5] SM cycles (clock64 of one thread per
- * CTA) of its phases: [0] reduced density matrix, [1] first FP32 Jacobi level,
- * [2] FP64 re-orthonormalisation of the FP32 eigenvectors, [3] V^dagger rho V
- * and the further FP32 levels on small-eigenvalue blocks, [4] FP64 Jacobi
- * sweeps, [5] truncation, Y matrices and the smaller end.  [6..13] rotations
- * applied in sweep 0..7 of the first FP32 level, [14..21] in FP64 sweep 0..7.
- * Synchronises. */
+ * CTA) of its phases: [0] the bond matrix (mixed: the reduced density matrix
+ * rho; complex128: the pivoted Cholesky roots of the Gram blocks, the core M
+ * and rho = M^H M), [1] first FP32 Jacobi level, [2] FP64 re-orthonormalisation
+ * of the FP32 eigenvectors, [3] mixed: V^dagger rho V and the further FP32
+ * levels on small-eigenvalue blocks; complex128: B = M V and the further FP32
+ * levels on blocks of small columns of B, [4] FP64 Jacobi sweeps (complex128:
+ * one-sided, on B), [5] truncation, Y matrices and the smaller end.  [6..13]
+ * rotations applied in sweep 0..7 of the first FP32 level, [14..21] in FP64
+ * sweep 0..7.  Synchronises. */
 int gpeps_bond_phase_cycles(gpeps_handle* h, int64_t* cycles);
 
 /*

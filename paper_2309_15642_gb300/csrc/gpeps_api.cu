@@ -231,7 +231,7 @@ int layered_per_sm(const gpeps_handle* h) {
     case 2: return 2;
     case 3: return 4;
     case 4:
-    case 5: return bond_footprint_global(h->D).smem <= bond_share_smem(2) ? 2 : 1;
+    case 5: return bond_footprint_global(h->D, h->elt).smem <= bond_share_smem(2) ? 2 : 1;
     default: return 1;
   }
 }
@@ -453,14 +453,18 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
       for (auto& pr : touched) last[pr.first] = pr.second;
     }
   }
-  // Jacobi thresholds: the bond matrix carries FP64 rounding (C128) or the
-  // FP32 rounding of its Gram inputs (mixed); eigenvalues below that level are noise.
-  // FP64 sweeps stop at |a_pq| <= max(tol sqrt(a_pp a_qq), floor_rel * trace):
-  // at FP64 rounding for complex128 (rho carries ~eps * trace), and a decade
-  // below the ~1e-7 * trace rounding that the mixed path's rho inherits from
-  // its FP32 inputs (resolving that rho further only fits noise)
-  h->jp.tol = dtype == GPEPS_C128 ? 1e-15 : 1e-9;
-  h->jp.floor_rel = dtype == GPEPS_C128 ? 4.4e-16 : 1e-8;
+  // Jacobi thresholds.  Mixed: the FP64 sweeps on the squared bond matrix stop at
+  // |a_pq| <= max(tol sqrt(a_pp a_qq), floor_rel * trace), a decade below the
+  // ~1e-7 * trace rounding that rho inherits from its FP32 inputs (resolving that
+  // rho further only fits noise).  Complex128: the one-sided sweeps on the bond
+  // core stop at |b_p^H b_q| <= max(tol |b_p| |b_q|, floor_rel * ||M||_F^2): tol
+  // at the rounding of a dot product of 2D terms (~2D eps), and a floor far
+  // below it so that Schmidt values down to ~1e-10 of the largest are resolved
+  // against each other (a floor at eps left lambda ~1e-8 off by 2e-8; at 1e-20
+  // lambda stays within 7e-11 of the oracle, at 1e-24 within 7e-13 for a
+  // quarter more FP64 work)
+  h->jp.tol = dtype == GPEPS_C128 ? 1e-14 : 1e-9;
+  h->jp.floor_rel = dtype == GPEPS_C128 ? 1e-20 : 1e-8;
   h->jp.tol32 = 1e-6;
   h->jp.floor32 = 2e-7;
   h->jp.ev_cut = 0.0;
@@ -505,8 +509,8 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   // blockIdx.x): beyond the shared-memory limit one slot per bond of the largest
   // class; otherwise slots for the two-CTAs-per-SM schedule only
   // (slots of the fused step are larger: they also hold the Gram sums and Y)
-  h->bond_slot = std::max(bond_footprint_global(D).slot, step_footprint(D, h->elt).slot);
-  h->bond_slots = bond_footprint(D, kBondSmemMax).slot ? h->max_bonds : std::min(h->max_bonds, 4 * kMaxSms);
+  h->bond_slot = std::max(bond_footprint_global(D, h->elt).slot, step_footprint(D, h->elt).slot);
+  h->bond_slots = bond_footprint(D, kBondSmemMax, h->elt).slot ? h->max_bonds : std::min(h->max_bonds, 4 * kMaxSms);
   h->bond_slots = std::max(h->bond_slots, std::min((int)h->tasks.size(), 2 * kMaxSms));
   h->w_bond_scratch = carve((size_t)h->bond_slots * h->bond_slot);
   h->w_tasks = carve(h->tasks.size() * sizeof(StepTask));
@@ -641,13 +645,13 @@ int gpeps_set_schedule(gpeps_handle* h, int32_t schedule) {
     if (fp.smem > kBondSmemMax || fp.slot > h->bond_slot) return GPEPS_EINVAL;
     if (std::min(2 * h->n_sms, (int)h->tasks.size()) > h->bond_slots) return GPEPS_EINVAL;
     // its layers (gpeps_zz_layer) run two CTAs per SM where they fit
-    const bool pair = bond_footprint_global(h->D).smem <= bond_share_smem(2);
+    const bool pair = bond_footprint_global(h->D, h->elt).smem <= bond_share_smem(2);
     if (pair && std::min(2 * h->n_sms, h->max_bonds) > h->bond_slots) return GPEPS_EINVAL;
   }
   if (schedule == 2 || schedule == 3) {
     // k CTAs per SM: shared memory of the FP32 level and a slot per CTA
     const int k = schedule == 3 ? 4 : 2;
-    if (!h->bound || bond_footprint_global(h->D).smem > bond_share_smem(k)) return GPEPS_EINVAL;
+    if (!h->bound || bond_footprint_global(h->D, h->elt).smem > bond_share_smem(k)) return GPEPS_EINVAL;
     if (std::min(k * h->n_sms, h->max_bonds) > h->bond_slots) return GPEPS_EINVAL;
   }
   h->schedule = schedule;

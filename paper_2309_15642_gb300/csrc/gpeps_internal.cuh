@@ -148,10 +148,12 @@ struct BondFootprint {
   size_t smem;
   size_t slot;
 };
-BondFootprint bond_footprint(int D, size_t smem_optin);
+// elt: bytes of a stored complex element (8: complex64, squared form; 16:
+// complex128, whose unsquared form always keeps its matrices in a global slot).
+BondFootprint bond_footprint(int D, size_t smem_optin, size_t elt);
 // The same with the n x n matrices always in a global slot (the FP32 level in
 // shared memory): the layout of the two-CTAs-per-SM schedule.
-BondFootprint bond_footprint_global(int D);
+BondFootprint bond_footprint_global(int D, size_t elt);
 // CTAs of the bond kernel sharing an SM in the global-matrix schedules: 2 of
 // 256 threads or 4 of 128 threads, each with at most 1/k of the SM's 228 KB of
 // shared memory (less 1 KB for the CTA's own reservation)

@@ -7,8 +7,9 @@
 // device), or a latency-critical loop that must not pay for an allocation.
 // Such a caller passes only its tensors; the scratch of the three launches
 // (Gram partials of the larger end, the Y matrices, the descriptors, the kick
-// angles and the flag word) lives in the file-scope device array below, which
-// every GPU that loads this library holds until the process exits.
+// angles, the flag word and, in complex128, the bond kernel's matrices) lives in
+// the file-scope device array below, which every GPU that loads this library
+// holds until the process exits.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -38,6 +39,8 @@ constexpr int kNoallocMaxD = 32;                                 // bond dimensi
 constexpr size_t kMaxTiles = (kNoallocMaxD * kNoallocMaxD + kTileRows - 1) / kTileRows;
 constexpr size_t kYOff = 1024;                                   // 2 D^2 complex
 constexpr size_t kPartOff = kYOff + (size_t)2 * kNoallocMaxD * kNoallocMaxD * 16;  // tiles x 2 D^2 complex
+// complex128: the global slot of the bond kernel's matrices (its size depends on D; checked per call)
+constexpr size_t kSlotOff = (kPartOff + kMaxTiles * 2 * kNoallocMaxD * kNoallocMaxD * 16 + 255) & ~(size_t)255;
 
 static_assert(kSweepsOff + kWorkCounters * sizeof(unsigned long long) <= kCyclesOff, "work counters");
 static_assert(kCyclesOff + kCounters * sizeof(unsigned long long) <= kPendingOff, "counter area");
@@ -120,7 +123,7 @@ int run(char* scratch, int D, void* base, const BondDesc& bd, int n_tiles, doubl
   cudaError_t e = Launch<T>::gram(tiles, n_tiles, bonds, base, lam, pending, partials, D, st);
   if (e == cudaSuccess)
     e = Launch<T>::bond(bonds, 1, partials, base, lam, pending, Y, theta_a, flags, sweeps, cycles, nullptr, D, jp,
-                        st);
+                        st, nullptr, 0, scratch + kSlotOff);
   if (e == cudaSuccess) e = Launch<T>::update(tiles, n_tiles, bonds, base, lam, Y, theta_a, D, st);
   (void)bd;
   return e == cudaSuccess ? GPEPS_OK : GPEPS_ECUDA;
@@ -138,6 +141,7 @@ extern "C" int gpeps_bond_update_noalloc(int32_t D, int32_t dtype, void* gamma_a
   if (leg_a < 0 || leg_a >= deg_a || leg_b < 0 || leg_b >= deg_b) return GPEPS_EINVAL;
   if (deg_a == 3 && deg_b == 3) return GPEPS_EINVAL;
   const size_t elt = dtype == GPEPS_C128 ? 16 : 8;
+  if (kSlotOff + bond_footprint(D, kBondSmemMax, elt).slot > GPEPS_NOALLOC_SCRATCH_BYTES) return GPEPS_EINVAL;
   const uintptr_t pa = reinterpret_cast<uintptr_t>(gamma_a), pb = reinterpret_cast<uintptr_t>(gamma_b);
   if ((pa % elt) || (pb % elt) || (reinterpret_cast<uintptr_t>(lam) % 8)) return GPEPS_EINVAL;
   void* sp = nullptr;
@@ -180,8 +184,8 @@ extern "C" int gpeps_bond_update_noalloc(int32_t D, int32_t dtype, void* gamma_a
   if (e != cudaSuccess) return GPEPS_ECUDA;
   // Jacobi thresholds of the batched path for this dtype
   JacobiParams jp{};
-  jp.tol = dtype == GPEPS_C128 ? 1e-15 : 1e-9;
-  jp.floor_rel = dtype == GPEPS_C128 ? 4.4e-16 : 1e-8;
+  jp.tol = dtype == GPEPS_C128 ? 1e-14 : 1e-9;
+  jp.floor_rel = dtype == GPEPS_C128 ? 1e-20 : 1e-8;
   jp.tol32 = 1e-6;
   jp.floor32 = 2e-7;
   jp.ev_cut = 0.0;

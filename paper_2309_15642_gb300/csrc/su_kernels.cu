@@ -183,15 +183,23 @@ struct BondSmem {
   size_t f32;
 };
 
-BondFootprint bond_footprint(int D, size_t smem_optin) {
+// Big part of the bond layout: the squared form (BondSmem) for complex64 storage,
+// the unsquared SVD form (SvdLayout, declared below) for complex128.
+__host__ __device__ size_t bond_big(int D, size_t elt);
+// Shared scratch after the small arrays: the FP32 level of the squared form, or
+// the FP32 warm start and levels of the unsquared form (svd_f32_bytes, below).
+__host__ __device__ size_t svd_f32_bytes(int D);
+static size_t bond_f32(int D, size_t elt) { return elt == 16 ? svd_f32_bytes(D) : BondSmem(D, 2 * D).f32; }
+
+BondFootprint bond_footprint(int D, size_t smem_optin, size_t elt) {
   const BondSmem L(D, 2 * D);
-  if (L.big + L.small <= smem_optin) return BondFootprint{L.big + L.small, 0};
-  return BondFootprint{L.small + L.f32, (L.big + 255) & ~(size_t)255};
+  if (elt == 8 && L.big + L.small <= smem_optin) return BondFootprint{L.big + L.small, 0};
+  return BondFootprint{L.small + bond_f32(D, elt), (bond_big(D, elt) + 255) & ~(size_t)255};
 }
 
-BondFootprint bond_footprint_global(int D) {
+BondFootprint bond_footprint_global(int D, size_t elt) {
   const BondSmem L(D, 2 * D);
-  return BondFootprint{L.small + L.f32, (L.big + 255) & ~(size_t)255};
+  return BondFootprint{L.small + bond_f32(D, elt), (bond_big(D, elt) + 255) & ~(size_t)255};
 }
 
 
@@ -302,21 +310,17 @@ __device__ double orthonormalise(double2* V, int n, double2* G, int ldg, double*
   return scal[6];
 }
 
-// Mixed-precision Jacobi eigensolver of the Hermitian n x n matrix RHO (FP64,
-// row stride n+1, trace > 0) in shared memory: FP32 sweeps to convergence on a
-// rounded copy, FP64 re-orthonormalisation of their eigenvectors, rho' =
-// V^dagger rho V in FP64, further FP32 levels on rescaled small-eigenvalue
-// blocks, FP64 sweeps to the thresholds of jp.  On return RHO is diagonal (the
-// eigenvalues) and Vm [n][n] holds the eigenvectors.  X is scratch of
-// max(n(n+1), n D) complex doubles; the small arrays as in bond_kernel.
-// Returns the FP64 sweeps (max_sweeps + 1 = cap hit).
-__device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, double trace, const JacobiParams& jp,
-                         double2* re, float2* re32, double* ev, double* rc, double* rs, double* scal, float* rc32,
-                         float* rs32, int* order, int* rp, int* rq, int* iflag, unsigned long long* sweeps_out,
-                         unsigned long long* cycles, int* flags, long long& t_prev, float2* f32s) {
+// FP32 warm start of a Hermitian eigenproblem: the FP64 n x n matrix RHO (row
+// stride n+1) rounded to FP32 and diagonalised there by parallel cyclic Jacobi
+// to convergence, its eigenvectors widened into Vm [n][n] and re-orthonormalised
+// in FP64 (`orthonormalise`, X as scratch).  The FP32 copies live in X, or
+// (f32s given: the n x n matrices are in global memory) packed in shared memory
+// at f32s.  Returns the FP32 sweeps.
+__device__ int fp32_warm_start(const double2* RHO, double2* Vm, double2* X, int n, double trace,
+                               const JacobiParams& jp, float2* re32, double* ev, double* scal, float* rc32,
+                               float* rs32, int* rp, int* rq, int* iflag, unsigned long long* sweeps_out,
+                               unsigned long long* cycles, int* flags, long long& t_prev, float2* f32s) {
   const int ldr = n + 1;
-  // FP32 level: rho32 [n][n+1] and V32 [n][n] in X, or (f32s given: the n x n
-  // matrices live in global memory) rho32 packed and V32 in shared memory f32s
   const bool packed = f32s != nullptr;
   float2* R32 = packed ? f32s : reinterpret_cast<float2*>(X);
   float2* V32 = packed ? f32s + (size_t)n * (n + 1) / 2 : R32 + (size_t)n * (n + 1);
@@ -327,7 +331,6 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
       t_prev = t;
     }
   };
-  // FP32 Jacobi on a rounded copy
   const HermPacked<float> P32{R32, n};
   if (packed) {
     for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
@@ -362,6 +365,32 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
   const double emax = orthonormalise(Vm, n, X, ldr, ev, scal);
   if (threadIdx.x == 0 && !(emax < 1e-4)) atomicOr(flags, 1);  // FP32 basis too far from unitary
   mark(2);
+  return sw32;
+}
+
+// Mixed-precision Jacobi eigensolver of the Hermitian n x n matrix RHO (FP64,
+// row stride n+1, trace > 0) in shared memory: FP32 sweeps to convergence on a
+// rounded copy, FP64 re-orthonormalisation of their eigenvectors, rho' =
+// V^dagger rho V in FP64, further FP32 levels on rescaled small-eigenvalue
+// blocks, FP64 sweeps to the thresholds of jp.  On return RHO is diagonal (the
+// eigenvalues) and Vm [n][n] holds the eigenvectors.  X is scratch of
+// max(n(n+1), n D) complex doubles; the small arrays as in bond_kernel.
+// Returns the FP64 sweeps (max_sweeps + 1 = cap hit).
+__device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, double trace, const JacobiParams& jp,
+                         double2* re, float2* re32, double* ev, double* rc, double* rs, double* scal, float* rc32,
+                         float* rs32, int* order, int* rp, int* rq, int* iflag, unsigned long long* sweeps_out,
+                         unsigned long long* cycles, int* flags, long long& t_prev, float2* f32s) {
+  const int ldr = n + 1;
+  const bool packed = f32s != nullptr;
+  auto mark = [&](int phase) {
+    if (threadIdx.x == 0 && cycles) {
+      const long long t = clock64();
+      atomicAdd(cycles + phase, (unsigned long long)(t - t_prev));
+      t_prev = t;
+    }
+  };
+  const int sw32 = fp32_warm_start(RHO, Vm, X, n, trace, jp, re32, ev, scal, rc32, rs32, rp, rq, iflag, sweeps_out,
+                                   cycles, flags, t_prev, f32s);
   // rho' = V^dagger rho V: W = rho V into X, then the upper triangle of V^dagger W into RHO
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int i = idx / n, j = idx - (idx / n) * n;
@@ -542,6 +571,617 @@ __device__ void load_F(const SideDesc& sb, const V2<T>* gamma, const double* lam
   }
 }
 
+// ---------------------------------------------------------------- unsquared bond SVD (complex128)
+// The squared form above resolves Schmidt values below ~sqrt(eps) of the
+// largest only approximately (rho = Psi^H Psi carries rounding of eps ||rho||).
+// The complex128 path takes the SVD of a 2D x n core of Psi itself.  Writing the
+// gated two-site matrix block by block in the physical index s of end a,
+//   Psi_s[r_a][x] = g(s, t_x) sum_k A~_s[r_a][k] lam_k F[x][k]  (x = (row of b, t)),
+// and G_s = R_s^H R_s for the Gram blocks G_s = A~_s^H A~_s of end a,
+// Psi = blockdiag(Q_0, Q_1) M with M[(s, j)][x] = g(s, t_x) sum_k R_s[j][k] lam_k F[x][k]
+// and Q_s isometric on the range of A~_s: Psi and M have the same singular
+// values and right singular vectors.  R_s is the pivoted Cholesky factor of G_s
+// (the bond's own lam enters only through M, so a pivot cut on G_s never drops a
+// bond index of small lam); the SVD of M is one-sided (Hestenes) Jacobi on B = M V0, preconditioned
+// by V0, the FP32 eigenvectors of M^H M re-orthonormalised in FP64, and by FP32
+// levels on rescaled blocks of B^H B whose columns are small (the Gram of B is
+// accurate relative to each column, unlike rho).  The Schmidt values are the
+// column norms of B, accurate to eps of the largest.
+
+constexpr double kCholCut = 1e-15;     // pivoted Cholesky stops below this fraction of the largest diagonal
+constexpr double kNoiseRelSvd = 1e-30; // columns of B with |b|^2 below this fraction of ||M||_F^2 are rounding
+
+// Global-slot layout (complex doubles) of the unsquared bond update, fixed for
+// n = 2D so that every bond of a launch shares it:
+//   Mt  [2D][2D]     M^T (Mt[x][s D + j]); F [n][D] again for the epilogue
+//   RB  [2D][2D+1]   rho = M^H M (row stride n + 1); then B^T (Bt[j][r] = B[r][j], row stride 2D)
+//   Vx  [2D][2D]     F [n][D] first; then V0 and finally V (row x, column j)
+//   Xs  [2D][2D+1]   G_s [2][D][D+1] and R_s [2][D][D] first; then the FP32
+//                    level's scratch; then V^T (Vt[j][x], row stride n)
+struct SvdLayout {
+  size_t off_Mt, off_RB, off_V, off_X, big;
+  __host__ __device__ explicit SvdLayout(int D) {
+    const size_t nm = (size_t)2 * D;
+    off_Mt = 0;
+    off_RB = off_Mt + nm * nm * 16;
+    off_V = off_RB + nm * (nm + 1) * 16;
+    off_X = off_V + nm * nm * 16;
+    big = off_X + nm * (nm + 1) * 16;
+  }
+};
+
+__host__ __device__ size_t bond_big(int D, size_t elt) {
+  return elt == 16 ? SvdLayout(D).big : BondSmem(D, 2 * D).big;
+}
+
+// Pivoted Cholesky of the two Hermitian positive semi-definite D x D matrices
+// G_0, G_1 (Cw, row stride D + 1, overwritten by their Schur complements), in
+// outer-product form with diagonal pivoting (the semi-definite Cholesky analysed
+// by Higham, 1990): step k takes the largest remaining diagonal C[p][p], row k of
+// R_s is C[p][j] / sqrt(C[p][p]) on the columns j not yet pivoted (sqrt(C[p][p])
+// at p, zero on the pivoted ones), and the unpivoted block is updated by
+// C[i][j] -= conj(R[k][i]) R[k][j].  A factor stops when its largest remaining
+// diagonal is <= kCholCut times its largest initial one (the rest is rounding);
+// its remaining rows are zero, so R_s^H R_s = G_s up to that cut.  Warps 0 and 1
+// choose the pivots of s = 0 and 1.  mask: 2D ints; piv: 4 ints; dk: 4 doubles.
+__device__ void pivoted_cholesky2(double2* Cw, double2* Rr, int D, int* mask, int* piv, double* dk) {
+  const int ldc = D + 1, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int idx = threadIdx.x; idx < 2 * D * D; idx += blockDim.x) Rr[idx] = make_double2(0.0, 0.0);
+  for (int idx = threadIdx.x; idx < 2 * D; idx += blockDim.x) mask[idx] = 1;
+  if (warp < 2) {
+    double mx = 0.0;
+    for (int i = lane; i < D; i += 32) mx = fmax(mx, Cw[(size_t)warp * D * ldc + i * ldc + i].x);
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) {
+      dk[2 + warp] = mx;  // largest initial diagonal
+      piv[2 + warp] = 1;  // factor still running
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < D; ++k) {
+    if (warp < 2) {
+      const int sidx = warp;
+      const double2* C = Cw + (size_t)sidx * D * ldc;
+      double best = -1.0;
+      int bi = D;
+      for (int i = lane; i < D; i += 32) {
+        if (mask[sidx * D + i]) {
+          const double d = C[i * ldc + i].x;
+          if (d > best) {
+            best = d;
+            bi = i;
+          }
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        const bool go = piv[2 + sidx] && bi < D && best > kCholCut * dk[2 + sidx] && best > 0.0;  // NaN stops
+        piv[sidx] = go ? bi : -1;
+        dk[sidx] = go ? best : 0.0;
+        if (go) mask[sidx * D + bi] = 0;
+        else piv[2 + sidx] = 0;
+      }
+    }
+    __syncthreads();
+    if (piv[0] < 0 && piv[1] < 0) break;
+    for (int idx = threadIdx.x; idx < 2 * D; idx += blockDim.x) {
+      const int sidx = idx / D, j = idx - (idx / D) * D, pv = piv[sidx];
+      if (pv < 0) continue;
+      const double r = sqrt(dk[sidx]);
+      double2 v = make_double2(0.0, 0.0);
+      if (j == pv) v = make_double2(r, 0.0);
+      else if (mask[sidx * D + j]) v = cscale(Cw[(size_t)sidx * D * ldc + pv * ldc + j], 1.0 / r);
+      Rr[(size_t)sidx * D * D + (size_t)k * D + j] = v;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 2 * D * D; idx += blockDim.x) {
+      const int sidx = idx / (D * D), ij = idx - sidx * D * D, i = ij / D, j = ij - (ij / D) * D;
+      if (piv[sidx] < 0 || !mask[sidx * D + i] || !mask[sidx * D + j]) continue;
+      const double2* r = Rr + (size_t)sidx * D * D + (size_t)k * D;
+      const double2 ri = r[i], rj = r[j];
+      double2& c = Cw[(size_t)sidx * D * ldc + i * ldc + j];
+      c.x -= ri.x * rj.x + ri.y * rj.y;
+      c.y -= ri.x * rj.y - ri.y * rj.x;
+    }
+    __syncthreads();
+  }
+}
+
+// Sum of a double over the lanes of a warp (every lane gets the total).
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// |b_j|^2 of the n columns of B (Bt [n][rows]) into alpha, one warp per column.
+__device__ void column_norms(const double2* Bt, int rows, int n, double* alpha) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < n; j += nw) {
+    const double2* b = Bt + (size_t)j * rows;
+    double a = 0.0;
+    for (int i = lane; i < rows; i += 32) a = fma(b[i].x, b[i].x, fma(b[i].y, b[i].y, a));
+    a = warp_sum(a);
+    if (lane == 0) alpha[j] = a;
+  }
+  __syncthreads();
+}
+
+// Pair k of round r of the round-robin pairing of n indices (as jacobi_hermitian).
+__device__ __forceinline__ void round_pair(int r, int k, int n, int& p, int& q) {
+  if (k == 0) {
+    p = r;
+    q = n - 1;
+  } else {
+    p = r + k;
+    if (p >= n - 1) p -= n - 1;
+    q = r - k;
+    if (q < 0) q += n - 1;
+  }
+}
+
+// Rotation of the column pair with squared norms a, b and inner product
+// g = b_p^H b_q (g != 0), the one that diagonalises [[a, g], [conj(g), b]]:
+// the phase e = conj(g) / |g| first, then t = tan of the angle from
+// t^2 + 2 zeta t - 1 = 0, zeta = (b - a) / (2 |g|) (Golub & Van Loan Alg. 8.4.1).
+// The three entries are first rescaled by the same power of two so that |g| ~ 1
+// (exact; the angle is scale-free), so that the FP32 seeds below cannot
+// underflow; then, as in `rotation`, 1/|g| and
+// t start in FP32 and are refined in FP64 by Newton steps, and c = 1/sqrt(1+t^2)
+// is Newton-normalised, so the rotation is unitary to FP64 rounding without FP64
+// divides or square roots.  When |zeta| is beyond FP32 range t = 1 / (2 zeta).
+// Also returns |g|.
+__device__ __forceinline__ void os_rotation(double a, double b, double2 g, double& c, double& s, double2& e,
+                                            double& ag) {
+  int ex;
+  frexp(fma(g.x, g.x, g.y * g.y), &ex);
+  const int k = ex >> 1;  // |g| ~ 2^k
+  a = ldexp(a, -k);
+  b = ldexp(b, -k);
+  g = make_double2(ldexp(g.x, -k), ldexp(g.y, -k));
+  const double g2 = fma(g.x, g.x, g.y * g.y);  // in [1/4, 2)
+  double ig = (double)rsqrtf((float)g2);
+  ig = ig * (1.5 - 0.5 * g2 * ig * ig);
+  ig = ig * (1.5 - 0.5 * g2 * ig * ig);
+  const double zeta = (b - a) * (0.5 * ig);
+  double t;
+  if (fabs(zeta) < 1e18) {
+    const float zf = (float)zeta;
+    t = (double)(copysignf(1.f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.f))));
+    const double f = fma(t, t, fma(2.0 * zeta, t, -1.0));
+    t -= f * (double)__frcp_rn((float)(2.0 * (t + zeta)));
+  } else {
+    t = 0.5 / zeta;
+  }
+  const double u = fma(t, t, 1.0);
+  double cc = (double)rsqrtf((float)u);
+  cc = cc * (1.5 - 0.5 * u * cc * cc);
+  cc = cc * (1.5 - 0.5 * u * cc * cc);
+  c = cc;
+  s = t * cc;
+  e = make_double2(g.x * ig, -g.y * ig);
+  ag = ldexp(g2 * ig, k);
+}
+
+// Rotation of a column pair in FP32 (the warm start and the levels): the same
+// angle as `os_rotation`, in plain FP32 arithmetic (the FP32 stages work on
+// matrices scaled to unit Frobenius norm and skip pairs with |g| below 1e-13,
+// so nothing underflows).  1/|g| and c = 1/sqrt(1+t^2) get one Newton step each
+// so that |e| = 1 and c^2 + s^2 = 1 to FP32 rounding: a column of a 128-wide
+// solve takes ~1500 rotations, and the ~2e-7 of rsqrtf alone would leave the
+// accumulated rotation ~3e-4 away from unitary.
+__device__ __forceinline__ void os_rot(float a, float b, float2 g, float& c, float& s, float2& e) {
+  const float g2 = fmaf(g.x, g.x, g.y * g.y);
+  float ig = rsqrtf(g2);
+  ig = ig * fmaf(-0.5f * g2, ig * ig, 1.5f);
+  const float zeta = (b - a) * (0.5f * ig);
+  const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+  const float u = fmaf(t, t, 1.f);
+  float cc = rsqrtf(u);
+  cc = cc * fmaf(-0.5f * u, cc * cc, 1.5f);
+  c = cc;
+  s = t * cc;
+  e = make_float2(g.x * ig, -g.y * ig);
+}
+__device__ __forceinline__ void os_rot(double a, double b, double2 g, double& c, double& s, double2& e) {
+  double ag;
+  os_rotation(a, b, g, c, s, e, ag);
+}
+
+// One-sided (Hestenes) Jacobi on the n columns of B (Bt [n][rows]), with V^T
+// (Vt [n][n]) rotated alongside, in the arithmetic of R (FP32 for the warm start
+// and the levels, FP64 for the final sweeps).  A sweep runs the n - 1 rounds of
+// the round-robin pairing; a round (1) forms |b_p|^2, |b_q|^2 and g = b_p^H b_q
+// of its n/2 disjoint pairs from the columns themselves (8 lanes per pair), (2)
+// decides and builds every rotation with one thread per pair (`os_rot`): pair
+// (p, q) rotates when |g| > max(tol |b_p| |b_q|, floor_abs), by
+// b_p <- c b_p - s e b_q, b_q <- s b_p + c e b_q, (3) applies the rotations of
+// the active pairs only, over the rows of B and V.  Norms are never carried
+// over from earlier rotations (a closed-form update loses digits when a pair is
+// nearly parallel, and every later angle of that column would inherit the
+// error).  A sweep without rotations ends the solve.  Returns the sweeps
+// (max_sweeps + 1 = cap hit); work[0] += pair checks, work[1] += rotations,
+// rot_count[sweep] += rotations of the first kRotSweeps sweeps (either may be
+// null).  rc, rs: n/2 reals; re: n/2 complex; iflag: the integer scratch of
+// jacobi_hermitian.  n <= 128.
+template <typename R>
+__device__ int one_sided_jacobi(V2<R>* Bt, int rows, V2<R>* Vt, int n, R tol, R floor_abs, int max_sweeps, R* rc,
+                                R* rs, V2<R>* re, int* iflag, unsigned long long* work,
+                                unsigned long long* rot_count) {
+  const int m = n / 2, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int sub = lane & 7, grp = lane >> 3;
+  int* act = iflag + 8;     // [2 warps][32] active pairs of the round
+  int* wcnt = iflag + 136;  // active pairs per warp
+  const R tol2 = tol * tol, floor2 = floor_abs * floor_abs;
+  const int len = rows + n;
+  unsigned long long n_chk = 0, n_rot = 0;
+  int result = max_sweeps + 1;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) iflag[3] = 0;
+    for (int r = 0; r < n - 1; ++r) {
+      // (1) norms and inner product of every pair: rc[k] = |b_p|^2, rs[k] = |b_q|^2, re[k] = g
+      for (int k0 = warp * 4; k0 < m; k0 += nw * 4) {
+        const int k = k0 + grp;
+        R a = 0, b = 0;
+        V2<R> g = mk<R>(0, 0);
+        if (k < m) {
+          int p, q;
+          round_pair(r, k, n, p, q);
+          const V2<R>* bp = Bt + (size_t)p * rows;
+          const V2<R>* bq = Bt + (size_t)q * rows;
+          for (int i = sub; i < rows; i += 8) {
+            const V2<R> u = bp[i], v = bq[i];
+            a = fma(u.x, u.x, fma(u.y, u.y, a));
+            b = fma(v.x, v.x, fma(v.y, v.y, b));
+            fma_conj<R>(g, u, v);
+          }
+        }
+        for (int off = 4; off > 0; off >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, off);
+          b += __shfl_xor_sync(0xffffffffu, b, off);
+          g.x += __shfl_xor_sync(0xffffffffu, g.x, off);
+          g.y += __shfl_xor_sync(0xffffffffu, g.y, off);
+        }
+        if (k < m && sub == 0) {
+          rc[k] = a;
+          rs[k] = b;
+          re[k] = g;
+        }
+      }
+      __syncthreads();
+      // (2) one thread per pair: test, rotation (c, s, e) into rc, rs, re, compacted active list
+      if (warp < 2) {
+        const int k = threadIdx.x;
+        bool on = false;
+        if (k < m) {
+          const V2<R> g = re[k];
+          const R a = rc[k], b = rs[k];
+          const R g2 = fma(g.x, g.x, g.y * g.y);
+          on = g2 > tol2 * a * b && g2 > floor2;
+          if (on) {
+            R c, sn;
+            V2<R> e;
+            os_rot(a, b, g, c, sn, e);
+            rc[k] = c;
+            rs[k] = sn;
+            re[k] = e;
+          }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, on);
+        if (on) act[warp * 32 + __popc(bal & ((1u << lane) - 1u))] = k;
+        if (lane == 0) wcnt[warp] = __popc(bal);
+      }
+      __syncthreads();
+      const int c0 = wcnt[0], na = c0 + wcnt[1];
+      if (threadIdx.x == 0) {
+        iflag[3] += na;
+        n_chk += (unsigned long long)m;
+        n_rot += (unsigned long long)na;
+      }
+      if (na == 0) continue;  // nothing below reads this round's scratch
+      // (3) the active rotations over the rows of B, then of V
+      for (int t = threadIdx.x; t < na * len; t += blockDim.x) {
+        const int ia = t / len, i = t - ia * len;
+        const int k = ia < c0 ? act[ia] : act[32 + ia - c0];
+        int p, q;
+        round_pair(r, k, n, p, q);
+        V2<R>* xp = i < rows ? Bt + (size_t)p * rows + i : Vt + (size_t)p * n + (i - rows);
+        V2<R>* xq = i < rows ? Bt + (size_t)q * rows + i : Vt + (size_t)q * n + (i - rows);
+        const R c = rc[k], sn = rs[k];
+        const V2<R> u = *xp, v = c_mul<R>(*xq, re[k]);
+        *xp = mk<R>(c * u.x - sn * v.x, c * u.y - sn * v.y);
+        *xq = mk<R>(sn * u.x + c * v.x, sn * u.y + c * v.y);
+      }
+      __syncthreads();
+    }
+    const int total = iflag[3];
+    if (threadIdx.x == 0 && rot_count && sweep < kRotSweeps) atomicAdd(rot_count + sweep, (unsigned long long)total);
+    __syncthreads();
+    if (total == 0) {
+      result = sweep + 1;
+      break;
+    }
+  }
+  if (work && threadIdx.x == 0) {
+    atomicAdd(work, n_chk);
+    atomicAdd(work + 1, n_rot);
+  }
+  return result;
+}
+
+// FP32 one-sided stages: relative threshold jp.tol32 (at the rounding of an FP32 dot product) and
+// this absolute one, in units of the largest squared column norm
+constexpr float kOsFloor32 = 1e-13f;
+
+// Shared scratch (bytes) after the small arrays of the unsquared bond update:
+// the FP32 warm start's B32 [n][2D] and V^T32 [n][n] (complex float) when D <= 32
+// (beyond, they use the global slot), and the FP32 levels' block of at most
+// lv = min(D, kMaxLevel) columns: B32 [lv][2D], W^T32 [lv][lv] (complex float),
+// W64 [lv][lv] and Gw [lv][lv+1] (complex double).
+__host__ __device__ size_t svd_level_w64_off(int cap, int rows) {
+  return ((size_t)cap * rows * 8 + (size_t)cap * cap * 8 + 15) & ~(size_t)15;
+}
+__host__ __device__ size_t svd_f32_bytes(int D) {
+  const size_t n = (size_t)2 * D, lv = D < kMaxLevel ? (size_t)D : (size_t)kMaxLevel;
+  const size_t lvl = svd_level_w64_off((int)lv, (int)n) + lv * lv * 16 + lv * (lv + 1) * 16;
+  const size_t warm = D <= 32 ? 2 * n * n * 8 : 0;
+  return lvl > warm ? lvl : warm;
+}
+
+// FP32 levels on the small columns of B: the columns whose squared norms lie
+// below jp.level_ratio x the scale of the last block that held them (the
+// largest column at first) and above rounding (kNoiseRelSvd of ||M||_F^2); the
+// largest ns <= lv of them form one block.  The block is copied to FP32, scaled
+// by the power of two that brings its largest column to norm ~1; FP32 one-sided
+// Jacobi makes those columns orthogonal to FP32 accuracy relative to each
+// column; the accumulated rotation W, re-orthonormalised in FP64, rotates those
+// columns of B and of V in FP64.  Meant to run after an FP64 sweep, which has
+// removed from the small columns their components along the large ones (else
+// the block would be their contamination).  lvl: as svd_f32_bytes.
+__device__ void svd_levels(double2* Bt, int rows, double2* Vt, int n, double tr, const JacobiParams& jp,
+                           double* alpha, double* rscale, int* mark_c, int* cand, double* scal, float2* re32,
+                           float* rc32, float* rs32, int* iflag, unsigned char* lvl, unsigned long long* sweeps_out) {
+  const int cap = (n / 2 < kMaxLevel) ? n / 2 : kMaxLevel;
+  float2* B32 = reinterpret_cast<float2*>(lvl);                                // [cap][rows]
+  float2* W32 = B32 + (size_t)cap * rows;                                      // [cap][cap], W^T
+  double2* W64 = reinterpret_cast<double2*>(lvl + svd_level_w64_off(cap, rows));  // [cap][cap]
+  double2* Gw = W64 + (size_t)cap * cap;                                       // [cap][cap+1]
+  const double lo = kNoiseRelSvd * tr;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int level = 0; level < jp.levels; ++level) {
+    column_norms(Bt, rows, n, alpha);
+    if (level == 0) {
+      if (threadIdx.x == 0) {
+        double s0 = 0.0;
+        for (int i = 0; i < n; ++i) s0 = fmax(s0, alpha[i]);
+        scal[3] = s0;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) rscale[i] = scal[3];
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      mark_c[i] = (alpha[i] > lo && alpha[i] <= jp.level_ratio * rscale[i]) ? 1 : 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      if (!mark_c[i]) continue;
+      const double ai = alpha[i];
+      int rank = 0;
+      for (int j = 0; j < n; ++j) rank += mark_c[j] && (alpha[j] > ai || (alpha[j] == ai && j < i));
+      if (rank < cap) cand[rank] = i;
+    }
+    if (threadIdx.x == 0) {
+      int cnt = 0;
+      for (int j = 0; j < n; ++j) cnt += mark_c[j];
+      iflag[1] = (cnt < cap ? cnt : cap) & ~1;  // even: the round-robin pairing needs it
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) scal[7] = iflag[1] > 0 ? alpha[cand[0]] : 0.0;
+    __syncthreads();
+    const int ns = iflag[1];
+    const double bscale = scal[7];
+    if (ns < 2 || !(bscale > 0.0)) break;
+    int ex;
+    frexp(bscale, &ex);
+    const double sc = ldexp(1.0, -(ex >> 1));  // the block's largest squared norm -> [1/2, 2)
+    for (int idx = threadIdx.x; idx < ns * rows; idx += blockDim.x) {
+      const int a = idx / rows, r = idx - (idx / rows) * rows;
+      const double2 v = Bt[(size_t)cand[a] * rows + r];
+      B32[idx] = make_float2((float)(v.x * sc), (float)(v.y * sc));
+    }
+    for (int idx = threadIdx.x; idx < ns * ns; idx += blockDim.x)
+      W32[idx] = make_float2((idx / ns) == (idx % ns) ? 1.f : 0.f, 0.f);
+    __syncthreads();
+    one_sided_jacobi<float>(B32, rows, W32, ns, (float)jp.tol32, kOsFloor32, jp.max_sweeps32, rc32, rs32, re32,
+                            iflag, sweeps_out + 6, nullptr);
+    for (int idx = threadIdx.x; idx < ns * ns; idx += blockDim.x) {
+      const int a = idx / ns, b = idx - (idx / ns) * ns;
+      const float2 v = W32[(size_t)b * ns + a];
+      W64[idx] = make_double2((double)v.x, (double)v.y);
+    }
+    __syncthreads();
+    orthonormalise(W64, ns, Gw, ns + 1, alpha, scal);
+    // rows of B (r < rows) and of V (x < n): new column cand[b] = sum_a old column cand[a] W[a][b]
+    for (int rr = warp; rr < rows + n; rr += nw) {
+      double2* base = rr < rows ? Bt + rr : Vt + (rr - rows);
+      const int ld = rr < rows ? rows : n;
+      double2 out = make_double2(0.0, 0.0);
+      if (lane < ns)
+        for (int a = 0; a < ns; ++a) fma_c<double>(out, base[(size_t)cand[a] * ld], W64[a * ns + lane]);
+      __syncwarp();
+      if (lane < ns) base[(size_t)cand[lane] * ld] = out;
+      __syncwarp();
+    }
+    for (int a = threadIdx.x; a < ns; a += blockDim.x) rscale[cand[a]] = bscale;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      atomicAdd(sweeps_out + 2, 1ull);
+      const unsigned long long nsl = (unsigned long long)ns;
+      atomicAdd(sweeps_out + 3, (unsigned long long)(rows + n) * nsl * nsl + 4ull * nsl * nsl * nsl / 3ull);
+    }
+  }
+}
+
+// Front half of the unsquared bond update (complex128): from the Gram blocks of
+// end a (FP64 sums in gsum, or this bond's partials) and end b, the right
+// singular vectors V (Vm [n][n], row x, column j) and squared singular values
+// (ev[j]) of the gated two-site matrix.  Returns false when M vanishes or is not
+// finite (the bond is then left unchanged by the caller).  lvl: the level
+// scratch in shared memory.
+template <bool kCG>
+__device__ bool bond_front_svd(const BondDesc& bd, const double2* __restrict__ partials, const double2* gsum,
+                               const double2* gamma, const double* lam, double th_b, int D, const JacobiParams& jp,
+                               unsigned char* big, double* lamo, double* ev, double* rc, double* rs, double2* re,
+                               double* scal, float2* re32, float* rc32, float* rs32, int* order, int* rp, int* rq,
+                               int* iflag,
+                               unsigned char* lvl, unsigned long long* sweeps_out, unsigned long long* cycles,
+                               int* flags, long long& t_prev, double2** Vm_out) {
+  const SideDesc& sb = bd.b;
+  const int n = 2 * sb.rows, rows = 2 * D, D2 = D * D, ldr = n + 1;
+  const SvdLayout L(D);
+  double2* Mt = reinterpret_cast<double2*>(big + L.off_Mt);
+  double2* RB = reinterpret_cast<double2*>(big + L.off_RB);
+  double2* Vx = reinterpret_cast<double2*>(big + L.off_V);
+  double2* Xs = reinterpret_cast<double2*>(big + L.off_X);
+  double2* Cw = Xs;                        // [2][D][D+1] Gram blocks G_s of end a
+  double2* Rr = Xs + (size_t)2 * D * (D + 1);  // [2][D][D]
+  double2* F = Vx;                         // [n][D]
+  int* mask = reinterpret_cast<int*>(Mt);  // [2][D] while the factors run
+  auto mark = [&](int phase) {
+    if (threadIdx.x == 0) {
+      const long long t = clock64();
+      atomicAdd(cycles + phase, (unsigned long long)(t - t_prev));
+      t_prev = t;
+    }
+  };
+  // G_s, FP64
+  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    if (gsum) {
+      acc = gsum[o];
+    } else {
+      for (int p = 0; p < bd.n_parts; ++p) {
+        const double2 v = partials[(int64_t)p * 2 * D2 + o];
+        acc.x += v.x;
+        acc.y += v.y;
+      }
+    }
+    const int sidx = o / D2, kl = o - sidx * D2, k = kl / D, l = kl - (kl / D) * D;
+    Cw[(size_t)sidx * D * (D + 1) + k * (D + 1) + l] = acc;
+  }
+  load_F<double, kCG>(sb, gamma, lam, th_b, F, D);
+  __syncthreads();
+  pivoted_cholesky2(Cw, Rr, D, mask, iflag + 8, scal + 4);
+  // M^T[x][s D + j] = g(s, t_x) sum_k R_s[j][k] lam_k F[x][k], g(s, t) = (1 + i sign) / sqrt 2 for
+  // s = t, (1 - i sign) / sqrt 2 otherwise (sign = gate_sign: exp(+-i pi/4 z_s z_t))
+  const double r2 = 0.70710678118654752440;
+  for (int idx = threadIdx.x; idx < n * rows; idx += blockDim.x) {
+    const int x = idx / rows, r = idx - (idx / rows) * rows, sidx = r / D, j = r - (r / D) * D;
+    const double2* Rj = Rr + (size_t)sidx * D2 + (size_t)j * D;
+    const double2* Fx = F + (size_t)x * D;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < D; ++k) fma_c<double>(acc, Rj[k], cscale(Fx[k], lamo[k]));
+    const double gi = ((sidx == (x & 1)) == (jp.gate_sign > 0)) ? r2 : -r2;
+    Mt[idx] = make_double2(r2 * acc.x - gi * acc.y, r2 * acc.y + gi * acc.x);
+  }
+  __syncthreads();
+  // ||M||_F^2
+  {
+    const int lane = threadIdx.x & 31;
+    double acc = 0.0;
+    for (int idx = threadIdx.x; idx < n * rows; idx += blockDim.x)
+      acc = fma(Mt[idx].x, Mt[idx].x, fma(Mt[idx].y, Mt[idx].y, acc));
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) scal[0] = 0.0;
+    __syncthreads();
+    if (lane == 0) atomicAdd(scal, acc);
+    __syncthreads();
+  }
+  const double trace = scal[0];
+  if (!(trace > 0.0) || !isfinite(trace)) return false;
+  mark(0);
+  // FP32 one-sided warm start on M scaled by the power of two that brings ||M||_F
+  // to ~1: its rotations leave a column of Schmidt value s_j at a cosine of
+  // ~1e-7 s_max / s_j against the others (the eigenvectors of the squared M^H M
+  // in FP32 would leave ~1e-7 (s_max / s_j)^3).  B32 [n][2D] and V^T32 [n][n] in
+  // shared memory up to D = 32, else over the free rho and scratch regions.
+  float2* B32 = D <= 32 ? reinterpret_cast<float2*>(lvl) : reinterpret_cast<float2*>(RB);
+  float2* Vt32 = D <= 32 ? B32 + (size_t)n * rows : reinterpret_cast<float2*>(Xs);
+  {
+    int ex;
+    frexp(trace, &ex);
+    const double sc = ldexp(1.0, -(ex >> 1));
+    for (int idx = threadIdx.x; idx < n * rows; idx += blockDim.x)
+      B32[idx] = make_float2((float)(Mt[idx].x * sc), (float)(Mt[idx].y * sc));
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x)
+      Vt32[idx] = make_float2((idx / n) == (idx % n) ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  const int sw32 = one_sided_jacobi<float>(B32, rows, Vt32, n, (float)jp.tol32, kOsFloor32, jp.max_sweeps32, rc32,
+                                           rs32, re32, iflag, sweeps_out + 6, cycles ? cycles + kPhases : nullptr);
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int x = idx / n, j = idx - (idx / n) * n;
+    const float2 v = Vt32[(size_t)j * n + x];
+    Vx[idx] = make_double2((double)v.x, (double)v.y);
+  }
+  __syncthreads();
+  mark(1);
+  {
+    const double emax = orthonormalise(Vx, n, Xs, ldr, ev, scal);
+    if (threadIdx.x == 0 && !(emax < 1e-4)) atomicOr(flags, 1);  // FP32 basis too far from unitary
+  }
+  mark(2);
+  // B = M V0 (Bt[j][r] = sum_x V0[x][j] M[r][x]) and V^T, over the free regions
+  double2* Bt = RB;
+  double2* Vt = Xs;
+  for (int idx = threadIdx.x; idx < n * rows; idx += blockDim.x) {
+    const int j = idx / rows, r = idx - (idx / rows) * rows;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int x = 0; x < n; ++x) fma_c<double>(acc, Vx[(size_t)x * n + j], Mt[(size_t)x * rows + r]);
+    Bt[idx] = acc;
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int j = idx / n, x = idx - (idx / n) * n;
+    Vt[idx] = Vx[(size_t)x * n + j];
+  }
+  __syncthreads();
+  // One FP64 sweep first: it converges the pairs of large columns and removes
+  // from the small columns their FP32-level components along the large ones
+  // (~1e-7 of the largest Schmidt value, which can exceed a small column's own
+  // size).  Only then are the small columns a clean block for the FP32 levels,
+  // whose rotations leave the last sweeps little to do.
+  unsigned long long* rot = cycles ? cycles + kPhases + kRotSweeps : nullptr;
+  const int sw1 = one_sided_jacobi(Bt, rows, Vt, n, jp.tol, jp.floor_rel * trace, 1, rc, rs, re, iflag,
+                                   sweeps_out + 4, rot);
+  mark(4);
+  // level marks in rp/rq (n ints, free until a level's Jacobi), candidates in order
+  svd_levels(Bt, rows, Vt, n, trace, jp, ev, rc, rp, order, scal, re32, rc32, rs32, iflag, lvl, sweeps_out);
+  mark(3);
+  const int sweeps = sw1 == 1 ? 1
+                              : 1 + one_sided_jacobi(Bt, rows, Vt, n, jp.tol, jp.floor_rel * trace, jp.max_sweeps - 1,
+                                                     rc, rs, re, iflag, sweeps_out + 4, rot ? rot + 1 : nullptr);
+  mark(4);
+  if (threadIdx.x == 0) {
+    if (sweeps > jp.max_sweeps) atomicOr(flags, 1);
+    atomicAdd(sweeps_out, (unsigned long long)(sweeps > jp.max_sweeps ? jp.max_sweeps : sweeps));
+    atomicAdd(sweeps_out + 1, (unsigned long long)(sw32 > jp.max_sweeps32 ? jp.max_sweeps32 : sw32));
+  }
+  // squared singular values (the column norms of B) and V back in row-major order
+  column_norms(Bt, rows, n, ev);
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int x = idx / n, j = idx - (idx / n) * n;
+    Vx[idx] = Vt[(size_t)j * n + x];
+  }
+  __syncthreads();
+  *Vm_out = Vx;
+  return true;
+}
+
 // Bond eigenproblem: rho (FP64), eigenvectors by FP32 Jacobi to convergence
 // (the FP32 pipe is 64x the FP64 pipe on this part), FP64 Cholesky-QR of the
 // FP32 eigenvectors, rho' = V^dagger rho V and FP64 Jacobi sweeps on rho' until
@@ -599,77 +1239,90 @@ __device__ void bond_body(const BondDesc bd, const V2<T>* __restrict__ partials,
 
   for (int k = threadIdx.x; k < D; k += blockDim.x) lamo[k] = ldst<kCG>(lam + bd.lam_e + k);
   __syncthreads();
-  for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
-    if (gsum) {
-      acc = gsum[o];
-    } else {
-      for (int p = 0; p < bd.n_parts; ++p) {
-        const V2<T> v = partials[(int64_t)p * 2 * D2 + o];
-        acc.x += (double)v.x;
-        acc.y += (double)v.y;
-      }
+  if constexpr (sizeof(T) == 8) {
+    // complex128: the unsquared SVD of the bond core, in the CTA's global slot
+    // (every launcher passes one for this dtype)
+    if (!big || !bond_front_svd<kCG>(bd, partials, gsum, gamma, lam, th_b, D, jp, big, lamo, ev, rc, rs, re, scal,
+                                     re32, rc32, rs32, order, rp, rq, iflag, smallp + L.small, sweeps_out, cycles,
+                                     flags, t_prev, &Vm)) {
+      bond_fail<T, kCG>(bd, Y, theta_a, pending, flags, D);
+      return;
     }
-    const int kl = o % D2;
-    const int k = kl / D, l = kl - (kl / D) * D;
-    const double2 v = cscale(acc, lamo[k] * lamo[l]);
-    Cs[o] = mk<T>((T)v.x, (T)v.y);
-  }
-  load_F<T, kCG>(sb, gamma, lam, th_b, F, D);
-  for (int idx = threadIdx.x; idx < n * ldr; idx += blockDim.x) RHO[idx] = make_double2(0.0, 0.0);
-  __syncthreads();
-  // rho = sum_s phase(s) o (conj(F) C_s F^T), upper triangle, then mirrored;
-  // products in the storage precision (the inputs carry no more), sum in FP64
-  for (int sidx = 0; sidx < 2; ++sidx) {
-    const V2<T>* C = Cs + sidx * D2;
-    for (int idx = threadIdx.x; idx < n * D; idx += blockDim.x) {
-      const int x = idx / D, l = idx - (idx / D) * D;
-      V2<T> acc = mk<T>(0, 0);
-      for (int k = 0; k < D; ++k) fma_conj<T>(acc, F[x * D + k], C[k * D + l]);
-      H[x * D + l] = acc;
+    F = reinterpret_cast<V2<T>*>(big + SvdLayout(D).off_Mt);
+    __syncthreads();
+  } else {
+    for (int o = threadIdx.x; o < 2 * D2; o += blockDim.x) {
+      double2 acc = make_double2(0.0, 0.0);
+      if (gsum) {
+        acc = gsum[o];
+      } else {
+        for (int p = 0; p < bd.n_parts; ++p) {
+          const V2<T> v = partials[(int64_t)p * 2 * D2 + o];
+          acc.x += (double)v.x;
+          acc.y += (double)v.y;
+        }
+      }
+      const int kl = o % D2;
+      const int k = kl / D, l = kl - (kl / D) * D;
+      const double2 v = cscale(acc, lamo[k] * lamo[l]);
+      Cs[o] = mk<T>((T)v.x, (T)v.y);
+    }
+    load_F<T, kCG>(sb, gamma, lam, th_b, F, D);
+    for (int idx = threadIdx.x; idx < n * ldr; idx += blockDim.x) RHO[idx] = make_double2(0.0, 0.0);
+    __syncthreads();
+    // rho = sum_s phase(s) o (conj(F) C_s F^T), upper triangle, then mirrored;
+    // products in the storage precision (the inputs carry no more), sum in FP64
+    for (int sidx = 0; sidx < 2; ++sidx) {
+      const V2<T>* C = Cs + sidx * D2;
+      for (int idx = threadIdx.x; idx < n * D; idx += blockDim.x) {
+        const int x = idx / D, l = idx - (idx / D) * D;
+        V2<T> acc = mk<T>(0, 0);
+        for (int k = 0; k < D; ++k) fma_conj<T>(acc, F[x * D + k], C[k * D + l]);
+        H[x * D + l] = acc;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+        int x, y;
+        upper_index(idx, n, x, y);
+        V2<T> acc = mk<T>(0, 0);
+        for (int l = 0; l < D; ++l) fma_c<T>(acc, H[x * D + l], F[y * D + l]);
+        const int tx = x & 1, ty = y & 1;
+        double2 v;
+        if (tx == ty) {
+          v = make_double2((double)acc.x, (double)acc.y);
+        } else if ((sidx == ty) == (jp.gate_sign > 0)) {  // +i (the conjugate gate swaps +i and -i)
+          v = make_double2(-(double)acc.y, (double)acc.x);
+        } else {  // -i
+          v = make_double2((double)acc.y, -(double)acc.x);
+        }
+        RHO[x * ldr + y] = cadd(RHO[x * ldr + y], v);
+      }
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int x = idx / n, y = idx - (idx / n) * n;
+      if (y > x) RHO[y * ldr + x] = cconj(RHO[x * ldr + y]);
+      if (y == x) RHO[x * ldr + x].y = 0.0;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
-      int x, y;
-      upper_index(idx, n, x, y);
-      V2<T> acc = mk<T>(0, 0);
-      for (int l = 0; l < D; ++l) fma_c<T>(acc, H[x * D + l], F[y * D + l]);
-      const int tx = x & 1, ty = y & 1;
-      double2 v;
-      if (tx == ty) {
-        v = make_double2((double)acc.x, (double)acc.y);
-      } else if ((sidx == ty) == (jp.gate_sign > 0)) {  // +i (the conjugate gate swaps +i and -i)
-        v = make_double2(-(double)acc.y, (double)acc.x);
-      } else {  // -i
-        v = make_double2((double)acc.y, -(double)acc.x);
-      }
-      RHO[x * ldr + y] = cadd(RHO[x * ldr + y], v);
+    if (threadIdx.x == 0) {
+      double tr = 0.0;
+      for (int i = 0; i < n; ++i) tr += RHO[i * ldr + i].x;
+      scal[0] = tr;
     }
     __syncthreads();
+    const double trace = scal[0];
+    if (!(trace > 0.0) || !isfinite(trace)) {
+      bond_fail<T, kCG>(bd, Y, theta_a, pending, flags, D);
+      return;
+    }
+    mark(0);
+    eig_mixed(RHO, Vm, X, n, D, trace, jp, re, re32, ev, rc, rs, scal, rc32, rs32, order, rp, rq, iflag, sweeps_out,
+              cycles, flags, t_prev, big ? reinterpret_cast<float2*>(smallp + L.small) : nullptr);
+    // eigenvalues sorted in decreasing order (ties by index)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ev[i] = RHO[i * ldr + i].x;
+    __syncthreads();
   }
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int x = idx / n, y = idx - (idx / n) * n;
-    if (y > x) RHO[y * ldr + x] = cconj(RHO[x * ldr + y]);
-    if (y == x) RHO[x * ldr + x].y = 0.0;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += RHO[i * ldr + i].x;
-    scal[0] = tr;
-  }
-  __syncthreads();
-  const double trace = scal[0];
-  if (!(trace > 0.0) || !isfinite(trace)) {
-    bond_fail<T, kCG>(bd, Y, theta_a, pending, flags, D);
-    return;
-  }
-  mark(0);
-  eig_mixed(RHO, Vm, X, n, D, trace, jp, re, re32, ev, rc, rs, scal, rc32, rs32, order, rp, rq, iflag, sweeps_out,
-            cycles, flags, t_prev, big ? reinterpret_cast<float2*>(smallp + L.small) : nullptr);
-  // eigenvalues sorted in decreasing order (ties by index)
-  for (int i = threadIdx.x; i < n; i += blockDim.x) ev[i] = RHO[i * ldr + i].x;
-  __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     int rank = 0;
     const double vi = ev[i];
@@ -1002,8 +1655,7 @@ __device__ void fused_update(const SideDesc& sa, V2<T>* gamma, const double* lam
 struct StepSlot {
   size_t off_gsum, off_Y, off_th, total;
   __host__ __device__ StepSlot(int D, size_t elt) {
-    const BondSmem L(D, 2 * D);
-    off_gsum = (L.big + 255) & ~(size_t)255;
+    off_gsum = (bond_big(D, elt) + 255) & ~(size_t)255;
     off_Y = off_gsum + (size_t)2 * D * D * 16;
     off_th = off_Y + (size_t)2 * D * D * elt;
     total = (off_th + 16 + 255) & ~(size_t)255;
@@ -1012,7 +1664,7 @@ struct StepSlot {
 
 BondFootprint step_footprint(int D, size_t elt) {
   const BondSmem L(D, 2 * D);
-  size_t sm = L.small + L.f32;
+  size_t sm = L.small + bond_f32(D, elt);
   const size_t gram = (size_t)kTileRows * (2 * D + 1) * elt;
   const size_t r = (size_t)kTileRows * (2 * D + 1), c = (size_t)(2 * D) * (kTileRows + 1);
   const size_t upd = (size_t)D * D * elt + (r > c ? r : c) * elt + (size_t)kTileRows * 4;
@@ -1290,7 +1942,7 @@ cudaError_t Launch<T>::bond(const BondDesc* bonds, int n_bonds, const void* part
                             unsigned int* queue, int n_ctas, void* scratch, int per_sm) {
   if (n_bonds == 0) return cudaSuccess;
   const bool shared = per_sm > 1;
-  const BondFootprint fp = shared ? bond_footprint_global(D) : bond_footprint(D, kBondSmemMax);
+  const BondFootprint fp = shared ? bond_footprint_global(D, sizeof(V2<T>)) : bond_footprint(D, kBondSmemMax, sizeof(V2<T>));
   if (fp.slot && !scratch) return cudaErrorInvalidValue;
   if (shared && (!queue || (per_sm != 2 && per_sm != 4) || fp.smem > bond_share_smem(per_sm)))
     return cudaErrorInvalidValue;

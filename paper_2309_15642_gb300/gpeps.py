@@ -206,9 +206,9 @@ class GPEPS:
     def set_jacobi(self, tol=None, floor_rel=None, tol32=1e-6, floor32=2e-7, max_sweeps=40, max_sweeps32=20):
         """Thresholds of the bond eigensolver (see gpeps_set_jacobi); None = the dtype's default."""
         if tol is None:
-            tol = 1e-15 if self.dtype == "c128" else 1e-9
+            tol = 1e-14 if self.dtype == "c128" else 1e-9
         if floor_rel is None:
-            floor_rel = 4.4e-16 if self.dtype == "c128" else 1e-8
+            floor_rel = 1e-20 if self.dtype == "c128" else 1e-8
         check(self.lib.gpeps_set_jacobi(self.h, float(tol), float(floor_rel), float(tol32), float(floor32),
                                         int(max_sweeps), int(max_sweeps32)), "gpeps_set_jacobi")
 

@@ -50,8 +50,9 @@ def sorted_lam(x):
 
 def lam_close(gpu, ref, dtype, truncated=False):
     """Sorted spectra: complex128 to 1e-6 everywhere and 1e-9 (5e-8 once truncated) where
-    lambda > 1e-3 (Schmidt values come from eigenvalues of the squared bond matrix, so the
-    small ones are resolved to ~sqrt(eps) of the largest); mixed to 2e-3."""
+    lambda > 1e-3 (after a regauge the bond weights come from the eigenproblem of the
+    squared matrix C C^H of the gauge, so the small ones are resolved to ~sqrt(eps) of
+    the largest); mixed to 2e-3."""
     d = np.abs(sorted_lam(gpu) - np.asarray(ref))
     if dtype != "c128":
         return d.max() < TOL_LAM["mixed"]

@@ -21,7 +21,7 @@ from ._gpu_util import gpu_lib, split
 pytestmark = pytest.mark.gpu
 
 TOL = {"c128": 1e-10, "mixed": 1e-4}
-TOL_TRUNC = {"c128": 5e-9, "mixed": 1e-4}
+TOL_TRUNC = {"c128": 1e-10, "mixed": 1e-4}
 CELL = heavy_hex_cell()
 COL = heavy_hex_cell_colour()
 

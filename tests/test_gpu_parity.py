@@ -1,17 +1,16 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle and the exact pins.
 
 Tolerances: |d<Z>| <= 1e-10 for the complex128 path and <= 1e-4 for the mixed
-path (complex64 tensors, FP64 bond eigensolver), on every qubit in the exact
-(untruncated) regime and on the mean <Z> always.  Per-qubit <Z> after many
-truncated steps in complex128 is held to 5e-9: the GPU obtains Schmidt vectors
-from the eigenproblem of a Gram-type (squared) matrix, whose eigenvectors are
-accurate to eps ||rho|| / gap, so components of relative size below ~1e-8 are
-resolved only approximately (the same formulation with LAPACK's eigensolver
-reaches 9e-10 on the 16-angle sweep).  lambda spectra: a Schmidt value is
-resolved down to ~sqrt(eps) of the largest: entries are compared to 1e-6
-(c128) / 2e-3 (mixed) absolute, and where the oracle's value exceeds 1e-3 to
-1e-9 (c128) in the exact regime and 5e-8 after many truncated steps (the
-state itself then differs from the oracle's by O(sqrt(eps)) in norm).
+path (complex64 tensors, FP64 bond eigensolver), on every qubit, in the exact
+(untruncated) regime and after many truncated steps alike.  The complex128 path
+takes the SVD of the gated two-site core itself (no squared matrix), so its
+Schmidt values carry absolute errors of eps times the largest: lambda is
+compared to 1e-9 absolute.  The mixed path forms the bond matrix from FP32 Gram
+partials (rounding ~1e-7 of its trace) and diagonalises that squared matrix, so
+a Schmidt value lam carries an absolute error of about 1e-7 / (2 lam): lambda is
+compared to 2e-3 absolute, and to 5e-6 / lam + 2e-4 where the oracle's value
+exceeds 1e-3 (the 2e-4 is the drift of the state itself after truncated steps,
+the size of the <Z> tolerance).
 """
 import json
 import math
@@ -30,7 +29,6 @@ from ._gpu_util import run_layers, run_step, split
 pytestmark = pytest.mark.gpu
 
 TOL = {"c128": 1e-10, "mixed": 1e-4}
-TOL_SITE_TRUNC = {"c128": 5e-9, "mixed": 1e-4}    # per qubit, long truncated runs
 M127, E127 = heavy_hex(*EAGLE)
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -46,11 +44,14 @@ def oracle_run(n, e, D, theta, steps):
 
 def lam_check(gpu_lam, orc_lam, dtype, truncated=False):
     d = np.abs(gpu_lam - orc_lam)
-    assert d.max() < (1e-6 if dtype == "c128" else 2e-3), d.max()
     if dtype == "c128":
-        big = orc_lam > 1e-3
-        if big.any():
-            assert d[big].max() < (5e-8 if truncated else 1e-9), d[big].max()
+        assert d.max() < 1e-9, d.max()
+        return
+    assert d.max() < 2e-3, d.max()
+    big = orc_lam > 1e-3
+    if big.any():
+        bound = 5e-6 / orc_lam[big] + 2e-4
+        assert (d[big] < bound).all(), (d[big] / bound).max()
 
 
 @pytest.mark.parametrize("dtype", ["c128", "mixed"])
@@ -199,7 +200,7 @@ def test_theta_sweep_16_instances(dtype):
     for k, inst in enumerate(gold["instances"]):
         if _is_clifford_tie(theta[k], w.steps, w.D):
             continue   # <Z> and lambda of a truncated flat spectrum are not unique
-        assert np.abs(zi[k] - np.array(inst["z"][str(w.steps)])).max() < TOL_SITE_TRUNC[dtype]
+        assert np.abs(zi[k] - np.array(inst["z"][str(w.steps)])).max() < TOL[dtype]
         for e, lam in inst["lambda"][str(w.steps)].items():
             lam_check(g.lambdas(k, int(e)), np.array(lam), dtype, truncated=True)
 
@@ -224,7 +225,7 @@ def test_heavyhex_mix_d32_full_size(dtype):
         z, _ = g.expect_z()
         zi = split(z.cpu().numpy(), graphs)
         for k, inst in enumerate(gold["instances"]):
-            tol = TOL[dtype] if 2 ** s <= w.D else TOL_SITE_TRUNC[dtype]
+            tol = TOL[dtype] if 2 ** s <= w.D else TOL[dtype]
             assert np.abs(zi[k] - np.array(inst["z"][str(s)])).max() < tol, (s, k)
             for e, lam in inst["lambda"][str(s)].items():
                 lam_check(g.lambdas(k, int(e)), np.array(lam), dtype, truncated=2 ** s > w.D)

@@ -22,7 +22,7 @@ from ._gpu_util import gpu_lib
 pytestmark = pytest.mark.gpu
 
 TOL = {"c128": 1e-10, "mixed": 1e-4}
-TOL_TRUNC = {"c128": 5e-9, "mixed": 1e-4}
+TOL_TRUNC = {"c128": 1e-10, "mixed": 1e-4}
 M127, E127 = heavy_hex(*EAGLE)
 
 
