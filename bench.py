@@ -62,6 +62,9 @@ def parse():
                     help="time Trotter steps with a belief-propagation regauge after each (the paper's BP "
                          "comparison) instead of the plain step")
     ap.add_argument("--bp-max-iter", type=int, default=200)
+    ap.add_argument("--no-condor", action="store_true", help="skip the 1121-qubit D = 64 record")
+    ap.add_argument("--cpu-leg", action="store_true",
+                    help="internal: time one leg of the CPU oracle baseline and print it as JSON")
     ap.add_argument("--floor-rel", type=float, default=None,
                     help="with --no-autotune: FP64 Jacobi floor (fraction of the trace) of the mixed path")
     return ap.parse_args()
@@ -153,27 +156,51 @@ NCU_TRAFFIC = {("heavyhex_mix_d32", "mixed", 4): 2.048679e9 + 1.742843e9,
 def bond_fixed_flops(graphs, D, dtype):
     """(FP64, FP32) flops of one Trotter step's bond eigenproblems that do not depend on how the
     Jacobi sweeps converge, per bond with its own n = 2 D^(deg - 1) (deg of the smaller end;
-    8 flops per complex MAC): re-orthonormalisation of the FP32 eigenvectors 4 n^3 / 3 MACs and
-    rho' = V^dagger rho V 3 n^3 / 2 MACs in FP64; the rho formation 2 (n D^2 + n(n+1)/2 D) MACs
-    and the Y matrices 2 D^2 n MACs in the storage precision (FP64 for complex128, FP32 for the
-    mixed path).  The extra FP32 levels' FP64 work is counted in the kernel."""
+    8 flops per complex MAC).  Mixed path (squared form): re-orthonormalisation of the FP32
+    eigenvectors 4 n^3 / 3 MACs and rho' = V^dagger rho V 3 n^3 / 2 MACs in FP64; the rho
+    formation 2 (n D^2 + n(n+1)/2 D) MACs and the Y matrices 2 D^2 n MACs in FP32.  Complex128
+    (unsquared form, all FP64): the pivoted Cholesky roots of the two D x D Gram blocks 2 D^3 / 3
+    MACs, the core M = 2D x n, 2D n D MACs, the re-orthonormalisation 4 n^3 / 3, B = M V0 2D n^2
+    and the Y matrices 2 D^2 n MACs.  The Jacobi sweeps and the levels are counted in the kernel."""
     import numpy as np
     f64 = f32 = 0.0
     for n_q, edges in graphs:
         deg = np.bincount(np.asarray(edges).ravel(), minlength=n_q)
         for a, b in edges:
             n = 2 * D ** (int(min(deg[a], deg[b])) - 1)
-            f64 += (4.0 * n ** 3 / 3.0 + 1.5 * n ** 3) * 8
-            prod = (2 * (n * D * D + n * (n + 1) / 2 * D) + 2 * D * D * n) * 8
             if dtype == "c128":
-                f64 += prod
-            else:
-                f32 += prod
+                f64 += (2.0 * D ** 3 / 3 + 2 * D * n * D + 4.0 * n ** 3 / 3 + 2 * D * n * n + 2 * D * D * n) * 8
+                continue
+            f64 += (4.0 * n ** 3 / 3.0 + 1.5 * n ** 3) * 8
+            f32 += (2 * (n * D * D + n * (n + 1) / 2 * D) + 2 * D * D * n) * 8
     return f64, f32
 
 
 # flops of one executed Jacobi 2x2 block update (both sides) and one eigenvector pair update
+# (two-sided, mixed path)
 JACOBI_BLOCK_FLOPS, JACOBI_VEC_FLOPS = 72, 18
+
+
+def one_sided_flops(D, checks, rotations):
+    """Real flops of the complex128 one-sided sweeps: a pair check forms |b_p|^2, |b_q|^2 and
+    b_p^H b_q over the 2D rows (16 flops per row), a rotation updates 2D rows of B and n <= 2D
+    rows of V (18 flops per row pair; counted at n = 2D)."""
+    return checks * 16 * 2 * D + rotations * 18 * 4 * D
+
+
+# ------------------------------------------------------------------ committed oracle values
+def load_golden(w):
+    """The committed FP64 oracle values of workload ``w`` (tests/golden), or None."""
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_{w.name}.json")
+    return json.load(open(path)) if os.path.exists(path) else None
+
+
+def golden_z(gold, step):
+    """Per-qubit <Z> of every instance after ``step`` steps, concatenated (or None)."""
+    import numpy as np
+    if gold is None or any(str(step) not in inst["z"] for inst in gold["instances"]):
+        return None
+    return np.concatenate([np.asarray(inst["z"][str(step)], dtype=np.float64) for inst in gold["instances"]])
 
 
 # FP32 vector peak from the unit counts and the maximum SM clock: 152 SMs x 128 FP32 FMA per
@@ -342,42 +369,53 @@ def step_bytes(graphs, D, elt):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_oracle(w, seconds_cap=30.0):
-    """The FP64 oracle on a bounded sample: the first lattice of the batch from |0...0>,
-    whole Trotter steps (kick, every colour class, readout) while fewer than ``seconds_cap / 2``
-    seconds have passed; a step that would run past ``seconds_cap`` is cut after the bond
-    update that crosses it (large D: one step of the 1121-qubit lattice at D = 64 takes
-    minutes).  Rate = bond updates / elapsed time."""
+def cpu_oracle_leg(w, warmup, seconds_cap):
+    """The FP64 oracle on the first lattice of the batch, in the GPU arm's steady-state window:
+    ``warmup`` Trotter steps from |0...0> untimed, then whole Trotter steps (kick, every colour
+    class, readout) timed while fewer than ``seconds_cap`` seconds have passed (at least one)."""
     import numpy as np
     from oracle.su import GPEPS as OraclePEPS
     from workloads import kick_angles
     (n, edges) = w.graphs()[0]
     th = kick_angles(w)[0]
     peps = OraclePEPS(n, edges, w.D)
+    for _ in range(warmup):
+        peps.step(th)
     t0 = time.perf_counter()
-    steps = bonds = 0
-    cut = False
-    while not cut and steps < w.steps and (steps == 0 or time.perf_counter() - t0 < seconds_cap * 0.5):
-        peps.kick(th)
-        for c in range(peps.n_colours):
-            for e in np.nonzero(peps.colour == c)[0]:
-                peps.bond_update(int(e))
-                bonds += 1
-                if time.perf_counter() - t0 > seconds_cap:
-                    cut = True
-                    break
-            if cut:
-                break
-        if not cut:
-            peps.expect_z()
-            steps += 1
+    steps = 0
+    while steps == 0 or (time.perf_counter() - t0 < seconds_cap and warmup + steps < w.steps):
+        peps.step(th)
+        peps.expect_z()
+        steps += 1
     dt = time.perf_counter() - t0
-    what = f"{steps} Trotter steps" + (" and part of the next" if cut else "")
-    return {"value": bonds / dt, "unit": "bond updates/s", "cores": os.cpu_count(),
-            "kind": "oracle",
-            "sample": f"{n}-qubit lattice of the batch, D={w.D}, {what} from |0...0> "
-                      f"({bonds} bond updates, numpy/LAPACK FP64, default BLAS threads)",
-            "seconds": dt, "steps": steps}
+    return {"bond_updates_per_s": len(edges) * steps / dt, "trotter_steps_per_s": steps / dt,
+            "window": f"{warmup + 1}..{warmup + steps}", "seconds": dt, "qubits": n, "bonds_per_step": len(edges)}
+
+
+def cpu_oracle(w, warmup, seconds_cap=10.0):
+    """Oracle baseline, two legs over the same window: numpy/LAPACK with its default thread
+    count, and a child process whose BLAS/OpenMP pools are set to one thread before numpy loads."""
+    allt = cpu_oracle_leg(w, warmup, seconds_cap)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    single = None
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-leg", "--workload", w.name,
+                            "--warmup", str(warmup)], env=env, capture_output=True, text=True, timeout=900)
+        if r.returncode == 0 and r.stdout.strip():
+            single = json.loads(r.stdout.strip().splitlines()[-1])
+    except (subprocess.TimeoutExpired, ValueError):
+        single = None
+    def sample(leg):
+        return (f"{leg['qubits']}-qubit lattice of the batch, D={w.D}, Trotter steps {leg['window']} after "
+                f"{warmup} untimed warm-up steps from |0...0> (the GPU arm's steady-state window), "
+                f"numpy/LAPACK FP64")
+    return {"value": allt["bond_updates_per_s"], "unit": "bond updates/s", "cores": os.cpu_count(),
+            "kind": "oracle", "sample": sample(allt) + ", default BLAS threads",
+            "trotter_steps_per_s_of_sample": allt["trotter_steps_per_s"], "seconds": allt["seconds"],
+            "single_thread": None if single is None else {
+                "value": single["bond_updates_per_s"], "unit": "bond updates/s", "cores": 1,
+                "window": single["window"], "seconds": single["seconds"],
+                "sample": sample(single) + ", OMP/OPENBLAS/MKL_NUM_THREADS=1"}}
 
 
 def golden_parity(w, means, W, K):
@@ -392,6 +430,42 @@ def golden_parity(w, means, W, K):
         return None
     d = float(np.abs(means[:K] - ref[W:W + K]).max())
     return {"max_abs_dmean_z": d, "steps": f"{W + 1}..{W + K}", "reference": "FP64 CPU oracle (committed values)"}
+
+
+def site_parity(g, w, th, first, last):
+    """Per-qubit parity of the setting just timed: the handle (as tuned) is reset and stepped to
+    every step s in [first, last] that has committed oracle values; max_i |<Z_i> - oracle| over
+    those steps and max |lambda - oracle| over the committed edges.  Runs after the timed region."""
+    import numpy as np
+    gold = load_golden(w)
+    if gold is None:
+        return None
+    steps = sorted(int(k) for k in gold["instances"][0]["z"] if first <= int(k) <= last)
+    if not steps:
+        return None
+    g.reset()
+    done, dz, dl = 0, 0.0, 0.0
+    for st in steps:
+        g.step(st - done, th)
+        done = st
+        z, _ = g.expect_z()
+        dz = max(dz, float(np.abs(z.cpu().numpy() - golden_z(gold, st)).max()))
+        for k, inst in enumerate(gold["instances"]):
+            for e, lam in inst["lambda"].get(str(st), {}).items():
+                dl = max(dl, float(np.abs(g.lambdas(k, int(e)) - np.asarray(lam)).max()))
+    return {"max_abs_dz_per_qubit": dz, "max_abs_dlambda_sampled": dl, "steps": steps}
+
+
+def parity_record(g, w, th, means, W, K):
+    """Mean <Z> of every timed step and every qubit at the committed steps inside the window."""
+    out = golden_parity(w, means, W, K)
+    site = site_parity(g, w, th, W + 1, W + K)
+    if out is None:
+        return site
+    if site is not None:
+        out.update(max_abs_dz_per_qubit=site["max_abs_dz_per_qubit"], per_qubit_steps=site["steps"],
+                   max_abs_dlambda_sampled=site["max_abs_dlambda_sampled"])
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -423,7 +497,8 @@ def run_gpeps(args, rank, world, local_rank):
                 g.set_jacobi(floor_rel=args.floor_rel)
         if tune:
             from paper_2309_15642_gb300.autotune import autotune
-            best, table = autotune(g, theta)
+            # candidates are also held to the committed oracle values after the tuner's 6 + 4 steps
+            best, table = autotune(g, theta, warm_steps=6, steps=4, reference_z=golden_z(load_golden(w), 10))
             tuning = {"chosen": best, "candidates": table}
         g.reset()
         th = torch.tensor(theta, dtype=torch.float64, device=dev)
@@ -484,8 +559,12 @@ def run_gpeps(args, rank, world, local_rank):
     # flops of one step's bond eigenproblems: the fixed dense phases plus the Jacobi work the
     # kernel executed (counted in the kernel; converged pairs are skipped and not counted)
     fix64, fix32 = bond_fixed_flops(graphs, w.D, args.dtype)
-    f64_step = fix64 + work_step[0] * JACOBI_BLOCK_FLOPS + work_step[1] * JACOBI_VEC_FLOPS + work_step[4] * 8
-    f32_step = fix32 + work_step[2] * JACOBI_BLOCK_FLOPS + work_step[3] * JACOBI_VEC_FLOPS
+    if args.dtype == "c128":   # one-sided sweeps: the counters are pair checks and rotations
+        f64_step = fix64 + one_sided_flops(w.D, work_step[0], work_step[1]) + work_step[4] * 8
+        f32_step = fix32 + one_sided_flops(w.D, work_step[2], work_step[3])
+    else:
+        f64_step = fix64 + work_step[0] * JACOBI_BLOCK_FLOPS + work_step[1] * JACOBI_VEC_FLOPS + work_step[4] * 8
+        f32_step = fix32 + work_step[2] * JACOBI_BLOCK_FLOPS + work_step[3] * JACOBI_VEC_FLOPS
     if fused:
         launch_ms = sum(prof["bond_updates"]) / max(len(prof["bond_updates"]), 1)
         bonds_per_launch = bonds_step
@@ -534,24 +613,97 @@ def run_gpeps(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     e2e = {"value": world * bonds_step * Ke / e2e_s, "unit": "bond updates/s",
            "h2d_bytes_per_step": th_host.numel() * 8, "d2h_bytes_per_step": res_host.numel() * 8}
+    parity = parity_record(g, w, th, out.cpu().numpy(), W, K)
     g.close()
 
     plain = None
     if not args.no_plain and args.dtype == "mixed":
         Kp, Wp = max(min(K, 10), 1), W
-        gp, _, outp, msp, _, flp, tunp = timed("c128", Kp, Wp, not args.no_autotune)
+        gp, thp, outp, msp, _, flp, tunp = timed("c128", Kp, Wp, not args.no_autotune)
         plain = {"dtype": "c128", "value": world * bonds_step * Kp / (msp * 1e-3), "unit": "bond updates/s",
                  "ms_per_step": msp / Kp, "steps": Kp, "warmup": Wp, "flags": flp,
                  "schedule": (tunp or {}).get("chosen"),
-                 "parity": golden_parity(w, outp.cpu().numpy(), Wp, Kp)}
+                 "parity": parity_record(gp, w, thp, outp.cpu().numpy(), Wp, Kp)}
         gp.close()
-    parity = golden_parity(w, out.cpu().numpy(), W, K)
     # kernels of ours per timed step: kick, the bond updates (one fused launch, or Gram + bond +
     # update per colour class), readout, mean
     launches_per_step = 1 + (1 if fused else 3 * g.n_colours) + 2
     return dict(value=value, ms=ms, bonds_step=bonds_step, clocks=clocks, flags=flags, roofline=roofline,
                 launches_per_step=launches_per_step,
                 e2e=e2e, plain=plain, hbm=hbm, mean_last=mean_last, w=w, tuning=tuning, parity=parity)
+
+
+def measured_hbm_gbs():
+    """The measured copy bandwidth (MEASURED_PEAKS.json), else the pool's earlier figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        v = json.load(open(path)).get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    return 6800.0, "fallback"
+
+
+def run_condor_d64(dev, Kc=3, Wc=6):
+    """The large configuration: 1121 qubits, D = 64, theta_h = 0.8 (workload condor_d64), in both
+    precisions on the fused step (schedule 4; mixed with FP64 floor 3e-8, its tuned setting at
+    D = 64).  Each: Wc warm-up steps from |0...0> (bonds saturate at step 6), Kc timed steps (CUDA
+    events on the library stream), then one profiled step for the step kernel's time and the FP64
+    work it executed.  Reports bond updates/s, Trotter steps/s, algorithmic HBM GB/s against the
+    measured copy bandwidth, the step kernel's FP64 rate against the derived FP64 peak, the tensor
+    pipe (idle: no tensor-core instruction on this path), and the largest per-qubit difference
+    between the two paths after the timed steps.  The complex128 path is held to the oracle at
+    1e-10 per qubit at D = 64 on the 127-qubit lattice; the oracle itself needs minutes per step
+    of this lattice, so there are no committed oracle values for it."""
+    import numpy as np
+    import torch
+    from paper_2309_15642_gb300 import GPEPS
+    from workloads import kick_angles, workload
+    wc = workload("condor_d64")
+    graphs = wc.graphs()
+    th = torch.tensor([float(t[0]) for t in kick_angles(wc)], dtype=torch.float64, device=dev)
+    hbm_peak, hbm_src = measured_hbm_gbs()
+    out, zs = {"workload": wc.name, "lattice_qubits": [n for n, _ in graphs], "D": wc.D,
+               "theta": list(wc.theta)}, {}
+    for dtype in ("mixed", "c128"):
+        g = GPEPS(graphs, wc.D, dtype=dtype, device=str(dev))
+        g.set_schedule(4)
+        if dtype == "mixed":
+            g.set_jacobi(floor_rel=3e-8)
+        g.reset()
+        g.step(Wc, th)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(g.stream)
+        g.step(Kc, th)
+        e1.record(g.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        z, _ = g.expect_z()
+        zs[dtype] = z.cpu().numpy()
+        w0 = g.jacobi_work()
+        kernel_ms = g.step_profiled(th)[1]
+        work = [b - a for a, b in zip(w0, g.jacobi_work())]
+        fix64, _ = bond_fixed_flops(graphs, wc.D, dtype)
+        f64 = fix64 + work[4] * 8 + (one_sided_flops(wc.D, work[0], work[1]) if dtype == "c128"
+                                     else work[0] * JACOBI_BLOCK_FLOPS + work[1] * JACOBI_VEC_FLOPS)
+        sb = step_bytes(graphs, wc.D, 8 if dtype == "mixed" else 16)
+        gbs = sb / (ms / Kc * 1e-3) / 1e9
+        gf = f64 / (kernel_ms * 1e-3) / 1e9
+        out[dtype] = {"value": g.bonds_per_step * Kc / (ms * 1e-3), "unit": "bond updates/s",
+                      "trotter_steps_per_s": Kc / (ms * 1e-3), "ms_per_step": ms / Kc,
+                      "timed_steps": f"{Wc + 1}..{Wc + Kc}",
+                      "hbm": {"algorithmic_bytes_per_step": sb, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
+                              "frac": gbs / hbm_peak, "peak_source": hbm_src},
+                      "fp64": {"kernel": "step_kernel", "kernel_ms": kernel_ms, "flops_per_launch": f64,
+                               "achieved_gflops": gf, "peak_gflops": FP64_PEAK_GFLOPS,
+                               "frac": gf / FP64_PEAK_GFLOPS},
+                      "tensor_pipe": {"utilisation": 0.0,
+                                      "note": "no tensor-core instruction in the step kernel: FP64 Jacobi and "
+                                              "FP32/FP64 CUDA-core products"},
+                      "flags": g.status()}
+        g.close()
+    out["max_abs_dz_per_qubit_mixed_vs_c128"] = float(np.abs(zs["mixed"] - zs["c128"]).max())
+    return out
 
 
 def main():
@@ -562,6 +714,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     from workloads import workload
     w = workload(args.workload)
+
+    if args.cpu_leg:
+        print(json.dumps(cpu_oracle_leg(w, args.warmup, 10.0)))
+        return
 
     if args.impl == "reference":
         if rank != 0:
@@ -582,7 +738,8 @@ def main():
             peps.expect_z()
         dt = time.perf_counter() - t0
         v = len(edges) * K / dt
-        sample = f"{n}-qubit lattice of the batch, D={w.D}, one Trotter step per step (numpy/LAPACK FP64)"
+        sample = (f"{n}-qubit lattice of the batch, D={w.D}, one Trotter step per step, steps {W + 1}..{W + K} "
+                  f"after {W} untimed warm-up steps from |0...0> (numpy/LAPACK FP64, default BLAS threads)")
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": v, "unit": "bond updates/s", "n_gpus": args.gpus,
             "steps": K, "warmup": W, "ms_per_step": dt / max(K, 1) * 1e3, "higher_is_better": True,
@@ -629,9 +786,13 @@ def main():
         torch.cuda.set_device(local_rank)
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     r = run_gpeps(args, rank, world, local_rank)
+    condor = None
+    if rank == 0 and world == 1 and not args.no_condor and args.workload == "heavyhex_mix_d32":
+        import torch
+        condor = run_condor_d64(torch.device("cuda", local_rank))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_oracle(w)
+        cpu = cpu_oracle(w, args.warmup)
     if rank == 0:
         line = {
             "metric": METRIC, "value": r["value"], "unit": "bond updates/s", "n_gpus": world,
@@ -644,7 +805,7 @@ def main():
                        "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{world}",
                        "timed_steps": f"{args.warmup + 1}..{args.warmup + args.steps} from |0...0>"},
             "roofline": r["roofline"], "hbm": r["hbm"], "clocks": r["clocks"], "e2e": r["e2e"],
-            "plain_c128": r["plain"], "cpu_baseline": cpu, "parity": r["parity"],
+            "plain_c128": r["plain"], "condor_d64": condor, "cpu_baseline": cpu, "parity": r["parity"],
             "tuning": (r["tuning"] or {}).get("chosen"),
             "gpu_launches": r["launches_per_step"] * args.steps, "device_flags": r["flags"],
             "mean_z_last_step": r["mean_last"],

@@ -4,8 +4,11 @@ For a bound handle: evolve a few Trotter steps to a representative state, save
 it, then for every candidate setting restore the state, time ``steps`` Trotter
 steps (CUDA events on the library stream) and keep <Z_i> after them.  The
 reference is the strictest setting; a candidate is accepted only if
-max_i |<Z_i> - <Z_i>_ref| <= ``budget``.  The fastest accepted candidate is
-applied to the handle and returned with the timings.
+max_i |<Z_i> - <Z_i>_ref| <= ``budget`` and, when the caller passes
+``reference_z`` (independent values of every <Z_i> after warm_steps + steps
+Trotter steps from |0...0>, e.g. the FP64 oracle's), also
+max_i |<Z_i> - reference_z_i| <= ``reference_budget``.  The fastest accepted
+candidate is applied to the handle and returned with the timings.
 
 Candidates (mixed path): schedule (one CTA per bond | work queue with one, two or
 four CTAs per SM | one fused launch per step; a schedule the handle rejects is
@@ -42,12 +45,15 @@ def _apply(g, cand):
     g.set_jacobi(**jac)
 
 
-def autotune(g, theta, warm_steps=6, steps=4, budget=1e-5, repeats=1):
+def autotune(g, theta, warm_steps=6, steps=4, budget=1e-5, repeats=1, reference_z=None, reference_budget=5e-5):
     """Tune handle ``g`` (a :class:`GPEPS`) in place; returns ``(best, table)``.
 
-    ``theta``: kick angles of the workload (per instance).  The handle is left
-    reset with the chosen setting applied."""
+    ``theta``: kick angles of the workload (per instance).  ``reference_z``: None,
+    or <Z_i> of every qubit (instance after instance) after warm_steps + steps
+    steps, from an independent computation.  The handle is left reset with the
+    chosen setting applied."""
     th = torch.as_tensor(theta, dtype=torch.float64, device=g.device)
+    ref_ext = None if reference_z is None else torch.as_tensor(reference_z, dtype=torch.float64, device=g.device)
     g.reset()
     _apply(g, dict(persistent=0, **(STRICT_MIXED if g.dtype == "mixed" else {})))
     g.step(warm_steps, th)
@@ -69,9 +75,13 @@ def autotune(g, theta, warm_steps=6, steps=4, budget=1e-5, repeats=1):
             best_ms = ms if best_ms is None else min(best_ms, ms)
         return best_ms, z
 
+    def ext_dz(z):
+        return None if ref_ext is None else float((z - ref_ext).abs().max().item())
+
     ref_cand = dict(persistent=0, **(STRICT_MIXED if g.dtype == "mixed" else {}))
     ref_ms, ref_z = run(ref_cand)
-    table = [dict(ref_cand, ms_per_step=ref_ms, max_dz=0.0, accepted=True, reference=True)]
+    table = [dict(ref_cand, ms_per_step=ref_ms, max_dz=0.0, max_dz_reference=ext_dz(ref_z), accepted=True,
+                  reference=True)]
     best = (ref_ms, ref_cand)
     from ._abi import GpepsError
     for cand in candidates(g.dtype):
@@ -82,8 +92,9 @@ def autotune(g, theta, warm_steps=6, steps=4, budget=1e-5, repeats=1):
             continue
         ms, z = run(cand)
         dz = float((z - ref_z).abs().max().item())
-        ok = dz <= budget and g.status() == 0
-        table.append(dict(cand, ms_per_step=ms, max_dz=dz, accepted=ok))
+        dz_ext = ext_dz(z)
+        ok = dz <= budget and g.status() == 0 and (dz_ext is None or dz_ext <= reference_budget)
+        table.append(dict(cand, ms_per_step=ms, max_dz=dz, max_dz_reference=dz_ext, accepted=ok))
         if ok and ms < best[0]:
             best = (ms, cand)
     _apply(g, best[1])

@@ -235,6 +235,38 @@ def test_heavyhex_mix_d32_full_size(dtype):
     assert g.status() == 0
 
 
+def test_heavyhex_mix_d32_benchmark_setting():
+    """The setting bench.py times on the benchmark batch (the autotuner's choice there: the fused
+    step with three CTAs per SM, FP64 stopping floor 1e-7 of the trace, four extra FP32 levels):
+    every qubit at the committed steps 5, 6, 10, 25 and 50 within 1e-4 of the oracle, and the
+    sampled lambda spectra, after graph replay from |0...0>."""
+    gold = _golden("heavyhex_mix_d32")
+    w = workload("heavyhex_mix_d32")
+    graphs = w.graphs()
+    from ._gpu_util import gpu_lib
+    import torch
+    g = gpu_lib()(graphs, w.D, dtype="mixed")
+    g.set_schedule(5)
+    g.set_jacobi(floor_rel=1e-7)
+    g.set_levels(level_ratio=1e-5, levels=4)
+    g.reset()
+    th = torch.tensor([0.7] * 3, dtype=torch.float64, device="cuda")
+    done, worst = 0, 0.0
+    for s in (5, 6, 10, 25, 50):
+        g.step(s - done, th)
+        done = s
+        z, _ = g.expect_z()
+        zi = split(z.cpu().numpy(), graphs)
+        for k, inst in enumerate(gold["instances"]):
+            d = float(np.abs(zi[k] - np.array(inst["z"][str(s)])).max())
+            worst = max(worst, d)
+            assert d < TOL["mixed"], (s, k, d)
+            for e, lam in inst["lambda"][str(s)].items():
+                lam_check(g.lambdas(k, int(e)), np.array(lam), "mixed", truncated=2 ** s > w.D)
+    assert g.status() == 0
+    g.close()
+
+
 def test_checkpoint_restore_and_readout_on_gpu_state():
     """(1) save_state after step 3, two more steps, restore, the same two steps: identical
     <Z>.  (2) the oracle's mean-field readout applied to the GPU's own tensors equals the
