@@ -407,6 +407,19 @@ int gpeps_bond_update_noalloc(int32_t D, int32_t dtype, void* gamma_a, int32_t d
                               void* gamma_b, int32_t deg_b, int32_t leg_b, double* lam, const double* theta,
                               void* stream, int32_t* flags_out);
 
+/*
+ * Diagnostic, no part of the paper's method: the FP64 Jacobi rotation helpers
+ * against the textbook formulas in CUDA's own FP64 hypot, sqrt and rsqrt.  For
+ * k < n, in[4k..4k+3] = (a, b, Re g, Im g) (device float64; g != 0) describes the
+ * 2 x 2 Hermitian [[a, g], [conj(g), b]]; out[8k..8k+7] (device float64)
+ * receives the helper's (c, s, Re e, Im e) and then the reference's.  which: 0
+ * the two-sided helper of the squared eigensolver (|g|^2 must be above FP32's
+ * smallest normal), 1 the one-sided helper of the complex128 bond SVD (any
+ * finite scale).  Asynchronous on stream.  Errors: GPEPS_EINVAL for n < 0, an
+ * unknown `which` or NULL arrays; GPEPS_ECUDA for a failed launch.
+ */
+int gpeps_selftest_rotation(int32_t which, int32_t n, const double* in, double* out, void* stream);
+
 int gpeps_destroy(gpeps_handle* h);
 const char* gpeps_error_string(int status);
 const char* gpeps_last_cuda_error(void);

@@ -44,6 +44,7 @@ SIGNATURES = {
     "gpeps_sizes": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
     "gpeps_sweeps": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
     "gpeps_bond_phase_cycles": (c_int, [c_void_p, POINTER(c_int64)]),
+    "gpeps_selftest_rotation": (c_int, [c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "gpeps_bond_update_noalloc": (c_int, [c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p, c_int32,
                                           c_int32, c_void_p, POINTER(c_double), c_void_p, POINTER(c_int32)]),
     "gpeps_destroy": (c_int, [c_void_p]),

@@ -87,9 +87,13 @@ __device__ __forceinline__ bool rotation(float app, float aqq, float2 apq, float
   e = make_float2(apq.x * ig, -apq.y * ig);
   return true;
 }
-// FP64 version: the angle is taken in FP32 and refined by one FP64 Newton step,
-// and (c, s) and e are normalised in FP64 by two Newton steps, so J is unitary
-// to FP64 rounding without FP64 divides or square roots.
+// FP64 version, without FP64 divides or square roots: 1/|a_pq| and c =
+// 1/sqrt(1 + t^2) start from FP32 rsqrtf and take two Newton-Raphson steps of
+// the reciprocal square root, y <- y (3 - x y^2) / 2 (each step squares the
+// relative error: 1e-7 -> 1e-14 -> rounding), so e and (c, s) are unit to FP64
+// rounding and J is unitary; t starts from the FP32 formula and takes one
+// Newton-Raphson step on f(t) = t^2 + 2 zeta t - 1 with an FP32 reciprocal of
+// f'(t), which leaves a relative error of about 1e-7 x 1e-7 in the angle.
 __device__ __forceinline__ bool rotation(double app, double aqq, double2 apq, double tol, double floor_abs,
                                          double& c, double& s, double2& e) {
   const double g2 = apq.x * apq.x + apq.y * apq.y;
@@ -116,6 +120,50 @@ __device__ __forceinline__ bool rotation(double app, double aqq, double2 apq, do
   s = t * cc;
   e = make_double2(apq.x * ig, -apq.y * ig);
   return true;
+}
+
+// Rotation of the column pair with squared norms a, b and inner product
+// g = b_p^H b_q (g != 0), the one that diagonalises [[a, g], [conj(g), b]]:
+// the phase e = conj(g) / |g| first, then t = tan of the angle from
+// t^2 + 2 zeta t - 1 = 0, zeta = (b - a) / (2 |g|) (Golub & Van Loan Alg. 8.4.1),
+// for the one-sided Jacobi of the unsquared bond SVD.  The three entries are
+// first rescaled by the same power of two so that |g| ~ 1 (exact; the angle is
+// scale-free), so that the FP32 seeds below cannot underflow; then the
+// Newton-Raphson refinements of `rotation` (two reciprocal-square-root steps
+// for 1/|g| and for c = 1/sqrt(1 + t^2), one step on the angle equation) make
+// the rotation unitary to FP64 rounding without FP64 divides or square roots.
+// When |zeta| is beyond FP32 range t = 1 / (2 zeta).
+// Also returns |g|.
+__device__ __forceinline__ void os_rotation(double a, double b, double2 g, double& c, double& s, double2& e,
+                                            double& ag) {
+  int ex;
+  frexp(fma(g.x, g.x, g.y * g.y), &ex);
+  const int k = ex >> 1;  // |g| ~ 2^k
+  a = ldexp(a, -k);
+  b = ldexp(b, -k);
+  g = make_double2(ldexp(g.x, -k), ldexp(g.y, -k));
+  const double g2 = fma(g.x, g.x, g.y * g.y);  // in [1/4, 2)
+  double ig = (double)rsqrtf((float)g2);
+  ig = ig * (1.5 - 0.5 * g2 * ig * ig);
+  ig = ig * (1.5 - 0.5 * g2 * ig * ig);
+  const double zeta = (b - a) * (0.5 * ig);
+  double t;
+  if (fabs(zeta) < 1e18) {
+    const float zf = (float)zeta;
+    t = (double)(copysignf(1.f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.f))));
+    const double f = fma(t, t, fma(2.0 * zeta, t, -1.0));
+    t -= f * (double)__frcp_rn((float)(2.0 * (t + zeta)));
+  } else {
+    t = 0.5 / zeta;
+  }
+  const double u = fma(t, t, 1.0);
+  double cc = (double)rsqrtf((float)u);
+  cc = cc * (1.5 - 0.5 * u * cc * cc);
+  cc = cc * (1.5 - 0.5 * u * cc * cc);
+  c = cc;
+  s = t * cc;
+  e = make_double2(g.x * ig, -g.y * ig);
+  ag = ldexp(g2 * ig, k);
 }
 
 // Storage of the Hermitian matrix of a Jacobi solve.  HermFull: n x n with row

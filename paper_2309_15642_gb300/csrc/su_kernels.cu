@@ -726,49 +726,6 @@ __device__ __forceinline__ void round_pair(int r, int k, int n, int& p, int& q) 
   }
 }
 
-// Rotation of the column pair with squared norms a, b and inner product
-// g = b_p^H b_q (g != 0), the one that diagonalises [[a, g], [conj(g), b]]:
-// the phase e = conj(g) / |g| first, then t = tan of the angle from
-// t^2 + 2 zeta t - 1 = 0, zeta = (b - a) / (2 |g|) (Golub & Van Loan Alg. 8.4.1).
-// The three entries are first rescaled by the same power of two so that |g| ~ 1
-// (exact; the angle is scale-free), so that the FP32 seeds below cannot
-// underflow; then, as in `rotation`, 1/|g| and
-// t start in FP32 and are refined in FP64 by Newton steps, and c = 1/sqrt(1+t^2)
-// is Newton-normalised, so the rotation is unitary to FP64 rounding without FP64
-// divides or square roots.  When |zeta| is beyond FP32 range t = 1 / (2 zeta).
-// Also returns |g|.
-__device__ __forceinline__ void os_rotation(double a, double b, double2 g, double& c, double& s, double2& e,
-                                            double& ag) {
-  int ex;
-  frexp(fma(g.x, g.x, g.y * g.y), &ex);
-  const int k = ex >> 1;  // |g| ~ 2^k
-  a = ldexp(a, -k);
-  b = ldexp(b, -k);
-  g = make_double2(ldexp(g.x, -k), ldexp(g.y, -k));
-  const double g2 = fma(g.x, g.x, g.y * g.y);  // in [1/4, 2)
-  double ig = (double)rsqrtf((float)g2);
-  ig = ig * (1.5 - 0.5 * g2 * ig * ig);
-  ig = ig * (1.5 - 0.5 * g2 * ig * ig);
-  const double zeta = (b - a) * (0.5 * ig);
-  double t;
-  if (fabs(zeta) < 1e18) {
-    const float zf = (float)zeta;
-    t = (double)(copysignf(1.f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.f))));
-    const double f = fma(t, t, fma(2.0 * zeta, t, -1.0));
-    t -= f * (double)__frcp_rn((float)(2.0 * (t + zeta)));
-  } else {
-    t = 0.5 / zeta;
-  }
-  const double u = fma(t, t, 1.0);
-  double cc = (double)rsqrtf((float)u);
-  cc = cc * (1.5 - 0.5 * u * cc * cc);
-  cc = cc * (1.5 - 0.5 * u * cc * cc);
-  c = cc;
-  s = t * cc;
-  e = make_double2(g.x * ig, -g.y * ig);
-  ag = ldexp(g2 * ig, k);
-}
-
 // Rotation of a column pair in FP32 (the warm start and the levels): the same
 // angle as `os_rotation`, in plain FP32 arithmetic (the FP32 stages work on
 // matrices scaled to unit Frobenius norm and skip pairs with |g| below 1e-13,
