@@ -27,7 +27,8 @@
  *
  * Scope: graphs in which every edge has an end of degree <= 2 and every vertex
  * has degree <= 3 (true of the heavy-hex lattices of the paper, Fig. 1);
- * 1 <= D <= 64 (gpeps_grad: D <= 16; gpeps_bond_update_noalloc: D <= 32).
+ * 1 <= D <= 64, and D <= 128 for GPEPS_C128 (gpeps_grad: D <= 16; BP regauging:
+ * D <= 64; gpeps_bond_update_noalloc: D <= 32).
  */
 #ifndef GPEPS_H
 #define GPEPS_H
@@ -82,7 +83,8 @@ typedef struct gpeps_handle gpeps_handle;
  * arrays are copied; *out receives the handle (free with gpeps_destroy).
  * Errors: GPEPS_EINVAL for a malformed graph, a colouring that is not a
  * matching, a vertex of degree > 3, an edge joining two degree-3 vertices,
- * D outside [1, 64] or an unknown dtype.
+ * D outside [1, 64] (GPEPS_MIXED_C64) or [1, 128] (GPEPS_C128), or an unknown
+ * dtype.
  */
 int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int32_t dtype,
                  void* stream, gpeps_handle** out);
@@ -91,8 +93,11 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
  * Bytes of the two caller-owned device buffers.  state: every Gamma_i (complex,
  * physical index outermost, legs in sorted-neighbour order, last leg fastest)
  * and every lambda_e (float64[D]).  work: kick angles, bond work lists,
- * per-bond scratch (for D > 34 also the 2D x 2D bond eigenproblems that do not
- * fit in shared memory: 772 KB per bond of the largest colour class at D = 64),
+ * per-bond scratch (the complex128 bond SVD's matrices, 264 KB per bond of the
+ * largest colour class at D = 32 and 4.2 MB at D = 128; in the mixed path for
+ * D > 34 the 2D x 2D bond eigenproblems that do not fit in shared memory, 772 KB
+ * at D = 64), Gram partials of the larger ends (2 D^2 complex per tile of 64
+ * rows, 32 rows in complex128 beyond D = 64),
  * <Z> outputs and the flag word.  Both need 256-byte alignment (cudaMalloc and
  * torch give it).
  */
@@ -177,7 +182,8 @@ int gpeps_set_levels(gpeps_handle* h, double level_ratio, int32_t levels);
 
 /*
  * Wait limit of the fused step (schedule 4), in SM clock cycles (default
- * 4e9, about 2 s; a bond update takes at most ~0.2 s at D = 64): a bond that waits longer for an earlier bond on one of its
+ * 4e9, about 2 s, where a bond update takes at most ~0.2 s (D <= 64); 6.4e10
+ * beyond D = 64, where one takes about a second): a bond that waits longer for an earlier bond on one of its
  * sites gives up, raises GPEPS_FLAG_TIMEOUT and runs on what it finds, so a
  * launch always ends.  0 gives up at once whenever a dependency is still
  * running (failure-detection tests use it).  Host-only; drops a captured step
@@ -331,7 +337,7 @@ int gpeps_grad(gpeps_handle* h, const double* theta, int32_t n_steps, int32_t ck
  * cannot be captured into a CUDA graph.  Device flags: GPEPS_FLAG_NOCONV (a
  * gauge eigenproblem hit its sweep cap), GPEPS_FLAG_NUMERIC (a message with
  * non-positive or non-finite trace, or a vanishing gauged bond: that edge keeps
- * its gauge).  Errors: GPEPS_EINVAL for an unbound handle, max_iter < 1,
+ * its gauge).  Errors: GPEPS_EINVAL for an unbound handle, D > 64, max_iter < 1,
  * negative or NaN tol, a NULL, misaligned or too small workspace.
  */
 int gpeps_query_bp_workspace(gpeps_handle* h, int32_t max_iter, size_t* bytes);

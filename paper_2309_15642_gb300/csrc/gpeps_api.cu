@@ -336,8 +336,10 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
                  gpeps_handle** out) {
   if (!out || !graphs || n_instances < 1) return GPEPS_EINVAL;
   *out = nullptr;
-  if (D < 1 || D > kMaxD) return GPEPS_EINVAL;
   if (dtype != GPEPS_C128 && dtype != GPEPS_MIXED_C64) return GPEPS_EINVAL;
+  // complex128 (the unsquared bond SVD) reaches D = 128; the mixed path's squared
+  // eigensolver keeps its n x n matrices and pair lists within D = 64
+  if (D < 1 || D > (dtype == GPEPS_C128 ? kMaxDc128 : kMaxD)) return GPEPS_EINVAL;
   gpeps_handle* h = new (std::nothrow) gpeps_handle();
   if (!h) return GPEPS_ENOMEM;
   h->D = D;
@@ -413,12 +415,13 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
     for (int bi = 0; bi < (int)cp.bonds.size(); ++bi) {
       BondDesc& bd = cp.bonds[bi];
       bd.part0 = cp.n_parts;
-      bd.n_parts = (bd.a.rows + kTileRows - 1) / kTileRows;
+      const int tr = tile_rows(D, dtype == GPEPS_C128 ? 16 : 8);
+      bd.n_parts = (bd.a.rows + tr - 1) / tr;
       for (int p = 0; p < bd.n_parts; ++p) {
         TileDesc t{};
         t.bond = bi;
-        t.row0 = p * kTileRows;
-        t.nrows = std::min(kTileRows, bd.a.rows - t.row0);
+        t.row0 = p * tr;
+        t.nrows = std::min(tr, bd.a.rows - t.row0);
         t.part = cp.n_parts + p;
         cp.tiles.push_back(t);
       }
@@ -472,7 +475,9 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   h->jp.max_sweeps32 = 20;
   h->jp.level_ratio = 1e-5;
   h->jp.levels = 4;
-  h->jp.wait_cycles = kWaitCycles;
+  // beyond D = 64 one task of the fused step (Gram pass over 16384 rows, bond SVD,
+  // update pass) takes about a second on its SM: its dependants may wait longer
+  h->jp.wait_cycles = kWaitCycles * (D > kMaxD ? 16 : 1);
   h->jp.gate_sign = 1;
   // layouts
   size_t s = 0;
@@ -1099,7 +1104,7 @@ BpLayout bp_layout(const gpeps_handle* h, int max_iter) {
 }  // namespace
 
 int gpeps_query_bp_workspace(gpeps_handle* h, int32_t max_iter, size_t* bytes) {
-  if (!h || !h->bound || !bytes || max_iter < 1) return GPEPS_EINVAL;
+  if (!h || !h->bound || !bytes || max_iter < 1 || h->D > kMaxD) return GPEPS_EINVAL;
   bp_plan(h);
   *bytes = bp_layout(h, max_iter).total;
   return GPEPS_OK;
@@ -1107,7 +1112,7 @@ int gpeps_query_bp_workspace(gpeps_handle* h, int32_t max_iter, size_t* bytes) {
 
 int gpeps_bp_regauge(gpeps_handle* h, int32_t max_iter, double tol, void* d_bp_work, size_t bp_work_bytes,
                      int32_t* iterations, double* residual, float* phase_ms) {
-  if (!h || !h->bound || max_iter < 1 || !(tol >= 0.0) || !d_bp_work) return GPEPS_EINVAL;
+  if (!h || !h->bound || max_iter < 1 || !(tol >= 0.0) || !d_bp_work || h->D > kMaxD) return GPEPS_EINVAL;
   if (reinterpret_cast<uintptr_t>(d_bp_work) & 255) return GPEPS_EINVAL;
   bp_plan(h);
   const BpLayout L = bp_layout(h, max_iter);

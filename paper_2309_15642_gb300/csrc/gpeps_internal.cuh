@@ -10,11 +10,18 @@
 
 namespace gpeps {
 
-constexpr int kMaxD = 64;          // bond dimension limit of the library
+constexpr int kMaxD = 64;          // bond dimension limit of the mixed path, BP regauging and the no-alloc update
+constexpr int kMaxDc128 = 128;     // bond dimension limit of the complex128 simple update
 constexpr int kMaxLevel = 32;      // indices of one extra FP32 level (one per lane of a warp)
 constexpr size_t kSmemOptin = 232448;  // opt-in shared memory per CTA of sm_100/sm_103 (227 KB)
 constexpr size_t kBondSmemMax = kSmemOptin - 1024;  // dynamic part of a bond CTA (static variables need the rest)
 constexpr int kTileRows = 64;      // rows of a big-side tile (Gram and update launches)
+// Rows of a big-side tile at (D, element bytes): kTileRows, or 32 for complex128
+// beyond D = 64, where a 64-row tile of 2D + 1 complex doubles (263 KB at D = 128)
+// would not fit the shared memory of a CTA
+__host__ __device__ constexpr int tile_rows(int D, size_t elt) { return (D > kMaxD && elt == 16) ? 32 : kTileRows; }
+// Columns of Y_s that the update passes hold in shared memory at once
+__host__ __device__ constexpr int y_cols(int D) { return D > kMaxD ? 32 : D; }
 constexpr int kThreads = 256;      // threads of the streaming and readout CTAs
 constexpr int kBondThreads = 512;  // threads of the bond-eigenproblem CTA (one CTA per SM: more warps hide FP64 latency)
 constexpr double kLambdaCut = 1e-13;  // pseudo-inverse threshold relative to max(lambda)
