@@ -73,12 +73,13 @@ def run(name, steps=None):
     print("wrote", path)
 
 
-GRAD_QUBITS = [0, 13, 37, 62, 100, 126]
+# 24 kick angles spread over the 127-qubit lattice (rows, bridges, both ends)
+GRAD_QUBITS = sorted(set(np.linspace(0, 126, 24).round().astype(int).tolist()))
 
 
 def run_grad(name):
     """Oracle gradient (central differences, h = 1e-5) of the mean <Z> after all steps with
-    respect to a few per-qubit kick angles."""
+    respect to the per-qubit kick angles of GRAD_QUBITS."""
     from oracle.gradient import fd_gradient, oracle_loss
     w = workload(name)
     (n, edges), th = w.graphs()[0], kick_angles(w)[0]

@@ -2,10 +2,11 @@
 
 References: the parameter-shift derivative of the exact state vector (exact
 regime: a heavy-hex tree, D = 2^n), central differences of the FP64 oracle
-(truncated 127-qubit lattice), central differences of the library's own
-gradient-path forward at the 127-qubit, D = 16, 20-step workload, and the
-oracle's derivative of that workload for a few angles.  Tolerance 1e-6
-relative to the largest derivative.
+(truncated 127-qubit lattice), and, at the 127-qubit, D = 16, 20-step workload
+with per-qubit angles, the oracle's central differences (h = 1e-5) for 24 angles
+spread over the lattice (committed values of tests/golden/make_oracle_golden.py)
+plus central differences of the library's own forward for six of them.
+Tolerance 1e-6 relative to the largest derivative.
 """
 import json
 import os
@@ -59,8 +60,23 @@ def test_grad_truncated_127_vs_oracle_fd():
         assert abs(g[q] - v) < REL * scale, (q, g[q], v)
 
 
-def test_grad_workload_d16_vs_fd_and_oracle():
-    """127 q, D = 16, 20 steps, theta_i ~ U[0.5, 0.9] (seeded), checkpoint every 5."""
+def test_grad_workload_d16_vs_oracle_fd():
+    """127 q, D = 16, 20 steps, theta_i ~ U[0.5, 0.9] (seeded), checkpoint every 5: the loss and
+    the derivative in every committed angle against the oracle's central differences."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_eagle_grad_d16.json")
+    gold = json.load(open(path))
+    w = workload("eagle_grad_d16")
+    (n, e), th = w.graphs()[0], kick_angles(w)[0]
+    L, g = _grad((n, e), w.D, th, w.steps, ckpt=5)
+    assert len(gold["dloss_dtheta"]) >= 20 and gold["h"] == 1e-5
+    assert abs(L - gold["loss"]) < 1e-10
+    scale = max(abs(v) for v in gold["dloss_dtheta"].values())
+    for q, v in gold["dloss_dtheta"].items():
+        assert abs(g[int(q)] - v) < REL * scale, (q, g[int(q)], v)
+
+
+def test_grad_workload_d16_vs_library_fd():
+    """The same workload against central differences of the library's own forward (six angles)."""
     w = workload("eagle_grad_d16")
     (n, e), th = w.graphs()[0], kick_angles(w)[0]
     weights = np.full(n, 1.0 / n)
@@ -81,12 +97,6 @@ def test_grad_workload_d16_vs_fd_and_oracle():
     scale = np.abs(g).max()
     for q in qs:
         assert abs(g[q] - fd[q]) < REL * scale, (q, g[q], fd[q])
-    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_eagle_grad_d16.json")
-    if os.path.exists(path):
-        gold = json.load(open(path))
-        assert abs(L - gold["loss"]) < 1e-8
-        for q, v in gold["dloss_dtheta"].items():
-            assert abs(g[int(q)] - v) < 1e-5 * scale, (q, g[int(q)], v)
 
 
 def test_grad_checkpoint_spacing_does_not_change_the_result():
