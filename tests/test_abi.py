@@ -75,7 +75,8 @@ def test_valid_heavy_hex(abi):
 
 @pytest.mark.parametrize("graph,D,dtype", [
     ((3, [[0, 1], [1, 2]]), 0, 0),               # D < 1
-    ((3, [[0, 1], [1, 2]]), 65, 0),              # D beyond the library limit (64)
+    ((3, [[0, 1], [1, 2]]), 129, 0),             # D beyond the complex128 limit (128)
+    ((3, [[0, 1], [1, 2]]), 65, 1),              # D beyond the mixed path's limit (64)
     ((3, [[0, 1], [1, 2]]), 4, 7),               # unknown dtype
     ((3, [[0, 1], [1, 1]]), 4, 0),               # self loop
     ((3, [[0, 1], [1, 3]]), 4, 0),               # label out of range
