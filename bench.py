@@ -62,7 +62,8 @@ def parse():
                     help="time Trotter steps with a belief-propagation regauge after each (the paper's BP "
                          "comparison) instead of the plain step")
     ap.add_argument("--bp-max-iter", type=int, default=200)
-    ap.add_argument("--no-condor", action="store_true", help="skip the 1121-qubit D = 64 record")
+    ap.add_argument("--no-condor", action="store_true",
+                    help="skip the sub-records (1121-qubit D = 64, BP regauging, D = 128)")
     ap.add_argument("--cpu-leg", action="store_true",
                     help="internal: time one leg of the CPU oracle baseline and print it as JSON")
     ap.add_argument("--floor-rel", type=float, default=None,
@@ -706,6 +707,93 @@ def run_condor_d64(dev, Kc=3, Wc=6):
     return out
 
 
+def run_bp_record(dev, W=5, K=3):
+    """BP regauging after each Trotter step (the paper's BP comparison) on workload eagle_bp_d32
+    (127 q, D = 32, theta_h = 0.7), mixed path, fused step: W steps each followed by a regauge to
+    convergence, then K timed steps (CUDA events on the library stream around step + regauge, the
+    regauge's per-iteration convergence read-back included).  Reports Trotter steps/s with BP,
+    BP iterations and per-phase device times, the message kernel against the derived FP32 peak,
+    and every qubit after the last step against the committed FP64 oracle values (BP included)."""
+    import numpy as np
+    import torch
+    from paper_2309_15642_gb300 import GPEPS
+    from workloads import kick_angles, workload
+    wb = workload("eagle_bp_d32")
+    graphs = wb.graphs()
+    th = torch.tensor([float(t[0]) for t in kick_angles(wb)], dtype=torch.float64, device=dev)
+    g = GPEPS(graphs, wb.D, dtype="mixed", device=str(dev))
+    g.set_schedule(4)
+    g.reset()
+    for _ in range(W):
+        g.step(1, th)
+        g.bp_regauge(200)
+    torch.cuda.synchronize(dev)
+    iters, phases = [], [0.0, 0.0, 0.0]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(g.stream)
+    for _ in range(K):
+        g.step(1, th)
+        it, _, ms3 = g.bp_regauge(200, profile=True)
+        iters.append(it)
+        phases = [x + y for x, y in zip(phases, ms3)]
+    e1.record(g.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    z, _ = g.expect_z()
+    gold = golden_z(load_golden(wb), W + K)
+    dz = None if gold is None else float(np.abs(z.cpu().numpy() - gold).max())
+    flops = bp_message_flops(graphs, wb.D)
+    msg_ms = phases[0] / max(sum(iters), 1)
+    gf = flops / (msg_ms * 1e-3) / 1e9
+    out = {"workload": wb.name, "dtype": "c64+f64", "value": K / (ms * 1e-3), "unit": "Trotter steps/s with BP",
+           "ms_per_step": ms / K, "timed_steps": f"{W + 1}..{W + K}", "bp_iterations": iters,
+           "ms_per_step_by_phase": {"messages": phases[0] / K, "gauge": phases[1] / K, "apply": phases[2] / K},
+           "message_kernel": {"launch_ms": msg_ms, "flops_per_launch": flops, "achieved_gflops": gf,
+                              "peak_gflops": FP32_PEAK_GFLOPS, "frac": gf / FP32_PEAK_GFLOPS, "bound": "alu (FP32)"},
+           "max_abs_dz_per_qubit": dz, "parity_step": W + K, "flags": g.status()}
+    g.close()
+    return out
+
+
+def run_large_chi_record(dev, W=7, K=2):
+    """The large-chi path (the paper's long-time runs, Figs. 5-7, at chi = 128): workload
+    eagle_d128, 127 q, D = 128 (256 x 256 bond cores, degree-3 ends of 16384 rows), theta_h = 1.0,
+    complex128, layered launches (faster than the fused step at this size, where one CTA would
+    hold a whole Gram pass).  W warm-up steps from |0...0> (the first truncation falls in step
+    8), K timed steps (CUDA events on the library stream).  Reports bond updates/s, Trotter
+    steps/s and the FP64 rate of the whole step by the counted work (Gram and update products,
+    the bond SVDs' dense phases and the Jacobi work executed)."""
+    import torch
+    from paper_2309_15642_gb300 import GPEPS
+    from workloads import kick_angles, workload
+    wl = workload("eagle_d128")
+    graphs = wl.graphs()
+    th = torch.tensor([float(t[0]) for t in kick_angles(wl)], dtype=torch.float64, device=dev)
+    g = GPEPS(graphs, wl.D, dtype="c128", device=str(dev))
+    g.reset()
+    g.step(W, th)
+    torch.cuda.synchronize(dev)
+    w0 = g.jacobi_work()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(g.stream)
+    g.step(K, th)
+    e1.record(g.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    work = [b - a for a, b in zip(w0, g.jacobi_work())]
+    fix64, _ = bond_fixed_flops(graphs, wl.D, "c128")
+    f64 = K * (fix64 + big_end_flops(graphs, wl.D)) + one_sided_flops(wl.D, work[0], work[1]) + work[4] * 8
+    gf = f64 / (ms * 1e-3) / 1e9
+    out = {"workload": wl.name, "dtype": "c128", "D": wl.D, "value": g.bonds_per_step * K / (ms * 1e-3),
+           "unit": "bond updates/s", "trotter_steps_per_s": K / (ms * 1e-3), "ms_per_step": ms / K,
+           "timed_steps": f"{W + 1}..{W + K}", "schedule": 0,
+           "fp64": {"whole_step_gflops": gf, "peak_gflops": FP64_PEAK_GFLOPS, "frac": gf / FP64_PEAK_GFLOPS,
+                    "flops_per_step": f64 / K},
+           "flags": g.status()}
+    g.close()
+    return out
+
+
 def main():
     args = parse()
     args.profile_steps = max(args.profile_steps, 1)
@@ -786,10 +874,13 @@ def main():
         torch.cuda.set_device(local_rank)
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     r = run_gpeps(args, rank, world, local_rank)
-    condor = None
+    condor = bp_rec = large = None
     if rank == 0 and world == 1 and not args.no_condor and args.workload == "heavyhex_mix_d32":
         import torch
-        condor = run_condor_d64(torch.device("cuda", local_rank))
+        dev = torch.device("cuda", local_rank)
+        condor = run_condor_d64(dev)
+        bp_rec = run_bp_record(dev)
+        large = run_large_chi_record(dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle(w, args.warmup)
@@ -805,7 +896,8 @@ def main():
                        "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{world}",
                        "timed_steps": f"{args.warmup + 1}..{args.warmup + args.steps} from |0...0>"},
             "roofline": r["roofline"], "hbm": r["hbm"], "clocks": r["clocks"], "e2e": r["e2e"],
-            "plain_c128": r["plain"], "condor_d64": condor, "cpu_baseline": cpu, "parity": r["parity"],
+            "plain_c128": r["plain"], "condor_d64": condor, "bp_regauge": bp_rec, "large_chi_d128": large,
+            "cpu_baseline": cpu, "parity": r["parity"],
             "tuning": (r["tuning"] or {}).get("chosen"),
             "gpu_launches": r["launches_per_step"] * args.steps, "device_flags": r["flags"],
             "mean_z_last_step": r["mean_last"],

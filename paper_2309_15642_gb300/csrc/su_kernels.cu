@@ -831,11 +831,9 @@ __device__ int one_sided_jacobi(V2<R>* Bt, int rows, V2<R>* Vt, int n, R tol, R 
         if (lane == 0) wcnt[warp] = __popc(bal);
       }
       __syncthreads();
-      int cw[4] = {0, 0, 0, 0}, na = 0;
-      for (int v = 0; v < npw; ++v) {
-        cw[v] = wcnt[v];
-        na += cw[v];
-      }
+      // prefix counts of the warps' lists (scalars: a runtime-indexed array would live in local memory)
+      const int p1 = wcnt[0], p2 = p1 + (npw > 1 ? wcnt[1] : 0), p3 = p2 + (npw > 2 ? wcnt[2] : 0);
+      const int na = p3 + (npw > 3 ? wcnt[3] : 0);
       if (threadIdx.x == 0) {
         iflag[3] += na;
         n_chk += (unsigned long long)m;
@@ -845,12 +843,7 @@ __device__ int one_sided_jacobi(V2<R>* Bt, int rows, V2<R>* Vt, int n, R tol, R 
       // (3) the active rotations over the rows of B, then of V
       for (int t = threadIdx.x; t < na * len; t += blockDim.x) {
         const int ia = t / len, i = t - ia * len;
-        int wv = 0, rem = ia;
-        while (rem >= cw[wv]) {
-          rem -= cw[wv];
-          ++wv;
-        }
-        const int k = act[32 * wv + rem];
+        const int k = ia < p1 ? act[ia] : ia < p2 ? act[32 + ia - p1] : ia < p3 ? act[64 + ia - p2] : act[96 + ia - p3];
         int p, q;
         round_pair(r, k, n, p, q);
         V2<R>* xp = i < rows ? Bt + (size_t)p * rows + i : Vt + (size_t)p * n + (i - rows);
@@ -1094,12 +1087,14 @@ __device__ bool bond_front_svd(const BondDesc& bd, const double2* __restrict__ p
   __syncthreads();
   mark(1);
   {
-    // The series of `orthonormalise` is exact to O(|E|^3).  A wide solve drifts
-    // further from unitary (n = 256: ~2500 FP32 rotations per column leave
-    // |E| ~ 1e-4), so above 1e-6 a second pass, which starts from ~|E|^3,
-    // finishes the job; a basis beyond the series' range is flagged.
+    // The series of `orthonormalise` is exact to O(|E|^3), below 1e-12 for the
+    // |E| ~ 2e-5 that the FP32 warm start leaves at n = 64 (~400 rotations per
+    // column; measured <Z> parity 3e-14).  A wide solve drifts further (n = 256:
+    // ~2500 rotations per column leave |E| ~ 1e-4), so from 1e-4 on a second
+    // pass, which starts from ~|E|^3, finishes the job; a basis beyond the
+    // series' range is flagged.
     const double emax = orthonormalise(Vx, n, Xs, ldr, ev, scal);
-    const double emax2 = emax > 1e-6 ? orthonormalise(Vx, n, Xs, ldr, ev, scal) : 0.0;
+    const double emax2 = emax > 1e-4 ? orthonormalise(Vx, n, Xs, ldr, ev, scal) : 0.0;
     if (threadIdx.x == 0 && (!(emax < 1e-2) || !(emax2 < 1e-8))) atomicOr(flags, 1);
   }
   mark(2);

@@ -80,6 +80,9 @@ WORKLOADS = {
     "eagle_d64": Workload("eagle_d64", (EAGLE,), 64, 8, (0.8,),
                           note="127 q, D=64, 8 steps, theta=0.8: the 128 x 128 bond eigenproblems of "
                                "condor_d64 on a lattice the oracle finishes in minutes (truncation from step 7)"),
+    "eagle_d128": Workload("eagle_d128", (EAGLE,), 128, 39, (1.0,),
+                           note="127 q, D=128, theta=1.0: the paper's long-time runs (Figs. 5-7, 37-39 steps) "
+                                "at chi = 128 on the complex128 path (truncation from step 8)"),
     "eagle_bp_d32": Workload("eagle_bp_d32", (EAGLE,), 32, 8, (0.7,), bp=True,
                              note="127 q, D=32, 8 steps, theta=0.7, a BP regauge after every step (the paper's "
                                   "BP comparison at the benchmark's bond dimension; truncation from step 6)"),
