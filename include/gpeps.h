@@ -215,6 +215,23 @@ int gpeps_set_wait_limit(gpeps_handle* h, int64_t cycles);
  */
 int gpeps_set_schedule(gpeps_handle* h, int32_t schedule);  /* 0..5 */
 
+/*
+ * Tensor cores for the two streaming products of every bond update in the
+ * mixed path ("Method": the absorb/reduce/contract products of the simple
+ * update; the spec form with TF32 products and FP32 accumulation): the
+ * Gram blocks G_s of the larger end and its update Gamma_a' = A~ Y_s run as
+ * tcgen05.mma (kind::tf32) products with FP32 accumulators in tensor memory,
+ * each FP32 operand split as hi + lo in TF32 (three products per pair, about
+ * 2^-22 relative error, FP32-level), the Gram read out per 64-row tile and
+ * summed in FP64 as the CUDA-core form does.  The bond eigenproblem, lambda
+ * and lambda^-1 stay FP64.  on = 0 returns to the CUDA-core products (the
+ * default).  Applies to the layered launches and to the fused step
+ * (schedules 4 and 5).  Host-only; drops a captured step graph.  Errors:
+ * GPEPS_EINVAL unless the handle is GPEPS_MIXED_C64 with D = 32 or 64, or if
+ * the fused schedule in use would no longer fit its shared memory.
+ */
+int gpeps_set_tensor_cores(gpeps_handle* h, int32_t on);
+
 /* Number of colour classes (the largest over the instances). */
 int gpeps_n_colours(const gpeps_handle* h, int32_t* n_colours);
 

@@ -27,6 +27,7 @@ SIGNATURES = {
     "gpeps_inverse_steps": (c_int, [c_void_p, c_int32, c_void_p, c_int32]),
     "gpeps_jacobi_work": (c_int, [c_void_p, POINTER(c_int64)]),
     "gpeps_set_schedule": (c_int, [c_void_p, c_int32]),
+    "gpeps_set_tensor_cores": (c_int, [c_void_p, c_int32]),
     "gpeps_n_colours": (c_int, [c_void_p, POINTER(c_int32)]),
     "gpeps_expect_z": (c_int, [c_void_p, c_void_p, c_void_p]),
     "gpeps_step": (c_int, [c_void_p, c_int32, c_void_p, c_int32, c_void_p]),

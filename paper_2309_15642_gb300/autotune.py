@@ -10,9 +10,10 @@ Trotter steps from |0...0>, e.g. the FP64 oracle's), also
 max_i |<Z_i> - reference_z_i| <= ``reference_budget``.  The fastest accepted
 candidate is applied to the handle and returned with the timings.
 
-Candidates (mixed path): schedule (one CTA per bond | work queue with one, two or
-four CTAs per SM | one fused launch per step; a schedule the handle rejects is
-skipped) x
+Candidates (mixed path): the Gram and update products on CUDA cores or on the
+tensor cores (D = 32 and 64) x schedule (one CTA per bond | work queue with one,
+two or four CTAs per SM | one fused launch per step; a schedule the handle
+rejects is skipped) x
 FP32-level thresholds (tol32, floor32) x FP64 stopping thresholds (tol,
 floor_rel = 1e-8, 3e-8 or 1e-7 of the trace: up to the ~1e-7 relative rounding
 that the bond matrix inherits from its FP32 Gram inputs); complex128 keeps its
@@ -28,20 +29,25 @@ STRICT_MIXED = dict(tol=1e-9, floor_rel=1e-11, tol32=1e-6, floor32=2e-7)
 FP32_LEVELS = [(1e-6, 2e-7), (3e-6, 1e-6)]
 FP64_STOPS = [(1e-9, 1e-8), (1e-9, 3e-8), (1e-9, 1e-7)]
 SCHEDULES = (0, 1, 2, 3, 4, 5)
+TENSOR_D = (32, 64)  # bond dimensions with tensor-core Gram and update passes (mixed path)
 
 
-def candidates(dtype):
+def candidates(dtype, D=None):
     if dtype == "c128":
         return [dict(persistent=p) for p in SCHEDULES]
+    tensor = (False, True) if D in TENSOR_D else (False,)
     out = []
-    for p, (t32, f32), (t64, f64) in itertools.product(SCHEDULES, FP32_LEVELS, FP64_STOPS):
-        out.append(dict(persistent=p, tol32=t32, floor32=f32, tol=t64, floor_rel=f64))
+    for tc, p, (t32, f32), (t64, f64) in itertools.product(tensor, SCHEDULES, FP32_LEVELS, FP64_STOPS):
+        out.append(dict(persistent=p, tensor=tc, tol32=t32, floor32=f32, tol=t64, floor_rel=f64))
     return out
 
 
 def _apply(g, cand):
+    g.set_schedule(0)
+    if g.dtype == "mixed":
+        g.set_tensor_cores(cand.get("tensor", False))
     g.set_schedule(cand.get("persistent", 0))
-    jac = {k: v for k, v in cand.items() if k != "persistent"}
+    jac = {k: v for k, v in cand.items() if k not in ("persistent", "tensor")}
     g.set_jacobi(**jac)
 
 
@@ -84,7 +90,7 @@ def autotune(g, theta, warm_steps=6, steps=4, budget=1e-5, repeats=1, reference_
                   reference=True)]
     best = (ref_ms, ref_cand)
     from ._abi import GpepsError
-    for cand in candidates(g.dtype):
+    for cand in candidates(g.dtype, g.D):
         try:
             _apply(g, cand)
         except GpepsError:

@@ -79,6 +79,7 @@ struct gpeps_handle {
   char* d_state = nullptr;
   char* d_work = nullptr;
   bool bound = false;
+  bool tensor = false;  // mixed path, D = 32 or 64: Gram and update passes of the larger ends on the tensor cores
   int schedule = 0;  // bond eigenproblems: 0 one CTA per bond; work queue with 1 (schedule 1), 2 (2) or 4 (3)
                      // CTAs per SM; 4 fused step (gpeps_step: one persistent launch over every colour class)
   std::vector<StepTask> tasks;  // fused step: every bond of a step, colour by colour, with its dependencies
@@ -238,7 +239,7 @@ int layered_per_sm(const gpeps_handle* h) {
 
 // CTAs per SM of the fused step launch
 int step_per_sm(const gpeps_handle* h) {
-  const size_t sm = step_footprint(h->D, h->elt).smem;
+  const size_t sm = step_footprint(h->D, h->elt, h->tensor).smem;
   if (h->schedule == 5 && sm <= bond_share_smem(3)) return 3;
   return sm <= bond_share_smem(2) ? 2 : 1;
 }
@@ -248,7 +249,7 @@ int fused_step_impl(gpeps_handle* h) {
   GP_CUDA(Launch<T>::step(h->at<StepTask>(h->w_tasks), (int)h->tasks.size(), h->at<unsigned int>(h->w_queue),
                           h->at<int>(h->w_done), h->gamma(), h->lam(), h->pending(), h->flags(), h->sweeps(),
                           h->cycles(), h->D, h->jp, h->stream, h->n_sms, h->d_work + h->w_bond_scratch,
-                          h->bond_slot, step_per_sm(h)));
+                          h->bond_slot, step_per_sm(h), h->tensor));
   h->bonds_since_reset += (int64_t)h->tasks.size();
   return GPEPS_OK;
 }
@@ -264,14 +265,22 @@ int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr, void* vsave = 
   void* Y = h->d_work + h->w_Y;
   double* theta_a = h->at<double>(h->w_theta_a);
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[0], h->stream));
-  GP_CUDA(Launch<T>::gram(tiles, nt, bonds, h->gamma(), h->lam(), h->pending(), partials, h->D, h->stream));
+  if (h->tensor)
+    GP_CUDA(Launch<T>::gram_tc(tiles, nt, bonds, h->gamma(), h->lam(), h->pending(), partials, h->flags(), h->D,
+                               h->stream));
+  else
+    GP_CUDA(Launch<T>::gram(tiles, nt, bonds, h->gamma(), h->lam(), h->pending(), partials, h->D, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[1], h->stream));
   GP_CUDA(Launch<T>::bond(bonds, nbd, partials, h->gamma(), h->lam(), h->pending(), Y, theta_a, h->flags(),
                           h->sweeps(), h->cycles(), vsave, h->D, h->jp, h->stream,
                           h->schedule ? h->at<unsigned int>(h->w_queue) : nullptr, h->n_sms,
                           h->d_work + h->w_bond_scratch, layered_per_sm(h)));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[2], h->stream));
-  GP_CUDA(Launch<T>::update(tiles, nt, bonds, h->gamma(), h->lam(), Y, theta_a, h->D, h->stream));
+  if (h->tensor)
+    GP_CUDA(Launch<T>::update_tc(tiles, nt, bonds, h->gamma(), h->lam(), Y, theta_a, h->flags(), h->D,
+                                 h->stream));
+  else
+    GP_CUDA(Launch<T>::update(tiles, nt, bonds, h->gamma(), h->lam(), Y, theta_a, h->D, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[3], h->stream));
   h->bonds_since_reset += nbd;
   return GPEPS_OK;
@@ -640,13 +649,13 @@ int gpeps_step_profiled(gpeps_handle* h, const double* theta, int32_t per_qubit,
 
 int gpeps_set_schedule(gpeps_handle* h, int32_t schedule) {
   if (!h || schedule < 0 || schedule > 5) return GPEPS_EINVAL;
-  if (schedule == 5 && (!h->bound || step_footprint(h->D, h->elt).smem > bond_share_smem(3) ||
+  if (schedule == 5 && (!h->bound || step_footprint(h->D, h->elt, h->tensor).smem > bond_share_smem(3) ||
                         std::min(3 * h->n_sms, (int)h->tasks.size()) > h->bond_slots))
     return GPEPS_EINVAL;
   if (schedule >= 4) {
     // fused step: shared memory of one CTA (alone or two per SM) and a slot per CTA
     if (!h->bound) return GPEPS_EINVAL;
-    const BondFootprint fp = step_footprint(h->D, h->elt);
+    const BondFootprint fp = step_footprint(h->D, h->elt, h->tensor);
     if (fp.smem > kBondSmemMax || fp.slot > h->bond_slot) return GPEPS_EINVAL;
     if (std::min(2 * h->n_sms, (int)h->tasks.size()) > h->bond_slots) return GPEPS_EINVAL;
     // its layers (gpeps_zz_layer) run two CTAs per SM where they fit
@@ -660,6 +669,22 @@ int gpeps_set_schedule(gpeps_handle* h, int32_t schedule) {
     if (std::min(k * h->n_sms, h->max_bonds) > h->bond_slots) return GPEPS_EINVAL;
   }
   h->schedule = schedule;
+  drop_graph(h);
+  return GPEPS_OK;
+}
+
+int gpeps_set_tensor_cores(gpeps_handle* h, int32_t on) {
+  if (!h) return GPEPS_EINVAL;
+  if (!on) {
+    h->tensor = false;
+    drop_graph(h);
+    return GPEPS_OK;
+  }
+  if (h->dtype != GPEPS_MIXED_C64 || !tc_supported(h->D)) return GPEPS_EINVAL;
+  // the fused schedule in use must still fit with the staged tensor-core operands
+  if (h->schedule == 5 && step_footprint(h->D, h->elt, true).smem > bond_share_smem(3)) return GPEPS_EINVAL;
+  if (h->schedule == 4 && step_footprint(h->D, h->elt, true).smem > kBondSmemMax) return GPEPS_EINVAL;
+  h->tensor = true;
   drop_graph(h);
   return GPEPS_OK;
 }

@@ -100,6 +100,20 @@ struct JacobiParams {
   int gate_sign;          // +1: the paper's exp(+i pi/4 Z Z); -1: its inverse exp(-i pi/4 Z Z)
 };
 
+// Tensor-core passes of the mixed path (bigend_tc.cuh): D = 32 or 64.
+constexpr int kTcKc = 32;  // K values of one staged operand chunk
+__host__ __device__ constexpr bool tc_supported(int D) { return D == 32 || D == 64; }
+// a wait for committed tensor-core products gives up after this many SM cycles (~2 s; a chunk takes microseconds)
+constexpr long long kTcWaitCycles = 4000000000LL;
+// TMEM columns of a CTA using the tensor-core passes (a power of two >= 32)
+__host__ __device__ constexpr uint32_t tc_cols(int D) { return (uint32_t)(4 * D); }
+// shared memory of the Gram chunk: hi and lo of P, 4D rows x kTcKc
+__host__ __device__ constexpr size_t tc_gram_smem(int D) { return (size_t)4 * D * kTcKc * 4 * 2; }
+// shared memory of the update chunk: hi and lo of A (128 rows) and of B (4D rows), kTcKc each, and the row mask
+__host__ __device__ constexpr size_t tc_update_smem(int D) {
+  return (size_t)(128 + 4 * D) * kTcKc * 4 * 2 + 128 * 4;
+}
+
 // Launchers (su_kernels.cu).  T = float for GPEPS_MIXED_C64, double for GPEPS_C128.
 template <typename T>
 struct Launch {
@@ -118,6 +132,14 @@ struct Launch {
                           void* scratch = nullptr, int per_sm = 1);
   static cudaError_t update(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, void* gamma,
                             const double* lam, const void* Y, const double* theta_a, int D, cudaStream_t st);
+  // The same two passes on the tensor cores (tcgen05, 3xTF32; complex64 storage, D = 32 or 64 only); a
+  // wait for the tensor core that runs past kTcWaitCycles raises GPEPS_FLAG_TIMEOUT.
+  static cudaError_t gram_tc(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, const void* gamma,
+                             const double* lam, const double* pending, void* partials, int* flags, int D,
+                             cudaStream_t st);
+  static cudaError_t update_tc(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, void* gamma,
+                               const double* lam, const void* Y, const double* theta_a, int* flags, int D,
+                               cudaStream_t st);
   static cudaError_t readout(const SiteDesc* sites, int n_sites, const void* gamma, const double* lam,
                              const double* pending, double* z, int D, cudaStream_t st);
   // Every bond update of one Trotter step in one persistent launch (per_sm CTAs
@@ -125,7 +147,7 @@ struct Launch {
   static cudaError_t step(const StepTask* tasks, int n_tasks, unsigned int* queue, int* done, void* gamma,
                           double* lam, double* pending, int* flags, unsigned long long* sweeps,
                           unsigned long long* cycles, int D, JacobiParams jp, cudaStream_t st, int n_ctas,
-                          void* scratch, size_t slot, int per_sm);
+                          void* scratch, size_t slot, int per_sm, bool tc = false);
 };
 
 
@@ -171,7 +193,8 @@ constexpr int kMaxSms = 256;          // SMs the shared-SM schedules have scratc
 // Memory of a fused-step CTA: dynamic shared memory, and the bytes of its
 // global slot (n x n matrices of the bond eigenproblem, FP64 Gram sums, Y and
 // the kick angle of end a).
-BondFootprint step_footprint(int D, size_t elt);
+// tc: the Gram and update passes on the tensor cores (their staged operands set the floor).
+BondFootprint step_footprint(int D, size_t elt, bool tc = false);
 constexpr long long kWaitCycles = 4000000000LL;  // default wait limit of the fused step (~2 s of SM cycles)
 
 // ---------------------------------------------------------------- BP regauging

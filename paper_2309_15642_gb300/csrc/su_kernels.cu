@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "gpeps_internal.cuh"
 #include "jacobi.cuh"
@@ -66,6 +67,11 @@ __device__ __forceinline__ double row_weight(const SideDesc& sd, const double* l
   if (sd.lam_o2 >= 0) w *= ldst<kCG>(lam + sd.lam_o2 + p.r2);
   return w;
 }
+
+}  // namespace gpeps
+// tensor-core passes (they use the row/element helpers above)
+#include "bigend_tc.cuh"
+namespace gpeps {
 
 // ---------------------------------------------------------------- reset / kick
 template <typename T>
@@ -1618,6 +1624,139 @@ __device__ void fused_update(const SideDesc& sa, V2<T>* gamma, const double* lam
   }
 }
 
+// ---------------------------------------------------------------- tensor-core passes (mixed path)
+// Allocate the CTA's TMEM (warp 0) and set up its mbarrier; every thread then
+// holds the TMEM base address.
+__device__ __forceinline__ uint32_t tc_setup(uint32_t* slot, uint64_t* bar, uint32_t ncols) {
+  if (threadIdx.x < 32) {
+    tc::tmem_alloc(slot, ncols);
+    tc::tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    tc::mbar_init(bar, 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  return *slot;
+}
+__device__ __forceinline__ void tc_teardown(uint32_t tmem, uint32_t ncols) {
+  tc::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, ncols);
+  }
+}
+
+// Row mask of the update: rows whose lambda on an other leg is at or below the
+// pseudo-inverse cut are zeroed (as in update_kernel).
+template <bool kCG>
+__device__ void tc_row_mask(const SideDesc& sa, const double* lam, int row0, int nrows, int D, float* mask,
+                            double* cut) {
+  if (threadIdx.x < 2) {
+    const int lo = threadIdx.x == 0 ? sa.lam_o1 : sa.lam_o2;
+    double mx = 0.0;
+    if (lo >= 0)
+      for (int k = 0; k < D; ++k) mx = fmax(mx, ldst<kCG>(lam + lo + k));
+    cut[threadIdx.x] = kLambdaCut * mx;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+    const RowPos p = row_pos(sa, row0 + r);
+    bool ok = true;
+    if (sa.lam_o1 >= 0) ok = ok && ldst<kCG>(lam + sa.lam_o1 + p.r1) > cut[0];
+    if (sa.lam_o2 >= 0) ok = ok && ldst<kCG>(lam + sa.lam_o2 + p.r2) > cut[1];
+    mask[r] = ok ? 1.f : 0.f;
+  }
+  __syncthreads();
+}
+
+// Gram partials of one 64-row tile on the tensor cores (layered form of the
+// mixed path; same partial layout as gram_kernel).
+__global__ void __launch_bounds__(128)
+    tc_gram_kernel(const TileDesc* __restrict__ tiles, const BondDesc* __restrict__ bonds,
+                   const float2* __restrict__ gamma, const double* __restrict__ lam,
+                   const double* __restrict__ pending, float2* __restrict__ partials, int* flags, int D,
+                   long long limit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  const uint32_t ncols = tc_cols(D);
+  const TcCtx cx{tc_setup(&tslot, &bar, ncols), &bar, limit};
+  uint32_t phase = 0;
+  const TileDesc t = tiles[blockIdx.x];
+  const SideDesc sa = bonds[t.bond].a;
+  const double th = pending[sa.site];
+  const float c = (float)cos(0.5 * th), s = (float)sin(0.5 * th);
+  const bool ok = tc_gram_rows<false>(sa, gamma, lam, c, s, t.row0, t.nrows, D, smem_raw, cx, phase, true);
+  float* out = reinterpret_cast<float*>(partials + (int64_t)t.part * 2 * D * D);
+  const int D2 = D * D;
+  tc_gram_read(D, cx, [&](int sp, int k, int l, int reim, float v) { out[2 * (sp * D2 + k * D + l) + reim] = v; });
+  if (!ok && threadIdx.x == 0) atomicOr(flags, 4);
+  tc_teardown(cx.tmem, ncols);
+}
+
+// Update of one tile of end a on the tensor cores (layered form of the mixed
+// path; the same product as update_kernel).
+__global__ void __launch_bounds__(128)
+    tc_update_kernel(const TileDesc* __restrict__ tiles, const BondDesc* __restrict__ bonds, float2* gamma,
+                     const double* __restrict__ lam, const float2* __restrict__ Y,
+                     const double* __restrict__ theta_a, int* flags, int D, long long limit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  __shared__ double cut[2];
+  const uint32_t ncols = tc_cols(D);
+  const TcCtx cx{tc_setup(&tslot, &bar, ncols), &bar, limit};
+  uint32_t phase = 0;
+  const TileDesc t = tiles[blockIdx.x];
+  const SideDesc sa = bonds[t.bond].a;
+  float* mask = reinterpret_cast<float*>(smem_raw + tc_update_smem(D) - 128 * 4);
+  tc_row_mask<false>(sa, lam, t.row0, t.nrows, D, mask, cut);
+  const double th = theta_a[t.bond];
+  const float c = (float)cos(0.5 * th), s = (float)sin(0.5 * th);
+  const bool ok = tc_update_rows<false>(sa, gamma, Y + (int64_t)t.bond * 2 * D * D, c, s, mask, t.row0, t.nrows, D,
+                                        smem_raw, cx, phase);
+  if (!ok && threadIdx.x == 0) atomicOr(flags, 4);
+  tc_teardown(cx.tmem, ncols);
+}
+
+// The fused step's Gram and update passes on the tensor cores: the Gram per
+// 64-row tile (read out and summed in FP64 in tile order, as the layered
+// partials are), the update per 128 rows.
+__device__ bool tc_fused_gram(const SideDesc& sa, const float2* gamma, const double* lam, double th, double2* gsum,
+                              int D, unsigned char* sm, const TcCtx& cx, uint32_t& phase) {
+  const int D2 = D * D, nout = 2 * D2;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) gsum[o] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const float c = (float)cos(0.5 * th), s = (float)sin(0.5 * th);
+  const int tr = tile_rows(D, sizeof(float2));
+  double* g = reinterpret_cast<double*>(gsum);
+  bool ok = true;
+  for (int row0 = 0; row0 < sa.rows && ok; row0 += tr) {
+    const int nrows = sa.rows - row0 < tr ? sa.rows - row0 : tr;
+    ok = tc_gram_rows<true>(sa, gamma, lam, c, s, row0, nrows, D, sm, cx, phase, true);
+    tc_gram_read(D, cx, [&](int sp, int k, int l, int reim, float v) { g[2 * (sp * D2 + k * D + l) + reim] += (double)v; });
+  }
+  return ok;
+}
+
+__device__ bool tc_fused_update(const SideDesc& sa, float2* gamma, const double* lam, const float2* Y, double th,
+                                int D, unsigned char* sm, const TcCtx& cx, uint32_t& phase) {
+  __shared__ double cut[2];
+  float* mask = reinterpret_cast<float*>(sm + tc_update_smem(D) - 128 * 4);
+  const float c = (float)cos(0.5 * th), s = (float)sin(0.5 * th);
+  bool ok = true;
+  for (int row0 = 0; row0 < sa.rows && ok; row0 += 128) {
+    const int nrows = sa.rows - row0 < 128 ? sa.rows - row0 : 128;
+    tc_row_mask<true>(sa, lam, row0, nrows, D, mask, cut);
+    ok = tc_update_rows<true>(sa, gamma, Y, c, s, mask, row0, nrows, D, sm, cx, phase);
+  }
+  return ok;
+}
+
 // Layout of a fused-step CTA's global slot: the big part of the bond layout at
 // n = 2D, then the FP64 Gram sums [2][D][D], Y [2][D][D] and the kick angle of end a.
 struct StepSlot {
@@ -1630,9 +1769,14 @@ struct StepSlot {
   }
 };
 
-BondFootprint step_footprint(int D, size_t elt) {
+BondFootprint step_footprint(int D, size_t elt, bool tc) {
   const BondSmem L(D, 2 * D);
   size_t sm = L.small + bond_f32(D, elt);
+  if (tc) {
+    if (tc_gram_smem(D) > sm) sm = tc_gram_smem(D);
+    if (tc_update_smem(D) > sm) sm = tc_update_smem(D);
+    return BondFootprint{(sm + 15) & ~(size_t)15, StepSlot(D, elt).total};
+  }
   const size_t tr = (size_t)tile_rows(D, elt);
   const size_t gram = tr * (2 * D + 1) * elt;
   const size_t r = tr * (2 * D + 1), c = (size_t)(2 * D) * (tr + 1);
@@ -1642,7 +1786,7 @@ BondFootprint step_footprint(int D, size_t elt) {
   return BondFootprint{(sm + 15) & ~(size_t)15, StepSlot(D, elt).total};
 }
 
-template <typename T, int kThr, int kMinB>
+template <typename T, int kThr, int kMinB, bool kTC>
 __global__ void __launch_bounds__(kThr, kMinB)
     step_kernel(const StepTask* __restrict__ tasks, int n_tasks, unsigned int* queue, int* done, V2<T>* gamma,
                 double* lam, double* pending, int* flags, unsigned long long* sweeps_out, unsigned long long* cycles,
@@ -1654,6 +1798,13 @@ __global__ void __launch_bounds__(kThr, kMinB)
   double2* gsum = reinterpret_cast<double2*>(mine + SL.off_gsum);
   V2<T>* Y = reinterpret_cast<V2<T>*>(mine + SL.off_Y);
   double* th_a = reinterpret_cast<double*>(mine + SL.off_th);
+  // tensor-core passes: TMEM for the whole launch, one mbarrier for the MMA commits
+  __shared__ __align__(8) uint64_t tc_bar;
+  __shared__ uint32_t tc_slot;
+  TcCtx cx{0u, &tc_bar, kTcWaitCycles};
+  uint32_t phase = 0;
+  bool tc_ok = true;
+  if constexpr (kTC) cx.tmem = tc_setup(&tc_slot, &tc_bar, tc_cols(D));
   for (;;) {
     if (threadIdx.x == 0) next = (int)atomicAdd(queue, 1u);
     __syncthreads();
@@ -1666,16 +1817,32 @@ __global__ void __launch_bounds__(kThr, kMinB)
       wait_done(done, tasks[ti].dep_b, flags, jp.wait_cycles);
     }
     __syncthreads();
-    fused_gram<T>(bd.a, gamma, lam, __ldcg(pending + bd.a.site), gsum, D, smem_raw);
+    if constexpr (kTC) {
+      if (tc_ok)
+        tc_ok = tc_fused_gram(bd.a, reinterpret_cast<const float2*>(gamma), lam, __ldcg(pending + bd.a.site), gsum, D,
+                              smem_raw, cx, phase);
+    } else {
+      fused_gram<T>(bd.a, gamma, lam, __ldcg(pending + bd.a.site), gsum, D, smem_raw);
+    }
     bond_body<T, true>(bd, nullptr, gsum, gamma, lam, pending, Y, th_a, flags, sweeps_out, cycles, nullptr, D, jp,
                        mine);
     __syncthreads();
-    fused_update<T>(bd.a, gamma, lam, Y, *th_a, D, smem_raw);
+    if constexpr (kTC) {
+      if (tc_ok)
+        tc_ok = tc_fused_update(bd.a, reinterpret_cast<float2*>(gamma), lam, reinterpret_cast<const float2*>(Y),
+                                *th_a, D, smem_raw, cx, phase);
+    } else {
+      fused_update<T>(bd.a, gamma, lam, Y, *th_a, D, smem_raw);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
       st_release(done + ti, 1);
     }
+  }
+  if constexpr (kTC) {
+    if (!tc_ok && threadIdx.x == 0) atomicOr(flags, 4);
+    tc_teardown(cx.tmem, tc_cols(D));
   }
 }
 
@@ -1866,15 +2033,31 @@ cudaError_t Launch<T>::init() {
   e = cudaFuncSetAttribute(bond_kernel_persistent<T, 128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bond_share_smem(4));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(step_kernel<T, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(step_kernel<T, 256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bond_share_smem(2));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(step_kernel<T, 192, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(step_kernel<T, 192, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bond_share_smem(3));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(step_kernel<T, kBondThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(step_kernel<T, kBondThreads, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kBondSmemMax);
   if (e != cudaSuccess) return e;
+  if constexpr (std::is_same<T, float>::value) {
+    e = cudaFuncSetAttribute(step_kernel<T, 256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bond_share_smem(2));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(step_kernel<T, 192, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bond_share_smem(3));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(step_kernel<T, kBondThreads, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kBondSmemMax);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_gram_smem(64));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc_update_smem(64));
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBondSmemMax);
 }
 
@@ -1907,6 +2090,30 @@ cudaError_t Launch<T>::gram(const TileDesc* tiles, int n_tiles, const BondDesc* 
   const size_t sm = gram_smem(D, sizeof(V2<T>));
   gram_kernel<T><<<n_tiles, kThreads, sm, st>>>(tiles, bonds, static_cast<const V2<T>*>(gamma), lam, pending,
                                                  static_cast<V2<T>*>(partials), D);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::gram_tc(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, const void* gamma,
+                               const double* lam, const double* pending, void* partials, int* flags, int D,
+                               cudaStream_t st) {
+  if (n_tiles == 0) return cudaSuccess;
+  if (!std::is_same<T, float>::value || !tc_supported(D)) return cudaErrorInvalidValue;
+  tc_gram_kernel<<<n_tiles, 128, tc_gram_smem(D), st>>>(tiles, bonds, static_cast<const float2*>(gamma), lam,
+                                                          pending, static_cast<float2*>(partials), flags, D,
+                                                          kTcWaitCycles);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::update_tc(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, void* gamma,
+                                 const double* lam, const void* Y, const double* theta_a, int* flags, int D,
+                                 cudaStream_t st) {
+  if (n_tiles == 0) return cudaSuccess;
+  if (!std::is_same<T, float>::value || !tc_supported(D)) return cudaErrorInvalidValue;
+  tc_update_kernel<<<n_tiles, 128, tc_update_smem(D), st>>>(tiles, bonds, static_cast<float2*>(gamma), lam,
+                                                              static_cast<const float2*>(Y), theta_a, flags, D,
+                                                              kTcWaitCycles);
   return cudaGetLastError();
 }
 
@@ -1975,9 +2182,10 @@ template <typename T>
 cudaError_t Launch<T>::step(const StepTask* tasks, int n_tasks, unsigned int* queue, int* done, void* gamma,
                             double* lam, double* pending, int* flags, unsigned long long* sweeps,
                             unsigned long long* cycles, int D, JacobiParams jp, cudaStream_t st, int n_ctas,
-                            void* scratch, size_t slot, int per_sm) {
+                            void* scratch, size_t slot, int per_sm, bool tc) {
   if (n_tasks == 0) return cudaSuccess;
-  const BondFootprint fp = step_footprint(D, sizeof(V2<T>));
+  if (tc && (!std::is_same<T, float>::value || !tc_supported(D))) return cudaErrorInvalidValue;
+  const BondFootprint fp = step_footprint(D, sizeof(V2<T>), tc);
   if (!scratch || slot < fp.slot || per_sm < 1 || per_sm > 3) return cudaErrorInvalidValue;
   if (fp.smem > (per_sm > 1 ? bond_share_smem(per_sm) : kBondSmemMax)) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), st);
@@ -1987,16 +2195,26 @@ cudaError_t Launch<T>::step(const StepTask* tasks, int n_tasks, unsigned int* qu
   const int want = per_sm * n_ctas;
   const int grid = want < n_tasks ? want : n_tasks;
   unsigned char* sp = static_cast<unsigned char*>(scratch);
-  if (per_sm == 3)
-    step_kernel<T, 192, 3><<<grid, 192, fp.smem, st>>>(tasks, n_tasks, queue, done, static_cast<V2<T>*>(gamma), lam,
-                                                       pending, flags, sweeps, cycles, D, jp, sp, slot);
-  else if (per_sm == 2)
-    step_kernel<T, 256, 2><<<grid, 256, fp.smem, st>>>(tasks, n_tasks, queue, done, static_cast<V2<T>*>(gamma), lam,
-                                                       pending, flags, sweeps, cycles, D, jp, sp, slot);
-  else
-    step_kernel<T, kBondThreads, 1><<<grid, kBondThreads, fp.smem, st>>>(
-        tasks, n_tasks, queue, done, static_cast<V2<T>*>(gamma), lam, pending, flags, sweeps, cycles, D, jp, sp,
-        slot);
+#define GP_STEP(THR, MINB, TC)                                                                                   \
+  step_kernel<T, THR, MINB, TC><<<grid, THR, fp.smem, st>>>(tasks, n_tasks, queue, done, static_cast<V2<T>*>(gamma), \
+                                                            lam, pending, flags, sweeps, cycles, D, jp, sp, slot)
+  if (tc) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (per_sm == 3)
+        GP_STEP(192, 3, true);
+      else if (per_sm == 2)
+        GP_STEP(256, 2, true);
+      else
+        GP_STEP(kBondThreads, 1, true);
+    }
+  } else if (per_sm == 3) {
+    GP_STEP(192, 3, false);
+  } else if (per_sm == 2) {
+    GP_STEP(256, 2, false);
+  } else {
+    GP_STEP(kBondThreads, 1, false);
+  }
+#undef GP_STEP
   return cudaGetLastError();
 }
 

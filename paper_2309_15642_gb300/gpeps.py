@@ -203,6 +203,11 @@ class GPEPS:
         gpeps_set_schedule)."""
         check(self.lib.gpeps_set_schedule(self.h, int(schedule)), "gpeps_set_schedule")
 
+    def set_tensor_cores(self, on: bool = True) -> None:
+        """Gram and update products of the larger ends on the tensor cores
+        (mixed path, D = 32 or 64; see gpeps_set_tensor_cores)."""
+        check(self.lib.gpeps_set_tensor_cores(self.h, 1 if on else 0), "gpeps_set_tensor_cores")
+
     def set_jacobi(self, tol=None, floor_rel=None, tol32=1e-6, floor32=2e-7, max_sweeps=40, max_sweeps32=20):
         """Thresholds of the bond eigensolver (see gpeps_set_jacobi); None = the dtype's default."""
         if tol is None:
