@@ -66,6 +66,8 @@ def parse():
                     help="skip the sub-records (1121-qubit D = 64, BP regauging, D = 128)")
     ap.add_argument("--cpu-leg", action="store_true",
                     help="internal: time one leg of the CPU oracle baseline and print it as JSON")
+    ap.add_argument("--tensor", action="store_true",
+                    help="with --no-autotune: Gram and update passes on the tensor cores (mixed, D = 32 or 64)")
     ap.add_argument("--floor-rel", type=float, default=None,
                     help="with --no-autotune: FP64 Jacobi floor (fraction of the trace) of the mixed path")
     return ap.parse_args()
@@ -149,9 +151,14 @@ class Clocks:
 # DRAM bytes per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by workload, dtype and schedule; reported as the roofline's
 # `traffic` only for that configuration (profiles/step_kernel_heavyhex_mix_d32.md)
-NCU_TRAFFIC = {("heavyhex_mix_d32", "mixed", 4): 2.048679e9 + 1.742843e9,
+# and whether the Gram and update passes ran on the tensor cores
+NCU_TRAFFIC = {("heavyhex_mix_d32", "mixed", 4, False): 2.048679e9 + 1.742843e9,
                # schedule 5 (three CTAs per SM): dram__bytes.sum.per_second 122.32 GB/s x 35.60 ms
-               ("heavyhex_mix_d32", "mixed", 5): 122.321021e9 * 35.601440e-3}
+               ("heavyhex_mix_d32", "mixed", 5, False): 122.321021e9 * 35.601440e-3}
+
+# TF32 tensor peak: the measured bf16 burst (MEASURED_PEAKS.json) x the nominal TF32 : BF16 dense ratio
+# (1.1 : 2.25 PFLOP/s)
+TF32_OVER_BF16 = 1.1 / 2.25
 
 # ------------------------------------------------------------------ algorithmic counts
 def bond_fixed_flops(graphs, D, dtype):
@@ -352,6 +359,49 @@ def big_end_flops(graphs, D):
     return float(tot)
 
 
+def tc_executed_flops(graphs, D):
+    """TF32 flops the tensor-core Gram and update passes execute in one Trotter step (3xTF32: three
+    products per operand pair).  Gram: per 32-row chunk of the larger end (rows padded to a multiple
+    of 8), one 128 x 128 product (D = 32: over all 4D columns) or two (D = 64: one per spin).
+    Update: per 128 rows, an M = 128 x N = 4D x K = 4D product."""
+    import numpy as np
+    tot = 0
+    for n, edges in graphs:
+        deg = np.bincount(np.asarray(edges).ravel(), minlength=n)
+        for a, b in edges:
+            rows = D ** (int(max(deg[a], deg[b])) - 1)
+            ngm = 2 if D == 64 else 1
+            for r0 in range(0, rows, 32):
+                kc8 = (min(32, rows - r0) + 7) // 8 * 8
+                tot += ngm * 2 * 128 * 128 * kc8
+            tot += ((rows + 127) // 128) * 2 * 128 * (4 * D) * (4 * D)
+    return 3.0 * tot
+
+
+def tf32_peak_tflops():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        v = json.load(open(path)).get("bf16_tflops")
+        if v:
+            return float(v) * TF32_OVER_BF16, "measured bf16 burst x nominal TF32/BF16 ratio 1.1/2.25"
+    return 1900.0 * TF32_OVER_BF16, "fallback bf16 1.9 PFLOP/s x nominal TF32/BF16 ratio 1.1/2.25"
+
+
+def tensor_pipe_record(graphs, D, kernel_ms, on):
+    """Tensor-pipe use of the dominant kernel: the TF32 flops its tensor-core passes executed over
+    its launch time, against the TF32 peak (a kernel-average figure: the step is FP64-bound)."""
+    if not on:
+        return {"tensor_cores": False, "utilisation": 0.0,
+                "note": "Gram and update passes on CUDA cores (the autotuner's or the caller's choice)"}
+    f = tc_executed_flops(graphs, D)
+    peak, src = tf32_peak_tflops()
+    achieved = f / (kernel_ms * 1e-3) / 1e12
+    return {"tensor_cores": True, "tf32_flops_per_launch": f, "achieved_tflops": achieved, "peak_tflops": peak,
+            "frac": achieved / peak, "peak_source": src,
+            "note": "tcgen05 kind::tf32 (3xTF32) Gram and update passes; kernel-average rate over the whole "
+                    "launch, which the FP64 bond eigenproblems dominate"}
+
+
 def step_bytes(graphs, D, elt):
     """Algorithmic HBM bytes of one Trotter step: every bond reads and writes both site
     tensors once (its larger end twice: Gram and update pass), the readout reads every
@@ -496,6 +546,10 @@ def run_gpeps(args, rank, world, local_rank):
                 g.set_schedule(args.schedule)
             if args.floor_rel is not None and dtype == "mixed":
                 g.set_jacobi(floor_rel=args.floor_rel)
+            if args.tensor and dtype == "mixed":
+                g.set_schedule(0)
+                g.set_tensor_cores(True)
+                g.set_schedule(args.schedule or 0)
         if tune:
             from paper_2309_15642_gb300.autotune import autotune
             # candidates are also held to the committed oracle values after the tuner's 6 + 4 steps
@@ -531,10 +585,11 @@ def run_gpeps(args, rank, world, local_rank):
     # per-kernel durations of profiled steps right after the timed region, under the schedule
     # of the timed region (fused: one launch per step; layered: three per colour class)
     sched = (tuning["chosen"].get("persistent", 0) if tuning else (args.schedule or 0))
+    tensor = bool(tuning["chosen"].get("tensor", False)) if tuning else (args.tensor and args.dtype == "mixed")
     fused = sched >= 4          # schedules 4 and 5: the fused step (two or three CTAs per SM)
     prof = {"gram": [], "bond": [], "update": []} if not fused else {"kick": [], "bond_updates": [], "readout": []}
     s0, q0, b0 = g.sweeps()
-    c0 = g.bond_phase_cycles()
+    c0 = g.bond_counters()
     w0 = g.jacobi_work()
     for _ in range(args.profile_steps):
         if fused:
@@ -548,12 +603,15 @@ def run_gpeps(args, rank, world, local_rank):
                 prof[k].append(v)
         g.expect_z()
     s1, q1, b1 = g.sweeps()
-    c1 = g.bond_phase_cycles()
+    c1 = g.bond_counters()
     w1 = g.jacobi_work()
     work_step = [(b - a) / max(args.profile_steps, 1) for a, b in zip(w0, w1)]
     phase_names = ["rho", "fp32_jacobi", "fp64_orthonormalise", "rotate_and_fp32_levels", "fp64_jacobi",
                    "epilogue"]
     phase_cycles = {k: (b - a) / max(b1 - b0, 1) for k, a, b in zip(phase_names, c0, c1)}
+    if fused:  # the Gram and update passes of the larger end inside the fused step
+        phase_cycles["gram_pass"] = (c1[22] - c0[22]) / max(b1 - b0, 1)
+        phase_cycles["update_pass"] = (c1[23] - c0[23]) / max(b1 - b0, 1)
     sweeps_per_bond = (s1 - s0) / max(b1 - b0, 1)
     sweeps32_per_bond = (q1 - q0) / max(b1 - b0, 1)
     layer_ms = {k: sum(v) / max(args.profile_steps, 1) for k, v in prof.items()}   # per step, all colours
@@ -584,7 +642,7 @@ def run_gpeps(args, rank, world, local_rank):
     roofline = {"kernel": kernel, "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
                 "frac": achieved / FP64_PEAK_GFLOPS,
-                "traffic": NCU_TRAFFIC.get((w.name, args.dtype, sched)),
+                "traffic": NCU_TRAFFIC.get((w.name, args.dtype, sched, tensor)),
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x 2.07 GHz (MEASURED_PEAKS.json has "
                                "no FP64 figure; an FP64 FMA loop measured 1197 GFLOP/s)",
                 "fp64_sweeps_per_bond": sweeps_per_bond, "fp32_sweeps_per_bond": sweeps32_per_bond,
@@ -593,7 +651,9 @@ def run_gpeps(args, rank, world, local_rank):
                 "jacobi_work_per_step": dict(zip(("fp64_blocks", "fp64_vector_pairs", "fp32_blocks",
                                                   "fp32_vector_pairs", "fp64_level_macs"), work_step)),
                 "launch_ms": launch_ms, "units_per_launch": bonds_per_launch, "schedule": sched,
-                "cycles_per_bond_by_phase": phase_cycles, "per_step_ms": layer_ms}
+                "cycles_per_bond_by_phase": phase_cycles, "per_step_ms": layer_ms,
+                "tensor_pipe": tensor_pipe_record(graphs, w.D, launch_ms if fused else
+                                                  layer_ms.get("gram", 0.0) + layer_ms.get("update", 0.0), tensor)}
     elt = 8 if args.dtype == "mixed" else 16
     sb = step_bytes(graphs, w.D, elt)
     hbm = {"algorithmic_bytes_per_step": sb, "achieved_gbs_whole_step": sb / (ms / K * 1e-3) / 1e9}
@@ -651,8 +711,8 @@ def run_condor_d64(dev, Kc=3, Wc=6):
     events on the library stream), then one profiled step for the step kernel's time and the FP64
     work it executed.  Reports bond updates/s, Trotter steps/s, algorithmic HBM GB/s against the
     measured copy bandwidth, the step kernel's FP64 rate against the derived FP64 peak, the tensor
-    pipe (idle: no tensor-core instruction on this path), and the largest per-qubit difference
-    between the two paths after the timed steps.  The complex128 path is held to the oracle at
+    pipe (the mixed path with its Gram and update passes on the tensor cores, beside the same path
+    on CUDA cores), and the largest per-qubit differences between the paths after the timed steps.  The complex128 path is held to the oracle at
     1e-10 per qubit at D = 64 on the 127-qubit lattice; the oracle itself needs minutes per step
     of this lattice, so there are no committed oracle values for it."""
     import numpy as np
@@ -665,8 +725,9 @@ def run_condor_d64(dev, Kc=3, Wc=6):
     hbm_peak, hbm_src = measured_hbm_gbs()
     out, zs = {"workload": wc.name, "lattice_qubits": [n for n, _ in graphs], "D": wc.D,
                "theta": list(wc.theta)}, {}
-    for dtype in ("mixed", "c128"):
+    for key, dtype, tensor in (("mixed", "mixed", True), ("mixed_cuda_cores", "mixed", False), ("c128", "c128", False)):
         g = GPEPS(graphs, wc.D, dtype=dtype, device=str(dev))
+        g.set_tensor_cores(tensor)
         g.set_schedule(4)
         if dtype == "mixed":
             g.set_jacobi(floor_rel=3e-8)
@@ -680,7 +741,7 @@ def run_condor_d64(dev, Kc=3, Wc=6):
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         z, _ = g.expect_z()
-        zs[dtype] = z.cpu().numpy()
+        zs[key] = z.cpu().numpy()
         w0 = g.jacobi_work()
         kernel_ms = g.step_profiled(th)[1]
         work = [b - a for a, b in zip(w0, g.jacobi_work())]
@@ -690,7 +751,7 @@ def run_condor_d64(dev, Kc=3, Wc=6):
         sb = step_bytes(graphs, wc.D, 8 if dtype == "mixed" else 16)
         gbs = sb / (ms / Kc * 1e-3) / 1e9
         gf = f64 / (kernel_ms * 1e-3) / 1e9
-        out[dtype] = {"value": g.bonds_per_step * Kc / (ms * 1e-3), "unit": "bond updates/s",
+        out[key] = {"value": g.bonds_per_step * Kc / (ms * 1e-3), "unit": "bond updates/s",
                       "trotter_steps_per_s": Kc / (ms * 1e-3), "ms_per_step": ms / Kc,
                       "timed_steps": f"{Wc + 1}..{Wc + Kc}",
                       "hbm": {"algorithmic_bytes_per_step": sb, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
@@ -698,12 +759,11 @@ def run_condor_d64(dev, Kc=3, Wc=6):
                       "fp64": {"kernel": "step_kernel", "kernel_ms": kernel_ms, "flops_per_launch": f64,
                                "achieved_gflops": gf, "peak_gflops": FP64_PEAK_GFLOPS,
                                "frac": gf / FP64_PEAK_GFLOPS},
-                      "tensor_pipe": {"utilisation": 0.0,
-                                      "note": "no tensor-core instruction in the step kernel: FP64 Jacobi and "
-                                              "FP32/FP64 CUDA-core products"},
+                      "tensor_pipe": tensor_pipe_record(graphs, wc.D, kernel_ms, tensor),
                       "flags": g.status()}
         g.close()
     out["max_abs_dz_per_qubit_mixed_vs_c128"] = float(np.abs(zs["mixed"] - zs["c128"]).max())
+    out["max_abs_dz_per_qubit_tensor_vs_cuda_cores"] = float(np.abs(zs["mixed"] - zs["mixed_cuda_cores"]).max())
     return out
 
 

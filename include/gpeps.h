@@ -381,7 +381,7 @@ int gpeps_sweeps(gpeps_handle* h, int64_t* sweeps64, int64_t* sweeps32, int64_t*
 int gpeps_jacobi_work(gpeps_handle* h, int64_t* work);
 
 /* Counters of the bond-eigenproblem kernel since the last gpeps_reset, summed
- * over bonds, host int64[22].  [0..5] SM cycles (clock64 of one thread per
+ * over bonds, host int64[24].  [0..5] SM cycles (clock64 of one thread per
  * CTA) of its phases: [0] the bond matrix (mixed: the reduced density matrix
  * rho; complex128: the pivoted Cholesky roots of the Gram blocks, the core M
  * and rho = M^H M), [1] first FP32 Jacobi level, [2] FP64 re-orthonormalisation
@@ -390,7 +390,9 @@ int gpeps_jacobi_work(gpeps_handle* h, int64_t* work);
  * levels on blocks of small columns of B, [4] FP64 Jacobi sweeps (complex128:
  * one-sided, on B), [5] truncation, Y matrices and the smaller end.  [6..13]
  * rotations applied in sweep 0..7 of the first FP32 level, [14..21] in FP64
- * sweep 0..7.  Synchronises. */
+ * sweep 0..7, [22] and [23] SM cycles of the Gram pass and of the update pass
+ * of the larger end inside the fused step (schedules 4 and 5; 0 otherwise).
+ * Synchronises. */
 int gpeps_bond_phase_cycles(gpeps_handle* h, int64_t* cycles);
 
 /*

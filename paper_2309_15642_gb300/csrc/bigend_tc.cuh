@@ -5,18 +5,18 @@
 // contract of the simple update) are real GEMMs once complex numbers are
 // split into their real and imaginary parts:
 //
-//   Gram    P[r][c], c = (s, k, re/im), holds the kicked, lambda-weighted end a;
-//           B = P^T P accumulates in TMEM over the rows r, and
-//           G_s[k][l] = (B[(s,k,re)][(s,l,re)] + B[(s,k,im)][(s,l,im)])
-//                     + i (B[(s,k,re)][(s,l,im)] - B[(s,k,im)][(s,l,re)]).
+//   Gram    P[r][c], c = (s, re/im, k) (spin-major, real parts then imaginary
+//           parts), holds the kicked, lambda-weighted end a; B = P^T P
+//           accumulates in TMEM over the rows r, and
+//           G_s[k][l] = (B[(s,re,k)][(s,re,l)] + B[(s,im,k)][(s,im,l)])
+//                     + i (B[(s,re,k)][(s,im,l)] - B[(s,im,k)][(s,re,l)]).
 //           D = 32: one 128 x 128 product over all 4D columns of P (the
 //           blocks s != s' are computed and not read); D = 64: one 128 x 128
 //           product per s.
 //   update  Gamma_a'[s][r][k'] = mask_r sum_t sum_k Gamma_t[r][k] K_st Y_s[k][k']
 //           with the kick K = exp(-i theta X / 2) folded into the right
-//           operand: one M = 128 (rows) x N = 4D ((s, k', re/im)) product over
-//           K = 4D ((t, k, re/im)) whose left operand is the stored tensor as it
-//           is (complex numbers are (re, im) pairs, i.e. K-major already).
+//           operand W: one M = 128 (rows) x N = 4D ((s, re/im, k')) product
+//           over K = 4D ((t, k, re/im)), staged in chunks of 8 complex k of one t.
 //
 // FP32 accuracy through the 3xTF32 split: every FP32 operand x is held as
 // hi = tf32(x) and lo = tf32(x - hi), and each product is
@@ -25,215 +25,294 @@
 // out of TMEM after every 64-row tile and summed in FP64, as the CUDA-core
 // passes do.
 //
-// Operands are staged by the CTA's threads in chunks of kTcKc values of K
-// (core-matrix layout of tcgen05.cuh); thread 0 issues the MMAs and commits
-// them to an mbarrier that every thread waits on (bounded).  Warps 0-3 read
-// the accumulator (warp w: TMEM lanes 32w .. 32w + 31).
+// Data movement: the rows of end a for the Gram are contiguous runs of the
+// state (the bond leg, or the faster other leg, is the last leg), so each
+// 32-row chunk is staged by bulk copies (cp.async.bulk, the TMA engine)
+// completing on an mbarrier, one chunk ahead of the conversion; the staged
+// complex numbers are kicked, weighted, split and written to the operand
+// layout, thread 0 issues the MMAs and commits them to a second mbarrier.
+// The update's left operand is loaded in batches (every thread's loads of a
+// chunk in flight at once) and its right operand is built from Y.  Lane
+// assignments keep the operand writes free of shared-memory bank conflicts
+// (8 consecutive operand rows x 4 consecutive K values per warp).
 //
 // Included by su_kernels.cu after its row/element helpers (row_pos, elem,
-// row_weight, ldst, kick2).
+// row_weight, ldst).
 #pragma once
 #include "tcgen05.cuh"
 
 namespace gpeps {
 
-
 struct TcCtx {
   uint32_t tmem;    // TMEM base address (tc_cols(D) columns)
   uint64_t* bar;    // mbarrier the MMA commits arrive on
+  uint64_t* sbar;   // mbarrier of the bulk-copy staging
   long long limit;  // wait budget in SM cycles
 };
 
-__device__ __forceinline__ void tc_put(unsigned char* hi, unsigned char* lo, int row, int q, float x) {
+// exp(-i theta X / 2) on the pair (g0, g1) with the rounding pinned (explicit
+// fused multiply-adds), so that every kernel that inlines it computes the same
+// bits whatever the compiler would contract
+__device__ __forceinline__ void tc_kick(float c, float s, float2 g0, float2 g1, float2& a0, float2& a1) {
+  a0 = make_float2(__fmaf_rn(c, g0.x, __fmul_rn(s, g1.y)), __fmaf_rn(c, g0.y, -__fmul_rn(s, g1.x)));
+  a1 = make_float2(__fmaf_rn(c, g1.x, __fmul_rn(s, g0.y)), __fmaf_rn(c, g1.y, -__fmul_rn(s, g0.x)));
+}
+
+__device__ __forceinline__ void tc_put(unsigned char* hi, unsigned char* lo, int row, int q, int Kt, float x) {
   float h, l;
   tc::split_tf32(x, h, l);
-  const uint32_t o = tc::kmajor_off(row, q, kTcKc);
+  const uint32_t o = tc::kmajor_off(row, q, Kt);
   *reinterpret_cast<float*>(hi + o) = h;
   *reinterpret_cast<float*>(lo + o) = l;
 }
 
-// Every thread waits for the committed products; the outcome is made uniform
-// over the CTA.  After a wait that gave up, a second bounded wait lets products
-// still in flight finish before the caller frees TMEM.
-__device__ __forceinline__ bool tc_wait_chunk(const TcCtx& cx, uint32_t& phase) {
-  const bool ok = __syncthreads_and(tc::mbar_wait(cx.bar, phase, cx.limit) ? 1 : 0) != 0;
-  if (!ok) tc::mbar_wait(cx.bar, phase, cx.limit);
+// Every thread waits for a phase of the mbarrier; the outcome is made uniform
+// over the CTA.  After a wait that gave up, a second bounded wait lets the
+// operations still in flight finish before the caller reuses the memory.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t& phase, long long limit) {
+  const bool ok = __syncthreads_and(tc::mbar_wait(bar, phase, limit) ? 1 : 0) != 0;
+  if (!ok) tc::mbar_wait(bar, phase, limit);
   phase ^= 1u;
   return ok;
 }
 
-// Make the staged chunk visible to the tensor core, issue the 3xTF32 products
-// of `nk` K values (a multiple of 8) from thread 0, and wait for them.
-// a/b: shared addresses of hi (lo follows at +lo_a / +lo_b bytes).
-__device__ __forceinline__ bool tc_mma_chunk(uint32_t a, uint32_t lo_a, uint32_t b, uint32_t lo_b, int nk,
-                                             uint32_t d_tmem, uint32_t idesc, bool fresh, const TcCtx& cx,
-                                             uint32_t& phase) {
-  tc::fence_async_smem();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    tc::fence_after_sync();
-    constexpr uint32_t kLbo = 128, kSbo = kTcKc * 32;
-    for (int ks = 0; ks < nk; ks += 8) {
-      const uint32_t off = (uint32_t)ks * 32;
-      const uint64_t ah = tc::smem_desc(a + off, kLbo, kSbo), al = tc::smem_desc(a + lo_a + off, kLbo, kSbo);
-      const uint64_t bh = tc::smem_desc(b + off, kLbo, kSbo), bl = tc::smem_desc(b + lo_b + off, kLbo, kSbo);
-      tc::mma_tf32(d_tmem, ah, bh, idesc, (fresh && ks == 0) ? 0u : 1u);
-      tc::mma_tf32(d_tmem, ah, bl, idesc, 1u);
-      tc::mma_tf32(d_tmem, al, bh, idesc, 1u);
-    }
-    tc::mma_commit(cx.bar);
+// Thread 0: the 3xTF32 products of `nk` K values (a multiple of 8) of the
+// staged operands.  a/b: shared addresses of hi (lo at +lo_a / +lo_b bytes);
+// Kt: K extent of the operand layout.
+__device__ __forceinline__ void tc_issue(uint32_t a, uint32_t lo_a, uint32_t b, uint32_t lo_b, int nk, int Kt,
+                                         uint32_t d_tmem, uint32_t idesc, bool fresh) {
+  const uint32_t lbo = 128, sbo = (uint32_t)Kt * 32;
+  for (int ks = 0; ks < nk; ks += 8) {
+    const uint32_t off = (uint32_t)ks * 32;
+    const uint64_t ah = tc::smem_desc(a + off, lbo, sbo), al = tc::smem_desc(a + lo_a + off, lbo, sbo);
+    const uint64_t bh = tc::smem_desc(b + off, lbo, sbo), bl = tc::smem_desc(b + lo_b + off, lbo, sbo);
+    tc::mma_tf32(d_tmem, ah, bh, idesc, (fresh && ks == 0) ? 0u : 1u);
+    tc::mma_tf32(d_tmem, ah, bl, idesc, 1u);
+    tc::mma_tf32(d_tmem, al, bh, idesc, 1u);
   }
-  return tc_wait_chunk(cx, phase);
 }
 
-// Gram of rows [row0, row0 + nrows) of end a into TMEM: a fresh accumulation
-// if `fresh`, else added to the one there.
-template <bool kCG>
-__device__ bool tc_gram_rows(const SideDesc& sa, const float2* gamma, const double* lam, float c, float s, int row0,
-                             int nrows, int D, unsigned char* sm, const TcCtx& cx, uint32_t& phase, bool fresh) {
+// Warp 0: bulk copies of rows [r0, r0 + kc) of end a (both spins) into the
+// staging area, completing on cx.sbar.  The chunk lies within one value of the
+// slower other leg, so each copy is a contiguous run: with the bond leg last
+// (str_k = 1) one run of kc x D elements per spin (staged [s][r][k]); else the
+// faster other leg is last (str_o2 = 1) and there is one run of kc rows per
+// (s, k) (staged [s][k][r]).  Every run starts on a 16-byte boundary (site
+// offsets and strides are multiples of D elements, r0 of 32) and is a multiple
+// of 16 bytes long.
+__device__ __forceinline__ void tc_stage_rows(const SideDesc& sa, const float2* gamma, int r0, int kc, int D,
+                                              float2* stg, const TcCtx& cx) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  const RowPos p = row_pos(sa, r0);
+  const int64_t base = sa.off + (int64_t)p.r1 * sa.str_o1 + (int64_t)p.r2 * sa.str_o2;
+  if (lane == 0) tc::mbar_expect_tx(cx.sbar, (uint32_t)(2 * kc * D * 8));
+  __syncwarp();
+  if (sa.str_k == 1) {
+    if (lane < 2)
+      tc::bulk_g2s(stg + (size_t)lane * kc * D, gamma + base + (int64_t)lane * sa.str_s, (uint32_t)(kc * D * 8),
+                   cx.sbar);
+  } else {
+    for (int i = lane; i < 2 * D; i += 32) {
+      const int sp = i / D, k = i - sp * D;
+      tc::bulk_g2s(stg + (size_t)i * kc, gamma + base + (int64_t)sp * sa.str_s + (int64_t)k * sa.str_k,
+                   (uint32_t)(kc * 8), cx.sbar);
+    }
+  }
+}
+
+// Gram pass over all rows of end a: per 64-row tile, the accumulator is read
+// and out(tile, s, k, l, re, im) is called once for every entry of G_0 and G_1.
+// Returns false if a wait gave up (the pass then stops).
+template <bool kCG, typename Out>
+__device__ bool tc_gram_pass(const SideDesc& sa, const float2* gamma, const double* lam, float c, float s, int D,
+                             unsigned char* sm, const TcCtx& cx, uint32_t& mphase, uint32_t& sphase, Out out) {
+  const TcGramSmem L(D);
   unsigned char* hi = sm;
   const uint32_t lo_off = (uint32_t)(4 * D * kTcKc * 4);
   unsigned char* lo = sm + lo_off;
+  float* dump = reinterpret_cast<float*>(sm);
+  float2* stg = reinterpret_cast<float2*>(sm + L.stage);
+  float* wrow = reinterpret_cast<float*>(sm + L.weight);
   const uint32_t idesc = tc::idesc_tf32(128, 128);
-  const uint32_t base = tc::smem_u32(hi);
+  const int rows = sa.rows, nchunk = (rows + kTcKc - 1) / kTcKc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int ldd = 2 * D + 1;
   bool ok = true;
-  for (int r0 = 0; r0 < nrows; r0 += kTcKc) {
-    const int kc = nrows - r0 < kTcKc ? nrows - r0 : kTcKc;
-    const int nel = kc * D;
-    for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
-      int r, k;
-      if (sa.str_k == 1) {
-        r = idx / D;
-        k = idx - r * D;
-      } else {
-        k = idx / kc;
-        r = idx - k * kc;
+  // the tensors and the shared memory were last touched by generic loads and stores (earlier
+  // bond updates, in this CTA or, ordered by the done flags, in others): order those before the
+  // bulk copies
+  tc::fence_async_all();
+  __syncthreads();
+  tc_stage_rows(sa, gamma, 0, rows < kTcKc ? rows : kTcKc, D, stg, cx);
+  for (int j = 0; j < nchunk && ok; ++j) {
+    const int r0 = j * kTcKc, kc = rows - r0 < kTcKc ? rows - r0 : kTcKc, kc8 = (kc + 7) & ~7;
+    for (int r = threadIdx.x; r < kc; r += blockDim.x)
+      wrow[r] = (float)row_weight<kCG>(sa, lam, row_pos(sa, r0 + r));
+    if (!tc_wait(cx.sbar, sphase, cx.limit)) {
+      ok = false;
+      break;
+    }
+    // items (r, k): a warp takes 4 rows x 8 consecutive k
+    const int ngr = (kc8 + 3) / 4, ngk = D / 8;
+    for (int g = warp; g < ngr * ngk; g += nwarps) {
+      const int gr = g / ngk, gk = g - gr * ngk;
+      const int r = gr * 4 + (lane >> 3), k = gk * 8 + (lane & 7);
+      float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+      if (r < kc) {
+        float2 g0, g1;
+        if (sa.str_k == 1) {
+          g0 = stg[(size_t)r * D + k];
+          g1 = stg[(size_t)(kc + r) * D + k];
+        } else {
+          g0 = stg[(size_t)k * kc + r];
+          g1 = stg[(size_t)(D + k) * kc + r];
+        }
+        const float w = wrow[r];
+        tc_kick(c, s, g0, g1, a0, a1);
+        a0 = make_float2(__fmul_rn(a0.x, w), __fmul_rn(a0.y, w));
+        a1 = make_float2(__fmul_rn(a1.x, w), __fmul_rn(a1.y, w));
       }
-      const RowPos p = row_pos(sa, row0 + r0 + r);
-      const int64_t e = elem(sa, 0, p, k);
-      const float w = (float)row_weight<kCG>(sa, lam, p);
-      float2 a0, a1;
-      kick2<float>(c, s, ldst<kCG>(gamma + e), ldst<kCG>(gamma + e + sa.str_s), a0, a1);
-      tc_put(hi, lo, 2 * k, r, a0.x * w);
-      tc_put(hi, lo, 2 * k + 1, r, a0.y * w);
-      tc_put(hi, lo, 2 * (D + k), r, a1.x * w);
-      tc_put(hi, lo, 2 * (D + k) + 1, r, a1.y * w);
+      if (r < kc8) {  // rows are the K extent: a ragged chunk is padded with zero rows
+        tc_put(hi, lo, k, r, kTcKc, a0.x);
+        tc_put(hi, lo, D + k, r, kTcKc, a0.y);
+        tc_put(hi, lo, 2 * D + k, r, kTcKc, a1.x);
+        tc_put(hi, lo, 3 * D + k, r, kTcKc, a1.y);
+      }
     }
-    // rows are the K extent here: pad a ragged chunk (a degree-1 end has one row) to a multiple of 8
-    const int kc8 = (kc + 7) & ~7;
-    for (int idx = threadIdx.x; idx < (kc8 - kc) * 4 * D; idx += blockDim.x) {
-      const int r = kc + idx / (4 * D), cc = idx - (idx / (4 * D)) * 4 * D;
-      tc_put(hi, lo, cc, r, 0.f);
-    }
-    // D = 32: rows 0..127 of P; D = 64: rows 128 g .. 128 g + 127 (spin g) into TMEM columns 128 g ..
-    const int ng = D == 64 ? 2 : 1;
     tc::fence_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
       tc::fence_after_sync();
-      constexpr uint32_t kLbo = 128, kSbo = kTcKc * 32;
-      for (int g = 0; g < ng; ++g) {
-        const uint32_t rb = base + (uint32_t)g * 16u * kSbo;
-        for (int ks = 0; ks < kc8; ks += 8) {
-          const uint32_t off = (uint32_t)ks * 32;
-          const uint64_t dh = tc::smem_desc(rb + off, kLbo, kSbo), dl = tc::smem_desc(rb + lo_off + off, kLbo, kSbo);
-          const uint32_t d = cx.tmem + (uint32_t)g * 128u;
-          tc::mma_tf32(d, dh, dh, idesc, (fresh && r0 == 0 && ks == 0) ? 0u : 1u);
-          tc::mma_tf32(d, dh, dl, idesc, 1u);
-          tc::mma_tf32(d, dl, dh, idesc, 1u);
-        }
+      const bool fresh = (r0 % kTileRows) == 0;
+      const uint32_t base = tc::smem_u32(hi);
+      for (int gm = 0; gm < (D == 64 ? 2 : 1); ++gm) {
+        const uint32_t rb = base + (uint32_t)gm * 16u * (uint32_t)(kTcKc * 32);
+        tc_issue(rb, lo_off, rb, lo_off, kc8, kTcKc, cx.tmem + (uint32_t)gm * 128u, idesc, fresh);
       }
       tc::mma_commit(cx.bar);
     }
-    ok = tc_wait_chunk(cx, phase);
-    if (!ok) break;
+    // the staging area is free (every thread is past the conversion): fetch the next chunk
+    if (j + 1 < nchunk) {
+      const int n0 = r0 + kTcKc;
+      tc_stage_rows(sa, gamma, n0, rows - n0 < kTcKc ? rows - n0 : kTcKc, D, stg, cx);
+    }
+    ok = tc_wait(cx.bar, mphase, cx.limit);
+    if (!ok) {
+      if (j + 1 < nchunk) tc_wait(cx.sbar, sphase, cx.limit);  // the copies in flight land before we return
+      break;
+    }
+    if ((r0 + kc) % kTileRows != 0 && j + 1 < nchunk) continue;
+    // tile complete: dump the same-spin columns of every accumulator row, then combine re/im rows
+    tc::fence_after_sync();
+    for (int gm = 0; gm < (D == 64 ? 2 : 1); ++gm) {
+      if (threadIdx.x < 128) {
+        const int m = threadIdx.x;
+        const int sp = D == 64 ? gm : (m >> 6);
+        const uint32_t col0 = D == 64 ? (uint32_t)gm * 128u : (uint32_t)sp * 64u;
+        for (int cb = 0; cb < 2 * D; cb += 32) {
+          float v[32];
+          tc::tmem_ld32(cx.tmem + ((uint32_t)(32 * (m >> 5)) << 16) + col0 + (uint32_t)cb, v);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) dump[m * ldd + cb + q] = v[q];
+        }
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+      const int ns = D == 64 ? 1 : 2;
+      for (int o = threadIdx.x; o < ns * D * D; o += blockDim.x) {
+        const int ss = o / (D * D), kl = o - ss * D * D, k = kl / D, l = kl - k * D;
+        const int sp = D == 64 ? gm : ss;
+        const int rre = (D == 64 ? 0 : sp * 64) + k, rim = rre + D;
+        const float re = __fadd_rn(dump[rre * ldd + l], dump[rim * ldd + D + l]);
+        const float im = __fsub_rn(dump[rre * ldd + D + l], dump[rim * ldd + l]);
+        out(r0 / kTileRows, sp, k, l, re, im);
+      }
+      __syncthreads();
+    }
   }
   return ok;
 }
 
-// Read the Gram accumulator: calls out(s, k, l, reim, value) once for every
-// component of G_s[k][l] (threads 0..127; the re/im rows of one (s, k) are the
-// neighbouring lanes m and m ^ 1).
-template <typename Out>
-__device__ __forceinline__ void tc_gram_read(int D, const TcCtx& cx, Out out) {
-  if (threadIdx.x < 128) {
-    tc::fence_after_sync();
-    const int m = threadIdx.x, warp = m >> 5, reim = m & 1;
-    const int ng = D == 64 ? 2 : 1;
-    for (int g = 0; g < ng; ++g) {
-      const int sp = D == 64 ? g : (m >> 6);
-      const int k = D == 64 ? (m >> 1) : ((m >> 1) & 31);
-      const uint32_t col0 = D == 64 ? (uint32_t)g * 128u : (uint32_t)sp * 64u;
-      for (int cb = 0; cb < 2 * D; cb += 32) {
-        float v[32];
-        tc::tmem_ld32(cx.tmem + ((uint32_t)(32 * warp) << 16) + col0 + (uint32_t)cb, v);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float po = __shfl_xor_sync(0xffffffffu, v[2 * j + 1], 1);
-          out(sp, k, cb / 2 + j, reim, reim == 0 ? v[2 * j] + po : po - v[2 * j]);
-        }
-      }
-    }
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-}
-
 // Update of rows [row0, row0 + nrows) of end a (nrows <= 128):
 // Gamma_a'[s][r][k'] = mask[r] sum_t sum_k Gamma_t[r][k] K_st Y_s[k][k'] in place.
-// Y: [2][D][D] complex of this bond; (c, s) the kick of end a.  The rows are
-// written by threads 0..127 after the product completes, so the in-place write
-// reads nothing it has overwritten.
+// Y: [2][D][D] complex of this bond; (c, s) the kick of end a.  Operand
+// chunks hold 8 complex k of one t with K value q = re/im * 8 + (k - k0).
+// The rows are written by threads 0..127 after the product completes, so the
+// in-place write reads nothing it has overwritten.
 template <bool kCG>
 __device__ bool tc_update_rows(const SideDesc& sa, float2* gamma, const float2* Y, float c, float s,
                                const float* mask, int row0, int nrows, int D, unsigned char* sm, const TcCtx& cx,
                                uint32_t& phase) {
+  constexpr int Ku = kTcKu, half = kTcKu / 2;
   unsigned char* ahi = sm;
-  const uint32_t a_lo = (uint32_t)(128 * kTcKc * 4);
+  const uint32_t a_lo = (uint32_t)(128 * Ku * 4);
   unsigned char* alo = ahi + a_lo;
   unsigned char* bhi = alo + a_lo;
-  const uint32_t b_lo = (uint32_t)(4 * D * kTcKc * 4);
+  const uint32_t b_lo = (uint32_t)(4 * D * Ku * 4);
   unsigned char* blo = bhi + b_lo;
-  const int D2 = D * D, nchunks = 4 * D / kTcKc, per_t = 2 * D / kTcKc;
+  const int D2 = D * D, nchunks = 4 * D / Ku, per_t = 2 * D / Ku;
   const uint32_t idesc = tc::idesc_tf32(128, 4 * D);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   bool ok = true;
   for (int j = 0; j < nchunks && ok; ++j) {
-    const int t = j / per_t, k0 = (j - t * per_t) * (kTcKc / 2);
-    // left operand: row r, K value q = 2 (k - k0) + re/im
-    const int na = nrows * (kTcKc / 2);
-    for (int idx = threadIdx.x; idx < na; idx += blockDim.x) {
-      int r, kk;
-      if (sa.str_k == 1) {
-        r = idx / (kTcKc / 2);
-        kk = idx - r * (kTcKc / 2);
-      } else {
-        kk = idx / nrows;
-        r = idx - kk * nrows;
+    const int t = j / per_t, k0 = (j - t * per_t) * half;
+    // left operand: a warp takes 8 rows x 4 k; all loads of a thread in flight at once
+    {
+      constexpr int kMaxItems = 8;  // 128 rows x 8 k / (4 warps x 32 lanes)
+      const int ngroups = ((nrows + 7) / 8) * (half / 4);
+      float2 gv[kMaxItems];
+#pragma unroll
+      for (int i = 0; i < kMaxItems; ++i) {
+        const int g = warp + i * nwarps;
+        gv[i] = make_float2(0.f, 0.f);
+        if (g < ngroups) {
+          const int gr = g / (half / 4), gk = g - gr * (half / 4);
+          const int r = gr * 8 + (lane & 7), kk = gk * 4 + (lane >> 3);
+          if (r < nrows) gv[i] = ldst<kCG>(gamma + elem(sa, t, row_pos(sa, row0 + r), k0 + kk));
+        }
       }
-      const RowPos p = row_pos(sa, row0 + r);
-      const float2 g = ldst<kCG>(gamma + elem(sa, t, p, k0 + kk));
-      tc_put(ahi, alo, r, 2 * kk, g.x);
-      tc_put(ahi, alo, r, 2 * kk + 1, g.y);
+#pragma unroll
+      for (int i = 0; i < kMaxItems; ++i) {
+        const int g = warp + i * nwarps;
+        if (g < ngroups) {
+          const int gr = g / (half / 4), gk = g - gr * (half / 4);
+          const int r = gr * 8 + (lane & 7), kk = gk * 4 + (lane >> 3);
+          tc_put(ahi, alo, r, kk, Ku, gv[i].x);
+          tc_put(ahi, alo, r, half + kk, Ku, gv[i].y);
+        }
+      }
     }
-    // right operand: row n = (s', k', re/im), K value q = 2 (k - k0) + re/im;
-    // w = K_{s't} Y_{s'}[k][k'] with K_00 = K_11 = c, K_01 = K_10 = -i s
-    const int nb = 2 * D * (kTcKc / 2);
-    for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-      const int kp = idx % D, rest = idx / D;
-      const int kk = rest % (kTcKc / 2), sp = rest / (kTcKc / 2);
-      const float2 y = ldst<kCG>(Y + sp * D2 + (k0 + kk) * D + kp);
-      const float2 w = sp == t ? make_float2(c * y.x, c * y.y) : make_float2(s * y.y, -s * y.x);
-      const int n0 = sp * 2 * D + 2 * kp, q0 = 2 * kk;
-      tc_put(bhi, blo, n0, q0, w.x);
-      tc_put(bhi, blo, n0, q0 + 1, -w.y);
-      tc_put(bhi, blo, n0 + 1, q0, w.y);
-      tc_put(bhi, blo, n0 + 1, q0 + 1, w.x);
+    // right operand: row n = (s', re/im, k'), K value q = re/im * 8 + (k - k0);
+    // w = K_{s't} Y_{s'}[k][k'] with K_00 = K_11 = c, K_01 = K_10 = -i s.  A warp takes 8 k' x 4 k.
+    {
+      const int ngroups = 2 * (D / 8) * (half / 4);
+      for (int g = warp; g < ngroups; g += nwarps) {
+        const int sp = g / ((D / 8) * (half / 4)), rest = g - sp * (D / 8) * (half / 4);
+        const int gp = rest / (half / 4), gk = rest - gp * (half / 4);
+        const int kp = gp * 8 + (lane & 7), kk = gk * 4 + (lane >> 3);
+        const float2 y = ldst<kCG>(Y + sp * D2 + (k0 + kk) * D + kp);
+        const float2 w = sp == t ? make_float2(__fmul_rn(c, y.x), __fmul_rn(c, y.y))
+                                 : make_float2(__fmul_rn(s, y.y), -__fmul_rn(s, y.x));
+        const int nre = sp * 2 * D + kp, nim = nre + D;
+        tc_put(bhi, blo, nre, kk, Ku, w.x);
+        tc_put(bhi, blo, nre, half + kk, Ku, -w.y);
+        tc_put(bhi, blo, nim, kk, Ku, w.y);
+        tc_put(bhi, blo, nim, half + kk, Ku, w.x);
+      }
     }
-    ok = tc_mma_chunk(tc::smem_u32(ahi), a_lo, tc::smem_u32(bhi), b_lo, kTcKc, cx.tmem, idesc, j == 0, cx, phase);
+    tc::fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc::fence_after_sync();
+      tc_issue(tc::smem_u32(ahi), a_lo, tc::smem_u32(bhi), b_lo, Ku, Ku, cx.tmem, idesc, j == 0);
+      tc::mma_commit(cx.bar);
+    }
+    ok = tc_wait(cx.bar, phase, cx.limit);
   }
   if (threadIdx.x < 128 && ok) {
     tc::fence_after_sync();
-    const int r = threadIdx.x, warp = r >> 5;
+    const int r = threadIdx.x, wq = r >> 5;
     const bool live = r < nrows;
     RowPos p{0, 0};
     float mk = 0.f;
@@ -241,13 +320,17 @@ __device__ bool tc_update_rows(const SideDesc& sa, float2* gamma, const float2* 
       p = row_pos(sa, row0 + r);
       mk = mask[r];
     }
-    for (int cb = 0; cb < 4 * D; cb += 32) {
-      float v[32];
-      tc::tmem_ld32(cx.tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cb, v);
-      if (live) {
-        const int sp = cb / (2 * D), kp0 = (cb - sp * 2 * D) / 2;
+    for (int sp = 0; sp < 2; ++sp) {
+      for (int kb = 0; kb < D; kb += 32) {
+        float vr[32], vi[32];
+        const uint32_t col = (uint32_t)(sp * 2 * D + kb);
+        tc::tmem_ld32(cx.tmem + ((uint32_t)(32 * wq) << 16) + col, vr);
+        tc::tmem_ld32(cx.tmem + ((uint32_t)(32 * wq) << 16) + col + (uint32_t)D, vi);
+        if (live) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) gamma[elem(sa, sp, p, kp0 + q)] = make_float2(v[2 * q] * mk, v[2 * q + 1] * mk);
+          for (int q = 0; q < 32; ++q)
+            gamma[elem(sa, sp, p, kb + q)] = make_float2(__fmul_rn(vr[q], mk), __fmul_rn(vi[q], mk));
+        }
       }
     }
   }

@@ -266,7 +266,7 @@ int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr, void* vsave = 
   double* theta_a = h->at<double>(h->w_theta_a);
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[0], h->stream));
   if (h->tensor)
-    GP_CUDA(Launch<T>::gram_tc(tiles, nt, bonds, h->gamma(), h->lam(), h->pending(), partials, h->flags(), h->D,
+    GP_CUDA(Launch<T>::gram_tc(bonds, nbd, h->gamma(), h->lam(), h->pending(), partials, h->flags(), h->D,
                                h->stream));
   else
     GP_CUDA(Launch<T>::gram(tiles, nt, bonds, h->gamma(), h->lam(), h->pending(), partials, h->D, h->stream));
@@ -277,8 +277,7 @@ int layer_impl(gpeps_handle* h, int c, PhaseEvents* pe = nullptr, void* vsave = 
                           h->d_work + h->w_bond_scratch, layered_per_sm(h)));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[2], h->stream));
   if (h->tensor)
-    GP_CUDA(Launch<T>::update_tc(tiles, nt, bonds, h->gamma(), h->lam(), Y, theta_a, h->flags(), h->D,
-                                 h->stream));
+    GP_CUDA(Launch<T>::update_tc(bonds, nbd, h->gamma(), h->lam(), Y, theta_a, h->flags(), h->D, h->stream));
   else
     GP_CUDA(Launch<T>::update(tiles, nt, bonds, h->gamma(), h->lam(), Y, theta_a, h->D, h->stream));
   if (pe) GP_CUDA(cudaEventRecord(pe->ev[3], h->stream));

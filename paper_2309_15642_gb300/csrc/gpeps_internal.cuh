@@ -27,7 +27,8 @@ constexpr int kBondThreads = 512;  // threads of the bond-eigenproblem CTA (one 
 constexpr double kLambdaCut = 1e-13;  // pseudo-inverse threshold relative to max(lambda)
 constexpr int kPhases = 6;            // phases of the bond kernel with SM-cycle counters
 constexpr int kRotSweeps = 8;         // rotation counters kept for the first sweeps of a solve
-constexpr int kCounters = kPhases + 2 * kRotSweeps;  // cycles, FP32 rotations, FP64 rotations
+constexpr int kPassCounters = 2;     // fused step: SM cycles of the Gram pass and of the update pass of end a
+constexpr int kCounters = kPhases + 2 * kRotSweeps + kPassCounters;  // cycles, FP32 rotations, FP64 rotations, passes
 // Work counters of the bond kernels (u64 each): [0] FP64 sweeps, [1] FP32 sweeps of the first
 // level, [2] extra FP32 levels, [3] FP64 complex MACs of the extra levels, [4] FP64 2x2 block
 // updates, [5] FP64 eigenvector
@@ -101,17 +102,29 @@ struct JacobiParams {
 };
 
 // Tensor-core passes of the mixed path (bigend_tc.cuh): D = 32 or 64.
-constexpr int kTcKc = 32;  // K values of one staged operand chunk
+constexpr int kTcKc = 32;  // Gram pass: rows (the K extent) of one staged chunk
+constexpr int kTcKu = 16;  // update pass: K values of one operand chunk (8 complex k of one spin)
 __host__ __device__ constexpr bool tc_supported(int D) { return D == 32 || D == 64; }
 // a wait for committed tensor-core products gives up after this many SM cycles (~2 s; a chunk takes microseconds)
 constexpr long long kTcWaitCycles = 4000000000LL;
 // TMEM columns of a CTA using the tensor-core passes (a power of two >= 32)
 __host__ __device__ constexpr uint32_t tc_cols(int D) { return (uint32_t)(4 * D); }
-// shared memory of the Gram chunk: hi and lo of P, 4D rows x kTcKc
-__host__ __device__ constexpr size_t tc_gram_smem(int D) { return (size_t)4 * D * kTcKc * 4 * 2; }
-// shared memory of the update chunk: hi and lo of A (128 rows) and of B (4D rows), kTcKc each, and the row mask
+// Shared memory of the Gram pass: the operand (hi | lo, 4D rows x kTcKc), the
+// readout dump aliasing it (128 rows x (2D + 1) floats), the bulk-copy staging
+// area (two spins x kTcKc rows x D complex) after both, one weight per row.
+struct TcGramSmem {
+  size_t stage, weight, total;
+  __host__ __device__ constexpr TcGramSmem(int D)
+      : stage((((size_t)4 * D * kTcKc * 8 > (size_t)128 * (2 * D + 1) * 4) ? (size_t)4 * D * kTcKc * 8
+                                                                            : (size_t)128 * (2 * D + 1) * 4) +
+                  15 & ~(size_t)15),
+        weight(stage + (size_t)2 * kTcKc * D * 8),
+        total(weight + (size_t)kTcKc * 4) {}
+};
+__host__ __device__ constexpr size_t tc_gram_smem(int D) { return TcGramSmem(D).total; }
+// shared memory of the update chunk: hi and lo of A (128 rows) and of W (4D rows), kTcKu each, and the row mask
 __host__ __device__ constexpr size_t tc_update_smem(int D) {
-  return (size_t)(128 + 4 * D) * kTcKc * 4 * 2 + 128 * 4;
+  return (size_t)(128 + 4 * D) * kTcKu * 4 * 2 + 128 * 4;
 }
 
 // Launchers (su_kernels.cu).  T = float for GPEPS_MIXED_C64, double for GPEPS_C128.
@@ -132,14 +145,12 @@ struct Launch {
                           void* scratch = nullptr, int per_sm = 1);
   static cudaError_t update(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, void* gamma,
                             const double* lam, const void* Y, const double* theta_a, int D, cudaStream_t st);
-  // The same two passes on the tensor cores (tcgen05, 3xTF32; complex64 storage, D = 32 or 64 only); a
-  // wait for the tensor core that runs past kTcWaitCycles raises GPEPS_FLAG_TIMEOUT.
-  static cudaError_t gram_tc(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, const void* gamma,
-                             const double* lam, const double* pending, void* partials, int* flags, int D,
-                             cudaStream_t st);
-  static cudaError_t update_tc(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, void* gamma,
-                               const double* lam, const void* Y, const double* theta_a, int* flags, int D,
-                               cudaStream_t st);
+  // The same two passes on the tensor cores (tcgen05, 3xTF32; complex64 storage, D = 32 or 64 only), one
+  // CTA per bond over its row tiles; a wait that runs past kTcWaitCycles raises GPEPS_FLAG_TIMEOUT.
+  static cudaError_t gram_tc(const BondDesc* bonds, int n_bonds, const void* gamma, const double* lam,
+                             const double* pending, void* partials, int* flags, int D, cudaStream_t st);
+  static cudaError_t update_tc(const BondDesc* bonds, int n_bonds, void* gamma, const double* lam, const void* Y,
+                               const double* theta_a, int* flags, int D, cudaStream_t st);
   static cudaError_t readout(const SiteDesc* sites, int n_sites, const void* gamma, const double* lam,
                              const double* pending, double* z, int D, cudaStream_t st);
   // Every bond update of one Trotter step in one persistent launch (per_sm CTAs

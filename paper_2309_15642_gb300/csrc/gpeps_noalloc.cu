@@ -33,7 +33,7 @@ void* g_scratch[kMaxDevices] = {};
 constexpr size_t kFlagsOff = 0;                                  // int flags[4]
 constexpr size_t kSweepsOff = 16;                                // u64[kWorkCounters]
 constexpr size_t kCyclesOff = 80;                                // u64[kCounters]
-constexpr size_t kPendingOff = 256;                              // double pending[2], theta_a[1]
+constexpr size_t kPendingOff = 320;                              // double pending[2], theta_a[1]
 constexpr size_t kDescOff = 512;                                 // BondDesc, TileDesc[...]
 constexpr int kNoallocMaxD = 32;                                 // bond dimension limit of this entry point
 constexpr size_t kMaxTiles = (kNoallocMaxD * kNoallocMaxD + kTileRows - 1) / kTileRows;

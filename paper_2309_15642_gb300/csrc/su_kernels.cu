@@ -1625,15 +1625,16 @@ __device__ void fused_update(const SideDesc& sa, V2<T>* gamma, const double* lam
 }
 
 // ---------------------------------------------------------------- tensor-core passes (mixed path)
-// Allocate the CTA's TMEM (warp 0) and set up its mbarrier; every thread then
-// holds the TMEM base address.
-__device__ __forceinline__ uint32_t tc_setup(uint32_t* slot, uint64_t* bar, uint32_t ncols) {
+// Allocate the CTA's TMEM (warp 0) and set up its two mbarriers (MMA commits,
+// bulk-copy staging); every thread then holds the TMEM base address.
+__device__ __forceinline__ uint32_t tc_setup(uint32_t* slot, uint64_t* bars, uint32_t ncols) {
   if (threadIdx.x < 32) {
     tc::tmem_alloc(slot, ncols);
     tc::tmem_relinquish();
   }
   if (threadIdx.x == 0) {
-    tc::mbar_init(bar, 1);
+    tc::mbar_init(bars, 1);
+    tc::mbar_init(bars + 1, 1);
     tc::mbar_fence_init();
   }
   tc::fence_before_sync();
@@ -1673,88 +1674,81 @@ __device__ void tc_row_mask(const SideDesc& sa, const double* lam, int row0, int
   __syncthreads();
 }
 
-// Gram partials of one 64-row tile on the tensor cores (layered form of the
-// mixed path; same partial layout as gram_kernel).
-__global__ void __launch_bounds__(128)
-    tc_gram_kernel(const TileDesc* __restrict__ tiles, const BondDesc* __restrict__ bonds,
-                   const float2* __restrict__ gamma, const double* __restrict__ lam,
-                   const double* __restrict__ pending, float2* __restrict__ partials, int* flags, int D,
-                   long long limit) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ uint32_t tslot;
-  const uint32_t ncols = tc_cols(D);
-  const TcCtx cx{tc_setup(&tslot, &bar, ncols), &bar, limit};
-  uint32_t phase = 0;
-  const TileDesc t = tiles[blockIdx.x];
-  const SideDesc sa = bonds[t.bond].a;
-  const double th = pending[sa.site];
-  const float c = (float)cos(0.5 * th), s = (float)sin(0.5 * th);
-  const bool ok = tc_gram_rows<false>(sa, gamma, lam, c, s, t.row0, t.nrows, D, smem_raw, cx, phase, true);
-  float* out = reinterpret_cast<float*>(partials + (int64_t)t.part * 2 * D * D);
-  const int D2 = D * D;
-  tc_gram_read(D, cx, [&](int sp, int k, int l, int reim, float v) { out[2 * (sp * D2 + k * D + l) + reim] = v; });
-  if (!ok && threadIdx.x == 0) atomicOr(flags, 4);
-  tc_teardown(cx.tmem, ncols);
-}
-
-// Update of one tile of end a on the tensor cores (layered form of the mixed
-// path; the same product as update_kernel).
-__global__ void __launch_bounds__(128)
-    tc_update_kernel(const TileDesc* __restrict__ tiles, const BondDesc* __restrict__ bonds, float2* gamma,
-                     const double* __restrict__ lam, const float2* __restrict__ Y,
-                     const double* __restrict__ theta_a, int* flags, int D, long long limit) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ uint32_t tslot;
-  __shared__ double cut[2];
-  const uint32_t ncols = tc_cols(D);
-  const TcCtx cx{tc_setup(&tslot, &bar, ncols), &bar, limit};
-  uint32_t phase = 0;
-  const TileDesc t = tiles[blockIdx.x];
-  const SideDesc sa = bonds[t.bond].a;
-  float* mask = reinterpret_cast<float*>(smem_raw + tc_update_smem(D) - 128 * 4);
-  tc_row_mask<false>(sa, lam, t.row0, t.nrows, D, mask, cut);
-  const double th = theta_a[t.bond];
-  const float c = (float)cos(0.5 * th), s = (float)sin(0.5 * th);
-  const bool ok = tc_update_rows<false>(sa, gamma, Y + (int64_t)t.bond * 2 * D * D, c, s, mask, t.row0, t.nrows, D,
-                                        smem_raw, cx, phase);
-  if (!ok && threadIdx.x == 0) atomicOr(flags, 4);
-  tc_teardown(cx.tmem, ncols);
-}
-
-// The fused step's Gram and update passes on the tensor cores: the Gram per
-// 64-row tile (read out and summed in FP64 in tile order, as the layered
-// partials are), the update per 128 rows.
-__device__ bool tc_fused_gram(const SideDesc& sa, const float2* gamma, const double* lam, double th, double2* gsum,
-                              int D, unsigned char* sm, const TcCtx& cx, uint32_t& phase) {
-  const int D2 = D * D, nout = 2 * D2;
-  for (int o = threadIdx.x; o < nout; o += blockDim.x) gsum[o] = make_double2(0.0, 0.0);
-  __syncthreads();
-  const float c = (float)cos(0.5 * th), s = (float)sin(0.5 * th);
-  const int tr = tile_rows(D, sizeof(float2));
-  double* g = reinterpret_cast<double*>(gsum);
-  bool ok = true;
-  for (int row0 = 0; row0 < sa.rows && ok; row0 += tr) {
-    const int nrows = sa.rows - row0 < tr ? sa.rows - row0 : tr;
-    ok = tc_gram_rows<true>(sa, gamma, lam, c, s, row0, nrows, D, sm, cx, phase, true);
-    tc_gram_read(D, cx, [&](int sp, int k, int l, int reim, float v) { g[2 * (sp * D2 + k * D + l) + reim] += (double)v; });
-  }
-  return ok;
-}
-
-__device__ bool tc_fused_update(const SideDesc& sa, float2* gamma, const double* lam, const float2* Y, double th,
-                                int D, unsigned char* sm, const TcCtx& cx, uint32_t& phase) {
+// Update pass over all rows of end a, 128 rows at a time.
+template <bool kCG>
+__device__ bool tc_update_pass(const SideDesc& sa, float2* gamma, const double* lam, const float2* Y, double th,
+                               int D, unsigned char* sm, const TcCtx& cx, uint32_t& phase) {
   __shared__ double cut[2];
   float* mask = reinterpret_cast<float*>(sm + tc_update_smem(D) - 128 * 4);
   const float c = (float)cos(0.5 * th), s = (float)sin(0.5 * th);
   bool ok = true;
   for (int row0 = 0; row0 < sa.rows && ok; row0 += 128) {
     const int nrows = sa.rows - row0 < 128 ? sa.rows - row0 : 128;
-    tc_row_mask<true>(sa, lam, row0, nrows, D, mask, cut);
-    ok = tc_update_rows<true>(sa, gamma, Y, c, s, mask, row0, nrows, D, sm, cx, phase);
+    tc_row_mask<kCG>(sa, lam, row0, nrows, D, mask, cut);
+    ok = tc_update_rows<kCG>(sa, gamma, Y, c, s, mask, row0, nrows, D, sm, cx, phase);
   }
   return ok;
+}
+
+// Gram partials of one bond on the tensor cores, one partial per 64-row tile
+// (layered form of the mixed path; the partial layout of gram_kernel).
+__global__ void __launch_bounds__(128)
+    tc_gram_kernel(const BondDesc* __restrict__ bonds, const float2* __restrict__ gamma,
+                   const double* __restrict__ lam, const double* __restrict__ pending, float2* __restrict__ partials,
+                   int* flags, int D, long long limit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tslot;
+  const uint32_t ncols = tc_cols(D);
+  const TcCtx cx{tc_setup(&tslot, bars, ncols), bars, bars + 1, limit};
+  uint32_t mphase = 0, sphase = 0;
+  const BondDesc& bd = bonds[blockIdx.x];
+  const SideDesc sa = bd.a;
+  const double th = pending[sa.site];
+  const float c = (float)cos(0.5 * th), s = (float)sin(0.5 * th);
+  const int D2 = D * D;
+  float2* out = partials + (int64_t)bd.part0 * 2 * D2;
+  const bool ok = tc_gram_pass<false>(sa, gamma, lam, c, s, D, smem_raw, cx, mphase, sphase,
+                                      [&](int tile, int sp, int k, int l, float re, float im) {
+                                        out[(int64_t)tile * 2 * D2 + sp * D2 + k * D + l] = make_float2(re, im);
+                                      });
+  if (!ok && threadIdx.x == 0) atomicOr(flags, 4);
+  tc_teardown(cx.tmem, ncols);
+}
+
+// Update of one bond's end a on the tensor cores (layered form of the mixed
+// path; the same product as update_kernel).
+__global__ void __launch_bounds__(128)
+    tc_update_kernel(const BondDesc* __restrict__ bonds, float2* gamma, const double* __restrict__ lam,
+                     const float2* __restrict__ Y, const double* __restrict__ theta_a, int* flags, int D,
+                     long long limit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tslot;
+  const uint32_t ncols = tc_cols(D);
+  const TcCtx cx{tc_setup(&tslot, bars, ncols), bars, bars + 1, limit};
+  uint32_t phase = 0;
+  const SideDesc sa = bonds[blockIdx.x].a;
+  const bool ok = tc_update_pass<false>(sa, gamma, lam, Y + (int64_t)blockIdx.x * 2 * D * D, theta_a[blockIdx.x], D,
+                                        smem_raw, cx, phase);
+  if (!ok && threadIdx.x == 0) atomicOr(flags, 4);
+  tc_teardown(cx.tmem, ncols);
+}
+
+// The fused step's Gram pass on the tensor cores: per 64-row tile read out and
+// summed in FP64 in tile order, as the layered partials are.
+__device__ bool tc_fused_gram(const SideDesc& sa, const float2* gamma, const double* lam, double th, double2* gsum,
+                              int D, unsigned char* sm, const TcCtx& cx, uint32_t& mphase, uint32_t& sphase) {
+  const int D2 = D * D, nout = 2 * D2;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) gsum[o] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const float c = (float)cos(0.5 * th), s = (float)sin(0.5 * th);
+  return tc_gram_pass<true>(sa, gamma, lam, c, s, D, sm, cx, mphase, sphase,
+                            [&](int, int sp, int k, int l, float re, float im) {
+                              double2& g = gsum[sp * D2 + k * D + l];
+                              g.x += (double)re;
+                              g.y += (double)im;
+                            });
 }
 
 // Layout of a fused-step CTA's global slot: the big part of the bond layout at
@@ -1798,13 +1792,13 @@ __global__ void __launch_bounds__(kThr, kMinB)
   double2* gsum = reinterpret_cast<double2*>(mine + SL.off_gsum);
   V2<T>* Y = reinterpret_cast<V2<T>*>(mine + SL.off_Y);
   double* th_a = reinterpret_cast<double*>(mine + SL.off_th);
-  // tensor-core passes: TMEM for the whole launch, one mbarrier for the MMA commits
-  __shared__ __align__(8) uint64_t tc_bar;
+  // tensor-core passes: TMEM for the whole launch, mbarriers of the MMA commits and of the staging
+  __shared__ __align__(8) uint64_t tc_bars[2];
   __shared__ uint32_t tc_slot;
-  TcCtx cx{0u, &tc_bar, kTcWaitCycles};
-  uint32_t phase = 0;
+  TcCtx cx{0u, tc_bars, tc_bars + 1, kTcWaitCycles};
+  uint32_t phase = 0, sphase = 0;
   bool tc_ok = true;
-  if constexpr (kTC) cx.tmem = tc_setup(&tc_slot, &tc_bar, tc_cols(D));
+  if constexpr (kTC) cx.tmem = tc_setup(&tc_slot, tc_bars, tc_cols(D));
   for (;;) {
     if (threadIdx.x == 0) next = (int)atomicAdd(queue, 1u);
     __syncthreads();
@@ -1817,24 +1811,30 @@ __global__ void __launch_bounds__(kThr, kMinB)
       wait_done(done, tasks[ti].dep_b, flags, jp.wait_cycles);
     }
     __syncthreads();
+    long long tp = 0;
+    if (threadIdx.x == 0 && cycles) tp = clock64();
     if constexpr (kTC) {
       if (tc_ok)
         tc_ok = tc_fused_gram(bd.a, reinterpret_cast<const float2*>(gamma), lam, __ldcg(pending + bd.a.site), gsum, D,
-                              smem_raw, cx, phase);
+                              smem_raw, cx, phase, sphase);
     } else {
       fused_gram<T>(bd.a, gamma, lam, __ldcg(pending + bd.a.site), gsum, D, smem_raw);
     }
+    if (threadIdx.x == 0 && cycles) atomicAdd(cycles + kPhases + 2 * kRotSweeps, (unsigned long long)(clock64() - tp));
     bond_body<T, true>(bd, nullptr, gsum, gamma, lam, pending, Y, th_a, flags, sweeps_out, cycles, nullptr, D, jp,
                        mine);
     __syncthreads();
+    if (threadIdx.x == 0 && cycles) tp = clock64();
     if constexpr (kTC) {
       if (tc_ok)
-        tc_ok = tc_fused_update(bd.a, reinterpret_cast<float2*>(gamma), lam, reinterpret_cast<const float2*>(Y),
-                                *th_a, D, smem_raw, cx, phase);
+        tc_ok = tc_update_pass<true>(bd.a, reinterpret_cast<float2*>(gamma), lam, reinterpret_cast<const float2*>(Y),
+                                     *th_a, D, smem_raw, cx, phase);
     } else {
       fused_update<T>(bd.a, gamma, lam, Y, *th_a, D, smem_raw);
     }
     __syncthreads();
+    if (threadIdx.x == 0 && cycles)
+      atomicAdd(cycles + kPhases + 2 * kRotSweeps + 1, (unsigned long long)(clock64() - tp));
     if (threadIdx.x == 0) {
       __threadfence();
       st_release(done + ti, 1);
@@ -2094,24 +2094,21 @@ cudaError_t Launch<T>::gram(const TileDesc* tiles, int n_tiles, const BondDesc* 
 }
 
 template <typename T>
-cudaError_t Launch<T>::gram_tc(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, const void* gamma,
-                               const double* lam, const double* pending, void* partials, int* flags, int D,
-                               cudaStream_t st) {
-  if (n_tiles == 0) return cudaSuccess;
+cudaError_t Launch<T>::gram_tc(const BondDesc* bonds, int n_bonds, const void* gamma, const double* lam,
+                               const double* pending, void* partials, int* flags, int D, cudaStream_t st) {
+  if (n_bonds == 0) return cudaSuccess;
   if (!std::is_same<T, float>::value || !tc_supported(D)) return cudaErrorInvalidValue;
-  tc_gram_kernel<<<n_tiles, 128, tc_gram_smem(D), st>>>(tiles, bonds, static_cast<const float2*>(gamma), lam,
-                                                          pending, static_cast<float2*>(partials), flags, D,
-                                                          kTcWaitCycles);
+  tc_gram_kernel<<<n_bonds, 128, tc_gram_smem(D), st>>>(bonds, static_cast<const float2*>(gamma), lam, pending,
+                                                          static_cast<float2*>(partials), flags, D, kTcWaitCycles);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Launch<T>::update_tc(const TileDesc* tiles, int n_tiles, const BondDesc* bonds, void* gamma,
-                                 const double* lam, const void* Y, const double* theta_a, int* flags, int D,
-                                 cudaStream_t st) {
-  if (n_tiles == 0) return cudaSuccess;
+cudaError_t Launch<T>::update_tc(const BondDesc* bonds, int n_bonds, void* gamma, const double* lam, const void* Y,
+                                 const double* theta_a, int* flags, int D, cudaStream_t st) {
+  if (n_bonds == 0) return cudaSuccess;
   if (!std::is_same<T, float>::value || !tc_supported(D)) return cudaErrorInvalidValue;
-  tc_update_kernel<<<n_tiles, 128, tc_update_smem(D), st>>>(tiles, bonds, static_cast<float2*>(gamma), lam,
+  tc_update_kernel<<<n_bonds, 128, tc_update_smem(D), st>>>(bonds, static_cast<float2*>(gamma), lam,
                                                               static_cast<const float2*>(Y), theta_a, flags, D,
                                                               kTcWaitCycles);
   return cudaGetLastError();

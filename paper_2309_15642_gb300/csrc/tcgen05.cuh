@@ -66,6 +66,9 @@ __device__ __forceinline__ void fence_after_sync() {
 }
 // generic-proxy writes to shared memory -> visible to the tensor core (async proxy)
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// generic-proxy accesses of global and shared memory ordered before later async-proxy ones
+// (bulk copies reading tensors that generic stores wrote, into shared memory generic code used)
+__device__ __forceinline__ void fence_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
 // ---------------------------------------------------------------- MMA
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.

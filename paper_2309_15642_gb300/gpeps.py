@@ -190,10 +190,15 @@ class GPEPS:
         check(self.lib.gpeps_jacobi_work(self.h, w), "gpeps_jacobi_work")
         return [int(x) for x in w]
 
+    def pass_cycles(self):
+        """SM cycles of the fused step's Gram and update passes of the larger ends since the last
+        reset (summed over bonds; zero for the layered launches)."""
+        return self.bond_counters()[22:24]
+
     def bond_counters(self):
         """All counters of the bond kernel: 6 phase cycle sums, rotations per FP32 sweep (8),
-        rotations per FP64 sweep (8)."""
-        c = (ctypes.c_int64 * 22)()
+        rotations per FP64 sweep (8), cycles of the fused step's Gram and update passes (2)."""
+        c = (ctypes.c_int64 * 24)()
         check(self.lib.gpeps_bond_phase_cycles(self.h, c), "gpeps_bond_phase_cycles")
         return [int(x) for x in c]
 
