@@ -121,12 +121,16 @@ __device__ __forceinline__ void tc_stage_rows(const SideDesc& sa, const float2* 
   }
 }
 
-// Gram pass over all rows of end a: per 64-row tile, the accumulator is read
-// and out(tile, s, k, l, re, im) is called once for every entry of G_0 and G_1.
-// Returns false if a wait gave up (the pass then stops).
-template <bool kCG, typename Out>
+// Gram pass over all rows of end a: per 64-row tile the accumulator is read,
+// and G_0, G_1 of the tile are either added in FP64 to gsum ([2][D][D], in tile
+// order) or, with gsum null, stored in FP32 to part + tile * 2 D^2 (the
+// layered partials).  kNb: entries of G per thread whose loads of gsum are in
+// flight together (registers permitting).  Returns false if a wait gave up
+// (the pass then stops).
+template <bool kCG, int kNb = 4>
 __device__ bool tc_gram_pass(const SideDesc& sa, const float2* gamma, const double* lam, float c, float s, int D,
-                             unsigned char* sm, const TcCtx& cx, uint32_t& mphase, uint32_t& sphase, Out out) {
+                             unsigned char* sm, const TcCtx& cx, uint32_t& mphase, uint32_t& sphase, double2* gsum,
+                             float2* part) {
   const TcGramSmem L(D);
   unsigned char* hi = sm;
   const uint32_t lo_off = (uint32_t)(4 * D * kTcKc * 4);
@@ -210,23 +214,42 @@ __device__ bool tc_gram_pass(const SideDesc& sa, const float2* gamma, const doub
         const int m = threadIdx.x;
         const int sp = D == 64 ? gm : (m >> 6);
         const uint32_t col0 = D == 64 ? (uint32_t)gm * 128u : (uint32_t)sp * 64u;
-        for (int cb = 0; cb < 2 * D; cb += 32) {
-          float v[32];
-          tc::tmem_ld32(cx.tmem + ((uint32_t)(32 * (m >> 5)) << 16) + col0 + (uint32_t)cb, v);
+        for (int cb = 0; cb < 2 * D; cb += 16) {
+          float v[16];
+          tc::tmem_ld16(cx.tmem + ((uint32_t)(32 * (m >> 5)) << 16) + col0 + (uint32_t)cb, v);
 #pragma unroll
-          for (int q = 0; q < 32; ++q) dump[m * ldd + cb + q] = v[q];
+          for (int q = 0; q < 16; ++q) dump[m * ldd + cb + q] = v[q];
         }
       }
       tc::fence_before_sync();
       __syncthreads();
-      const int ns = D == 64 ? 1 : 2;
-      for (int o = threadIdx.x; o < ns * D * D; o += blockDim.x) {
-        const int ss = o / (D * D), kl = o - ss * D * D, k = kl / D, l = kl - k * D;
-        const int sp = D == 64 ? gm : ss;
-        const int rre = (D == 64 ? 0 : sp * 64) + k, rim = rre + D;
-        const float re = __fadd_rn(dump[rre * ldd + l], dump[rim * ldd + D + l]);
-        const float im = __fsub_rn(dump[rre * ldd + D + l], dump[rim * ldd + l]);
-        out(r0 / kTileRows, sp, k, l, re, im);
+      // entries of G in index order sp * D^2 + k * D + l; a batch's loads of gsum are in flight
+      // before its stores
+      const int n = (D == 64 ? 1 : 2) * D * D, g0 = D == 64 ? gm * D * D : 0;
+      for (int o0 = threadIdx.x; o0 < n; o0 += kNb * blockDim.x) {
+        float re[kNb], im[kNb];
+        double2 old[kNb];
+#pragma unroll
+        for (int b = 0; b < kNb; ++b) {
+          const int o = o0 + b * blockDim.x;
+          if (o < n) {
+            const int ss = o / (D * D), kl = o - ss * D * D, k = kl / D, l = kl - k * D;
+            const int rre = (D == 64 ? 0 : ss * 64) + k, rim = rre + D;
+            re[b] = __fadd_rn(dump[rre * ldd + l], dump[rim * ldd + D + l]);
+            im[b] = __fsub_rn(dump[rre * ldd + D + l], dump[rim * ldd + l]);
+            if (gsum) old[b] = gsum[g0 + o];
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < kNb; ++b) {
+          const int o = o0 + b * blockDim.x;
+          if (o < n) {
+            if (gsum)
+              gsum[g0 + o] = make_double2(old[b].x + (double)re[b], old[b].y + (double)im[b]);
+            else
+              part[(int64_t)(r0 / kTileRows) * 2 * D * D + g0 + o] = make_float2(re[b], im[b]);
+          }
+        }
       }
       __syncthreads();
     }
@@ -259,39 +282,56 @@ __device__ bool tc_update_rows(const SideDesc& sa, float2* gamma, const float2* 
     const int t = j / per_t, k0 = (j - t * per_t) * half;
     // left operand: a warp takes 8 rows x 4 k; all loads of a thread in flight at once
     {
-      constexpr int kMaxItems = 8;  // 128 rows x 8 k / (4 warps x 32 lanes)
+      constexpr int kBatch = 4;  // loads of a thread in flight together
       const int ngroups = ((nrows + 7) / 8) * (half / 4);
-      float2 gv[kMaxItems];
+      for (int g0 = warp; g0 < ngroups; g0 += kBatch * nwarps) {
+        float2 gv[kBatch];
 #pragma unroll
-      for (int i = 0; i < kMaxItems; ++i) {
-        const int g = warp + i * nwarps;
-        gv[i] = make_float2(0.f, 0.f);
-        if (g < ngroups) {
-          const int gr = g / (half / 4), gk = g - gr * (half / 4);
-          const int r = gr * 8 + (lane & 7), kk = gk * 4 + (lane >> 3);
-          if (r < nrows) gv[i] = ldst<kCG>(gamma + elem(sa, t, row_pos(sa, row0 + r), k0 + kk));
+        for (int i = 0; i < kBatch; ++i) {
+          const int g = g0 + i * nwarps;
+          gv[i] = make_float2(0.f, 0.f);
+          if (g < ngroups) {
+            const int gr = g / (half / 4), gk = g - gr * (half / 4);
+            const int r = gr * 8 + (lane & 7), kk = gk * 4 + (lane >> 3);
+            if (r < nrows) gv[i] = ldst<kCG>(gamma + elem(sa, t, row_pos(sa, row0 + r), k0 + kk));
+          }
         }
-      }
 #pragma unroll
-      for (int i = 0; i < kMaxItems; ++i) {
-        const int g = warp + i * nwarps;
-        if (g < ngroups) {
-          const int gr = g / (half / 4), gk = g - gr * (half / 4);
-          const int r = gr * 8 + (lane & 7), kk = gk * 4 + (lane >> 3);
-          tc_put(ahi, alo, r, kk, Ku, gv[i].x);
-          tc_put(ahi, alo, r, half + kk, Ku, gv[i].y);
+        for (int i = 0; i < kBatch; ++i) {
+          const int g = g0 + i * nwarps;
+          if (g < ngroups) {
+            const int gr = g / (half / 4), gk = g - gr * (half / 4);
+            const int r = gr * 8 + (lane & 7), kk = gk * 4 + (lane >> 3);
+            tc_put(ahi, alo, r, kk, Ku, gv[i].x);
+            tc_put(ahi, alo, r, half + kk, Ku, gv[i].y);
+          }
         }
       }
     }
     // right operand: row n = (s', re/im, k'), K value q = re/im * 8 + (k - k0);
     // w = K_{s't} Y_{s'}[k][k'] with K_00 = K_11 = c, K_01 = K_10 = -i s.  A warp takes 8 k' x 4 k.
     {
+      constexpr int kBatch = 4;
       const int ngroups = 2 * (D / 8) * (half / 4);
-      for (int g = warp; g < ngroups; g += nwarps) {
+      for (int g0 = warp; g0 < ngroups; g0 += kBatch * nwarps) {
+      float2 yv[kBatch];
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i) {
+        const int g = g0 + i * nwarps;
+        if (g < ngroups) {
+          const int sp = g / ((D / 8) * (half / 4)), rest = g - sp * (D / 8) * (half / 4);
+          const int gp = rest / (half / 4), gk = rest - gp * (half / 4);
+          yv[i] = ldst<kCG>(Y + sp * D2 + (k0 + gk * 4 + (lane >> 3)) * D + gp * 8 + (lane & 7));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i) {
+        const int g = g0 + i * nwarps;
+        if (g >= ngroups) continue;
         const int sp = g / ((D / 8) * (half / 4)), rest = g - sp * (D / 8) * (half / 4);
         const int gp = rest / (half / 4), gk = rest - gp * (half / 4);
         const int kp = gp * 8 + (lane & 7), kk = gk * 4 + (lane >> 3);
-        const float2 y = ldst<kCG>(Y + sp * D2 + (k0 + kk) * D + kp);
+        const float2 y = yv[i];
         const float2 w = sp == t ? make_float2(__fmul_rn(c, y.x), __fmul_rn(c, y.y))
                                  : make_float2(__fmul_rn(s, y.y), -__fmul_rn(s, y.x));
         const int nre = sp * 2 * D + kp, nim = nre + D;
@@ -299,6 +339,7 @@ __device__ bool tc_update_rows(const SideDesc& sa, float2* gamma, const float2* 
         tc_put(bhi, blo, nre, half + kk, Ku, -w.y);
         tc_put(bhi, blo, nim, kk, Ku, w.y);
         tc_put(bhi, blo, nim, half + kk, Ku, w.x);
+      }
       }
     }
     tc::fence_async_smem();
@@ -321,14 +362,14 @@ __device__ bool tc_update_rows(const SideDesc& sa, float2* gamma, const float2* 
       mk = mask[r];
     }
     for (int sp = 0; sp < 2; ++sp) {
-      for (int kb = 0; kb < D; kb += 32) {
-        float vr[32], vi[32];
+      for (int kb = 0; kb < D; kb += 16) {
+        float vr[16], vi[16];
         const uint32_t col = (uint32_t)(sp * 2 * D + kb);
-        tc::tmem_ld32(cx.tmem + ((uint32_t)(32 * wq) << 16) + col, vr);
-        tc::tmem_ld32(cx.tmem + ((uint32_t)(32 * wq) << 16) + col + (uint32_t)D, vi);
+        tc::tmem_ld16(cx.tmem + ((uint32_t)(32 * wq) << 16) + col, vr);
+        tc::tmem_ld16(cx.tmem + ((uint32_t)(32 * wq) << 16) + col + (uint32_t)D, vi);
         if (live) {
 #pragma unroll
-          for (int q = 0; q < 32; ++q)
+          for (int q = 0; q < 16; ++q)
             gamma[elem(sa, sp, p, kb + q)] = make_float2(__fmul_rn(vr[q], mk), __fmul_rn(vi[q], mk));
         }
       }

@@ -1707,11 +1707,8 @@ __global__ void __launch_bounds__(128)
   const double th = pending[sa.site];
   const float c = (float)cos(0.5 * th), s = (float)sin(0.5 * th);
   const int D2 = D * D;
-  float2* out = partials + (int64_t)bd.part0 * 2 * D2;
-  const bool ok = tc_gram_pass<false>(sa, gamma, lam, c, s, D, smem_raw, cx, mphase, sphase,
-                                      [&](int tile, int sp, int k, int l, float re, float im) {
-                                        out[(int64_t)tile * 2 * D2 + sp * D2 + k * D + l] = make_float2(re, im);
-                                      });
+  const bool ok = tc_gram_pass<false>(sa, gamma, lam, c, s, D, smem_raw, cx, mphase, sphase, nullptr,
+                                      partials + (int64_t)bd.part0 * 2 * D2);
   if (!ok && threadIdx.x == 0) atomicOr(flags, 4);
   tc_teardown(cx.tmem, ncols);
 }
@@ -1736,30 +1733,37 @@ __global__ void __launch_bounds__(128)
 }
 
 // The fused step's Gram pass on the tensor cores: per 64-row tile read out and
-// summed in FP64 in tile order, as the layered partials are.
+// summed in FP64 in tile order, as the layered partials are.  kNb: see
+// tc_gram_pass (1 where three CTAs share an SM and registers are scarce).
+// With gsum null the tiles' FP32 partials go to part instead (see StepSlot).
+template <int kNb>
 __device__ bool tc_fused_gram(const SideDesc& sa, const float2* gamma, const double* lam, double th, double2* gsum,
-                              int D, unsigned char* sm, const TcCtx& cx, uint32_t& mphase, uint32_t& sphase) {
+                              float2* part, int D, unsigned char* sm, const TcCtx& cx, uint32_t& mphase,
+                              uint32_t& sphase) {
   const int D2 = D * D, nout = 2 * D2;
-  for (int o = threadIdx.x; o < nout; o += blockDim.x) gsum[o] = make_double2(0.0, 0.0);
-  __syncthreads();
+  if (gsum) {
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) gsum[o] = make_double2(0.0, 0.0);
+    __syncthreads();
+  }
   const float c = (float)cos(0.5 * th), s = (float)sin(0.5 * th);
-  return tc_gram_pass<true>(sa, gamma, lam, c, s, D, sm, cx, mphase, sphase,
-                            [&](int, int sp, int k, int l, float re, float im) {
-                              double2& g = gsum[sp * D2 + k * D + l];
-                              g.x += (double)re;
-                              g.y += (double)im;
-                            });
+  return tc_gram_pass<true, kNb>(sa, gamma, lam, c, s, D, sm, cx, mphase, sphase, gsum, part);
 }
 
 // Layout of a fused-step CTA's global slot: the big part of the bond layout at
 // n = 2D, then the FP64 Gram sums [2][D][D], Y [2][D][D] and the kick angle of end a.
+// Complex64 storage up to D = 32 adds the FP32 Gram partials of the tensor-core
+// pass, one per 64-row tile of the largest end (ceil(D^2 / 64) x 2 D^2 complex):
+// stored per tile and summed by the bond eigenproblem in tile order, as the
+// layered launches do, with no read-modify-write of an FP64 sum per tile.
 struct StepSlot {
-  size_t off_gsum, off_Y, off_th, total;
+  size_t off_gsum, off_Y, off_th, off_part, total;
   __host__ __device__ StepSlot(int D, size_t elt) {
     off_gsum = (bond_big(D, elt) + 255) & ~(size_t)255;
     off_Y = off_gsum + (size_t)2 * D * D * 16;
     off_th = off_Y + (size_t)2 * D * D * elt;
-    total = (off_th + 16 + 255) & ~(size_t)255;
+    off_part = (off_th + 16 + 255) & ~(size_t)255;
+    const size_t part = (elt == 8 && D <= 32) ? (size_t)((D * D + kTileRows - 1) / kTileRows) * 2 * D * D * 8 : 0;
+    total = (off_part + part + 255) & ~(size_t)255;
   }
 };
 
@@ -1792,13 +1796,21 @@ __global__ void __launch_bounds__(kThr, kMinB)
   double2* gsum = reinterpret_cast<double2*>(mine + SL.off_gsum);
   V2<T>* Y = reinterpret_cast<V2<T>*>(mine + SL.off_Y);
   double* th_a = reinterpret_cast<double*>(mine + SL.off_th);
-  // tensor-core passes: TMEM for the whole launch, mbarriers of the MMA commits and of the staging
+  float2* tc_part = reinterpret_cast<float2*>(mine + SL.off_part);  // tensor-core Gram partials (D <= 32)
+  // tensor-core passes: TMEM for the whole launch, mbarriers of the MMA commits and of the
+  // staging; between the passes their state (the two phase bits, ok) lives in shared memory, so
+  // that nothing of it occupies registers during the bond eigenproblem
   __shared__ __align__(8) uint64_t tc_bars[2];
-  __shared__ uint32_t tc_slot;
-  TcCtx cx{0u, tc_bars, tc_bars + 1, kTcWaitCycles};
-  uint32_t phase = 0, sphase = 0;
-  bool tc_ok = true;
-  if constexpr (kTC) cx.tmem = tc_setup(&tc_slot, tc_bars, tc_cols(D));
+  __shared__ uint32_t tc_slot, tc_state[3];
+  if constexpr (kTC) {
+    tc_setup(&tc_slot, tc_bars, tc_cols(D));
+    if (threadIdx.x == 0) {
+      tc_state[0] = 0u;
+      tc_state[1] = 0u;
+      tc_state[2] = 1u;
+    }
+    __syncthreads();
+  }
   for (;;) {
     if (threadIdx.x == 0) next = (int)atomicAdd(queue, 1u);
     __syncthreads();
@@ -1814,21 +1826,44 @@ __global__ void __launch_bounds__(kThr, kMinB)
     long long tp = 0;
     if (threadIdx.x == 0 && cycles) tp = clock64();
     if constexpr (kTC) {
-      if (tc_ok)
-        tc_ok = tc_fused_gram(bd.a, reinterpret_cast<const float2*>(gamma), lam, __ldcg(pending + bd.a.site), gsum, D,
-                              smem_raw, cx, phase, sphase);
+      const TcCtx cx{tc_slot, tc_bars, tc_bars + 1, kTcWaitCycles};
+      uint32_t ph = tc_state[0], sph = tc_state[1];
+      bool ok = tc_state[2] != 0;
+      // D <= 32: per-tile FP32 partials in the slot, summed by the bond eigenproblem; else FP64 sums
+      if (ok)
+        ok = tc_fused_gram<(kMinB >= 3 ? 1 : 4)>(bd.a, reinterpret_cast<const float2*>(gamma), lam,
+                                                 __ldcg(pending + bd.a.site), D <= 32 ? nullptr : gsum,
+                                                 D <= 32 ? tc_part : nullptr, D, smem_raw, cx, ph, sph);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tc_state[0] = ph;
+        tc_state[1] = sph;
+        tc_state[2] = ok ? 1u : 0u;
+      }
+      __syncthreads();
     } else {
       fused_gram<T>(bd.a, gamma, lam, __ldcg(pending + bd.a.site), gsum, D, smem_raw);
     }
     if (threadIdx.x == 0 && cycles) atomicAdd(cycles + kPhases + 2 * kRotSweeps, (unsigned long long)(clock64() - tp));
-    bond_body<T, true>(bd, nullptr, gsum, gamma, lam, pending, Y, th_a, flags, sweeps_out, cycles, nullptr, D, jp,
-                       mine);
+    {
+      const bool parts = kTC && D <= 32;
+      bond_body<T, true>(bd, parts ? reinterpret_cast<const V2<T>*>(tc_part) : nullptr, parts ? nullptr : gsum,
+                         gamma, lam, pending, Y, th_a, flags, sweeps_out, cycles, nullptr, D, jp, mine);
+    }
     __syncthreads();
     if (threadIdx.x == 0 && cycles) tp = clock64();
     if constexpr (kTC) {
-      if (tc_ok)
-        tc_ok = tc_update_pass<true>(bd.a, reinterpret_cast<float2*>(gamma), lam, reinterpret_cast<const float2*>(Y),
-                                     *th_a, D, smem_raw, cx, phase);
+      const TcCtx cx{tc_slot, tc_bars, tc_bars + 1, kTcWaitCycles};
+      uint32_t ph = tc_state[0];
+      bool ok = tc_state[2] != 0;
+      if (ok)
+        ok = tc_update_pass<true>(bd.a, reinterpret_cast<float2*>(gamma), lam, reinterpret_cast<const float2*>(Y),
+                                  *th_a, D, smem_raw, cx, ph);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tc_state[0] = ph;
+        tc_state[2] = ok ? 1u : 0u;
+      }
     } else {
       fused_update<T>(bd.a, gamma, lam, Y, *th_a, D, smem_raw);
     }
@@ -1841,8 +1876,9 @@ __global__ void __launch_bounds__(kThr, kMinB)
     }
   }
   if constexpr (kTC) {
-    if (!tc_ok && threadIdx.x == 0) atomicOr(flags, 4);
-    tc_teardown(cx.tmem, tc_cols(D));
+    __syncthreads();
+    if (!tc_state[2] && threadIdx.x == 0) atomicOr(flags, 4);
+    tc_teardown(tc_slot, tc_cols(D));
   }
 }
 
