@@ -154,7 +154,9 @@ class Clocks:
 # and whether the Gram and update passes ran on the tensor cores
 NCU_TRAFFIC = {("heavyhex_mix_d32", "mixed", 4, False): 2.048679e9 + 1.742843e9,
                # schedule 5 (three CTAs per SM): dram__bytes.sum.per_second 122.32 GB/s x 35.60 ms
-               ("heavyhex_mix_d32", "mixed", 5, False): 122.321021e9 * 35.601440e-3}
+               ("heavyhex_mix_d32", "mixed", 5, False): 122.321021e9 * 35.601440e-3,
+               # schedule 5 with the tensor-core passes: 166.087239 GB/s x 29.725280 ms
+               ("heavyhex_mix_d32", "mixed", 5, True): 166.087239e9 * 29.725280e-3}
 
 # TF32 tensor peak: the measured bf16 burst (MEASURED_PEAKS.json) x the nominal TF32 : BF16 dense ratio
 # (1.1 : 2.25 PFLOP/s)
