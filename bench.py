@@ -769,13 +769,15 @@ def run_condor_d64(dev, Kc=3, Wc=6):
     return out
 
 
-def run_bp_record(dev, W=5, K=3):
+def run_bp_record(dev, W=5, K=3, tensor=True):
     """BP regauging after each Trotter step (the paper's BP comparison) on workload eagle_bp_d32
-    (127 q, D = 32, theta_h = 0.7), mixed path, fused step: W steps each followed by a regauge to
-    convergence, then K timed steps (CUDA events on the library stream around step + regauge, the
-    regauge's per-iteration convergence read-back included).  Reports Trotter steps/s with BP,
-    BP iterations and per-phase device times, the message kernel against the derived FP32 peak,
-    and every qubit after the last step against the committed FP64 oracle values (BP included)."""
+    (127 q, D = 32, theta_h = 0.7), mixed path, fused step, the simple update's passes and the
+    message products on the tensor cores (tensor=True) or on CUDA cores: W steps each followed by
+    a regauge to convergence, then K timed steps (CUDA events on the library stream around step +
+    regauge, the regauge's per-iteration convergence read-back included).  Reports Trotter
+    steps/s with BP, BP iterations and per-phase device times, the message kernel's algorithmic
+    FP32 work rate against the derived FP32 peak, and every qubit after the last step against the
+    committed FP64 oracle values (BP included)."""
     import numpy as np
     import torch
     from paper_2309_15642_gb300 import GPEPS
@@ -784,6 +786,7 @@ def run_bp_record(dev, W=5, K=3):
     graphs = wb.graphs()
     th = torch.tensor([float(t[0]) for t in kick_angles(wb)], dtype=torch.float64, device=dev)
     g = GPEPS(graphs, wb.D, dtype="mixed", device=str(dev))
+    g.set_tensor_cores(tensor)
     g.set_schedule(4)
     g.reset()
     for _ in range(W):
@@ -807,7 +810,8 @@ def run_bp_record(dev, W=5, K=3):
     flops = bp_message_flops(graphs, wb.D)
     msg_ms = phases[0] / max(sum(iters), 1)
     gf = flops / (msg_ms * 1e-3) / 1e9
-    out = {"workload": wb.name, "dtype": "c64+f64", "value": K / (ms * 1e-3), "unit": "Trotter steps/s with BP",
+    out = {"workload": wb.name, "dtype": "c64+f64", "tensor_cores": tensor,
+           "value": K / (ms * 1e-3), "unit": "Trotter steps/s with BP",
            "ms_per_step": ms / K, "timed_steps": f"{W + 1}..{W + K}", "bp_iterations": iters,
            "ms_per_step_by_phase": {"messages": phases[0] / K, "gauge": phases[1] / K, "apply": phases[2] / K},
            "message_kernel": {"launch_ms": msg_ms, "flops_per_launch": flops, "achieved_gflops": gf,
@@ -942,6 +946,9 @@ def main():
         dev = torch.device("cuda", local_rank)
         condor = run_condor_d64(dev)
         bp_rec = run_bp_record(dev)
+        cc = run_bp_record(dev, tensor=False)
+        bp_rec["cuda_cores"] = {k: cc[k] for k in ("value", "ms_per_step", "ms_per_step_by_phase", "message_kernel",
+                                                   "max_abs_dz_per_qubit")}
         large = run_large_chi_record(dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -226,7 +226,8 @@ int gpeps_set_schedule(gpeps_handle* h, int32_t schedule);  /* 0..5 */
  * summed in FP64 as the CUDA-core form does.  The bond eigenproblem, lambda
  * and lambda^-1 stay FP64.  on = 0 returns to the CUDA-core products (the
  * default).  Applies to the layered launches and to the fused step
- * (schedules 4 and 5).  Host-only; drops a captured step graph.  Errors:
+ * (schedules 4 and 5), and at D = 32 also to the message products of
+ * gpeps_bp_regauge (leg products and message Gram, 3xTF32).  Host-only; drops a captured step graph.  Errors:
  * GPEPS_EINVAL unless the handle is GPEPS_MIXED_C64 with D = 32 or 64, or if
  * the fused schedule in use would no longer fit its shared memory.
  */

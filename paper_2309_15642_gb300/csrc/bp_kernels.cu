@@ -43,6 +43,7 @@
 #include "gpeps.h"
 #include "gpeps_internal.cuh"
 #include "jacobi.cuh"
+#include "tcgen05.cuh"
 
 namespace gpeps {
 
@@ -324,6 +325,53 @@ __global__ void bp_identity_kernel(double2* msgs, int64_t n, int D) {
   msgs[i] = make_double2(a == b ? 1.0 / D : 0.0, 0.0);
 }
 
+// The end of a message: restrict Mo (the summed Gram, [D][D]) to the support of
+// the bond's lambda, normalise it to unit trace, store it and fold the largest
+// change against the previous iteration into my_res (bad: not finite).
+__device__ void bp_message_finish(const BpMsgTask& tk, const double2* Mo, const double* __restrict__ lam,
+                                  const double2* __restrict__ msg_in, double2* __restrict__ msg_out, int D,
+                                  double support_cut, double& my_res, bool& bad) {
+  __shared__ double s_trace, s_cut;
+  // the support of lambda_e: entries k with lambda_e[k] <= support_cut * max are zero
+  const double* le = lam + tk.lam[tk.leg];
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int a = 0; a < D; ++a) mx = fmax(mx, le[a]);
+    const double cut = support_cut * mx;
+    double tr = 0.0;
+    for (int a = 0; a < D; ++a)
+      if (le[a] > cut) tr += Mo[a * D + a].x;
+    s_trace = tr;
+    s_cut = cut;
+  }
+  __syncthreads();
+  const double tr = s_trace, cut = s_cut;
+  const bool ok = tr > 0.0 && isfinite(tr);
+  const double inv = ok ? 1.0 / tr : 0.0;
+  double2* mo = msg_out + (int64_t)tk.out * D * D;
+  const double2* mprev = msg_in + (int64_t)tk.out * D * D;
+  for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
+    double2 v = Mo[idx];
+    if (ok) {
+      const int a = idx / D, b = idx - a * D;
+      const double w = (le[a] > cut && le[b] > cut) ? inv : 0.0;
+      v.x *= w;
+      v.y *= w;
+    } else {
+      const int a = idx / D;
+      v = make_double2(a * D + a == idx ? 1.0 / D : 0.0, 0.0);
+    }
+    const double2 o = mprev[idx];
+    const double dx = v.x - o.x, dy = v.y - o.y;
+    const double d = sqrt(dx * dx + dy * dy);
+    if (!isfinite(d)) bad = true;
+    else my_res = fmax(my_res, d);
+    mo[idx] = v;
+  }
+  if (!ok) bad = true;
+  __syncthreads();
+}
+
 // One BP iteration.  A message is computed one physical component s at a time
 // (the products never mix s), so the scratch tensor X of a CTA holds D^deg
 // elements and the launch's scratch stays in L2.
@@ -337,7 +385,6 @@ __global__ void __launch_bounds__(kBpMsgThreads, sizeof(T) == 4 && K == kGramPer
                                                                 unsigned long long* residual, int* flags) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
-  __shared__ double s_trace, s_cut;
   const int ld = D + 1;
   V2<T>* M = reinterpret_cast<V2<T>*>(smem);  // [D][D + 1]: the environment of one other leg
   V2<T>* tA = M + D * ld;                      // [32][D + 1]
@@ -406,44 +453,7 @@ __global__ void __launch_bounds__(kBpMsgThreads, sizeof(T) == 4 && K == kGramPer
     if (tile32) gram32.store(Mo);
     else gram.store(Mo, D);
     __syncthreads();
-    // the support of lambda_e: entries k with lambda_e[k] <= support_cut * max are zero
-    const double* le = lam + tk.lam[p];
-    if (threadIdx.x == 0) {
-      double mx = 0.0;
-      for (int a = 0; a < D; ++a) mx = fmax(mx, le[a]);
-      const double cut = support_cut * mx;
-      double tr = 0.0;
-      for (int a = 0; a < D; ++a)
-        if (le[a] > cut) tr += Mo[a * D + a].x;
-      s_trace = tr;
-      s_cut = cut;
-    }
-    __syncthreads();
-    const double tr = s_trace, cut = s_cut;
-    const bool ok = tr > 0.0 && isfinite(tr);
-    const double inv = ok ? 1.0 / tr : 0.0;
-    double2* mo = msg_out + (int64_t)tk.out * D * D;
-    const double2* mprev = msg_in + (int64_t)tk.out * D * D;
-    for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
-      double2 v = Mo[idx];
-      if (ok) {
-        const int a = idx / D, b = idx - a * D;
-        const double w = (le[a] > cut && le[b] > cut) ? inv : 0.0;
-        v.x *= w;
-        v.y *= w;
-      } else {
-        const int a = idx / D;
-        v = make_double2(a * D + a == idx ? 1.0 / D : 0.0, 0.0);
-      }
-      const double2 o = mprev[idx];
-      const double dx = v.x - o.x, dy = v.y - o.y;
-      const double d = sqrt(dx * dx + dy * dy);
-      if (!isfinite(d)) bad = true;
-      else my_res = fmax(my_res, d);
-      mo[idx] = v;
-    }
-    if (!ok) bad = true;
-    __syncthreads();
+    bp_message_finish(tk, Mo, lam, msg_in, msg_out, D, support_cut, my_res, bad);
   }
   const double r = block_max(my_res, red);
   const int any_bad = __syncthreads_or(bad);
@@ -454,6 +464,252 @@ __global__ void __launch_bounds__(kBpMsgThreads, sizeof(T) == 4 && K == kGramPer
     } else {
       atomicMax(residual, (unsigned long long)__double_as_longlong(r));
     }
+  }
+}
+
+// ---------------------------------------------------------------- tensor-core messages (complex64, D = 32)
+// The products of bp_message_kernel on the tensor cores (tcgen05 kind::tf32 with
+// FP32 accumulators in TMEM; every FP32 operand split into a TF32 pair, three
+// products per pair, as in the simple update's tensor-core passes):
+//   leg product  dst(c, b) = sum_b' M[b][b'] src(c, b') for 128 columns c at a
+//                time: an M = 128 (c) x N = 64 ((re/im, b)) x K = 64 ((re/im, b'))
+//                product whose right operand W, the realified environment M of
+//                the leg, is staged once per leg;
+//   Gram         m[a][a'] = sum_c A(c, a) B(c, a') over 32-column chunks of both
+//                spins into a second accumulator: rows (re/im, a), columns
+//                (re/im, a') (rows 64..127 of the M = 128 product unused);
+//                m = (B_rr - B_ii) + i (B_ri + B_ir), summed whole and stored as
+//                its upper triangle with the conjugate mirror, as the CUDA-core
+//                kernel does.
+// Operands are K-major without swizzle (tcgen05.cuh) with real and imaginary
+// parts in separate planes, written 8 rows x 4 K values per warp (32 banks).
+// Every wait is bounded; a wait that gives up raises GPEPS_FLAG_TIMEOUT and the
+// CTA stops issuing products (its messages are then wrong, the flag says so).
+constexpr int kBpTcD = 32;
+constexpr int kBpTcThreads = 256;
+struct BpTcSmem {  // bytes
+  static constexpr size_t W = 0;                     // hi | lo of W: 64 rows x 64 K (2 x 16 KB)
+  static constexpr size_t A = 32768;                 // leg product hi | lo: 128 x 64 (2 x 32 KB); Gram: A hi | lo
+                                                     // 128 x 32 (2 x 16 KB), B hi | lo 64 x 32 (2 x 8 KB); readout
+                                                     // dump 64 x 65 floats
+  static constexpr size_t Mo = A + 65536;            // double2 [32][32]
+  static constexpr size_t total = Mo + (size_t)kBpTcD * kBpTcD * 16;
+};
+
+__global__ void __launch_bounds__(kBpTcThreads, 2)
+    bp_message_tc_kernel(const BpMsgTask* __restrict__ tasks, int n_tasks, const float2* __restrict__ gamma,
+                         const double* __restrict__ lam, const double2* __restrict__ msg_in,
+                         double2* __restrict__ msg_out, float2* scratch, int64_t slot_elems, double support_cut,
+                         unsigned long long* residual, int* flags) {
+  constexpr int D = kBpTcD;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  if (threadIdx.x < 32) {
+    tc::tmem_alloc(&tslot, 128u);  // [0, 64): leg product, [64, 128): Gram
+    tc::tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  uint32_t phase = 0;
+  bool tc_ok = true;
+  unsigned char* Wh = smem + BpTcSmem::W;
+  unsigned char* Wl = Wh + 16384;
+  unsigned char* Ah = smem + BpTcSmem::A;
+  unsigned char* Al = Ah + 32768;
+  unsigned char* gAh = Ah;
+  unsigned char* gAl = gAh + 16384;
+  unsigned char* gBh = gAh + 32768;
+  unsigned char* gBl = gBh + 8192;
+  float* dump = reinterpret_cast<float*>(smem + BpTcSmem::A);
+  double2* Mo = reinterpret_cast<double2*>(smem + BpTcSmem::Mo);
+  float2* X = scratch + (int64_t)blockIdx.x * slot_elems;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const uint32_t idesc = tc::idesc_tf32(128, 64);
+  double my_res = 0.0;
+  bool bad = false;
+  for (int t = blockIdx.x; t < n_tasks; t += gridDim.x) {
+    const BpMsgTask tk = tasks[t];
+    const float2* G = gamma + tk.off;
+    const int z = tk.deg, p = tk.leg;
+    int half = 1;
+    for (int k = 1; k < z; ++k) half *= D;
+    const int64_t sz = (int64_t)half * D;
+    int legs[2] = {-1, -1}, nl = 0;
+    for (int q = 0; q < z; ++q)
+      if (q != p) legs[nl++] = q;
+    int Ip = 1;
+    for (int k = p + 1; k < z; ++k) Ip *= D;
+    bool fresh_gram = true;
+    for (int s = 0; s < 2; ++s) {
+      const int c0 = s * half, c1 = c0 + half;
+      const int64_t off = s * sz;
+      for (int l = 0; l < nl; ++l) {
+        // W: the environment E_q = diag(lambda_q) m_q diag(lambda_q), rounded to FP32 as in the
+        // CUDA-core kernel, realified (rows (re/im, b), K (re/im, b')); a warp takes 8 b x 4 b'
+        const double* lq = lam + tk.lam[legs[l]];
+        const double2* mi = msg_in + (int64_t)tk.in[legs[l]] * D * D;
+        for (int g = warp; g < (D / 8) * (D / 4); g += nwarps) {
+          const int b = (g / (D / 4)) * 8 + (lane & 7), bp = (g % (D / 4)) * 4 + (lane >> 3);
+          const double2 v = mi[b * D + bp];
+          const double w = lq[b] * lq[bp];
+          const float mr = (float)(v.x * w), mim = (float)(v.y * w);
+          tc_put(Wh, Wl, b, bp, 64, mr);
+          tc_put(Wh, Wl, b, D + bp, 64, -mim);
+          tc_put(Wh, Wl, D + b, bp, 64, mim);
+          tc_put(Wh, Wl, D + b, D + bp, 64, mr);
+        }
+        int I = 1;
+        for (int k = legs[l] + 1; k < z; ++k) I *= D;
+        // the first leg reads conj(Gamma), the second the scratch in place (a tile's columns are
+        // read completely before any of them is written back)
+        const float2* src = l == 0 ? G : X;
+        const int64_t soff = l == 0 ? 0 : off;
+        const float conj = l == 0 ? -1.f : 1.f;
+        for (int ct = c0; ct < c1; ct += 128) {
+          const int nc = c1 - ct < 128 ? c1 - ct : 128;
+          const int ngroups = ((nc + 7) / 8) * (D / 4);
+          for (int g0 = warp; g0 < ngroups; g0 += 4 * nwarps) {
+            float2 v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int g = g0 + i * nwarps;
+              const int c = (g / (D / 4)) * 8 + (lane & 7), bp = (g % (D / 4)) * 4 + (lane >> 3);
+              v[i] = (g < ngroups && c < nc) ? src[leg_addr(ct + c, bp, I, D) - soff] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int g = g0 + i * nwarps;
+              if (g < ngroups) {
+                const int c = (g / (D / 4)) * 8 + (lane & 7), bp = (g % (D / 4)) * 4 + (lane >> 3);
+                tc_put(Ah, Al, c, bp, 64, v[i].x);
+                tc_put(Ah, Al, c, D + bp, 64, conj * v[i].y);
+              }
+            }
+          }
+          tc::fence_async_smem();
+          __syncthreads();
+          if (tc_ok) {
+            if (threadIdx.x == 0) {
+              tc::fence_after_sync();
+              tc_issue(tc::smem_u32(Ah), 32768u, tc::smem_u32(Wh), 16384u, 64, 64, tmem, idesc, true);
+              tc::mma_commit(&bar);
+            }
+            tc_ok = tc_wait(&bar, phase, kTcWaitCycles);
+          }
+          if (threadIdx.x < 128 && tc_ok) {
+            tc::fence_after_sync();
+            const int c = threadIdx.x;
+            for (int bb = 0; bb < D; bb += 16) {
+              float re[16], im[16];
+              tc::tmem_ld16(tmem + ((uint32_t)(32 * (c >> 5)) << 16) + (uint32_t)bb, re);
+              tc::tmem_ld16(tmem + ((uint32_t)(32 * (c >> 5)) << 16) + (uint32_t)(D + bb), im);
+              if (c < nc) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) X[leg_addr(ct + c, bb + q, I, D) - off] = make_float2(re[q], im[q]);
+              }
+            }
+          }
+          tc::fence_before_sync();
+          __syncthreads();
+        }
+      }
+      // Gram over the columns of leg p, 32 at a time (rows a and D + a of both operands: the
+      // real and imaginary parts; K = the column, zero-padded to a multiple of 8)
+      for (int cg = c0; cg < c1; cg += 32) {
+        const int nc = c1 - cg < 32 ? c1 - cg : 32, nc8 = (nc + 7) & ~7;
+        const int ngroups = (D / 8) * (nc8 / 4);
+        for (int g0 = warp; g0 < ngroups; g0 += 4 * nwarps) {  // a thread's loads in flight together
+          float2 va[4], vb[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int g = g0 + i * nwarps;
+            const int a = (g % (D / 8)) * 8 + (lane & 7), cc = (g / (D / 8)) * 4 + (lane >> 3);
+            va[i] = make_float2(0.f, 0.f);
+            vb[i] = va[i];
+            if (g < ngroups && cc < nc) {
+              const int64_t ad = leg_addr(cg + cc, a, Ip, D);
+              va[i] = G[ad];
+              vb[i] = nl == 0 ? make_float2(va[i].x, -va[i].y) : X[ad - off];
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int g = g0 + i * nwarps;
+            if (g >= ngroups) continue;
+            const int a = (g % (D / 8)) * 8 + (lane & 7), cc = (g / (D / 8)) * 4 + (lane >> 3);
+            tc_put(gAh, gAl, a, cc, 32, va[i].x);
+            tc_put(gAh, gAl, D + a, cc, 32, va[i].y);
+            tc_put(gBh, gBl, a, cc, 32, vb[i].x);
+            tc_put(gBh, gBl, D + a, cc, 32, vb[i].y);
+          }
+        }
+        tc::fence_async_smem();
+        __syncthreads();
+        if (tc_ok) {
+          if (threadIdx.x == 0) {
+            tc::fence_after_sync();
+            tc_issue(tc::smem_u32(gAh), 16384u, tc::smem_u32(gBh), 8192u, nc8, 32, tmem + 64u, idesc, fresh_gram);
+            tc::mma_commit(&bar);
+          }
+          tc_ok = tc_wait(&bar, phase, kTcWaitCycles);
+        }
+        fresh_gram = false;
+      }
+    }
+    // read the Gram (threads 0..63: rows (re/im, a)), combine and store the upper triangle mirrored
+    if (threadIdx.x < 64 && tc_ok) {
+      tc::fence_after_sync();
+      const int m = threadIdx.x;
+      for (int cb = 0; cb < 2 * D; cb += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * (m >> 5)) << 16) + 64u + (uint32_t)cb, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) dump[m * (2 * D + 1) + cb + q] = v[q];
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
+      const int a = idx / D, b = idx - a * D;
+      if (a > b) continue;
+      const float* ra = dump + a * (2 * D + 1);
+      const float* ia = dump + (D + a) * (2 * D + 1);
+      const double re = (double)__fsub_rn(ra[b], ia[D + b]);
+      const double im = (double)__fadd_rn(ra[D + b], ia[b]);
+      if (a == b) {
+        Mo[a * D + a] = make_double2(re, 0.0);
+      } else {
+        Mo[a * D + b] = make_double2(re, im);
+        Mo[b * D + a] = make_double2(re, -im);
+      }
+    }
+    __syncthreads();
+    bp_message_finish(tk, Mo, lam, msg_in, msg_out, D, support_cut, my_res, bad);
+  }
+  const double r = block_max(my_res, red);
+  const int any_bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) {
+    if (!tc_ok) atomicOr(flags, GPEPS_FLAG_TIMEOUT);
+    if (any_bad) {
+      atomicOr(flags, GPEPS_FLAG_NUMERIC);
+      atomicMax(residual, 0x7FF0000000000000ULL);  // +inf
+    } else {
+      atomicMax(residual, (unsigned long long)__double_as_longlong(r));
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 128u);
   }
 }
 
@@ -821,6 +1077,11 @@ cudaError_t BpLaunch<T>::init() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(bp_gauge_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGaugeSmemMax);
   if (e != cudaSuccess) return e;
+  if constexpr (sizeof(T) == 4) {
+    e = cudaFuncSetAttribute(bp_message_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BpTcSmem::total);
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(bp_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)apply_smem(kMaxD));
 }
@@ -847,10 +1108,24 @@ cudaError_t BpLaunch<T>::identity(double2* msgs, int n_half, int D, cudaStream_t
 template <typename T>
 cudaError_t BpLaunch<T>::message(const BpMsgTask* tasks, int n_tasks, const void* gamma, const double* lam,
                                  const double2* msg_in, double2* msg_out, void* scratch, int64_t slot_elems, int D,
-                                 unsigned long long* residual, int* flags, int n_ctas, cudaStream_t st) {
+                                 unsigned long long* residual, int* flags, int n_ctas, cudaStream_t st,
+                                 bool tensor) {
   if (n_tasks == 0) return cudaSuccess;
-  const int grid = n_tasks < n_ctas ? n_tasks : n_ctas;
+  int grid = n_tasks < n_ctas ? n_tasks : n_ctas;
   const double cut = sizeof(T) == 4 ? kBpSupportCutF32 : kLambdaCut;
+  if (tensor) {
+    if (sizeof(T) != 4 || D != kBpTcD) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (grid > 2 * sms) grid = 2 * sms;  // two 112 KB CTAs per SM; the scratch has n_ctas >= grid slots
+    if constexpr (sizeof(T) == 4)
+      bp_message_tc_kernel<<<grid, kBpTcThreads, BpTcSmem::total, st>>>(
+          tasks, n_tasks, static_cast<const float2*>(gamma), lam, msg_in, msg_out, static_cast<float2*>(scratch),
+          slot_elems, cut, residual, flags);
+    return cudaGetLastError();
+  }
   if (D <= 32)
     bp_message_kernel<T, kGramPerSmall><<<grid, kBpMsgThreads, message_smem(D), st>>>(
         tasks, n_tasks, static_cast<const V2<T>*>(gamma), lam, msg_in, msg_out, static_cast<V2<T>*>(scratch),

@@ -1181,7 +1181,8 @@ int gpeps_bp_regauge(gpeps_handle* h, int32_t max_iter, double tol, void* d_bp_w
     cudaError_t e = c128 ? BpLaunch<double>::message(tasks, (int)h->bp_msgs.size(), h->gamma(), h->lam(), cur, nxt,
                                                     scratch, slot_t, D, res + it, h->flags(), L.n_ctas, s)
                          : BpLaunch<float>::message(tasks, (int)h->bp_msgs.size(), h->gamma(), h->lam(), cur, nxt,
-                                                   scratch, slot_t, D, res + it, h->flags(), L.n_ctas, s);
+                                                   scratch, slot_t, D, res + it, h->flags(), L.n_ctas, s,
+                                                   h->tensor && D == 32);
     GP_CUDA(e);
     if (phase_ms) GP_CUDA(cudaEventRecord(ev[1], s));
     unsigned long long bits = 0;

@@ -249,7 +249,8 @@ struct BpLaunch {
   static cudaError_t identity(double2* msgs, int n_half, int D, cudaStream_t st);
   static cudaError_t message(const BpMsgTask* tasks, int n_tasks, const void* gamma, const double* lam,
                              const double2* msg_in, double2* msg_out, void* scratch, int64_t slot_elems, int D,
-                             unsigned long long* residual, int* flags, int n_ctas, cudaStream_t st);
+                             unsigned long long* residual, int* flags, int n_ctas, cudaStream_t st,
+                             bool tensor = false);  // tensor: tcgen05 products (complex64, D = 32 only)
   static cudaError_t apply(const BpSiteTask* sites, int n_sites, void* gamma, const double2* P, int D,
                            cudaStream_t st);
   // gauge of every edge in the arithmetic of T; scratch: 7 n x n complex of T per CTA, n = D

@@ -175,4 +175,47 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
 }
 
 }  // namespace tc
+
+// ---------------------------------------------------------------- shared pieces of the tensor-core passes
+struct TcCtx {
+  uint32_t tmem;    // TMEM base address (tc_cols(D) columns)
+  uint64_t* bar;    // mbarrier the MMA commits arrive on
+  uint64_t* sbar;   // mbarrier of the bulk-copy staging
+  long long limit;  // wait budget in SM cycles
+};
+
+__device__ __forceinline__ void tc_put(unsigned char* hi, unsigned char* lo, int row, int q, int Kt, float x) {
+  float h, l;
+  tc::split_tf32(x, h, l);
+  const uint32_t o = tc::kmajor_off(row, q, Kt);
+  *reinterpret_cast<float*>(hi + o) = h;
+  *reinterpret_cast<float*>(lo + o) = l;
+}
+
+// Every thread waits for a phase of the mbarrier; the outcome is made uniform
+// over the CTA.  After a wait that gave up, a second bounded wait lets the
+// operations still in flight finish before the caller reuses the memory.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t& phase, long long limit) {
+  const bool ok = __syncthreads_and(tc::mbar_wait(bar, phase, limit) ? 1 : 0) != 0;
+  if (!ok) tc::mbar_wait(bar, phase, limit);
+  phase ^= 1u;
+  return ok;
+}
+
+// Thread 0: the 3xTF32 products of `nk` K values (a multiple of 8) of the
+// staged operands.  a/b: shared addresses of hi (lo at +lo_a / +lo_b bytes);
+// Kt: K extent of the operand layout.
+__device__ __forceinline__ void tc_issue(uint32_t a, uint32_t lo_a, uint32_t b, uint32_t lo_b, int nk, int Kt,
+                                         uint32_t d_tmem, uint32_t idesc, bool fresh) {
+  const uint32_t lbo = 128, sbo = (uint32_t)Kt * 32;
+  for (int ks = 0; ks < nk; ks += 8) {
+    const uint32_t off = (uint32_t)ks * 32;
+    const uint64_t ah = tc::smem_desc(a + off, lbo, sbo), al = tc::smem_desc(a + lo_a + off, lbo, sbo);
+    const uint64_t bh = tc::smem_desc(b + off, lbo, sbo), bl = tc::smem_desc(b + lo_b + off, lbo, sbo);
+    tc::mma_tf32(d_tmem, ah, bh, idesc, (fresh && ks == 0) ? 0u : 1u);
+    tc::mma_tf32(d_tmem, ah, bl, idesc, 1u);
+    tc::mma_tf32(d_tmem, al, bh, idesc, 1u);
+  }
+}
+
 }  // namespace gpeps

@@ -163,3 +163,53 @@ def test_tensor_cores_rejected_where_unsupported():
             g.set_tensor_cores(True)
         g.set_tensor_cores(False)
         g.close()
+
+
+def test_tensor_cores_bp_regauge_matches_oracle_golden():
+    """BP regauging with the message products on the tensor cores (leg products and message
+    Gram, 3xTF32) and the simple update's passes too: 127 qubits, D = 32, theta = 0.7, a regauge
+    to convergence after each of 8 steps; the mean of every step, every qubit and the sampled
+    lambda at the committed steps against the FP64 oracle (the mixed path's tolerances)."""
+    from workloads import workload
+    from .test_gpu_bp import lam_close
+    inst = _golden("eagle_bp_d32")["instances"][0]
+    w = workload("eagle_bp_d32")
+    g = gpu_lib()(w.graphs(), w.D, dtype="mixed")
+    g.set_tensor_cores(True)
+    g.reset()
+    th = torch.tensor([w.theta[0]], dtype=torch.float64, device="cuda")
+    for s in range(1, w.steps + 1):
+        g.step(1, th)
+        it, res = g.bp_regauge(300)
+        assert it < 300, (s, it, res)
+        z, mean = g.expect_z()
+        assert abs(float(mean.cpu().numpy()[0]) - inst["mean_z"][s - 1]) < TOL, s
+        if str(s) in inst["z"]:
+            assert np.abs(z.cpu().numpy() - np.array(inst["z"][str(s)])).max() < TOL, s
+            for e, lam in inst["lambda"][str(s)].items():
+                assert lam_close(g.lambdas(0, int(e)), lam, "mixed", truncated=2 ** s > w.D), (s, e)
+    assert g.status() == 0
+    g.close()
+
+
+def test_tensor_core_messages_agree_with_cuda_cores():
+    """From one state (127 qubits, D = 32, 7 steps: sites of degree 1, 2 and 3, truncated bonds),
+    a regauge with the tensor-core message products and one with the CUDA-core products reach
+    the same <Z_i> within 1e-5 and the same lambda spectra within 1e-4."""
+    g = gpu_lib()([(M127, E127)], 32, dtype="mixed")
+    g.reset()
+    th = torch.tensor([0.7], dtype=torch.float64, device="cuda")
+    g.step(7, th)
+    saved = g.save_state()
+    out = {}
+    for tc in (False, True):
+        g.load_state(saved)
+        g.set_tensor_cores(tc)
+        it, res = g.bp_regauge(300)
+        assert it < 300, (tc, it, res)
+        z, _ = g.expect_z()
+        out[tc] = (z.cpu().numpy(), np.array([g.lambdas(0, e) for e in (0, 50, 100, 143)]))
+    assert g.status() == 0
+    g.close()
+    assert np.abs(out[True][0] - out[False][0]).max() < 1e-5
+    assert np.abs(out[True][1] - out[False][1]).max() < 1e-4
