@@ -285,6 +285,12 @@ def run_bp(args, local_rank):
         from paper_2309_15642_gb300.autotune import autotune
         best, _ = autotune(g, theta)
         tuning = best
+    else:
+        if args.tensor and args.dtype == "mixed":
+            g.set_tensor_cores(True)
+        g.set_schedule(args.schedule or 0)
+        if args.floor_rel is not None and args.dtype == "mixed":
+            g.set_jacobi(floor_rel=args.floor_rel)
     g.reset()
     th = torch.tensor(theta, dtype=torch.float64, device=dev)
     out = torch.empty((1, g.n_instances), dtype=torch.float64, device=dev)
