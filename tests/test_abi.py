@@ -155,3 +155,19 @@ def test_state_layout_host_only(abi):
         off = ctypes.c_int64()
         assert lib.gpeps_lambda_layout(h, 2, 0, ctypes.byref(off)) == abi.GPEPS_EINVAL
         lib.gpeps_destroy(h)
+
+
+def test_tensor_core_switch_host_checks(abi):
+    """gpeps_set_tensor_cores (host-only): accepted for the complex64 path at D = 32 and 64,
+    rejected for complex128, for other bond dimensions and for a NULL handle; off is always
+    accepted."""
+    lib = abi.load()
+    n, e = heavy_hex(*EAGLE)
+    assert lib.gpeps_set_tensor_cores(None, 1) == abi.GPEPS_EINVAL
+    for dtype, D, ok in ((1, 32, True), (1, 64, True), (1, 16, False), (1, 8, False), (0, 32, False),
+                         (0, 64, False)):
+        st, h = _create(abi, [(n, e)], D=D, dtype=dtype)
+        assert st == 0
+        assert lib.gpeps_set_tensor_cores(h, 1) == (0 if ok else abi.GPEPS_EINVAL), (dtype, D)
+        assert lib.gpeps_set_tensor_cores(h, 0) == 0
+        assert lib.gpeps_destroy(h) == 0
