@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(kBpMsgThreads, sizeof(T) == 4 && K == kGramPer
 //                time: an M = 128 (c) x N = 64 ((re/im, b)) x K = 64 ((re/im, b'))
 //                product whose right operand W, the realified environment M of
 //                the leg, is staged once per leg;
-//   Gram         m[a][a'] = sum_c A(c, a) B(c, a') over 32-column chunks of both
+//   Gram         m[a][a'] = sum_c A(c, a) B(c, a') over 64-column chunks of both
 //                spins into a second accumulator: rows (re/im, a), columns
 //                (re/im, a') (rows 64..127 of the M = 128 product unused);
 //                m = (B_rr - B_ii) + i (B_ri + B_ir), summed whole and stored as
@@ -487,11 +487,12 @@ __global__ void __launch_bounds__(kBpMsgThreads, sizeof(T) == 4 && K == kGramPer
 // CTA stops issuing products (its messages are then wrong, the flag says so).
 constexpr int kBpTcD = 32;
 constexpr int kBpTcThreads = 256;
+constexpr int kTcBatch = 8;  // loads of a thread in flight together in the operand staging
 struct BpTcSmem {  // bytes
   static constexpr size_t W = 0;                     // hi | lo of W: 64 rows x 64 K (2 x 16 KB)
   static constexpr size_t A = 32768;                 // leg product hi | lo: 128 x 64 (2 x 32 KB); Gram: A hi | lo
-                                                     // 128 x 32 (2 x 16 KB), B hi | lo 64 x 32 (2 x 8 KB); readout
-                                                     // dump 64 x 65 floats
+                                                     // 128 x 64 (2 x 32 KB, B in the region of W); readout dump
+                                                     // 64 x 65 floats
   static constexpr size_t Mo = A + 65536;            // double2 [32][32]
   static constexpr size_t total = Mo + (size_t)kBpTcD * kBpTcD * 16;
 };
@@ -524,10 +525,10 @@ __global__ void __launch_bounds__(kBpTcThreads, 2)
   unsigned char* Wl = Wh + 16384;
   unsigned char* Ah = smem + BpTcSmem::A;
   unsigned char* Al = Ah + 32768;
-  unsigned char* gAh = Ah;
-  unsigned char* gAl = gAh + 16384;
-  unsigned char* gBh = gAh + 32768;
-  unsigned char* gBl = gBh + 8192;
+  unsigned char* gAh = Ah;            // Gram: A hi | lo, 128 rows x 64 K (the leg product's region)
+  unsigned char* gAl = gAh + 32768;
+  unsigned char* gBh = Wh;            // Gram: B hi | lo, 64 rows x 64 K (W is rebuilt before its next use)
+  unsigned char* gBl = gBh + 16384;
   float* dump = reinterpret_cast<float*>(smem + BpTcSmem::A);
   double2* Mo = reinterpret_cast<double2*>(smem + BpTcSmem::Mo);
   float2* X = scratch + (int64_t)blockIdx.x * slot_elems;
@@ -576,16 +577,16 @@ __global__ void __launch_bounds__(kBpTcThreads, 2)
         for (int ct = c0; ct < c1; ct += 128) {
           const int nc = c1 - ct < 128 ? c1 - ct : 128;
           const int ngroups = ((nc + 7) / 8) * (D / 4);
-          for (int g0 = warp; g0 < ngroups; g0 += 4 * nwarps) {
-            float2 v[4];
+          for (int g0 = warp; g0 < ngroups; g0 += kTcBatch * nwarps) {
+            float2 v[kTcBatch];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < kTcBatch; ++i) {
               const int g = g0 + i * nwarps;
               const int c = (g / (D / 4)) * 8 + (lane & 7), bp = (g % (D / 4)) * 4 + (lane >> 3);
               v[i] = (g < ngroups && c < nc) ? src[leg_addr(ct + c, bp, I, D) - soff] : make_float2(0.f, 0.f);
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < kTcBatch; ++i) {
               const int g = g0 + i * nwarps;
               if (g < ngroups) {
                 const int c = (g / (D / 4)) * 8 + (lane & 7), bp = (g % (D / 4)) * 4 + (lane >> 3);
@@ -604,10 +605,10 @@ __global__ void __launch_bounds__(kBpTcThreads, 2)
             }
             tc_ok = tc_wait(&bar, phase, kTcWaitCycles);
           }
-          if (threadIdx.x < 128 && tc_ok) {
+          if (tc_ok) {  // warps w and w + 4 read TMEM lanes 32 (w % 4) ..: each takes 16 of the 32 b
             tc::fence_after_sync();
-            const int c = threadIdx.x;
-            for (int bb = 0; bb < D; bb += 16) {
+            const int c = threadIdx.x & 127;
+            for (int bb = (threadIdx.x >> 7) * 16; bb < D; bb += 16 * (blockDim.x >> 7)) {
               float re[16], im[16];
               tc::tmem_ld16(tmem + ((uint32_t)(32 * (c >> 5)) << 16) + (uint32_t)bb, re);
               tc::tmem_ld16(tmem + ((uint32_t)(32 * (c >> 5)) << 16) + (uint32_t)(D + bb), im);
@@ -621,15 +622,15 @@ __global__ void __launch_bounds__(kBpTcThreads, 2)
           __syncthreads();
         }
       }
-      // Gram over the columns of leg p, 32 at a time (rows a and D + a of both operands: the
+      // Gram over the columns of leg p, 64 at a time (rows a and D + a of both operands: the
       // real and imaginary parts; K = the column, zero-padded to a multiple of 8)
-      for (int cg = c0; cg < c1; cg += 32) {
-        const int nc = c1 - cg < 32 ? c1 - cg : 32, nc8 = (nc + 7) & ~7;
+      for (int cg = c0; cg < c1; cg += 64) {
+        const int nc = c1 - cg < 64 ? c1 - cg : 64, nc8 = (nc + 7) & ~7;
         const int ngroups = (D / 8) * (nc8 / 4);
-        for (int g0 = warp; g0 < ngroups; g0 += 4 * nwarps) {  // a thread's loads in flight together
-          float2 va[4], vb[4];
+        for (int g0 = warp; g0 < ngroups; g0 += kTcBatch * nwarps) {  // a thread's loads in flight together
+          float2 va[kTcBatch], vb[kTcBatch];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
+          for (int i = 0; i < kTcBatch; ++i) {
             const int g = g0 + i * nwarps;
             const int a = (g % (D / 8)) * 8 + (lane & 7), cc = (g / (D / 8)) * 4 + (lane >> 3);
             va[i] = make_float2(0.f, 0.f);
@@ -641,14 +642,14 @@ __global__ void __launch_bounds__(kBpTcThreads, 2)
             }
           }
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
+          for (int i = 0; i < kTcBatch; ++i) {
             const int g = g0 + i * nwarps;
             if (g >= ngroups) continue;
             const int a = (g % (D / 8)) * 8 + (lane & 7), cc = (g / (D / 8)) * 4 + (lane >> 3);
-            tc_put(gAh, gAl, a, cc, 32, va[i].x);
-            tc_put(gAh, gAl, D + a, cc, 32, va[i].y);
-            tc_put(gBh, gBl, a, cc, 32, vb[i].x);
-            tc_put(gBh, gBl, D + a, cc, 32, vb[i].y);
+            tc_put(gAh, gAl, a, cc, 64, va[i].x);
+            tc_put(gAh, gAl, D + a, cc, 64, va[i].y);
+            tc_put(gBh, gBl, a, cc, 64, vb[i].x);
+            tc_put(gBh, gBl, D + a, cc, 64, vb[i].y);
           }
         }
         tc::fence_async_smem();
@@ -656,7 +657,7 @@ __global__ void __launch_bounds__(kBpTcThreads, 2)
         if (tc_ok) {
           if (threadIdx.x == 0) {
             tc::fence_after_sync();
-            tc_issue(tc::smem_u32(gAh), 16384u, tc::smem_u32(gBh), 8192u, nc8, 32, tmem + 64u, idesc, fresh_gram);
+            tc_issue(tc::smem_u32(gAh), 32768u, tc::smem_u32(gBh), 16384u, nc8, 64, tmem + 64u, idesc, fresh_gram);
             tc::mma_commit(&bar);
           }
           tc_ok = tc_wait(&bar, phase, kTcWaitCycles);
