@@ -777,7 +777,8 @@ def run_condor_d64(dev, Kc=3, Wc=6):
 
 def run_bp_record(dev, W=5, K=3, tensor=True):
     """BP regauging after each Trotter step (the paper's BP comparison) on workload eagle_bp_d32
-    (127 q, D = 32, theta_h = 0.7), mixed path, fused step, the simple update's passes and the
+    (127 q, D = 32, theta_h = 0.7), mixed path, fused step (three CTAs per SM where they fit, FP64
+    floor 1e-7 as in the headline's tuned setting), the simple update's passes and the
     message products on the tensor cores (tensor=True) or on CUDA cores: W steps each followed by
     a regauge to convergence, then K timed steps (CUDA events on the library stream around step +
     regauge, the regauge's per-iteration convergence read-back included).  Reports Trotter
@@ -793,7 +794,12 @@ def run_bp_record(dev, W=5, K=3, tensor=True):
     th = torch.tensor([float(t[0]) for t in kick_angles(wb)], dtype=torch.float64, device=dev)
     g = GPEPS(graphs, wb.D, dtype="mixed", device=str(dev))
     g.set_tensor_cores(tensor)
-    g.set_schedule(4)
+    from paper_2309_15642_gb300._abi import GpepsError
+    try:
+        g.set_schedule(5)      # the fused step with three CTAs per SM, as timed in the headline
+    except GpepsError:
+        g.set_schedule(4)
+    g.set_jacobi(floor_rel=1e-7)
     g.reset()
     for _ in range(W):
         g.step(1, th)
