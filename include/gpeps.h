@@ -160,7 +160,7 @@ int gpeps_step_profiled(gpeps_handle* h, const double* theta, int32_t per_qubit,
  * FP64 one-sided sweeps on the bond core B stop rotating a column pair when
  * |b_p^H b_q| <= max(tol |b_p| |b_q|, floor_rel ||B||_F^2) (1e-14, 1e-20).  The
  * FP32 stages use tol32 (1e-6; complex128: relative to the two columns) and
- * floor32 (1e-7; mixed only); sweep caps
+ * floor32 (2e-7; mixed only); sweep caps
  * max_sweeps (40; hitting it sets GPEPS_FLAG_NOCONV) and max_sweeps32 (20).
  * Host-only; drops a captured step graph.  Errors: GPEPS_EINVAL for
  * non-positive thresholds or caps outside [1, 200] (FP64) / [0, 200] (FP32).

@@ -477,7 +477,7 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   h->jp.tol = dtype == GPEPS_C128 ? 1e-14 : 1e-9;
   h->jp.floor_rel = dtype == GPEPS_C128 ? 1e-20 : 1e-8;
   h->jp.tol32 = 1e-6;
-  h->jp.floor32 = 1e-7;
+  h->jp.floor32 = 2e-7;
   h->jp.ev_cut = 0.0;
   h->jp.max_sweeps = 40;
   h->jp.max_sweeps32 = 20;

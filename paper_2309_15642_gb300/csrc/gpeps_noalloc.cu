@@ -187,7 +187,7 @@ extern "C" int gpeps_bond_update_noalloc(int32_t D, int32_t dtype, void* gamma_a
   jp.tol = dtype == GPEPS_C128 ? 1e-14 : 1e-9;
   jp.floor_rel = dtype == GPEPS_C128 ? 1e-20 : 1e-8;
   jp.tol32 = 1e-6;
-  jp.floor32 = 1e-7;
+  jp.floor32 = 2e-7;
   jp.ev_cut = 0.0;
   jp.max_sweeps = 40;
   jp.max_sweeps32 = 20;

@@ -213,7 +213,7 @@ class GPEPS:
         (mixed path, D = 32 or 64; see gpeps_set_tensor_cores)."""
         check(self.lib.gpeps_set_tensor_cores(self.h, 1 if on else 0), "gpeps_set_tensor_cores")
 
-    def set_jacobi(self, tol=None, floor_rel=None, tol32=1e-6, floor32=1e-7, max_sweeps=40, max_sweeps32=20):
+    def set_jacobi(self, tol=None, floor_rel=None, tol32=1e-6, floor32=2e-7, max_sweeps=40, max_sweeps32=20):
         """Thresholds of the bond eigensolver (see gpeps_set_jacobi); None = the dtype's default."""
         if tol is None:
             tol = 1e-14 if self.dtype == "c128" else 1e-9
