@@ -86,17 +86,19 @@ def test_tensor_cores_fused_step_bit_identical_d64():
     assert torch.equal(a[1], b[1])
 
 
-def test_tensor_cores_benchmark_setting_matches_oracle():
-    """The benchmark batch in the setting bench.py times with the tensor cores on (fused step,
-    three CTAs per SM, FP64 floor 1e-7, four extra FP32 levels): every qubit at the committed
-    steps 5, 6, 10, 25 and 50 within 1e-4 of the FP64 oracle, and the sampled lambda spectra."""
+@pytest.mark.parametrize("floor32,floor_rel", [(2e-7, 1e-7), (1e-7, 7e-8)])
+def test_tensor_cores_benchmark_setting_matches_oracle(floor32, floor_rel):
+    """The benchmark batch in the settings the autotuner chooses between for bench.py with the
+    tensor cores on (fused step, three CTAs per SM, FP32 / FP64 stopping floors 2e-7 / 1e-7 or
+    1e-7 / 7e-8 of the trace, four extra FP32 levels): every qubit at the committed steps 5, 6,
+    10, 25 and 50 within 1e-4 of the FP64 oracle, and the sampled lambda spectra."""
     gold = _golden("heavyhex_mix_d32")
     w = workload("heavyhex_mix_d32")
     graphs = w.graphs()
     g = gpu_lib()(graphs, w.D, dtype="mixed")
     g.set_schedule(5)
     g.set_tensor_cores(True)
-    g.set_jacobi(floor_rel=1e-7)
+    g.set_jacobi(floor_rel=floor_rel, floor32=floor32)
     g.set_levels(level_ratio=1e-5, levels=4)
     g.reset()
     th = torch.tensor([0.7] * 3, dtype=torch.float64, device="cuda")
