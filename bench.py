@@ -70,6 +70,9 @@ def parse():
                     help="with --no-autotune: Gram and update passes on the tensor cores (mixed, D = 32 or 64)")
     ap.add_argument("--floor-rel", type=float, default=None,
                     help="with --no-autotune: FP64 Jacobi floor (fraction of the trace) of the mixed path")
+    ap.add_argument("--floor32", type=float, default=None,
+                    help="with --no-autotune and --floor-rel: FP32-level floor (fraction of the trace) of the "
+                         "mixed path")
     return ap.parse_args()
 
 
@@ -166,9 +169,11 @@ TF32_OVER_BF16 = 1.1 / 2.25
 def bond_fixed_flops(graphs, D, dtype):
     """(FP64, FP32) flops of one Trotter step's bond eigenproblems that do not depend on how the
     Jacobi sweeps converge, per bond with its own n = 2 D^(deg - 1) (deg of the smaller end;
-    8 flops per complex MAC).  Mixed path (squared form): re-orthonormalisation of the FP32
-    eigenvectors 4 n^3 / 3 MACs and rho' = V^dagger rho V 3 n^3 / 2 MACs in FP64; the rho
-    formation 2 (n D^2 + n(n+1)/2 D) MACs and the Y matrices 2 D^2 n MACs in FP32.  Complex128
+    8 flops per complex MAC).  Mixed path (squared form): of the re-orthonormalisation of the FP32
+    eigenvectors, E = V^dagger V - I (n^3 / 2 MACs) and Q = V R^-1 (n^3 / 2) in FP64 and the
+    E-sized products X1^dagger X1 and X^2 (n^3 / 6 MACs each) in FP32; rho' = V^dagger rho V
+    3 n^3 / 2 MACs in FP64; the rho formation 2 (n D^2 + n(n+1)/2 D) MACs and the Y matrices
+    2 D^2 n MACs in FP32.  Complex128
     (unsquared form, all FP64): the pivoted Cholesky roots of the two D x D Gram blocks 2 D^3 / 3
     MACs, the core M = 2D x n, 2D n D MACs, the re-orthonormalisation 4 n^3 / 3, B = M V0 2D n^2
     and the Y matrices 2 D^2 n MACs.  The Jacobi sweeps and the levels are counted in the kernel."""
@@ -181,8 +186,8 @@ def bond_fixed_flops(graphs, D, dtype):
             if dtype == "c128":
                 f64 += (2.0 * D ** 3 / 3 + 2 * D * n * D + 4.0 * n ** 3 / 3 + 2 * D * n * n + 2 * D * D * n) * 8
                 continue
-            f64 += (4.0 * n ** 3 / 3.0 + 1.5 * n ** 3) * 8
-            f32 += (2 * (n * D * D + n * (n + 1) / 2 * D) + 2 * D * D * n) * 8
+            f64 += (n ** 3 + 1.5 * n ** 3) * 8
+            f32 += (2 * (n * D * D + n * (n + 1) / 2 * D) + 2 * D * D * n + n ** 3 / 3.0) * 8
     return f64, f32
 
 
@@ -290,7 +295,7 @@ def run_bp(args, local_rank):
             g.set_tensor_cores(True)
         g.set_schedule(args.schedule or 0)
         if args.floor_rel is not None and args.dtype == "mixed":
-            g.set_jacobi(floor_rel=args.floor_rel)
+            g.set_jacobi(floor_rel=args.floor_rel, **({} if args.floor32 is None else {"floor32": args.floor32}))
     g.reset()
     th = torch.tensor(theta, dtype=torch.float64, device=dev)
     out = torch.empty((1, g.n_instances), dtype=torch.float64, device=dev)
@@ -553,7 +558,7 @@ def run_gpeps(args, rank, world, local_rank):
             if args.schedule is not None:
                 g.set_schedule(args.schedule)
             if args.floor_rel is not None and dtype == "mixed":
-                g.set_jacobi(floor_rel=args.floor_rel)
+                g.set_jacobi(floor_rel=args.floor_rel, **({} if args.floor32 is None else {"floor32": args.floor32}))
             if args.tensor and dtype == "mixed":
                 g.set_schedule(0)
                 g.set_tensor_cores(True)

@@ -212,7 +212,12 @@ struct HermPacked {
 // executed, work[0] and work[1].  iflag: 8 ints, followed by 136 ints of scratch:
 // the active and the idle pairs of the round, per warp ([2][32] each), and their
 // counts, double-buffered by round parity ([2][4]).
-template <typename R, bool kExact, typename S>
+// kRowsFastest: the eigenvector update gives consecutive threads consecutive rows of V
+// for one pair (its rotation read as a broadcast); with an odd row stride ldv (in
+// elements of 8 bytes) the 16 rows of a half-warp then fall in distinct banks.  The
+// default gives consecutive threads the active pairs of one row.  Both perform the same
+// operations on every element.
+template <typename R, bool kExact, typename S, bool kRowsFastest = false>
 __device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_abs, int max_sweeps,
                                 R* rc, R* rs, V2<R>* re, int* rp, int* rq, int* iflag,
                                 unsigned long long* rot_count, unsigned long long* work = nullptr) {
@@ -321,8 +326,7 @@ __device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_ab
         A.put(qa, pb, n10, !diag);
         A.put(qa, qb, n11, !diag);
       }
-      for (int t = threadIdx.x; t < n * na; t += blockDim.x) {
-        const int i = t / na, k = active(t - i * na);
+      auto vec_update = [&](int i, int k) {
         ++n_vec;
         const R cs = rc[k], sn = rs[k];
         const int p = rp[k], q = rq[k];
@@ -330,6 +334,20 @@ __device__ int jacobi_hermitian(S A, V2<R>* V, int ldv, int n, R tol, R floor_ab
         const V2<R> vqe = c_mul<R>(V[i * ldv + q], re[k]);
         V[i * ldv + p] = c_sub<R>(c_scale<R>(vp, cs), c_scale<R>(vqe, sn));
         V[i * ldv + q] = c_add<R>(c_scale<R>(vp, sn), c_scale<R>(vqe, cs));
+      };
+      if (kRowsFastest && blockDim.x % n == 0) {
+        const int i = threadIdx.x % n, step = blockDim.x / n;
+        for (int j = threadIdx.x / n; j < na; j += step) vec_update(i, active(j));
+      } else if (kRowsFastest) {
+        for (int t = threadIdx.x; t < n * na; t += blockDim.x) {
+          const int j = t / n;
+          vec_update(t - j * n, active(j));
+        }
+      } else {
+        for (int t = threadIdx.x; t < n * na; t += blockDim.x) {
+          const int i = t / na;
+          vec_update(i, active(t - i * na));
+        }
       }
       __syncthreads();
     }

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kThreads)
 // (n = 2 nb).  Three large regions of complex doubles (the big part):
 //   R    [n][n+1]                 the bond matrix rho, later V^dagger rho V
 //   Vr   max(n*n, 2D^2 + n*D)     Gram blocks C_s and H while rho is formed, then V
-//   X    max(n*(n+1), n*D)        F; then the FP32 copies rho32 [n][n+1] and V32 [n][n];
+//   X    max(n*(n+1), n*D)        F; then the FP32 copies rho32 [n][n+1] and V32 [n][n+1];
 //                                 then the Gram/Cholesky factor of V; then rho V; then F again
 // and the small arrays (rotations of both precisions, eigenvalues, indices).
 // Both parts sit in shared memory when they fit (D <= 34); beyond that the big
@@ -181,7 +181,7 @@ struct BondSmem {
     // arrays, and later the scratch of the extra levels (lv = min(n/2, 32)
     // indices: W64 [lv][lv], Gw [lv][lv+1] complex double, B32 [lv][lv+1],
     // W32 [lv][lv] complex float)
-    f32 = ((size_t)n * (n + 1) / 2 + (size_t)n * n) * 8;
+    f32 = ((size_t)n * (n + 1) / 2 + (size_t)n * (n + 1)) * 8;
     const size_t lv = (size_t)(m < kMaxLevel ? m : kMaxLevel);
     const size_t lvl = lv * (48 * lv + 24);
     if (lvl > f32) f32 = lvl;
@@ -233,78 +233,177 @@ __device__ __forceinline__ void upper_index(int idx, int n, int& i, int& j) {
 // is formed row by row in place (one warp per row).  G holds E and X in its
 // upper triangle and X1^dagger X1, X^2 in its strict lower triangle (row
 // stride ldg); dg[n] holds their diagonals.  Returns max |E_ij|.
+//
+// kF32Products (the complex64 path, whose bond matrix carries FP32 rounding):
+// the two products of E-sized factors, X1^dagger X1 and X^2, run in FP32 on
+// FP32 copies of X1 and X.  Their entries are O(n |E|^2) ~ 1e-10, so FP32's
+// relative 1e-7 leaves absolute errors at or below the FP64 rounding of E itself
+// at the |E| ~ 1e-6 of a 64-wide FP32 solve; E = V^dagger V - I and Q = V R^-1
+// stay FP64.  The FP32 copy of upper entry (i, j) sits in the otherwise unused
+// 16 bytes mirrored below the diagonal, (j, i) for i < j and the padding column
+// (i, n) for i = j (ldg >= n + 1): X1 in its first 8 bytes, X in its last 8.
+// Q pairs the columns j and n-1-j on one lane (n <= 128).
+__device__ __forceinline__ float2* tri32(double2* G, int ldg, int n, int i, int j) {
+  return reinterpret_cast<float2*>(i < j ? G + j * ldg + i : G + i * ldg + n);
+}
+
+template <bool kF32Products>
 __device__ double orthonormalise(double2* V, int n, double2* G, int ldg, double* dg, double* scal) {
-  // E = V^dagger V - I (upper triangle)
-  for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
-    int i, j;
-    upper_index(idx, n, i, j);
-    double2 acc = make_double2(i == j ? -1.0 : 0.0, 0.0);
-    for (int r = 0; r < n; ++r) fma_conj<double>(acc, V[r * n + i], V[r * n + j]);
-    if (i == j) acc.y = 0.0;
-    G[i * ldg + j] = acc;
-  }
-  if (threadIdx.x == 0) scal[6] = 0.0;
-  __syncthreads();
-  // K = X1^dagger X1 with X1 = P(E): K_ij = sum_{k <= i} conj(X1_ki) X1_kj  (i <= j)
-  for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
-    int i, j;
-    upper_index(idx, n, i, j);
-    double2 acc = make_double2(0.0, 0.0);
-    for (int k = 0; k <= i; ++k) {
-      double2 xki = G[k * ldg + i], xkj = G[k * ldg + j];
-      if (k == i) xki = cscale(xki, 0.5);
-      if (k == j) xkj = cscale(xkj, 0.5);
-      fma_conj<double>(acc, xki, xkj);
+  if constexpr (kF32Products) {
+    // E = V^dagger V - I (upper triangle, FP64) and the FP32 copy of X1 = P(E)
+    for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+      int i, j;
+      upper_index(idx, n, i, j);
+      double2 acc = make_double2(i == j ? -1.0 : 0.0, 0.0);
+      for (int r = 0; r < n; ++r) fma_conj<double>(acc, V[r * n + i], V[r * n + j]);
+      if (i == j) acc.y = 0.0;
+      G[i * ldg + j] = acc;
+      tri32(G, ldg, n, i, j)[0] =
+          i == j ? make_float2((float)(0.5 * acc.x), 0.f) : make_float2((float)acc.x, (float)acc.y);
     }
-    if (i == j) dg[i] = acc.x;
-    else G[j * ldg + i] = acc;
-  }
-  __syncthreads();
-  // X = P(E - K) in the upper triangle; record max |E|
-  for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
-    int i, j;
-    upper_index(idx, n, i, j);
-    const double2 e = G[i * ldg + j];
-    const double ae = fabs(e.x) + fabs(e.y);
-    if (ae > scal[6]) atomicMax(reinterpret_cast<unsigned long long*>(scal + 6), __double_as_longlong(ae));
-    if (i == j) G[i * ldg + i] = make_double2(0.5 * (e.x - dg[i]), 0.0);
-    else G[i * ldg + j] = csub(e, G[j * ldg + i]);
-  }
-  __syncthreads();
-  // X^2 (upper triangular) into the strict lower triangle and dg
-  for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
-    int i, j;
-    upper_index(idx, n, i, j);
-    double2 acc = make_double2(0.0, 0.0);
-    for (int k = i; k <= j; ++k) fma_c<double>(acc, G[i * ldg + k], G[k * ldg + j]);
-    if (i == j) dg[i] = acc.x;
-    else G[j * ldg + i] = acc;
-  }
-  __syncthreads();
-  // M = X^2 - X in the upper triangle
-  for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
-    int i, j;
-    upper_index(idx, n, i, j);
-    if (i == j) G[i * ldg + i] = make_double2(dg[i] - G[i * ldg + i].x, 0.0);
-    else G[i * ldg + j] = csub(G[j * ldg + i], G[i * ldg + j]);
-  }
-  __syncthreads();
-  // Q[r][j] = V[r][j] + sum_{i <= j} V[r][i] M[i][j], one warp per row, in place:
-  // 32-column chunks from the right, since a chunk reads only columns at or
-  // left of its own (each lane computes its column before any lane writes)
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = warp; r < n; r += nw) {
-    double2* v = V + r * n;
-    for (int c = (n - 1) >> 5; c >= 0; --c) {
-      const int j = lane + 32 * c;
+    if (threadIdx.x == 0) scal[6] = 0.0;
+    __syncthreads();
+    // K = X1^dagger X1 (FP32, K_ij = sum_{k <= i} conj(X1_ki) X1_kj), X = P(E - K) in FP64
+    // over E, and its FP32 copy; record max |E|
+    for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+      int i, j;
+      upper_index(idx, n, i, j);
+      float2 k32 = make_float2(0.f, 0.f);
+      for (int k = 0; k <= i; ++k) fma_conj<float>(k32, tri32(G, ldg, n, k, i)[0], tri32(G, ldg, n, k, j)[0]);
+      const double2 e = G[i * ldg + j];
+      const double ae = fabs(e.x) + fabs(e.y);
+      if (ae > scal[6]) atomicMax(reinterpret_cast<unsigned long long*>(scal + 6), __double_as_longlong(ae));
+      const double2 x = i == j ? make_double2(0.5 * (e.x - (double)k32.x), 0.0)
+                               : make_double2(e.x - (double)k32.x, e.y - (double)k32.y);
+      G[i * ldg + j] = x;
+      tri32(G, ldg, n, i, j)[1] = make_float2((float)x.x, (float)x.y);
+    }
+    __syncthreads();
+    // M = X^2 - X in the upper triangle (X^2 upper triangular, FP32: (X^2)_ij = sum_{i<=k<=j} X_ik X_kj)
+    for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+      int i, j;
+      upper_index(idx, n, i, j);
+      float2 s32 = make_float2(0.f, 0.f);
+      for (int k = i; k <= j; ++k) fma_c<float>(s32, tri32(G, ldg, n, i, k)[1], tri32(G, ldg, n, k, j)[1]);
+      const double2 x = G[i * ldg + j];
+      G[i * ldg + j] = i == j ? make_double2((double)s32.x - x.x, 0.0)
+                              : make_double2((double)s32.x - x.x, (double)s32.y - x.y);
+    }
+    __syncthreads();
+  } else {
+    // E = V^dagger V - I (upper triangle)
+    for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+      int i, j;
+      upper_index(idx, n, i, j);
+      double2 acc = make_double2(i == j ? -1.0 : 0.0, 0.0);
+      for (int r = 0; r < n; ++r) fma_conj<double>(acc, V[r * n + i], V[r * n + j]);
+      if (i == j) acc.y = 0.0;
+      G[i * ldg + j] = acc;
+    }
+    if (threadIdx.x == 0) scal[6] = 0.0;
+    __syncthreads();
+    // K = X1^dagger X1 with X1 = P(E): K_ij = sum_{k <= i} conj(X1_ki) X1_kj  (i <= j)
+    for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+      int i, j;
+      upper_index(idx, n, i, j);
       double2 acc = make_double2(0.0, 0.0);
-      if (j < n) {
-        acc = v[j];
-        for (int i = 0; i <= j; ++i) fma_c<double>(acc, v[i], G[i * ldg + j]);
+      for (int k = 0; k <= i; ++k) {
+        double2 xki = G[k * ldg + i], xkj = G[k * ldg + j];
+        if (k == i) xki = cscale(xki, 0.5);
+        if (k == j) xkj = cscale(xkj, 0.5);
+        fma_conj<double>(acc, xki, xkj);
+      }
+      if (i == j) dg[i] = acc.x;
+      else G[j * ldg + i] = acc;
+    }
+    __syncthreads();
+    // X = P(E - K) in the upper triangle; record max |E|
+    for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+      int i, j;
+      upper_index(idx, n, i, j);
+      const double2 e = G[i * ldg + j];
+      const double ae = fabs(e.x) + fabs(e.y);
+      if (ae > scal[6]) atomicMax(reinterpret_cast<unsigned long long*>(scal + 6), __double_as_longlong(ae));
+      if (i == j) G[i * ldg + i] = make_double2(0.5 * (e.x - dg[i]), 0.0);
+      else G[i * ldg + j] = csub(e, G[j * ldg + i]);
+    }
+    __syncthreads();
+    // X^2 (upper triangular) into the strict lower triangle and dg
+    for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+      int i, j;
+      upper_index(idx, n, i, j);
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = i; k <= j; ++k) fma_c<double>(acc, G[i * ldg + k], G[k * ldg + j]);
+      if (i == j) dg[i] = acc.x;
+      else G[j * ldg + i] = acc;
+    }
+    __syncthreads();
+    // M = X^2 - X in the upper triangle
+    for (int idx = threadIdx.x; idx < n * (n + 1) / 2; idx += blockDim.x) {
+      int i, j;
+      upper_index(idx, n, i, j);
+      if (i == j) G[i * ldg + i] = make_double2(dg[i] - G[i * ldg + i].x, 0.0);
+      else G[i * ldg + j] = csub(G[j * ldg + i], G[i * ldg + j]);
+    }
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (kF32Products && n <= 128) {
+    // Q[r][j] = V[r][j] + sum_{i <= j} V[r][i] M[i][j], one warp per row, in place: lane l
+    // forms the column pairs (j, n-1-j) for j = l and l + 32 (below n/2) in one pass of n + 1
+    // products each (i = t for column j while t <= j, then i = t - j - 1 for column n-1-j),
+    // so that no lane of an FP64 instruction idles on a shorter column, and writes after
+    // the whole warp has read the row
+    const int h = n >> 1;
+    for (int r = warp; r < n; r += nw) {
+      double2* v = V + r * n;
+      double2 out[4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int j = lane + 32 * u;
+        if (j < h) {
+          const int j2 = n - 1 - j;
+          double2 acc = v[j];
+          for (int t = 0; t <= n; ++t) {
+            if (t == j + 1) {
+              out[2 * u] = acc;
+              acc = v[j2];
+            }
+            const bool first = t <= j;
+            const int i = first ? t : t - j - 1;
+            fma_c<double>(acc, v[i], G[i * ldg + (first ? j : j2)]);
+          }
+          out[2 * u + 1] = acc;
+        }
       }
       __syncwarp();
-      if (j < n) v[j] = acc;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int j = lane + 32 * u;
+        if (j < h) {
+          v[j] = out[2 * u];
+          v[n - 1 - j] = out[2 * u + 1];
+        }
+      }
       __syncwarp();
+    }
+  } else {
+    // Q[r][j] = V[r][j] + sum_{i <= j} V[r][i] M[i][j], one warp per row, in place:
+    // 32-column chunks from the right, since a chunk reads only columns at or
+    // left of its own (each lane computes its column before any lane writes)
+    for (int r = warp; r < n; r += nw) {
+      double2* v = V + r * n;
+      for (int c = (n - 1) >> 5; c >= 0; --c) {
+        const int j = lane + 32 * c;
+        double2 acc = make_double2(0.0, 0.0);
+        if (j < n) {
+          acc = v[j];
+          for (int i = 0; i <= j; ++i) fma_c<double>(acc, v[i], G[i * ldg + j]);
+        }
+        __syncwarp();
+        if (j < n) v[j] = acc;
+        __syncwarp();
+      }
     }
   }
   __syncthreads();
@@ -325,6 +424,7 @@ __device__ int fp32_warm_start(const double2* RHO, double2* Vm, double2* X, int 
   const bool packed = f32s != nullptr;
   float2* R32 = packed ? f32s : reinterpret_cast<float2*>(X);
   float2* V32 = packed ? f32s + (size_t)n * (n + 1) / 2 : R32 + (size_t)n * (n + 1);
+  const int ldv32 = n + 1;  // odd row stride: the eigenvector updates run conflict-free down the rows
   auto mark = [&](int phase) {
     if (threadIdx.x == 0 && cycles) {
       const long long t = clock64();
@@ -346,24 +446,25 @@ __device__ int fp32_warm_start(const double2* RHO, double2* Vm, double2* X, int 
       R32[idx] = make_float2((float)v.x, (float)v.y);
     }
   }
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x)
-    V32[idx] = make_float2((idx / n) == (idx % n) ? 1.f : 0.f, 0.f);
+  for (int idx = threadIdx.x; idx < n * ldv32; idx += blockDim.x)
+    V32[idx] = make_float2((idx / ldv32) == (idx % ldv32) ? 1.f : 0.f, 0.f);
   __syncthreads();
   unsigned long long* rc32_count = cycles ? cycles + kPhases : nullptr;
   const int sw32 =
-      packed ? jacobi_hermitian<float, true>(P32, V32, n, n, (float)jp.tol32, (float)(jp.floor32 * trace),
-                                             jp.max_sweeps32, rc32, rs32, re32, rp, rq, iflag, rc32_count,
-                                             sweeps_out + 6)
-             : jacobi_hermitian<float, true>(HermFull<float>{R32, ldr}, V32, n, n, (float)jp.tol32,
-                                             (float)(jp.floor32 * trace), jp.max_sweeps32, rc32, rs32, re32, rp,
-                                             rq, iflag, rc32_count, sweeps_out + 6);
+      packed ? jacobi_hermitian<float, true, HermPacked<float>, true>(
+                   P32, V32, ldv32, n, (float)jp.tol32, (float)(jp.floor32 * trace), jp.max_sweeps32, rc32, rs32,
+                   re32, rp, rq, iflag, rc32_count, sweeps_out + 6)
+             : jacobi_hermitian<float, true, HermFull<float>, true>(
+                   HermFull<float>{R32, ldr}, V32, ldv32, n, (float)jp.tol32, (float)(jp.floor32 * trace),
+                   jp.max_sweeps32, rc32, rs32, re32, rp, rq, iflag, rc32_count, sweeps_out + 6);
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const float2 v = V32[idx];
+    const int i = idx / n, j = idx - (idx / n) * n;
+    const float2 v = V32[i * ldv32 + j];
     Vm[idx] = make_double2((double)v.x, (double)v.y);
   }
   __syncthreads();
   mark(1);
-  const double emax = orthonormalise(Vm, n, X, ldr, ev, scal);
+  const double emax = orthonormalise<true>(Vm, n, X, ldr, ev, scal);
   if (threadIdx.x == 0 && !(emax < 1e-4)) atomicOr(flags, 1);  // FP32 basis too far from unitary
   mark(2);
   return sw32;
@@ -488,28 +589,36 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
         W64[idx] = make_double2((double)v.x, (double)v.y);
       }
       __syncthreads();
-      orthonormalise(W64, ns, Gw, ldb, dcur, scal);
-      // rows of V and rho': X[r][cand] <- X[r][cand] W (one warp per row, ns <= 32 per lane pass)
+      orthonormalise<true>(W64, ns, Gw, ldb, dcur, scal);
+      // rows of V and rho': X[r][cand] <- X[r][cand] W, then the columns of rho':
+      // rho'[cand][c] <- W^dagger rho'[cand][c]; a row (column) per segment of seg >= ns
+      // lanes, 32 / seg of them per warp, so that a small level does not leave most
+      // lanes of each FP64 instruction idle
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-      for (int rr = warp; rr < 2 * n; rr += nw) {
+      const int seg = ns <= 8 ? 8 : (ns <= 16 ? 16 : 32), per = 32 / seg;
+      const int sub = lane / seg, sl = lane - (lane / seg) * seg;
+      for (int r0 = warp * per; r0 < 2 * n; r0 += nw * per) {
+        const int rr = r0 + sub;
+        const bool on = rr < 2 * n && sl < ns;
         double2* row = rr < n ? Vm + rr * n : RHO + (rr - n) * ldr;
         double2 out = make_double2(0.0, 0.0);
-        if (lane < ns) {
-          for (int a = 0; a < ns; ++a) fma_c<double>(out, row[cand[a]], W64[a * ns + lane]);
+        if (on) {
+          for (int a = 0; a < ns; ++a) fma_c<double>(out, row[cand[a]], W64[a * ns + sl]);
         }
         __syncwarp();
-        if (lane < ns) row[cand[lane]] = out;
+        if (on) row[cand[sl]] = out;
         __syncwarp();
       }
       __syncthreads();
-      // columns of rho': rho'[cand][c] <- W^dagger rho'[cand][c]
-      for (int c = warp; c < n; c += nw) {
+      for (int c0 = warp * per; c0 < n; c0 += nw * per) {
+        const int c = c0 + sub;
+        const bool on = c < n && sl < ns;
         double2 out = make_double2(0.0, 0.0);
-        if (lane < ns) {
-          for (int a = 0; a < ns; ++a) fma_conj<double>(out, W64[a * ns + lane], RHO[cand[a] * ldr + c]);
+        if (on) {
+          for (int a = 0; a < ns; ++a) fma_conj<double>(out, W64[a * ns + sl], RHO[cand[a] * ldr + c]);
         }
         __syncwarp();
-        if (lane < ns) RHO[cand[lane] * ldr + c] = out;
+        if (on) RHO[cand[sl] * ldr + c] = out;
         __syncwarp();
       }
       for (int a = threadIdx.x; a < ns; a += blockDim.x) rscale[cand[a]] = bscale;
@@ -517,9 +626,10 @@ __device__ int eig_mixed(double2* RHO, double2* Vm, double2* X, int n, int D, do
       if (threadIdx.x == 0) {
         atomicAdd(sweeps_out + 2, 1ull);
         // FP64 complex MACs of this level: rows of V and rho' (2n x ns x ns), columns of
-        // rho' (n x ns x ns), re-orthonormalisation of W (about 4 ns^3 / 3)
+        // rho' (n x ns x ns), the re-orthonormalisation of W (its Gram and Q = W R^-1,
+        // about ns^3 / 2 each; its other products run in FP32)
         const unsigned long long nsl = (unsigned long long)ns;
-        atomicAdd(sweeps_out + 3, 3ull * n * nsl * nsl + 4ull * nsl * nsl * nsl / 3ull);
+        atomicAdd(sweeps_out + 3, 3ull * n * nsl * nsl + nsl * nsl * nsl);
       }
     }
   }
@@ -966,7 +1076,7 @@ __device__ void svd_levels(double2* Bt, int rows, double2* Vt, int n, double tr,
       W64[idx] = make_double2((double)v.x, (double)v.y);
     }
     __syncthreads();
-    orthonormalise(W64, ns, Gw, ns + 1, alpha, scal);
+    orthonormalise<false>(W64, ns, Gw, ns + 1, alpha, scal);
     // rows of B (r < rows) and of V (x < n): new column cand[b] = sum_a old column cand[a] W[a][b]
     for (int rr = warp; rr < rows + n; rr += nw) {
       double2* base = rr < rows ? Bt + rr : Vt + (rr - rows);
@@ -1099,8 +1209,8 @@ __device__ bool bond_front_svd(const BondDesc& bd, const double2* __restrict__ p
     // ~2500 rotations per column leave |E| ~ 1e-4), so from 1e-4 on a second
     // pass, which starts from ~|E|^3, finishes the job; a basis beyond the
     // series' range is flagged.
-    const double emax = orthonormalise(Vx, n, Xs, ldr, ev, scal);
-    const double emax2 = emax > 1e-4 ? orthonormalise(Vx, n, Xs, ldr, ev, scal) : 0.0;
+    const double emax = orthonormalise<false>(Vx, n, Xs, ldr, ev, scal);
+    const double emax2 = emax > 1e-4 ? orthonormalise<false>(Vx, n, Xs, ldr, ev, scal) : 0.0;
     if (threadIdx.x == 0 && (!(emax < 1e-2) || !(emax2 < 1e-8))) atomicOr(flags, 1);
   }
   mark(2);
