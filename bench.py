@@ -155,11 +155,11 @@ class Clocks:
 # dram__bytes_write.sum), keyed by workload, dtype and schedule; reported as the roofline's
 # `traffic` only for that configuration (profiles/step_kernel_heavyhex_mix_d32.md)
 # and whether the Gram and update passes ran on the tensor cores
-NCU_TRAFFIC = {("heavyhex_mix_d32", "mixed", 4, False): 2.048679e9 + 1.742843e9,
-               # schedule 5 (three CTAs per SM): dram__bytes.sum.per_second 122.32 GB/s x 35.60 ms
-               ("heavyhex_mix_d32", "mixed", 5, False): 122.321021e9 * 35.601440e-3,
-               # schedule 5 with the tensor-core passes: 166.087239 GB/s x 29.725280 ms
-               ("heavyhex_mix_d32", "mixed", 5, True): 166.087239e9 * 29.725280e-3}
+NCU_TRAFFIC = {
+    # one steady-state launch (Trotter step 8) of the fused step, three CTAs per SM, floors 1e-7 / 7e-8:
+    # CUDA-core Gram and update passes, and the tensor-core passes
+    ("heavyhex_mix_d32", "mixed", 5, False): 2253342208 + 2040923904,
+    ("heavyhex_mix_d32", "mixed", 5, True): 2443752000 + 2472390000}
 
 # TF32 tensor peak: the measured bf16 burst (MEASURED_PEAKS.json) x the nominal TF32 : BF16 dense ratio
 # (1.1 : 2.25 PFLOP/s)
