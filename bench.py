@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule and thresholds")
     ap.add_argument("--schedule", type=int, default=None,
                     help="with --no-autotune: bond schedule (0 one CTA per bond; 1, 2, 3 work queue with 1, 2, 4 "
-                         "CTAs per SM)")
+                         "CTAs per SM; 4, 5, 6 the fused step with up to 2, 3, 4 CTAs per SM)")
     ap.add_argument("--bp", action="store_true",
                     help="time Trotter steps with a belief-propagation regauge after each (the paper's BP "
                          "comparison) instead of the plain step")
@@ -599,7 +599,7 @@ def run_gpeps(args, rank, world, local_rank):
     # of the timed region (fused: one launch per step; layered: three per colour class)
     sched = (tuning["chosen"].get("persistent", 0) if tuning else (args.schedule or 0))
     tensor = bool(tuning["chosen"].get("tensor", False)) if tuning else (args.tensor and args.dtype == "mixed")
-    fused = sched >= 4          # schedules 4 and 5: the fused step (two or three CTAs per SM)
+    fused = sched >= 4          # schedules 4, 5 and 6: the fused step (two, three or four CTAs per SM)
     prof = {"gram": [], "bond": [], "update": []} if not fused else {"kick": [], "bond_updates": [], "readout": []}
     s0, q0, b0 = g.sweeps()
     c0 = g.bond_counters()
@@ -643,7 +643,7 @@ def run_gpeps(args, rank, world, local_rank):
         launches_step = 1
         f32_big = big_end_flops(graphs, w.D)          # Gram and update passes inside the launch
         kernel = ("step_kernel (fused step: Gram pass, 2D x 2D bond eigenproblem with FP64 Jacobi and update "
-                  f"of every bond of a Trotter step, one launch, {3 if sched == 5 else 2} CTAs per SM where they fit)")
+                  f"of every bond of a Trotter step, one launch, {({5: 3, 6: 4}).get(sched, 2)} CTAs per SM where they fit)")
     else:
         launch_ms = sum(prof["bond"]) / max(len(prof["bond"]), 1)
         bonds_per_launch = bonds_step / g.n_colours

@@ -12,8 +12,8 @@ candidate is applied to the handle and returned with the timings.
 
 Candidates (mixed path): the Gram and update products on CUDA cores or on the
 tensor cores (D = 32 and 64) x schedule (one CTA per bond | work queue with one,
-two or four CTAs per SM | one fused launch per step; a schedule the handle
-rejects is skipped) x
+two or four CTAs per SM | one fused launch per step with up to two, three or four
+CTAs per SM; a schedule the handle rejects is skipped) x
 FP32-level thresholds (tol32, floor32 = 2e-7 or 1e-7 of the trace) x FP64 stopping
 thresholds (tol, floor_rel = 1e-8, 3e-8, 7e-8 or 1e-7 of the trace: up to the ~1e-7
 relative rounding that the bond matrix inherits from its FP32 Gram inputs), the FP64
@@ -35,7 +35,7 @@ FP64_STOPS = [(1e-9, 1e-8), (1e-9, 3e-8), (1e-9, 7e-8), (1e-9, 1e-7)]
 # drifted to 1.3e-4 per qubit from the oracle by step 50, against 5.8e-5 with FP64 floor 7e-8 and
 # 9.0e-5 for 2e-7 / 1e-7).  So the FP64 floor stays at most this fraction of the FP32 floor.
 FLOOR_RATIO = 0.7
-SCHEDULES = (0, 1, 2, 3, 4, 5)
+SCHEDULES = (0, 1, 2, 3, 4, 5, 6)
 TENSOR_D = (32, 64)  # bond dimensions with tensor-core Gram and update passes (mixed path)
 
 

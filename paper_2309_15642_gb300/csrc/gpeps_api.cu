@@ -81,7 +81,8 @@ struct gpeps_handle {
   bool bound = false;
   bool tensor = false;  // mixed path, D = 32 or 64: Gram and update passes of the larger ends on the tensor cores
   int schedule = 0;  // bond eigenproblems: 0 one CTA per bond; work queue with 1 (schedule 1), 2 (2) or 4 (3)
-                     // CTAs per SM; 4 fused step (gpeps_step: one persistent launch over every colour class)
+                     // CTAs per SM; 4 fused step (gpeps_step: one persistent launch over every colour class);
+                     // 5 and 6 the fused step with three or four CTAs per SM
   std::vector<StepTask> tasks;  // fused step: every bond of a step, colour by colour, with its dependencies
   // BP regauging: half-edges (one per leg of every site), work lists built on first use
   int64_t n_half = 0;
@@ -232,7 +233,8 @@ int layered_per_sm(const gpeps_handle* h) {
     case 2: return 2;
     case 3: return 4;
     case 4:
-    case 5: return bond_footprint_global(h->D, h->elt).smem <= bond_share_smem(2) ? 2 : 1;
+    case 5:
+    case 6: return bond_footprint_global(h->D, h->elt).smem <= bond_share_smem(2) ? 2 : 1;
     default: return 1;
   }
 }
@@ -240,7 +242,8 @@ int layered_per_sm(const gpeps_handle* h) {
 // CTAs per SM of the fused step launch
 int step_per_sm(const gpeps_handle* h) {
   const size_t sm = step_footprint(h->D, h->elt, h->tensor).smem;
-  if (h->schedule == 5 && sm <= bond_share_smem(3)) return 3;
+  if (h->schedule == 6 && !h->tensor && sm <= bond_share_smem(4)) return 4;
+  if (h->schedule >= 5 && sm <= bond_share_smem(3)) return 3;
   return sm <= bond_share_smem(2) ? 2 : 1;
 }
 
@@ -525,6 +528,9 @@ int gpeps_create(const gpeps_graph* graphs, int32_t n_instances, int32_t D, int3
   h->bond_slot = std::max(bond_footprint_global(D, h->elt).slot, step_footprint(D, h->elt).slot);
   h->bond_slots = bond_footprint(D, kBondSmemMax, h->elt).slot ? h->max_bonds : std::min(h->max_bonds, 4 * kMaxSms);
   h->bond_slots = std::max(h->bond_slots, std::min((int)h->tasks.size(), 2 * kMaxSms));
+  // four fused-step CTAs per SM where their shared memory fits (schedule 6)
+  if (h->elt == 8 && step_footprint(D, h->elt, false).smem <= bond_share_smem(4))
+    h->bond_slots = std::max(h->bond_slots, std::min((int)h->tasks.size(), 4 * kMaxSms));
   h->w_bond_scratch = carve((size_t)h->bond_slots * h->bond_slot);
   h->w_tasks = carve(h->tasks.size() * sizeof(StepTask));
   h->w_done = carve(h->tasks.size() * sizeof(int));
@@ -647,9 +653,13 @@ int gpeps_step_profiled(gpeps_handle* h, const double* theta, int32_t per_qubit,
 }
 
 int gpeps_set_schedule(gpeps_handle* h, int32_t schedule) {
-  if (!h || schedule < 0 || schedule > 5) return GPEPS_EINVAL;
+  if (!h || schedule < 0 || schedule > 6) return GPEPS_EINVAL;
   if (schedule == 5 && (!h->bound || step_footprint(h->D, h->elt, h->tensor).smem > bond_share_smem(3) ||
                         std::min(3 * h->n_sms, (int)h->tasks.size()) > h->bond_slots))
+    return GPEPS_EINVAL;
+  if (schedule == 6 && (!h->bound || h->tensor || h->dtype != GPEPS_MIXED_C64 ||
+                        step_footprint(h->D, h->elt, false).smem > bond_share_smem(4) ||
+                        std::min(4 * h->n_sms, (int)h->tasks.size()) > h->bond_slots))
     return GPEPS_EINVAL;
   if (schedule >= 4) {
     // fused step: shared memory of one CTA (alone or two per SM) and a slot per CTA
@@ -683,6 +693,7 @@ int gpeps_set_tensor_cores(gpeps_handle* h, int32_t on) {
   // the fused schedule in use must still fit with the staged tensor-core operands
   if (h->schedule == 5 && step_footprint(h->D, h->elt, true).smem > bond_share_smem(3)) return GPEPS_EINVAL;
   if (h->schedule == 4 && step_footprint(h->D, h->elt, true).smem > kBondSmemMax) return GPEPS_EINVAL;
+  if (h->schedule == 6) return GPEPS_EINVAL;  // four CTAs per SM run the passes on CUDA cores only
   h->tensor = true;
   drop_graph(h);
   return GPEPS_OK;

@@ -2189,6 +2189,9 @@ cudaError_t Launch<T>::init() {
                            (int)kBondSmemMax);
   if (e != cudaSuccess) return e;
   if constexpr (std::is_same<T, float>::value) {
+    e = cudaFuncSetAttribute(step_kernel<T, 192, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bond_share_smem(4));
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(step_kernel<T, 256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bond_share_smem(2));
     if (e != cudaSuccess) return e;
@@ -2329,7 +2332,7 @@ cudaError_t Launch<T>::step(const StepTask* tasks, int n_tasks, unsigned int* qu
   if (n_tasks == 0) return cudaSuccess;
   if (tc && (!std::is_same<T, float>::value || !tc_supported(D))) return cudaErrorInvalidValue;
   const BondFootprint fp = step_footprint(D, sizeof(V2<T>), tc);
-  if (!scratch || slot < fp.slot || per_sm < 1 || per_sm > 3) return cudaErrorInvalidValue;
+  if (!scratch || slot < fp.slot || per_sm < 1 || per_sm > 4 || (per_sm == 4 && tc)) return cudaErrorInvalidValue;
   if (fp.smem > (per_sm > 1 ? bond_share_smem(per_sm) : kBondSmemMax)) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
@@ -2349,6 +2352,12 @@ cudaError_t Launch<T>::step(const StepTask* tasks, int n_tasks, unsigned int* qu
         GP_STEP(256, 2, true);
       else
         GP_STEP(kBondThreads, 1, true);
+    }
+  } else if (per_sm == 4) {
+    if constexpr (std::is_same<T, float>::value) {
+      GP_STEP(192, 4, false);
+    } else {
+      return cudaErrorInvalidValue;
     }
   } else if (per_sm == 3) {
     GP_STEP(192, 3, false);

@@ -204,8 +204,8 @@ class GPEPS:
 
     def set_schedule(self, schedule):
         """Bond eigenproblems: 0 one CTA per bond; 1, 2, 3 work queue with one, two or four CTAs
-        per SM; 4 one fused persistent launch per Trotter step in :meth:`step` (see
-        gpeps_set_schedule)."""
+        per SM; 4 one fused persistent launch per Trotter step in :meth:`step`, 5 and 6 the same
+        with three or four CTAs per SM (see gpeps_set_schedule)."""
         check(self.lib.gpeps_set_schedule(self.h, int(schedule)), "gpeps_set_schedule")
 
     def set_tensor_cores(self, on: bool = True) -> None:

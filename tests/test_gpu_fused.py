@@ -30,6 +30,17 @@ def _run(graphs, D, dtype, theta, steps, schedule):
     return m, z.cpu().numpy(), lam, flags
 
 
+def test_four_ctas_per_sm_fused_step_bit_identical_benchmark_batch():
+    """The benchmark batch at D = 32 (mixed) with four 192-thread fused-step CTAs per SM
+    (schedule 6): the same state as the layered launches after 7 steps."""
+    w = workload("heavyhex_mix_d32")
+    a = _run(w.graphs(), 32, "mixed", [0.7] * 3, 7, 2)
+    b = _run(w.graphs(), 32, "mixed", [0.7] * 3, 7, 6)
+    assert a[3] == 0 and b[3] == 0
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert torch.equal(a[2], b[2])
+
+
 @pytest.mark.parametrize("dtype", ["mixed", "c128"])
 def test_fused_step_bit_identical_benchmark_batch(dtype):
     """127 + 433 + 1121 qubits, D = 32, theta = 0.7, 7 steps: the whole state after the fused

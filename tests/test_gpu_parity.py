@@ -302,7 +302,7 @@ def test_schedules_are_bit_identical():
     import torch
     from ._gpu_util import gpu_lib
     outs = []
-    for persistent in (0, 1, 2, 3, 4, 5):
+    for persistent in (0, 1, 2, 3, 4, 5, 6):
         g = gpu_lib()([(M127, E127), heavy_hex(*OSPREY)], 8, dtype="mixed")
         g.set_schedule(persistent)
         g.reset()
