@@ -235,19 +235,21 @@ def test_heavyhex_mix_d32_full_size(dtype):
     assert g.status() == 0
 
 
-def test_heavyhex_mix_d32_benchmark_setting():
-    """The setting bench.py times on the benchmark batch (the autotuner's choice there: the fused
-    step with three CTAs per SM, FP64 stopping floor 1e-7 of the trace, four extra FP32 levels):
-    every qubit at the committed steps 5, 6, 10, 25 and 50 within 1e-4 of the oracle, and the
-    sampled lambda spectra, after graph replay from |0...0>."""
+@pytest.mark.parametrize("schedule,floor32,floor_rel", [(5, 2e-7, 1e-7), (6, 1e-7, 7e-8)])
+def test_heavyhex_mix_d32_benchmark_setting(schedule, floor32, floor_rel):
+    """The settings bench.py chooses between on the benchmark batch with the CUDA-core Gram and
+    update passes (the fused step with three or four CTAs per SM, FP32 / FP64 stopping floors
+    2e-7 / 1e-7 or 1e-7 / 7e-8 of the trace, four extra FP32 levels): every qubit at the
+    committed steps 5, 6, 10, 25 and 50 within 1e-4 of the oracle, and the sampled lambda
+    spectra, after graph replay from |0...0>."""
     gold = _golden("heavyhex_mix_d32")
     w = workload("heavyhex_mix_d32")
     graphs = w.graphs()
     from ._gpu_util import gpu_lib
     import torch
     g = gpu_lib()(graphs, w.D, dtype="mixed")
-    g.set_schedule(5)
-    g.set_jacobi(floor_rel=1e-7)
+    g.set_schedule(schedule)
+    g.set_jacobi(floor_rel=floor_rel, floor32=floor32)
     g.set_levels(level_ratio=1e-5, levels=4)
     g.reset()
     th = torch.tensor([0.7] * 3, dtype=torch.float64, device="cuda")
