@@ -208,13 +208,12 @@ int gpeps_set_wait_limit(gpeps_handle* h, int64_t cycles);
  * after ~2 s raises GPEPS_FLAG_TIMEOUT instead of hanging); gpeps_zz_layer
  * then uses schedule 2 (or 1 where 2 does not fit).  5 is the fused step with
  * three 192-thread CTAs per SM (where their shared memory fits, D <= 32), 6
- * with four (GPEPS_MIXED_C64 with the CUDA-core Gram and update passes only,
- * where their shared memory fits, D <= 32).
+ * with four (GPEPS_MIXED_C64 where their shared memory fits, D <= 32; with the
+ * tensor cores on, their TMEM, four times 4D columns, must fit the SM's 512).
  * Host-only; drops a captured step graph.  Errors: GPEPS_EINVAL for other
  * values, and for 2 to 6 on an unbound handle, when the FP32 level does not
  * fit the CTA's share of shared memory (D above 47 for 2, above 32 for 3, 5
- * and 6), for 6 with the tensor cores on or complex128, or on a device with
- * more than 256 SMs.
+ * and 6), for 6 with complex128, or on a device with more than 256 SMs.
  */
 int gpeps_set_schedule(gpeps_handle* h, int32_t schedule);  /* 0..6 */
 
@@ -231,9 +230,9 @@ int gpeps_set_schedule(gpeps_handle* h, int32_t schedule);  /* 0..6 */
  * default).  Applies to the layered launches and to the fused step
  * (schedules 4 and 5), and at D = 32 also to the message products of
  * gpeps_bp_regauge (leg products and message Gram, 3xTF32).  Host-only; drops a captured step graph.  Errors:
- * GPEPS_EINVAL unless the handle is GPEPS_MIXED_C64 with D = 32 or 64, if
- * the fused schedule in use would no longer fit its shared memory, or under
- * schedule 6.
+ * GPEPS_EINVAL unless the handle is GPEPS_MIXED_C64 with D = 32 or 64, or if
+ * the fused schedule in use would no longer fit its shared memory (or, under
+ * schedule 6, four CTAs' TMEM).
  */
 int gpeps_set_tensor_cores(gpeps_handle* h, int32_t on);
 

@@ -242,7 +242,7 @@ int layered_per_sm(const gpeps_handle* h) {
 // CTAs per SM of the fused step launch
 int step_per_sm(const gpeps_handle* h) {
   const size_t sm = step_footprint(h->D, h->elt, h->tensor).smem;
-  if (h->schedule == 6 && !h->tensor && sm <= bond_share_smem(4)) return 4;
+  if (h->schedule == 6 && sm <= bond_share_smem(4) && (!h->tensor || 4 * tc_cols(h->D) <= 512)) return 4;
   if (h->schedule >= 5 && sm <= bond_share_smem(3)) return 3;
   return sm <= bond_share_smem(2) ? 2 : 1;
 }
@@ -657,8 +657,9 @@ int gpeps_set_schedule(gpeps_handle* h, int32_t schedule) {
   if (schedule == 5 && (!h->bound || step_footprint(h->D, h->elt, h->tensor).smem > bond_share_smem(3) ||
                         std::min(3 * h->n_sms, (int)h->tasks.size()) > h->bond_slots))
     return GPEPS_EINVAL;
-  if (schedule == 6 && (!h->bound || h->tensor || h->dtype != GPEPS_MIXED_C64 ||
-                        step_footprint(h->D, h->elt, false).smem > bond_share_smem(4) ||
+  if (schedule == 6 && (!h->bound || h->dtype != GPEPS_MIXED_C64 ||
+                        step_footprint(h->D, h->elt, h->tensor).smem > bond_share_smem(4) ||
+                        (h->tensor && 4 * tc_cols(h->D) > 512) ||
                         std::min(4 * h->n_sms, (int)h->tasks.size()) > h->bond_slots))
     return GPEPS_EINVAL;
   if (schedule >= 4) {
@@ -693,7 +694,9 @@ int gpeps_set_tensor_cores(gpeps_handle* h, int32_t on) {
   // the fused schedule in use must still fit with the staged tensor-core operands
   if (h->schedule == 5 && step_footprint(h->D, h->elt, true).smem > bond_share_smem(3)) return GPEPS_EINVAL;
   if (h->schedule == 4 && step_footprint(h->D, h->elt, true).smem > kBondSmemMax) return GPEPS_EINVAL;
-  if (h->schedule == 6) return GPEPS_EINVAL;  // four CTAs per SM run the passes on CUDA cores only
+  // four CTAs per SM: shared memory of the staged operands, and four times the TMEM columns
+  if (h->schedule == 6 && (step_footprint(h->D, h->elt, true).smem > bond_share_smem(4) || 4 * tc_cols(h->D) > 512))
+    return GPEPS_EINVAL;
   h->tensor = true;
   drop_graph(h);
   return GPEPS_OK;

@@ -2239,6 +2239,9 @@ cudaError_t Launch<T>::init() {
     e = cudaFuncSetAttribute(step_kernel<T, 192, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bond_share_smem(4));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(step_kernel<T, 192, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bond_share_smem(4));
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(step_kernel<T, 256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bond_share_smem(2));
     if (e != cudaSuccess) return e;
@@ -2379,7 +2382,9 @@ cudaError_t Launch<T>::step(const StepTask* tasks, int n_tasks, unsigned int* qu
   if (n_tasks == 0) return cudaSuccess;
   if (tc && (!std::is_same<T, float>::value || !tc_supported(D))) return cudaErrorInvalidValue;
   const BondFootprint fp = step_footprint(D, sizeof(V2<T>), tc);
-  if (!scratch || slot < fp.slot || per_sm < 1 || per_sm > 4 || (per_sm == 4 && tc)) return cudaErrorInvalidValue;
+  // four CTAs per SM with the tensor-core passes: 4 x tc_cols(D) TMEM columns must fit the SM's 512
+  if (!scratch || slot < fp.slot || per_sm < 1 || per_sm > 4 || (per_sm == 4 && tc && 4 * tc_cols(D) > 512))
+    return cudaErrorInvalidValue;
   if (fp.smem > (per_sm > 1 ? bond_share_smem(per_sm) : kBondSmemMax)) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
@@ -2393,7 +2398,9 @@ cudaError_t Launch<T>::step(const StepTask* tasks, int n_tasks, unsigned int* qu
                                                             lam, pending, flags, sweeps, cycles, D, jp, sp, slot)
   if (tc) {
     if constexpr (std::is_same<T, float>::value) {
-      if (per_sm == 3)
+      if (per_sm == 4)
+        GP_STEP(192, 4, true);
+      else if (per_sm == 3)
         GP_STEP(192, 3, true);
       else if (per_sm == 2)
         GP_STEP(256, 2, true);
