@@ -156,11 +156,12 @@ class Clocks:
 # `traffic` only for that configuration (profiles/step_kernel_heavyhex_mix_d32.md)
 # and whether the Gram and update passes ran on the tensor cores
 NCU_TRAFFIC = {
-    # one steady-state launch (Trotter step 8) of the fused step, floors 1e-7 / 7e-8: three CTAs per SM
-    # with the CUDA-core and with the tensor-core Gram and update passes, four CTAs per SM (CUDA cores)
+    # one steady-state launch (Trotter step 8) of the fused step, floors 1e-7 / 7e-8: three and four
+    # CTAs per SM, each with the CUDA-core and with the tensor-core Gram and update passes
     ("heavyhex_mix_d32", "mixed", 5, False): 2253342208 + 2040923904,
     ("heavyhex_mix_d32", "mixed", 5, True): 2443752000 + 2472390000,
-    ("heavyhex_mix_d32", "mixed", 6, False): 2417434000 + 2293279000}
+    ("heavyhex_mix_d32", "mixed", 6, False): 2417434000 + 2293279000,
+    ("heavyhex_mix_d32", "mixed", 6, True): 2693205760 + 2721358336}
 
 # TF32 tensor peak: the measured bf16 burst (MEASURED_PEAKS.json) x the nominal TF32 : BF16 dense ratio
 # (1.1 : 2.25 PFLOP/s)
