@@ -52,6 +52,24 @@ def candidates(dtype, D=None):
     return out
 
 
+_RESULT_KEYS = ("ms_per_step", "max_dz", "max_dz_reference", "accepted", "reference")
+
+
+def select(table, slack=TENSOR_SLACK):
+    """``(ms_per_step, candidate)`` chosen from an autotuner table: the fastest accepted row (the
+    earliest of equal times), except that the streaming products belong on the tensor cores, so
+    the fastest accepted tensor-core row wins when it is within ``slack`` of it (one timed run per
+    candidate does not separate closer timings)."""
+    ok = [r for r in table if r["accepted"] and r["ms_per_step"] is not None]
+    best = min(ok, key=lambda r: r["ms_per_step"])
+    tc = [r for r in ok if r.get("tensor") and not r.get("reference")]
+    if tc:
+        t = min(tc, key=lambda r: r["ms_per_step"])
+        if t["ms_per_step"] <= best["ms_per_step"] * (1.0 + slack):
+            best = t
+    return best["ms_per_step"], {k: v for k, v in best.items() if k not in _RESULT_KEYS}
+
+
 def _apply(g, cand):
     g.set_schedule(0)
     if g.dtype == "mixed":
@@ -98,7 +116,6 @@ def autotune(g, theta, warm_steps=6, steps=4, budget=1e-5, repeats=1, reference_
     ref_ms, ref_z = run(ref_cand)
     table = [dict(ref_cand, ms_per_step=ref_ms, max_dz=0.0, max_dz_reference=ext_dz(ref_z), accepted=True,
                   reference=True)]
-    best = (ref_ms, ref_cand)
     from ._abi import GpepsError
     for cand in candidates(g.dtype, g.D):
         try:
@@ -111,17 +128,7 @@ def autotune(g, theta, warm_steps=6, steps=4, budget=1e-5, repeats=1, reference_
         dz_ext = ext_dz(z)
         ok = dz <= budget and g.status() == 0 and (dz_ext is None or dz_ext <= reference_budget)
         table.append(dict(cand, ms_per_step=ms, max_dz=dz, max_dz_reference=dz_ext, accepted=ok))
-        if ok and ms < best[0]:
-            best = (ms, cand)
-    # the streaming products belong on the tensor cores: the fastest accepted tensor-core
-    # candidate wins when it is within TENSOR_SLACK of the fastest overall (one timed run per
-    # candidate does not separate closer timings)
-    tc_ok = [(r["ms_per_step"], r) for r in table if r.get("tensor") and r["accepted"] and not r.get("reference")]
-    if tc_ok:
-        ms_tc, row = min(tc_ok, key=lambda x: x[0])
-        if ms_tc <= best[0] * (1.0 + TENSOR_SLACK):
-            best = (ms_tc, {k: v for k, v in row.items()
-                            if k not in ("ms_per_step", "max_dz", "max_dz_reference", "accepted", "reference")})
+    best = select(table)
     _apply(g, best[1])
     g.reset()
     return dict(best[1], ms_per_step=best[0]), table
