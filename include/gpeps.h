@@ -220,7 +220,7 @@ int gpeps_set_schedule(gpeps_handle* h, int32_t schedule);  /* 0..6 */
 /*
  * Tensor cores for the two streaming products of every bond update in the
  * mixed path ("Method": the absorb/reduce/contract products of the simple
- * update; the spec form with TF32 products and FP32 accumulation): the
+ * update, here as TF32 products with FP32 accumulation): the
  * Gram blocks G_s of the larger end and its update Gamma_a' = A~ Y_s run as
  * tcgen05.mma (kind::tf32) products with FP32 accumulators in tensor memory,
  * each FP32 operand split as hi + lo in TF32 (three products per pair, about
