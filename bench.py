@@ -710,7 +710,8 @@ def run_gpeps(args, rank, world, local_rank):
 
 
 def measured_hbm_gbs():
-    """The measured copy bandwidth (MEASURED_PEAKS.json), else the pool's earlier figure."""
+    """The measured copy bandwidth of this GPU model (MEASURED_PEAKS.json at the repository root),
+    else an earlier measurement on a GB300, 6.8 TB/s."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         v = json.load(open(path)).get("hbm_gbs")
