@@ -171,3 +171,19 @@ def test_tensor_core_switch_host_checks(abi):
         assert lib.gpeps_set_tensor_cores(h, 1) == (0 if ok else abi.GPEPS_EINVAL), (dtype, D)
         assert lib.gpeps_set_tensor_cores(h, 0) == 0
         assert lib.gpeps_destroy(h) == 0
+
+
+def test_schedule_host_checks(abi):
+    """gpeps_set_schedule (host-only): 0 and 1 need nothing bound; 2 to 6 need the work buffer
+    and are rejected on an unbound handle; values outside 0..6 and a NULL handle are rejected."""
+    lib = abi.load()
+    n, e = heavy_hex(*EAGLE)
+    assert lib.gpeps_set_schedule(None, 0) == abi.GPEPS_EINVAL
+    for dtype in (0, 1):
+        st, h = _create(abi, [(n, e)], D=32, dtype=dtype)
+        assert st == 0
+        for s in (0, 1):
+            assert lib.gpeps_set_schedule(h, s) == 0, (dtype, s)
+        for s in (2, 3, 4, 5, 6, 7, -1):
+            assert lib.gpeps_set_schedule(h, s) == abi.GPEPS_EINVAL, (dtype, s)
+        assert lib.gpeps_destroy(h) == 0
